@@ -1,0 +1,331 @@
+"""Benchmark: projection steps of the channel-flow solver on GB300.
+
+A step is one pass of the whole hot path (eddy viscosity when enabled,
+explicit terms + AB3, Crank-Nicolson sweeps, divergence, the SRJ pressure
+solve to 1e-8 relative residual with the previous pressure as the guess,
+velocity correction) over the supercritical instability workload
+(128 x 64 x 128, Re 7500, Poiseuille + Orr-Sommerfeld mode + noise,
+dt 2e-3).  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|fp64]
+  python bench.py --impl reference ...   (the CPU oracle on the host cores)
+
+N > 1 runs under torch.distributed.run: independent replicas, one per GPU,
+no data exchange ("replicas only"); the timed region is bracketed by a
+barrier and the maximum over ranks is reported.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "os_instability"
+WORKLOAD_DESC = "os_instability 128x64x128 Re=7500 dt=2e-3 Poiseuille+OS mode 1e-4+noise 1e-6, ptol 1e-8"
+METRIC = "Mcell*steps/s (projection step, Poisson to 1e-8 rel. residual)"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--grid", default=None, help="override the cell counts, NXxNYxNZ (profiling runs)")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def traffic_for(kernel_src, precision):
+    """Per-launch DRAM bytes of the SRJ sweep from the committed ncu summary,
+    if the kernel source is unchanged since the capture; else None."""
+    path = os.path.join(ROOT, "profiles", "srj_sweep_traffic.json")
+    try:
+        rec = json.load(open(path))
+        src = open(kernel_src, "rb").read()
+        if rec.get("source_sha256") != hashlib.sha256(src).hexdigest():
+            return None
+        return rec["bytes_per_launch"].get(precision)
+    except Exception:
+        return None
+
+
+def cpu_baseline_sample(cfg, fields, sweeps_per_step):
+    """The CPU oracle on the host cores: one step of the same workload from
+    the same initial fields, its pressure solve held to the GPU's mean sweep
+    count per step (the same work per step)."""
+    import numpy as np  # noqa: F401
+
+    import oracle
+    from oracle import srj
+    ncores = len(os.sched_getaffinity(0))
+    oracle.set_threads(ncores)
+    om, _, _ = srj.schedule_for(cfg["nx"], cfg["ny"], cfg["nz"], cfg["Lx"], cfg["Ly"], cfg["Lz"],
+                                cfg.get("stretch", 0.0))
+    M = len(om)
+    cycles = max(1, int(round(sweeps_per_step / M)))
+    o = oracle.Oracle(dict(cfg, omega=om, ptol=0.0, pmaxit=cycles * M, cn_sweeps=cfg["cn_sweeps"]))
+    o.set_fields(*fields)
+    t0 = time.perf_counter()
+    o.step(1)
+    dt = time.perf_counter() - t0
+    cells = cfg["nx"] * cfg["ny"] * cfg["nz"]
+    return {"value": cells / dt / 1e6, "unit": "Mcell*steps/s", "cores": oracle.get_threads(), "kind": "oracle",
+            "sample": "1 FP64 oracle step of the full %dx%dx%d workload from the initial fields, SRJ held to "
+                      "%d sweeps (%d cycles of %d, the GPU's mean per timed step); %.2f s wall"
+                      % (cfg["nx"], cfg["ny"], cfg["nz"], cycles * M, cycles, M, dt)}
+
+
+def run_reference(args):
+    """The oracle (plain FP64 C, OpenMP over z) time-stepping the workload with
+    its own tolerance-driven pressure solves, on rank 0's host cores."""
+    world, rank, local = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    from oracle import srj
+    from paper_1511_07800_gb300 import inputs
+    cfg = inputs.preset(WORKLOAD)
+    ncores = len(os.sched_getaffinity(0))
+    oracle.set_threads(ncores)
+    om, _, _ = srj.schedule_for(cfg["nx"], cfg["ny"], cfg["nz"], cfg["Lx"], cfg["Ly"], cfg["Lz"], 0.0)
+    cn = _auto_cn(cfg)
+    o = oracle.Oracle(dict(cfg, omega=om, cn_sweeps=cn))
+    o.set_fields(*inputs.initial_fields(WORKLOAD, cfg, seed=0))
+    for _ in range(args.warmup):
+        o.step(1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.step(1)
+    dt = time.perf_counter() - t0
+    cells = cfg["nx"] * cfg["ny"] * cfg["nz"]
+    val = cells * args.steps / dt / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "Mcell*steps/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD_DESC, "cells": cells, "srj_M": len(om),
+                                            "cn_sweeps": cn},
+            "cpu_baseline": {"value": val, "unit": "Mcell*steps/s", "cores": oracle.get_threads(), "kind": "oracle",
+                             "sample": "%d full FP64 oracle steps after %d warm-up steps" % (args.steps, args.warmup)},
+            "e2e": {"value": val, "unit": "Mcell*steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _auto_cn(cfg):
+    """Crank-Nicolson Jacobi sweeps for the workload, by the library's rule
+    (contraction hS/(1+hS) per sweep, down to 1e-12); both arms get the
+    count explicitly so they run the same sweeps."""
+    from paper_1511_07800_gb300 import inputs
+    zf = inputs.zfaces(cfg)
+    dz = [zf[k + 1] - zf[k] for k in range(cfg["nz"])]
+    zc = [0.5 * (zf[k] + zf[k + 1]) for k in range(cfg["nz"])]
+    dzf = [dz[0]] + [zc[k] - zc[k - 1] for k in range(1, cfg["nz"])] + [dz[-1]]
+    dx, dy = cfg["Lx"] / cfg["nx"], cfg["Ly"] / cfg["ny"]
+    smax = max(4 / dx**2 + 4 / dy**2 + 2 / (dzf[k] * dz[k]) + 2 / (dzf[k + 1] * dz[k]) for k in range(cfg["nz"]))
+    hs = 0.5 * cfg["dt"] * cfg["nu"] * (4.0 if cfg.get("les") else 1.0) * smax
+    rho = hs / (1 + hs)
+    if rho <= 0:
+        return 1
+    return max(2, min(int(math.ceil(math.log(1e-12) / math.log(rho))), 200))
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_1511_07800_gb300 import build, inputs, stp
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    build.build()
+    cfg = inputs.preset(WORKLOAD)
+    if args.grid:
+        nx, ny, nz = (int(x) for x in args.grid.lower().split("x"))
+        cfg.update(nx=nx, ny=ny, nz=nz)
+    cfg["cn_sweeps"] = _auto_cn(cfg)
+    fields = inputs.initial_fields(WORKLOAD, cfg, seed=0)
+    stream = torch.cuda.current_stream()
+    ch = stp.Channel(cfg, precision=args.precision, device=local, stream=stream.cuda_stream)
+    ch.set_fields(*fields)
+    cells = cfg["nx"] * cfg["ny"] * cfg["nz"]
+    for _ in range(max(3, args.warmup)):
+        ch.step(1)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clk = Clocks(local)
+    clk.start()
+    ms, sweeps, launches, solve_ms, passes = 0.0, 0, 0, 0.0, 0
+    conv = True
+    for _ in range(args.steps):
+        flush.zero_()                      # L2 flush between timed steps (untimed)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = ch.step(1)
+        e1.record(stream)
+        e1.synchronize()
+        ms += e0.elapsed_time(e1)
+        sweeps += st["sweeps"]
+        passes += st["passes"]
+        launches += st["launches"]
+        solve_ms += st["solve_ms"]
+        conv = conv and st["converged"]
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = clk.stop()
+    ms_max = ms
+    if world > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_max = float(t.item())
+    value = world * cells * args.steps / (ms_max / 1e3) / 1e6
+
+    # end to end through the C ABI with host buffers: copy the step's inputs
+    # in, step, copy the result out, every step
+    e2e = None
+    if not args.no_e2e:
+        host = ch.get_fields()
+        hu, hv, hw, hp = (np.ascontiguousarray(host[k]) for k in ("u", "v", "w", "p"))
+        torch.cuda.synchronize()
+        ke = max(1, min(args.steps, 5))
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            ch.set_fields(hu, hv, hw, hp)
+            ch.step(1)
+            ch.get_fields(dict(u=hu, v=hv, w=hw, p=hp, nu=None))
+        te = time.perf_counter() - t0
+        nb = 8 * (3 * cells + cells + cfg["nx"] * cfg["ny"])
+        e2e = {"value": world * cells * ke / te / 1e6, "unit": "Mcell*steps/s", "h2d_bytes_per_step": nb,
+               "d2h_bytes_per_step": nb}
+
+    peaks = measured_peaks()
+    word = 4 if args.precision == "fp32" else 8
+    bytes_per_sweep = 3 * word * cells
+    # mean SRJ sweep duration: GPU time of the solve graphs (events on the
+    # launching stream) over the sweeps they ran; the once-per-cycle checks
+    # (and FP32 refinement kernels) are charged to the sweeps, so this is a
+    # lower bound on the sweep kernel's own bandwidth
+    t_sweep = solve_ms / max(1, sweeps) / 1e3
+    achieved = bytes_per_sweep / t_sweep / 1e9 if sweeps else None
+    peak = peaks.get("hbm_gbs", 6800.0)
+    kern = os.path.join(ROOT, "paper_1511_07800_gb300", "csrc", "kernels_poisson.cu")
+    traffic = traffic_for(kern, args.precision)
+    line = {
+        "metric": METRIC, "value": value, "unit": "Mcell*steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if args.precision == "fp32" else "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC if not args.grid else WORKLOAD_DESC + " at " + args.grid,
+                   "cells": cells, "precision": args.precision,
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "flushed between timed steps (256 MB write, untimed)",
+                   "srj_M": len(stp.srj_schedule(cfg)[0])},
+        "poisson": {"sweeps_per_step": sweeps / args.steps, "refine_passes_per_step": passes / args.steps,
+                    "all_converged": conv, "ms_per_step": solve_ms / args.steps},
+        "roofline": {"bound": "hbm", "kernel": "k_sweep<%s> (SRJ sweep)" % ("float" if word == 4 else "double"),
+                     "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                     "bytes_per_launch": bytes_per_sweep, "mean_launch_us": t_sweep * 1e6,
+                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if "hbm_gbs" in peaks else "fallback"},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "e2e": e2e,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            line["cpu_baseline"] = cpu_baseline_sample(cfg, fields, sweeps / args.steps)
+        except Exception as ex:  # report, never fake
+            line["cpu_baseline"] = {"value": None, "error": str(ex)[:200]}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ch.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

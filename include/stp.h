@@ -1,0 +1,173 @@
+/*
+ * stp.h -- C ABI of the GB300 projection step for incompressible channel flow.
+ *
+ * One handle holds one channel on one GPU: a 3-D MAC grid, periodic in x and
+ * y, with no-slip walls at z = 0 and z = Lz (arXiv 1511.07800, Sec. 2.1 and
+ * Fig. "computational domain").  A time step is the projection method of
+ * Sec. 3.1:
+ *   nu_T     Smagorinsky eddy viscosity with van Driest damping (Sec. 2.2)
+ *   N^n      -u.grad u + d_j(nu_T d_i u_j) + f   (Eq. more_conv; AB3)
+ *   u*       Crank-Nicolson on d_j(nu_T d_j u_i) (Eq. more_diff)
+ *   b        div u* / dt                          (Eq. presdiv)
+ *   p        L p = b by Scheduled Relaxation Jacobi (Sec. 3.4)
+ *   u^{n+1}  u* - dt grad p                       (Eq. project u_p_1)
+ *
+ * Layouts (all arrays x fastest, C order, double on the ABI):
+ *   u, v, p, nu_t : [nz][ny][nx]   u(i) at x = i dx, v(j) at y = j dy,
+ *                                  p, nu_t at cell centres
+ *   w             : [nz+1][ny][nx] w(k) at z = zf[k]; the planes k = 0 and
+ *                                  k = nz are the walls and must be zero
+ *
+ * Pointers: `where` = STP_HOST for host memory, STP_DEVICE for memory on the
+ * handle's device.  The library never keeps a caller pointer after a call
+ * returns; it owns all its device memory and frees it in stp_destroy.
+ *
+ * Errors: every int-returning call returns STP_OK (0) or a negative STP_E*
+ * code; stp_last_error gives a one-line message.  No call aborts the process.
+ * Calls on one handle must not overlap (one handle per host thread).
+ */
+#ifndef STP_H
+#define STP_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define STP_OK 0
+#define STP_EINVAL (-1)        /* bad argument, size or configuration           */
+#define STP_ENOMEM (-2)        /* device or host allocation failed              */
+#define STP_ECUDA (-3)         /* a CUDA runtime call failed                    */
+#define STP_ENOTCONVERGED (-4) /* pressure solve hit its sweep cap              */
+#define STP_EDIVERGED (-5)     /* NaN/Inf in a residual or the velocity         */
+#define STP_ECFL (-6)          /* U_max dt > 0.1 dx (Eq. cfl_cond), if checked   */
+
+#define STP_HOST 0
+#define STP_DEVICE 1
+
+#define STP_FP64 0        /* every field and sweep in FP64                       */
+#define STP_FP32_REFINE 1 /* FP32 fields and sweeps; FP64 pressure, norms and an
+                             FP64 iterative-refinement loop around FP32 SRJ       */
+
+typedef struct stp_config {
+    int nx, ny, nz;          /* cells; nx, ny >= 3, nz >= 2                      */
+    double Lx, Ly, Lz;       /* box; z in [0, Lz]                                */
+    double nu;               /* molecular viscosity 1/Re                         */
+    double dt;               /* time step                                        */
+    int forcing;             /* 0: constant body force fx (= -dp/dx) on u;
+                                1: constant bulk velocity ubulk (flux fix-up)     */
+    double fx;
+    double ubulk;
+    int les;                 /* 1: nu_T = nu + (cs Delta phi_w)^2 |S|            */
+    double cs;               /* Smagorinsky constant (0.1)                       */
+    double vd_a;             /* van Driest constant A (25)                       */
+    double re_tau;           /* friction Reynolds number used in d+ = d Re_tau/(Lz/2) */
+    double stretch;          /* 0: uniform z; gamma > 0: zf = Lz/2 (1 + tanh(gamma(2k/nz-1))/tanh gamma) */
+    int precision;           /* STP_FP64 or STP_FP32_REFINE                     */
+    double ptol;             /* pressure: stop when ||b - Lp||_2 <= ptol ||b||_2 */
+    int pmaxit;              /* cap on SRJ sweeps per solve                      */
+    int cn_sweeps;           /* Jacobi sweeps of the CN system; 0: automatic     */
+    int srj_m;               /* SRJ cycle length; 0: automatic (power of two)    */
+    const double *srj_omega; /* optional schedule omega_1..omega_M (M = srj_m);
+                                NULL: Chebyshev schedule built by the library     */
+    double inner_tol;        /* FP32 inner solve: relative reduction per
+                                refinement pass (default 1e-3)                    */
+    int cfl_check;           /* 1: return STP_ECFL when U_max dt > 0.1 dx         */
+    int device;              /* CUDA device ordinal                              */
+    void *stream;            /* cudaStream_t to run on; NULL: the library's own  */
+} stp_config;
+
+typedef struct stp_step_stats {
+    int poisson_sweeps;      /* SRJ sweeps of the last step (inner sweeps in FP32) */
+    int refine_passes;       /* FP64 refinement passes of the last step         */
+    int converged;           /* 1 if every pressure solve met ptol               */
+    double rel_residual;     /* ||b - Lp|| / ||b|| at the end of the last solve  */
+    double ubulk;            /* volume mean of u after the last step             */
+    double umax;             /* max |u| after the last step                      */
+    double dpdx;             /* implied -dp/dx of the flux fix-up (forcing 1)    */
+    long long step;          /* steps taken since stp_set_fields                 */
+    long long launches;      /* kernels run by this stp_step call (host launches
+                                plus the kernels of the solve graphs)             */
+    long long solve_sweeps;  /* SRJ sweeps of all solves of this call           */
+    double solve_ms;         /* GPU time of those solves (CUDA events on the
+                                handle's stream around each solve graph; includes
+                                the once-per-cycle residual checks and, in FP32
+                                mode, the refinement kernels)                     */
+} stp_step_stats;
+
+typedef struct stp_solve_stats {
+    int sweeps;
+    int refine_passes;
+    int converged;
+    double rel_residual;
+} stp_solve_stats;
+
+typedef struct stp_handle stp_handle;
+
+/* Fill `cfg` with defaults: 32^3 unit-Re channel, FP64, ptol 1e-8,
+   automatic CN sweeps and SRJ schedule, Cs 0.1, A 25, Re_tau 180. */
+void stp_config_defaults(stp_config *cfg);
+
+/* Create a handle: validates cfg (STP_EINVAL), selects cfg->device, allocates
+   every device buffer (STP_ENOMEM), builds the SRJ schedule.  Fields start at
+   zero.  On failure *out is NULL and stp_last_error(NULL) explains. */
+int stp_init(const stp_config *cfg, stp_handle **out);
+
+/* Free the handle and its device memory (NULL is a no-op). */
+void stp_destroy(stp_handle *h);
+
+/* Message of the last failed call on h (h NULL: last stp_init failure of the
+   calling thread).  Valid until the next call on h. */
+const char *stp_last_error(const stp_handle *h);
+
+/* Copy initial fields in (Sec. 2.1 layout above).  p may be NULL (zero).
+   Resets the Adams-Bashforth history (the next step is forward Euler, the
+   one after AB2) and the step counter.  STP_EINVAL if a wall plane of w is
+   non-zero. */
+int stp_set_fields(stp_handle *h, const double *u, const double *v, const double *w, const double *p,
+                   int where);
+
+/* Copy the current fields out.  Any pointer may be NULL.  nu_t receives the
+   total viscosity nu_T of the last step (nu without LES). */
+int stp_get_fields(stp_handle *h, double *u, double *v, double *w, double *p, double *nu_t, int where);
+
+/* Advance nsteps projection steps (Sec. 3.1), each with its pressure solved
+   to ptol from the previous pressure.  Blocks until done.  Returns
+   STP_ENOTCONVERGED if a solve hit pmaxit (the step still completes),
+   STP_EDIVERGED on NaN/Inf, STP_ECFL when cfl_check is set and violated.
+   stats (nullable) describes the last step. */
+int stp_step(stp_handle *h, int nsteps, stp_step_stats *stats);
+
+/* Solve L p = rhs (Sec. 3.4 SRJ; Eq. presdiv operator with Neumann walls)
+   to ||rhs - Lp||_2 <= tol ||rhs||_2 starting from p_inout, capped at maxit
+   sweeps (0: pmaxit).  rhs [nz][ny][nx] must have zero volume-weighted mean
+   to within round-off (its mean is not removed).  p_inout receives the
+   result; its additive constant is not fixed.  Uses the handle's buffers:
+   the current pressure field is overwritten. */
+int stp_poisson_solve(stp_handle *h, const double *rhs, double *p_inout, double tol, int maxit, int where,
+                      stp_solve_stats *stats);
+
+/* Terms of the step evaluated on the current fields, for checks:
+     STP_TERM_VISCOSITY  a = nu_T                         (Sec. 2.2)
+     STP_TERM_EXPLICIT   a,b,c = N = -u.grad u + d_j(nu_T d_i u_j) + f
+     STP_TERM_DIFFUSION  a,b,c = d_j(nu_T d_j u_i)        (nu_T from the
+                         current fields)
+     STP_TERM_DIVERGENCE a = D u                          (Eq. presdiv)
+     STP_TERM_LAPLACIAN  a = L p                          (L = D G)
+   b, c are w-shaped ([nz+1]) where the term is a velocity. */
+#define STP_TERM_VISCOSITY 1
+#define STP_TERM_EXPLICIT 2
+#define STP_TERM_DIFFUSION 3
+#define STP_TERM_DIVERGENCE 4
+#define STP_TERM_LAPLACIAN 5
+int stp_eval(stp_handle *h, int term, double *a, double *b, double *c, int where);
+
+/* The SRJ schedule (Sec. 3.4) the library would use for cfg: the Chebyshev
+   factors of [mu_min, mu_max] for the Jacobi-preconditioned operator, in the
+   mirror-pair order.  M = 0 picks the cycle length; omega needs room for
+   1024 values.  Host only. */
+int stp_srj_schedule(const stp_config *cfg, int M, double *omega, int *M_out, double *mu_min, double *mu_max);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* STP_H */

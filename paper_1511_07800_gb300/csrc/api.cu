@@ -1,0 +1,1023 @@
+// Host side of the C ABI (include/stp.h): handle, device buffers, metrics,
+// the SRJ schedule, and the drivers of the projection step and of the
+// pressure solve.  Every kernel lives in kernels_step.cu / kernels_poisson.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "stp_internal.cuh"
+
+using namespace stp;
+
+namespace {
+
+thread_local std::string g_init_error;
+
+}  // namespace
+
+struct stp_handle {
+  stp_config cfg{};
+  int prec = 0;
+  int dev = 0;
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  int nx = 0, ny = 0, nz = 0;
+  size_t nc = 0, nw = 0, nplane = 0;
+  size_t esz = 8;
+
+  double* m64 = nullptr;
+  float* m32 = nullptr;
+  Geom<double> g64{};
+  Geom<float> g32{};
+
+  void *u = nullptr, *v = nullptr, *w = nullptr;
+  void *ru = nullptr, *rv = nullptr, *rw = nullptr;
+  void *tu = nullptr, *tv = nullptr, *tw = nullptr;
+  void *Nu[3] = {}, *Nv[3] = {}, *Nw[3] = {};
+  void* nu = nullptr;
+  double* b = nullptr;
+  double *p = nullptr, *p2 = nullptr;
+  float *d1 = nullptr, *d2 = nullptr, *r32 = nullptr;
+  double* stage = nullptr;
+
+  Red red{};
+  double* h_sc = nullptr;  // pinned copies of red.sc and red.flag
+  int* h_flag = nullptr;
+
+  std::vector<double> omega;
+  int cn_sweeps = 0;
+  int nhist = 0;
+  long long step = 0;
+  double last_dpdx = 0.0;
+  std::vector<void*> allocs;
+  std::string err;
+  // accounting of the current API call
+  long long launches = 0;     // kernels launched directly from the host
+  long long solve_sweeps = 0;
+  double solve_ms = 0.0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // device-steered pressure solve
+  cudaStream_t cap = nullptr;  // private stream used only for graph capture
+  SolveCtl* ctl = nullptr;
+  SolveCtl* h_ctl = nullptr;   // pinned
+  cudaGraph_t solve_graph = nullptr;
+  cudaGraphExec_t solve_exec = nullptr;
+};
+
+namespace {
+
+// true for the launch_* wrappers (each launches exactly one kernel)
+constexpr bool is_launch(const char* s) {
+  while (*s == ' ' || *s == '(') s++;
+  return s[0] == 'l' && s[1] == 'a' && s[2] == 'u' && s[3] == 'n' && s[4] == 'c' && s[5] == 'h' && s[6] == '_';
+}
+
+int fail(stp_handle* h, int code, const std::string& msg) {
+  if (h)
+    h->err = msg;
+  else
+    g_init_error = msg;
+  return code;
+}
+
+#define CUDA_TRY(h, call)                                                                  \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (is_launch(#call)) h->launches++;                                                   \
+    if (e_ != cudaSuccess)                                                                 \
+      return fail(h, e_ == cudaErrorMemoryAllocation ? STP_ENOMEM : STP_ECUDA,             \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                     \
+  } while (0)
+
+int dalloc(stp_handle* h, void** p, size_t bytes) {
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return fail(h, STP_ENOMEM, std::string("cudaMalloc of ") + std::to_string(bytes) + " bytes: " +
+                                   cudaGetErrorString(e));
+  }
+  h->allocs.push_back(*p);
+  return STP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// z grid and metrics (FP64 on the host)
+// ---------------------------------------------------------------------------
+struct ZGrid {
+  std::vector<double> zf, zc, dz, hz, dzf;
+};
+
+ZGrid make_z(const stp_config& c) {
+  ZGrid z;
+  const int nz = c.nz;
+  z.zf.resize(nz + 1);
+  for (int k = 0; k <= nz; k++) {
+    const double s = (double)k / nz;
+    z.zf[k] = c.stretch > 0 ? 0.5 * c.Lz * (1.0 + std::tanh(c.stretch * (2.0 * s - 1.0)) / std::tanh(c.stretch))
+                            : c.Lz * s;
+  }
+  z.zf[0] = 0.0;
+  z.zf[nz] = c.Lz;
+  z.dz.resize(nz);
+  z.zc.resize(nz);
+  for (int k = 0; k < nz; k++) {
+    z.dz[k] = z.zf[k + 1] - z.zf[k];
+    z.zc[k] = 0.5 * (z.zf[k] + z.zf[k + 1]);
+  }
+  z.hz.assign(nz + 1, 0.0);
+  z.hz[0] = z.zc[0] - z.zf[0];
+  z.hz[nz] = z.zf[nz] - z.zc[nz - 1];
+  for (int k = 1; k < nz; k++) z.hz[k] = z.zc[k] - z.zc[k - 1];
+  z.dzf.assign(nz + 1, 0.0);
+  z.dzf[0] = z.dz[0];
+  z.dzf[nz] = z.dz[nz - 1];
+  for (int k = 1; k < nz; k++) z.dzf[k] = z.hz[k];
+  return z;
+}
+
+// Poisson couplings in z: cup_k to k+1, cdn_k to k-1 (zero through the walls)
+void poisson_z(const stp_config& c, const ZGrid& z, std::vector<double>& cup, std::vector<double>& cdn) {
+  const int nz = c.nz;
+  cup.assign(nz, 0.0);
+  cdn.assign(nz, 0.0);
+  for (int k = 0; k < nz; k++) {
+    if (k < nz - 1) cup[k] = 1.0 / (z.hz[k + 1] * z.dz[k]);
+    if (k > 0) cdn[k] = 1.0 / (z.hz[k] * z.dz[k]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// SRJ schedule (Sec. 3.4).  Eigenvalues mu of D^-1(-L) separate into Fourier
+// modes in x, y and, for each x-y eigenvalue a, a symmetric generalized
+// tridiagonal problem in z:  W(a - L_z) phi = mu W S phi, W = diag(dz).
+// Its eigenvalues come from Sturm-sequence bisection.
+// ---------------------------------------------------------------------------
+struct Tridiag {
+  std::vector<double> d, e;  // diagonal, off-diagonal of B^-1/2 A B^-1/2
+};
+
+Tridiag z_problem(const stp_config& c, const ZGrid& z, double a) {
+  const int nz = c.nz;
+  std::vector<double> cup, cdn;
+  poisson_z(c, z, cup, cdn);
+  const double dx = c.Lx / c.nx, dy = c.Ly / c.ny;
+  Tridiag t;
+  t.d.resize(nz);
+  t.e.assign(nz > 1 ? nz - 1 : 0, 0.0);
+  std::vector<double> B(nz);
+  for (int k = 0; k < nz; k++) {
+    const double S = 2.0 / (dx * dx) + 2.0 / (dy * dy) + cup[k] + cdn[k];
+    B[k] = z.dz[k] * S;
+    t.d[k] = z.dz[k] * (a + cup[k] + cdn[k]) / B[k];
+  }
+  for (int k = 0; k + 1 < nz; k++) t.e[k] = (-1.0 / z.hz[k + 1]) / std::sqrt(B[k] * B[k + 1]);
+  return t;
+}
+
+// number of eigenvalues < x
+int sturm_count(const Tridiag& t, double x) {
+  int cnt = 0;
+  double q = 1.0;
+  for (size_t k = 0; k < t.d.size(); k++) {
+    const double e2 = k ? t.e[k - 1] * t.e[k - 1] : 0.0;
+    q = (t.d[k] - x) - (k ? e2 / q : 0.0);
+    if (q == 0.0) q = -1e-300;
+    if (q < 0) cnt++;
+  }
+  return cnt;
+}
+
+// m-th smallest eigenvalue (0-based)
+double tri_eig(const Tridiag& t, int m) {
+  double lo = 1e300, hi = -1e300;
+  const size_t n = t.d.size();
+  for (size_t k = 0; k < n; k++) {
+    const double r = (k ? std::fabs(t.e[k - 1]) : 0.0) + (k + 1 < n ? std::fabs(t.e[k]) : 0.0);
+    lo = std::min(lo, t.d[k] - r);
+    hi = std::max(hi, t.d[k] + r);
+  }
+  for (int it = 0; it < 400 && hi - lo > 1e-17 * std::max(1.0, std::fabs(hi)); it++) {
+    const double mid = 0.5 * (lo + hi);
+    if (sturm_count(t, mid) > m)
+      hi = mid;
+    else
+      lo = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+void jacobi_bounds(const stp_config& c, double* mn, double* mx) {
+  const ZGrid z = make_z(c);
+  const double dx = c.Lx / c.nx, dy = c.Ly / c.ny;
+  const double pi = 3.14159265358979323846;
+  auto lx = [&](int m) { return 4.0 / (dx * dx) * std::pow(std::sin(pi * m / c.nx), 2); };
+  auto ly = [&](int n) { return 4.0 / (dy * dy) * std::pow(std::sin(pi * n / c.ny), 2); };
+  double lo = c.nz > 1 ? tri_eig(z_problem(c, z, 0.0), 1) : 1e300;
+  if (c.nx > 1) lo = std::min(lo, tri_eig(z_problem(c, z, lx(1)), 0));
+  if (c.ny > 1) lo = std::min(lo, tri_eig(z_problem(c, z, ly(1)), 0));
+  *mn = lo;
+  *mx = tri_eig(z_problem(c, z, lx(c.nx / 2) + ly(c.ny / 2)), c.nz - 1);
+}
+
+double cycle_factor(double mn, double mx, int M) {
+  const double x0 = (mx + mn) / (mx - mn);
+  return 1.0 / std::cosh(M * std::acosh(x0));
+}
+
+// odd numbers 1..2M-1 in the recursive mirror-pair order (M a power of two)
+std::vector<int> mirror_order(int M) {
+  std::vector<int> th{1};
+  for (int m = 1; m < M; m *= 2) {
+    std::vector<int> nx;
+    nx.reserve(2 * th.size());
+    for (int t : th) {
+      nx.push_back(t);
+      nx.push_back(4 * m - t);
+    }
+    th.swap(nx);
+  }
+  return th;
+}
+
+std::vector<double> chebyshev(double mn, double mx, int M) {
+  const double pi = 3.14159265358979323846;
+  const double mid = 0.5 * (mx + mn), half = 0.5 * (mx - mn);
+  std::vector<double> om;
+  for (int t : mirror_order(M)) om.push_back(1.0 / (mid + half * std::cos(t * pi / (2.0 * M))));
+  return om;
+}
+
+bool pow2(int m) { return m >= 1 && (m & (m - 1)) == 0; }
+
+int auto_cycle(double mn, double mx) {
+  int M = 2;
+  while (M < 1024 && cycle_factor(mn, mx, M) > 0.01) M *= 2;
+  return M;
+}
+
+// Jacobi sweeps for the CN system: the iteration contracts by at most
+// hS/(1+hS), S the largest diagonal weight (nu_T bounded by 4 nu with LES);
+// enough sweeps to reach 1e-12.
+int auto_cn_sweeps(const stp_config& c, const ZGrid& z) {
+  const double dx = c.Lx / c.nx, dy = c.Ly / c.ny;
+  double smax = 0.0;
+  for (int k = 0; k < c.nz; k++) {
+    const double sz = 2.0 / (z.dzf[k] * z.dz[k]) + 2.0 / (z.dzf[k + 1] * z.dz[k]);
+    smax = std::max(smax, 4.0 / (dx * dx) + 4.0 / (dy * dy) + sz);
+  }
+  const double nu = c.nu * (c.les ? 4.0 : 1.0);
+  const double hs = 0.5 * c.dt * nu * smax;
+  const double rho = hs / (1.0 + hs);
+  if (rho <= 0) return 1;
+  int k = (int)std::ceil(std::log(1e-12) / std::log(rho));
+  return std::max(2, std::min(k, 200));
+}
+
+int validate(const stp_config* c, std::string* why) {
+  if (!c) return *why = "config is NULL", STP_EINVAL;
+  if (c->nx < 3 || c->ny < 3 || c->nz < 2) return *why = "need nx, ny >= 3 and nz >= 2", STP_EINVAL;
+  if ((double)c->nx * c->ny * (c->nz + 1) > 2.0e9) return *why = "grid too large (cells must fit a 31-bit index)", STP_EINVAL;
+  if (!(c->Lx > 0 && c->Ly > 0 && c->Lz > 0)) return *why = "box lengths must be positive", STP_EINVAL;
+  if (!(c->nu >= 0) || !(c->dt > 0)) return *why = "need nu >= 0 and dt > 0", STP_EINVAL;
+  if (c->precision != STP_FP64 && c->precision != STP_FP32_REFINE) return *why = "unknown precision", STP_EINVAL;
+  if (c->forcing != 0 && c->forcing != 1) return *why = "forcing must be 0 or 1", STP_EINVAL;
+  if (c->stretch < 0) return *why = "stretch must be >= 0", STP_EINVAL;
+  if (!(c->ptol >= 0) || c->pmaxit < 0 || c->cn_sweeps < 0) return *why = "bad solver limits", STP_EINVAL;
+  if (c->srj_m < 0 || c->srj_m > 4096) return *why = "srj_m out of range", STP_EINVAL;
+  if (c->srj_omega && c->srj_m <= 0) return *why = "srj_omega given without srj_m", STP_EINVAL;
+  if (c->srj_m % 2) return *why = "the SRJ cycle length must be even", STP_EINVAL;
+  if (!c->srj_omega && c->srj_m > 0 && !pow2(c->srj_m)) return *why = "library schedules need srj_m a power of two", STP_EINVAL;
+  if (c->les && !(c->cs >= 0 && c->vd_a > 0 && c->re_tau > 0)) return *why = "bad LES constants", STP_EINVAL;
+  return STP_OK;
+}
+
+template <typename T>
+Geom<T> geom_from(const stp_handle* h, T* pack) {
+  const int nz = h->nz, L = nz + 1;
+  const double dx = h->cfg.Lx / h->nx, dy = h->cfg.Ly / h->ny;
+  Geom<T> g;
+  g.nx = h->nx;
+  g.ny = h->ny;
+  g.nz = nz;
+  g.idx = (T)(1.0 / dx);
+  g.idy = (T)(1.0 / dy);
+  g.idx2 = (T)(1.0 / (dx * dx));
+  g.idy2 = (T)(1.0 / (dy * dy));
+  g.hidx = (T)(0.5 / dx);
+  g.hidy = (T)(0.5 / dy);
+  g.idxdy = (T)(1.0 / (dx * dy));
+  g.idz = pack + 0 * L;
+  g.ihz = pack + 1 * L;
+  g.idzf = pack + 2 * L;
+  g.i2dzc = pack + 3 * L;
+  g.idzw = pack + 4 * L;
+  g.cup = pack + 5 * L;
+  g.cdn = pack + 6 * L;
+  g.iS = pack + 7 * L;
+  g.S = pack + 8 * L;
+  g.lm2 = pack + 9 * L;
+  g.dzv = pack + 10 * L;
+  return g;
+}
+
+std::vector<double> metric_pack(const stp_config& c) {
+  const int nz = c.nz, L = nz + 1;
+  const ZGrid z = make_z(c);
+  std::vector<double> cup, cdn;
+  poisson_z(c, z, cup, cdn);
+  const double dx = c.Lx / c.nx, dy = c.Ly / c.ny;
+  std::vector<double> m((size_t)kMetricArrays * L, 0.0);
+  for (int k = 0; k < nz; k++) {
+    m[0 * L + k] = 1.0 / z.dz[k];
+    const double up = (k < nz - 1) ? z.hz[k + 1] : z.dz[nz - 1];
+    const double dn = (k > 0) ? z.hz[k] : z.dz[0];
+    m[3 * L + k] = 1.0 / (up + dn);
+    m[5 * L + k] = cup[k];
+    m[6 * L + k] = cdn[k];
+    const double S = 2.0 / (dx * dx) + 2.0 / (dy * dy) + cup[k] + cdn[k];
+    m[7 * L + k] = 1.0 / S;
+    m[8 * L + k] = S;
+    const double delta = 2.0 * std::cbrt(dx * dy * z.dz[k]);
+    const double d = std::min(z.zc[k], c.Lz - z.zc[k]);
+    const double dplus = d * c.re_tau / (0.5 * c.Lz);
+    const double phi = c.les ? 1.0 - std::exp(-dplus / c.vd_a) : 0.0;
+    const double lm = c.cs * delta * phi;
+    m[9 * L + k] = lm * lm;
+    m[10 * L + k] = z.dz[k];
+  }
+  for (int k = 0; k <= nz; k++) {
+    m[1 * L + k] = (k >= 1 && k < nz) ? 1.0 / z.hz[k] : 0.0;
+    m[2 * L + k] = 1.0 / z.dzf[k];
+    m[4 * L + k] = (k >= 1 && k < nz) ? 1.0 / (z.dz[k] + z.dz[k - 1]) : 0.0;
+  }
+  return m;
+}
+
+int sync_scalars(stp_handle* h) {
+  CUDA_TRY(h, cudaMemcpyAsync(h->h_sc, h->red.sc, sizeof(double) * SC_COUNT, cudaMemcpyDeviceToHost, h->st));
+  CUDA_TRY(h, cudaMemcpyAsync(h->h_flag, h->red.flag, sizeof(int) * FL_COUNT, cudaMemcpyDeviceToHost, h->st));
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  return STP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Pressure solves (Sec. 3.4) as CUDA graphs steered from the device.
+//   FP64: begin -> WHILE(loop) { check -> IF(body) { M sweeps } }
+//   FP32: begin -> outer -> WHILE(pass) { d = 0 -> WHILE(loop) { check ->
+//         IF(body) { M sweeps } } -> p += d -> outer }
+// As in the oracle, each cycle first measures ||b - L p|| of its input and
+// either stops (that input is the answer) or runs its M sweeps.  With M
+// even the answer is always back in the first buffer, so the graphs are
+// built once per handle.  On entry sc[SC_BNORM] = ||b||.
+// ---------------------------------------------------------------------------
+struct SolveOut {
+  int sweeps = 0, passes = 0, converged = 0, bad = 0;
+  double rel = 0.0;
+  long long kernels = 0, tot_sweeps = 0;
+  int nonconv = 0;
+};
+
+cudaGraphNode_t leaf_node(cudaGraph_t g) {
+  size_t n = 0;
+  cudaGraphGetNodes(g, nullptr, &n);
+  std::vector<cudaGraphNode_t> v(n);
+  cudaGraphGetNodes(g, v.data(), &n);
+  for (cudaGraphNode_t x : v) {
+    size_t d = 0;
+    cudaGraphNodeGetDependentNodes(x, nullptr, nullptr, &d);
+    if (d == 0) return x;
+  }
+  return nullptr;
+}
+
+// WHILE or IF node after `dep` in graph g; returns its body graph
+int add_conditional(stp_handle* h, cudaGraph_t g, cudaGraphNode_t dep, cudaGraphConditionalHandle hc,
+                    cudaGraphConditionalNodeType type, cudaGraph_t* body, cudaGraphNode_t* node) {
+  cudaGraphNodeParams prm = {};
+  prm.type = cudaGraphNodeTypeConditional;
+  prm.conditional.handle = hc;
+  prm.conditional.type = type;
+  prm.conditional.size = 1;
+  CUDA_TRY(h, cudaGraphAddNode(node, g, dep ? &dep : nullptr, nullptr, dep ? 1 : 0, &prm));
+  *body = prm.conditional.phGraph_out[0];
+  return STP_OK;
+}
+
+int begin_capture(stp_handle* h, cudaGraph_t g, cudaGraphNode_t dep) {
+  CUDA_TRY(h, cudaStreamBeginCaptureToGraph(h->cap, g, dep ? &dep : nullptr, nullptr, dep ? 1 : 0,
+                                            cudaStreamCaptureModeRelaxed));
+  return STP_OK;
+}
+int end_capture(stp_handle* h, cudaGraph_t g) {
+  cudaGraph_t out = g;
+  CUDA_TRY(h, cudaStreamEndCapture(h->cap, &out));
+  return STP_OK;
+}
+
+// the cycle: check -> IF { M sweeps }, inside the WHILE body `wb`
+template <typename T>
+int build_cycle(stp_handle* h, const Geom<T>& g, cudaGraph_t wb, cudaGraphConditionalHandle h_loop, T* A, T* B,
+                const T* rhs, int mode) {
+  cudaGraphConditionalHandle h_body;
+  CUDA_TRY(h, cudaGraphConditionalHandleCreate(&h_body, wb, 0, cudaGraphCondAssignDefault));
+  int rc;
+  if ((rc = begin_capture(h, wb, nullptr))) return rc;
+  CUDA_TRY(h, launch_check<T>(g, A, rhs, mode, h->ctl, h->red, h_loop, h_body, h->cap));
+  if ((rc = end_capture(h, wb))) return rc;
+  cudaGraph_t ib;
+  cudaGraphNode_t ifn;
+  if ((rc = add_conditional(h, wb, leaf_node(wb), h_body, cudaGraphCondTypeIf, &ib, &ifn))) return rc;
+  if ((rc = begin_capture(h, ib, nullptr))) return rc;
+  const int M = (int)h->omega.size();
+  for (int m = 0; m < M; m++) {
+    const T* src = (m % 2 == 0) ? A : B;
+    T* dst = (m % 2 == 0) ? B : A;
+    CUDA_TRY(h, launch_sweep<T>(g, src, rhs, (T)h->omega[m], dst, h->cap));
+  }
+  return end_capture(h, ib);
+}
+
+int build_solve_graph(stp_handle* h) {
+  if (h->solve_exec) return STP_OK;
+  cudaGraph_t G;
+  CUDA_TRY(h, cudaGraphCreate(&G, 0));
+  h->solve_graph = G;
+  int rc;
+  cudaGraph_t wb, pb;
+  cudaGraphNode_t wn, pn;
+  if (h->prec == STP_FP64) {
+    cudaGraphConditionalHandle h_loop;
+    CUDA_TRY(h, cudaGraphConditionalHandleCreate(&h_loop, G, 1, cudaGraphCondAssignDefault));
+    if ((rc = begin_capture(h, G, nullptr))) return rc;
+    CUDA_TRY(h, launch_begin(h->ctl, h->cap));
+    if ((rc = end_capture(h, G))) return rc;
+    if ((rc = add_conditional(h, G, leaf_node(G), h_loop, cudaGraphCondTypeWhile, &wb, &wn))) return rc;
+    if ((rc = build_cycle<double>(h, h->g64, wb, h_loop, h->p, h->p2, h->b, 0))) return rc;
+  } else {
+    cudaGraphConditionalHandle h_pass, h_loop;
+    CUDA_TRY(h, cudaGraphConditionalHandleCreate(&h_pass, G, 0, cudaGraphCondAssignDefault));
+    if ((rc = begin_capture(h, G, nullptr))) return rc;
+    CUDA_TRY(h, launch_begin(h->ctl, h->cap));
+    CUDA_TRY(h, launch_outer(h->g64, h->p, h->b, h->r32, h->ctl, h->red, 0, h_pass, h->cap));
+    if ((rc = end_capture(h, G))) return rc;
+    if ((rc = add_conditional(h, G, leaf_node(G), h_pass, cudaGraphCondTypeWhile, &pb, &pn))) return rc;
+    // pass body: d = 0, arm the loop -> WHILE(loop){cycle} -> p += d -> outer
+    // residual.  The loop handle is set explicitly each pass: a handle's
+    // default value is applied only when the top-level graph launches.
+    CUDA_TRY(h, cudaGraphConditionalHandleCreate(&h_loop, pb, 1, 0));
+    if ((rc = begin_capture(h, pb, nullptr))) return rc;
+    CUDA_TRY(h, launch_pass_begin(h->d1, h->nc, h_loop, h->cap));
+    if ((rc = end_capture(h, pb))) return rc;
+    if ((rc = add_conditional(h, pb, leaf_node(pb), h_loop, cudaGraphCondTypeWhile, &wb, &wn))) return rc;
+    if ((rc = build_cycle<float>(h, h->g32, wb, h_loop, h->d1, h->d2, h->r32, 1))) return rc;
+    if ((rc = begin_capture(h, pb, wn))) return rc;
+    CUDA_TRY(h, launch_addcorr(h->p, h->d1, h->nc, h->cap));
+    CUDA_TRY(h, launch_outer(h->g64, h->p, h->b, h->r32, h->ctl, h->red, 1, h_pass, h->cap));
+    if ((rc = end_capture(h, pb))) return rc;
+  }
+  CUDA_TRY(h, cudaGraphInstantiate(&h->solve_exec, G, 0));
+  return STP_OK;
+}
+
+// write the solve parameters and clear the totals (once per API call)
+int arm_solves(stp_handle* h, double tol, int maxit) {
+  SolveCtl c = {};
+  c.tol = tol;
+  c.inner_tol = h->cfg.inner_tol > 0 ? h->cfg.inner_tol : 1e-3;
+  c.max_sweeps = maxit;
+  c.max_passes = 64;
+  c.M = (int)h->omega.size();
+  *h->h_ctl = c;
+  CUDA_TRY(h, cudaMemcpyAsync(h->ctl, h->h_ctl, sizeof(SolveCtl), cudaMemcpyHostToDevice, h->st));
+  return STP_OK;
+}
+
+// one solve on the stream; timed with events when `timed`
+int launch_solve(stp_handle* h) {
+  int rc = build_solve_graph(h);
+  if (rc) return rc;
+  CUDA_TRY(h, cudaEventRecord(h->ev0, h->st));
+  CUDA_TRY(h, cudaGraphLaunch(h->solve_exec, h->st));
+  CUDA_TRY(h, cudaEventRecord(h->ev1, h->st));
+  return STP_OK;
+}
+
+// after a sync: elapsed time of the last solve and its counters
+int finish_solve(stp_handle* h, SolveOut* o) {
+  float ms = 0.f;
+  CUDA_TRY(h, cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+  CUDA_TRY(h, cudaMemcpy(h->h_ctl, h->ctl, sizeof(SolveCtl), cudaMemcpyDeviceToHost));
+  const SolveCtl& c = *h->h_ctl;
+  o->sweeps = c.sweeps;
+  o->passes = c.passes;
+  o->converged = c.converged;
+  o->bad = c.bad;
+  o->kernels = c.tot_kernels + c.kernels;
+  o->tot_sweeps = c.tot_sweeps + c.sweeps;
+  o->nonconv = c.nonconv + (c.converged ? 0 : 1);
+  const double nb = h->h_sc[SC_BNORM];
+  o->rel = nb > 0 ? c.res / nb : c.res;
+  h->solve_ms += ms;
+  h->solve_sweeps += c.sweeps;
+  return STP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// one projection step (Sec. 3.1)
+// ---------------------------------------------------------------------------
+template <typename T>
+int step_impl(stp_handle* h, const Geom<T>& g) {
+  const stp_config& c = h->cfg;
+  // history ring: slot 0 becomes level n
+  std::swap(h->Nu[2], h->Nu[1]);
+  std::swap(h->Nv[2], h->Nv[1]);
+  std::swap(h->Nw[2], h->Nw[1]);
+  std::swap(h->Nu[1], h->Nu[0]);
+  std::swap(h->Nv[1], h->Nv[0]);
+  std::swap(h->Nw[1], h->Nw[0]);
+  if (h->nhist < 3) h->nhist++;
+  double b0 = 1, b1 = 0, b2 = 0;
+  if (h->nhist == 2) {
+    b0 = 1.5;
+    b1 = -0.5;
+  } else if (h->nhist == 3) {
+    b0 = 23.0 / 12.0;
+    b1 = -16.0 / 12.0;
+    b2 = 5.0 / 12.0;
+  }
+  T *u = (T*)h->u, *v = (T*)h->v, *w = (T*)h->w;
+  T* nu = (T*)h->nu;
+  const T nu0 = (T)c.nu;
+  if (c.les) CUDA_TRY(h, launch_viscosity<T>(g, u, v, w, nu0, nu, h->st));
+  const T fx = (T)(c.forcing == 0 ? c.fx : 0.0);
+  CUDA_TRY(h, launch_momentum<T>(g, c.les != 0, u, v, w, nu, nu0, fx, (T*)h->Nu[0], (T*)h->Nv[0], (T*)h->Nw[0],
+                                 (const T*)h->Nu[1], (const T*)h->Nv[1], (const T*)h->Nw[1], (const T*)h->Nu[2],
+                                 (const T*)h->Nv[2], (const T*)h->Nw[2], (T)b0, (T)b1, (T)b2, (T)c.dt, (T*)h->ru,
+                                 (T*)h->rv, (T*)h->rw, h->st));
+  // Crank-Nicolson Jacobi sweeps: rhs is the first iterate; buffers rotate
+  // over (t, u) so that the rhs stays intact.
+  void* in[3] = {h->ru, h->rv, h->rw};
+  void* bufA[3] = {h->tu, h->tv, h->tw};
+  void* bufB[3] = {h->u, h->v, h->w};
+  void** cur = in;
+  for (int s = 0; s < h->cn_sweeps; s++) {
+    void** out = (s % 2 == 0) ? bufA : bufB;
+    CUDA_TRY(h, launch_cn_sweep<T>(g, c.les != 0, nu, nu0, (T)(0.5 * c.dt), (const T*)h->ru, (const T*)h->rv,
+                                   (const T*)h->rw, (const T*)cur[0], (const T*)cur[1], (const T*)cur[2],
+                                   (T*)out[0], (T*)out[1], (T*)out[2], h->st));
+    cur = out;
+  }
+  T *su = (T*)cur[0], *sv = (T*)cur[1], *sw = (T*)cur[2];
+  // b = D u* / dt
+  CUDA_TRY(h, launch_divergence_rhs<T>(g, su, sv, sw, 1.0 / c.dt, h->b, h->red, h->st));
+  int rc = launch_solve(h);
+  if (rc) return rc;
+  const double inv_vol = 1.0 / ((double)h->nx * h->ny * c.Lz);
+  CUDA_TRY(h, launch_correct_impl<T>(g, h->p, c.dt, su, sv, sw, h->g64.ihz, h->g64.dzv, inv_vol, h->red, h->st));
+  if (c.forcing == 1) CUDA_TRY(h, launch_flux_shift<T>(g, su, c.ubulk, h->red, h->st));
+  // the buffer holding u^{n+1} becomes the current field
+  if (cur == bufA) {
+    std::swap(h->u, h->tu);
+    std::swap(h->v, h->tv);
+    std::swap(h->w, h->tw);
+  } else if (cur == in) {
+    std::swap(h->u, h->ru);
+    std::swap(h->v, h->rv);
+    std::swap(h->w, h->rw);
+  }
+  h->step++;
+  return STP_OK;
+}
+
+// copy a double field (host or device) into a T device field
+template <typename T>
+int put_field(stp_handle* h, T* dst, const double* src, size_t n, int where) {
+  const cudaMemcpyKind kind = where == STP_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  if (sizeof(T) == sizeof(double)) {
+    CUDA_TRY(h, cudaMemcpyAsync(dst, src, n * sizeof(double), kind, h->st));
+  } else {
+    CUDA_TRY(h, cudaMemcpyAsync(h->stage, src, n * sizeof(double), kind, h->st));
+    CUDA_TRY(h, (launch_convert<float, double>((float*)dst, h->stage, n, h->st)));
+  }
+  return STP_OK;
+}
+
+template <typename T>
+int get_field(stp_handle* h, double* dst, const T* src, size_t n, int where) {
+  const cudaMemcpyKind kind = where == STP_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  if (sizeof(T) == sizeof(double)) {
+    CUDA_TRY(h, cudaMemcpyAsync(dst, src, n * sizeof(double), kind, h->st));
+  } else {
+    CUDA_TRY(h, (launch_convert<double, float>(h->stage, (const float*)src, n, h->st)));
+    CUDA_TRY(h, cudaMemcpyAsync(dst, h->stage, n * sizeof(double), kind, h->st));
+  }
+  return STP_OK;
+}
+
+int put_any(stp_handle* h, void* dst, const double* src, size_t n, int where) {
+  return h->prec == STP_FP64 ? put_field<double>(h, (double*)dst, src, n, where)
+                             : put_field<float>(h, (float*)dst, src, n, where);
+}
+int get_any(stp_handle* h, double* dst, const void* src, size_t n, int where) {
+  return h->prec == STP_FP64 ? get_field<double>(h, dst, (const double*)src, n, where)
+                             : get_field<float>(h, dst, (const float*)src, n, where);
+}
+
+int fill_const(stp_handle* h, double* dst, double val, size_t n, int where) {
+  std::vector<double> tmp(n, val);
+  if (where == STP_HOST) {
+    std::copy(tmp.begin(), tmp.end(), dst);
+    return STP_OK;
+  }
+  CUDA_TRY(h, cudaMemcpyAsync(dst, tmp.data(), n * sizeof(double), cudaMemcpyHostToDevice, h->st));
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  return STP_OK;
+}
+
+int check_where(stp_handle* h, int where) {
+  if (where != STP_HOST && where != STP_DEVICE) return fail(h, STP_EINVAL, "where must be STP_HOST or STP_DEVICE");
+  return STP_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+void stp_config_defaults(stp_config* c) {
+  if (!c) return;
+  std::memset(c, 0, sizeof(*c));
+  c->nx = c->ny = c->nz = 32;
+  c->Lx = 2.0 * 3.14159265358979323846;
+  c->Ly = 3.14159265358979323846;
+  c->Lz = 2.0;
+  c->nu = 1.0;
+  c->dt = 1e-3;
+  c->cs = 0.1;
+  c->vd_a = 25.0;
+  c->re_tau = 180.0;
+  c->precision = STP_FP64;
+  c->ptol = 1e-8;
+  c->pmaxit = 200000;
+  c->inner_tol = 1e-3;
+}
+
+const char* stp_last_error(const stp_handle* h) { return h ? h->err.c_str() : g_init_error.c_str(); }
+
+void stp_destroy(stp_handle* h) {
+  if (!h) return;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(h->dev);
+  if (h->st) cudaStreamSynchronize(h->st);
+  for (void* p : h->allocs) cudaFree(p);
+  if (h->h_sc) cudaFreeHost(h->h_sc);
+  if (h->h_flag) cudaFreeHost(h->h_flag);
+  if (h->solve_exec) cudaGraphExecDestroy(h->solve_exec);
+  if (h->solve_graph) cudaGraphDestroy(h->solve_graph);
+  if (h->cap) cudaStreamDestroy(h->cap);
+  if (h->h_ctl) cudaFreeHost(h->h_ctl);
+  if (h->ev0) cudaEventDestroy(h->ev0);
+  if (h->ev1) cudaEventDestroy(h->ev1);
+  if (h->own_stream && h->st) cudaStreamDestroy(h->st);
+  cudaSetDevice(cur);
+  delete h;
+}
+
+int stp_srj_schedule(const stp_config* cfg, int M, double* omega, int* M_out, double* mu_min, double* mu_max) {
+  std::string why;
+  if (int rc = validate(cfg, &why)) return fail(nullptr, rc, why);
+  if (M != 0 && (!pow2(M) || M > 1024)) return fail(nullptr, STP_EINVAL, "M must be 0 or a power of two <= 1024");
+  double mn, mx;
+  jacobi_bounds(*cfg, &mn, &mx);
+  if (M == 0) M = auto_cycle(mn, mx);
+  const std::vector<double> om = chebyshev(mn, mx, M);
+  if (omega) std::copy(om.begin(), om.end(), omega);
+  if (M_out) *M_out = M;
+  if (mu_min) *mu_min = mn;
+  if (mu_max) *mu_max = mx;
+  return STP_OK;
+}
+
+int stp_init(const stp_config* cfg, stp_handle** out) {
+  if (!out) return fail(nullptr, STP_EINVAL, "out is NULL");
+  *out = nullptr;
+  std::string why;
+  if (int rc = validate(cfg, &why)) return fail(nullptr, rc, why);
+  stp_handle* h = new (std::nothrow) stp_handle();
+  if (!h) return fail(nullptr, STP_ENOMEM, "host allocation failed");
+  h->cfg = *cfg;
+  h->cfg.srj_omega = nullptr;
+  h->prec = cfg->precision;
+  h->dev = cfg->device;
+  h->nx = cfg->nx;
+  h->ny = cfg->ny;
+  h->nz = cfg->nz;
+  h->nplane = (size_t)cfg->nx * cfg->ny;
+  h->nc = h->nplane * cfg->nz;
+  h->nw = h->nplane * (cfg->nz + 1);
+  h->esz = h->prec == STP_FP64 ? sizeof(double) : sizeof(float);
+  auto bail = [&](int rc) {
+    g_init_error = h->err;
+    stp_destroy(h);
+    return rc;
+  };
+  cudaError_t e = cudaSetDevice(h->dev);
+  if (e != cudaSuccess) return bail(fail(h, STP_ECUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e)));
+  if (cfg->stream) {
+    h->st = (cudaStream_t)cfg->stream;
+  } else {
+    e = cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return bail(fail(h, STP_ECUDA, std::string("cudaStreamCreate: ") + cudaGetErrorString(e)));
+    h->own_stream = true;
+  }
+  if (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess)
+    return bail(fail(h, STP_ECUDA, "event or stream creation failed"));
+  // schedule
+  if (cfg->srj_omega) {
+    h->omega.assign(cfg->srj_omega, cfg->srj_omega + cfg->srj_m);
+  } else {
+    double mn, mx;
+    jacobi_bounds(*cfg, &mn, &mx);
+    const int M = cfg->srj_m > 0 ? cfg->srj_m : auto_cycle(mn, mx);
+    h->omega = chebyshev(mn, mx, M);
+  }
+  h->cfg.srj_m = (int)h->omega.size();
+  const ZGrid z = make_z(*cfg);
+  h->cn_sweeps = cfg->cn_sweeps > 0 ? cfg->cn_sweeps : auto_cn_sweeps(*cfg, z);
+  // device memory
+  const size_t es = h->esz, nc = h->nc, nw = h->nw;
+  int rc = STP_OK;
+  auto A = [&](void** p, size_t bytes) {
+    if (rc == STP_OK) rc = dalloc(h, p, bytes);
+  };
+  const int L = h->nz + 1;
+  A((void**)&h->m64, sizeof(double) * kMetricArrays * L);
+  A((void**)&h->m32, sizeof(float) * kMetricArrays * L);
+  A(&h->u, es * nc);
+  A(&h->v, es * nc);
+  A(&h->w, es * nw);
+  A(&h->ru, es * nc);
+  A(&h->rv, es * nc);
+  A(&h->rw, es * nw);
+  A(&h->tu, es * nc);
+  A(&h->tv, es * nc);
+  A(&h->tw, es * nw);
+  for (int l = 0; l < 3; l++) {
+    A(&h->Nu[l], es * nc);
+    A(&h->Nv[l], es * nc);
+    A(&h->Nw[l], es * nw);
+  }
+  if (cfg->les) A(&h->nu, es * nc);
+  A((void**)&h->b, sizeof(double) * nc);
+  A((void**)&h->p, sizeof(double) * nc);
+  A((void**)&h->p2, sizeof(double) * nc);
+  if (h->prec == STP_FP32_REFINE) {
+    A((void**)&h->d1, sizeof(float) * nc);
+    A((void**)&h->d2, sizeof(float) * nc);
+    A((void**)&h->r32, sizeof(float) * nc);
+  }
+  A((void**)&h->stage, sizeof(double) * nw);
+  const Launch big = {dim3((h->nx + 31) / 32, (h->ny + 7) / 8, h->nz + 1), dim3(32, 8, 1), 0};
+  const size_t maxblocks = (size_t)big.grid.x * big.grid.y * big.grid.z + 152 * 32;
+  A((void**)&h->red.partial, sizeof(double) * 2 * maxblocks);
+  A((void**)&h->red.counter, sizeof(unsigned) * 4);
+  A((void**)&h->red.sc, sizeof(double) * SC_COUNT);
+  A((void**)&h->red.flag, sizeof(int) * FL_COUNT);
+  A((void**)&h->ctl, sizeof(SolveCtl));
+  if (rc) return bail(rc);
+  if (cudaMallocHost((void**)&h->h_sc, sizeof(double) * SC_COUNT) != cudaSuccess ||
+      cudaMallocHost((void**)&h->h_flag, sizeof(int) * FL_COUNT) != cudaSuccess ||
+      cudaMallocHost((void**)&h->h_ctl, sizeof(SolveCtl)) != cudaSuccess)
+    return bail(fail(h, STP_ENOMEM, "cudaMallocHost failed"));
+  // metrics
+  const std::vector<double> m = metric_pack(*cfg);
+  std::vector<float> mf(m.begin(), m.end());
+  h->g64 = geom_from<double>(h, h->m64);
+  h->g32 = geom_from<float>(h, h->m32);
+  e = cudaMemcpyAsync(h->m64, m.data(), sizeof(double) * m.size(), cudaMemcpyHostToDevice, h->st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->m32, mf.data(), sizeof(float) * mf.size(), cudaMemcpyHostToDevice, h->st);
+  // every field starts at zero
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->u, 0, es * nc, h->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->v, 0, es * nc, h->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->w, 0, es * nw, h->st);
+  for (int l = 0; l < 3 && e == cudaSuccess; l++) {
+    e = cudaMemsetAsync(h->Nu[l], 0, es * nc, h->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->Nv[l], 0, es * nc, h->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->Nw[l], 0, es * nw, h->st);
+  }
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->p, 0, sizeof(double) * nc, h->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->p2, 0, sizeof(double) * nc, h->st);
+  if (e == cudaSuccess && h->nu) e = cudaMemsetAsync(h->nu, 0, es * nc, h->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->red.counter, 0, sizeof(unsigned) * 4, h->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->red.sc, 0, sizeof(double) * SC_COUNT, h->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->red.flag, 0, sizeof(int) * FL_COUNT, h->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->ctl, 0, sizeof(SolveCtl), h->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+  if (e != cudaSuccess) return bail(fail(h, STP_ECUDA, std::string("init copies: ") + cudaGetErrorString(e)));
+  *out = h;
+  return STP_OK;
+}
+
+int stp_set_fields(stp_handle* h, const double* u, const double* v, const double* w, const double* p, int where) {
+  if (!h) return STP_EINVAL;
+  if (int rc = check_where(h, where)) return rc;
+  if (!u || !v || !w) return fail(h, STP_EINVAL, "u, v and w are required");
+  CUDA_TRY(h, cudaSetDevice(h->dev));
+  // the wall planes of w must be zero
+  std::vector<double> walls(2 * h->nplane);
+  const cudaMemcpyKind k = where == STP_HOST ? cudaMemcpyHostToHost : cudaMemcpyDeviceToHost;
+  CUDA_TRY(h, cudaMemcpyAsync(walls.data(), w, sizeof(double) * h->nplane, k, h->st));
+  CUDA_TRY(h, cudaMemcpyAsync(walls.data() + h->nplane, w + h->nplane * h->nz, sizeof(double) * h->nplane, k, h->st));
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  for (double x : walls)
+    if (x != 0.0) return fail(h, STP_EINVAL, "w must be zero on the wall planes k = 0 and k = nz");
+  int rc;
+  if ((rc = put_any(h, h->u, u, h->nc, where))) return rc;
+  if ((rc = put_any(h, h->v, v, h->nc, where))) return rc;
+  if ((rc = put_any(h, h->w, w, h->nw, where))) return rc;
+  if (p) {
+    CUDA_TRY(h, cudaMemcpyAsync(h->p, p, sizeof(double) * h->nc,
+                                where == STP_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, h->st));
+  } else {
+    CUDA_TRY(h, cudaMemsetAsync(h->p, 0, sizeof(double) * h->nc, h->st));
+  }
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  h->nhist = 0;
+  h->step = 0;
+  h->last_dpdx = 0.0;
+  return STP_OK;
+}
+
+int stp_get_fields(stp_handle* h, double* u, double* v, double* w, double* p, double* nu_t, int where) {
+  if (!h) return STP_EINVAL;
+  if (int rc = check_where(h, where)) return rc;
+  CUDA_TRY(h, cudaSetDevice(h->dev));
+  int rc;
+  if (u && (rc = get_any(h, u, h->u, h->nc, where))) return rc;
+  if (v && (rc = get_any(h, v, h->v, h->nc, where))) return rc;
+  if (w && (rc = get_any(h, w, h->w, h->nw, where))) return rc;
+  if (p)
+    CUDA_TRY(h, cudaMemcpyAsync(p, h->p, sizeof(double) * h->nc,
+                                where == STP_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, h->st));
+  if (nu_t) {
+    if (h->cfg.les) {
+      if ((rc = get_any(h, nu_t, h->nu, h->nc, where))) return rc;
+    } else {
+      CUDA_TRY(h, cudaStreamSynchronize(h->st));
+      if ((rc = fill_const(h, nu_t, h->cfg.nu, h->nc, where))) return rc;
+    }
+  }
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  return STP_OK;
+}
+
+int stp_step(stp_handle* h, int nsteps, stp_step_stats* stats) {
+  if (!h) return STP_EINVAL;
+  if (nsteps < 0) return fail(h, STP_EINVAL, "nsteps < 0");
+  CUDA_TRY(h, cudaSetDevice(h->dev));
+  h->launches = 0;
+  h->solve_sweeps = 0;
+  h->solve_ms = 0.0;
+  int rc = arm_solves(h, h->cfg.ptol, h->cfg.pmaxit);
+  if (rc) return rc;
+  SolveOut so;
+  for (int n = 0; n < nsteps; n++) {
+    rc = h->prec == STP_FP64 ? step_impl<double>(h, h->g64) : step_impl<float>(h, h->g32);
+    if (rc) return rc;
+    if ((rc = sync_scalars(h))) return rc;
+    if ((rc = finish_solve(h, &so))) return rc;
+    if (so.bad) return fail(h, STP_EDIVERGED, "NaN or Inf in the pressure residual");
+    if (h->h_flag[FL_BAD]) return fail(h, STP_EDIVERGED, "NaN or Inf in the velocity");
+  }
+  if (h->cfg.forcing == 1 && nsteps > 0) h->last_dpdx = h->h_sc[SC_SHIFT] / h->cfg.dt;
+  if (stats) {
+    stats->poisson_sweeps = so.sweeps;
+    stats->refine_passes = so.passes;
+    stats->converged = nsteps > 0 ? so.nonconv == 0 : 1;
+    stats->rel_residual = so.rel;
+    stats->ubulk = h->h_sc[SC_BULK] + (h->cfg.forcing == 1 ? h->h_sc[SC_SHIFT] : 0.0);
+    stats->umax = h->h_sc[SC_UMAX];
+    stats->dpdx = h->last_dpdx;
+    stats->step = h->step;
+    stats->launches = h->launches + so.kernels;
+    stats->solve_sweeps = so.tot_sweeps;
+    stats->solve_ms = h->solve_ms;
+  }
+  if (nsteps > 0 && so.nonconv) return fail(h, STP_ENOTCONVERGED, "a pressure solve hit pmaxit");
+  if (h->cfg.cfl_check && h->h_sc[SC_UMAX] * h->cfg.dt > 0.1 * h->cfg.Lx / h->nx)
+    return fail(h, STP_ECFL, "U_max dt > 0.1 dx");
+  return STP_OK;
+}
+
+int stp_poisson_solve(stp_handle* h, const double* rhs, double* p_inout, double tol, int maxit, int where,
+                      stp_solve_stats* stats) {
+  if (!h) return STP_EINVAL;
+  if (int rc = check_where(h, where)) return rc;
+  if (!rhs || !p_inout) return fail(h, STP_EINVAL, "rhs and p_inout are required");
+  if (!(tol >= 0)) return fail(h, STP_EINVAL, "tol must be >= 0");
+  CUDA_TRY(h, cudaSetDevice(h->dev));
+  const cudaMemcpyKind kin = where == STP_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  CUDA_TRY(h, cudaMemcpyAsync(h->b, rhs, sizeof(double) * h->nc, kin, h->st));
+  CUDA_TRY(h, cudaMemcpyAsync(h->p, p_inout, sizeof(double) * h->nc, kin, h->st));
+  CUDA_TRY(h, launch_norm(h->b, h->nc, SC_BNORM, h->red, h->st));
+  int rc = arm_solves(h, tol, maxit > 0 ? maxit : h->cfg.pmaxit);
+  if (rc) return rc;
+  h->solve_ms = 0.0;
+  h->solve_sweeps = 0;
+  if ((rc = launch_solve(h))) return rc;
+  CUDA_TRY(h, cudaMemcpyAsync(p_inout, h->p, sizeof(double) * h->nc,
+                              where == STP_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, h->st));
+  if ((rc = sync_scalars(h))) return rc;
+  SolveOut so;
+  if ((rc = finish_solve(h, &so))) return rc;
+  if (so.bad) return fail(h, STP_EDIVERGED, "NaN or Inf in the pressure residual");
+  if (stats) {
+    stats->sweeps = so.sweeps;
+    stats->refine_passes = so.passes;
+    stats->converged = so.converged;
+    stats->rel_residual = so.rel;
+  }
+  return so.converged ? STP_OK : fail(h, STP_ENOTCONVERGED, "pressure solve hit maxit");
+}
+
+int stp_eval(stp_handle* h, int term, double* a, double* b, double* c, int where) {
+  if (!h) return STP_EINVAL;
+  if (int rc = check_where(h, where)) return rc;
+  if (!a) return fail(h, STP_EINVAL, "output a is required");
+  CUDA_TRY(h, cudaSetDevice(h->dev));
+  const stp_config& cf = h->cfg;
+  int rc = STP_OK;
+  auto visc = [&]() -> int {
+    if (!cf.les) return STP_OK;
+    if (h->prec == STP_FP64)
+      CUDA_TRY(h, launch_viscosity<double>(h->g64, (double*)h->u, (double*)h->v, (double*)h->w, cf.nu,
+                                           (double*)h->nu, h->st));
+    else
+      CUDA_TRY(h, launch_viscosity<float>(h->g32, (float*)h->u, (float*)h->v, (float*)h->w, (float)cf.nu,
+                                          (float*)h->nu, h->st));
+    return STP_OK;
+  };
+  switch (term) {
+    case STP_TERM_VISCOSITY:
+      if ((rc = visc())) return rc;
+      return stp_get_fields(h, nullptr, nullptr, nullptr, nullptr, a, where);
+    case STP_TERM_EXPLICIT:
+    case STP_TERM_DIFFUSION: {
+      if (!b || !c) return fail(h, STP_EINVAL, "velocity terms need a, b and c");
+      if ((rc = visc())) return rc;
+      const double fx = cf.forcing == 0 ? cf.fx : 0.0;
+      if (h->prec == STP_FP64) {
+        if (term == STP_TERM_EXPLICIT)
+          CUDA_TRY(h, launch_explicit_only<double>(h->g64, cf.les != 0, (double*)h->u, (double*)h->v, (double*)h->w,
+                                                   (double*)h->nu, cf.nu, fx, (double*)h->tu, (double*)h->tv,
+                                                   (double*)h->tw, h->st));
+        else
+          CUDA_TRY(h, launch_diffusion_only<double>(h->g64, cf.les != 0, (double*)h->u, (double*)h->v, (double*)h->w,
+                                                    (double*)h->nu, cf.nu, (double*)h->tu, (double*)h->tv,
+                                                    (double*)h->tw, h->st));
+      } else {
+        if (term == STP_TERM_EXPLICIT)
+          CUDA_TRY(h, launch_explicit_only<float>(h->g32, cf.les != 0, (float*)h->u, (float*)h->v, (float*)h->w,
+                                                  (float*)h->nu, (float)cf.nu, (float)fx, (float*)h->tu,
+                                                  (float*)h->tv, (float*)h->tw, h->st));
+        else
+          CUDA_TRY(h, launch_diffusion_only<float>(h->g32, cf.les != 0, (float*)h->u, (float*)h->v, (float*)h->w,
+                                                   (float*)h->nu, (float)cf.nu, (float*)h->tu, (float*)h->tv,
+                                                   (float*)h->tw, h->st));
+      }
+      if ((rc = get_any(h, a, h->tu, h->nc, where))) return rc;
+      if ((rc = get_any(h, b, h->tv, h->nc, where))) return rc;
+      if ((rc = get_any(h, c, h->tw, h->nw, where))) return rc;
+      break;
+    }
+    case STP_TERM_DIVERGENCE:
+      if (h->prec == STP_FP64)
+        CUDA_TRY(h, launch_divergence_rhs<double>(h->g64, (double*)h->u, (double*)h->v, (double*)h->w, 1.0, h->stage,
+                                                  h->red, h->st));
+      else
+        CUDA_TRY(h, launch_divergence_rhs<float>(h->g32, (float*)h->u, (float*)h->v, (float*)h->w, 1.0, h->stage,
+                                                 h->red, h->st));
+      CUDA_TRY(h, cudaMemcpyAsync(a, h->stage, sizeof(double) * h->nc,
+                                  where == STP_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, h->st));
+      break;
+    case STP_TERM_LAPLACIAN:
+      CUDA_TRY(h, launch_laplacian(h->g64, h->p, h->stage, h->st));
+      CUDA_TRY(h, cudaMemcpyAsync(a, h->stage, sizeof(double) * h->nc,
+                                  where == STP_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, h->st));
+      break;
+    default:
+      return fail(h, STP_EINVAL, "unknown term");
+  }
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  return STP_OK;
+}
+
+}  // extern "C"

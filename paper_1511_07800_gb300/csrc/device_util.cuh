@@ -1,0 +1,104 @@
+// Device helpers shared by the kernels: indexing on the periodic x-y plane,
+// the wall ghosts, and the deterministic block / grid reductions.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "stp_internal.cuh"
+
+namespace stp {
+
+constexpr int kBX = 32;  // threads along x (one warp: coalesced rows)
+constexpr int kBY = 8;   // threads along y
+
+__host__ inline Launch plane_launch(int nx, int ny, int nlev) {
+  Launch l;
+  l.block = dim3(kBX, kBY, 1);
+  l.grid = dim3((nx + kBX - 1) / kBX, (ny + kBY - 1) / kBY, nlev);
+  l.nblocks = l.grid.x * l.grid.y * l.grid.z;
+  return l;
+}
+
+// Index of (i, j, k) in an x-fastest array with ny rows of nx.
+__device__ __forceinline__ int at(int nx, int ny, int i, int j, int k) { return (k * ny + j) * nx + i; }
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Sum (and max) over the block; result valid in thread 0.  Fixed tree order.
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  const int nthr = blockDim.x * blockDim.y * blockDim.z;
+  v = warp_sum(v);
+  __syncthreads();
+  if ((tid & 31) == 0) sh[tid >> 5] = v;
+  __syncthreads();
+  if (tid < 32) {
+    v = (tid < (nthr >> 5)) ? sh[tid] : 0.0;
+    v = warp_sum(v);
+  }
+  return v;
+}
+__device__ __forceinline__ double block_max(double v, double* sh) {
+  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  const int nthr = blockDim.x * blockDim.y * blockDim.z;
+  v = warp_max(v);
+  __syncthreads();
+  if ((tid & 31) == 0) sh[tid >> 5] = v;
+  __syncthreads();
+  if (tid < 32) {
+    v = (tid < (nthr >> 5)) ? sh[tid] : 0.0;
+    v = warp_max(v);
+  }
+  return v;
+}
+
+__device__ __forceinline__ unsigned block_linear() {
+  return blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+}
+
+// Publish this block's partial(s); returns true in every thread of the last
+// block to arrive, which then owns the final reduction.
+__device__ __forceinline__ bool publish_partial(Red red, unsigned nblocks, double a, double b, bool two) {
+  __shared__ bool last;
+  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  if (tid == 0) {
+    const unsigned bl = block_linear();
+    red.partial[bl] = a;
+    if (two) red.partial[nblocks + bl] = b;
+    __threadfence();
+    const unsigned t = atomicAdd(red.counter, 1u);
+    last = (t == nblocks - 1);
+  }
+  __syncthreads();
+  return last;
+}
+
+// In the last block: sum of partial[0..n) in a fixed order (strided per
+// thread, then the block tree).  Valid in thread 0.
+__device__ __forceinline__ double final_sum(const double* part, unsigned n, double* sh) {
+  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  const int nthr = blockDim.x * blockDim.y * blockDim.z;
+  double s = 0.0;
+  for (unsigned q = tid; q < n; q += nthr) s += __ldcg(part + q);
+  return block_sum(s, sh);
+}
+__device__ __forceinline__ double final_max(const double* part, unsigned n, double* sh) {
+  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  const int nthr = blockDim.x * blockDim.y * blockDim.z;
+  double s = 0.0;
+  for (unsigned q = tid; q < n; q += nthr) s = fmax(s, __ldcg(part + q));
+  return block_max(s, sh);
+}
+
+__device__ __forceinline__ int flag_read(const int* f) { return __ldcg(f); }
+
+}  // namespace stp

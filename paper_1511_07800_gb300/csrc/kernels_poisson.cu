@@ -1,0 +1,301 @@
+// Pressure-Poisson kernels (arXiv 1511.07800, Sec. 3.4 and Eq. presdiv).
+//
+// L p = D G p on the MAC grid: periodic in x and y, zero flux through the
+// walls (Neumann):
+//   (L p)_k = [(p_{i+1} - p_i) - (p_i - p_{i-1})]/dx^2 + (same in y)
+//             + cup_k (p_{k+1} - p_k) - cdn_k (p_k - p_{k-1}),
+// cup_k = 1/(hz_{k+1} dz_k) (0 at the top), cdn_k = 1/(hz_k dz_k) (0 at the
+// bottom), S_k = 2/dx^2 + 2/dy^2 + cup_k + cdn_k.
+//
+// Jacobi-SOR (Eq. Jacobi-SOR in 3-D): p' = (1 - omega) p + omega p^J with
+// p^J = (sum_nb c p_nb - b)/S.  Since p^J - p = -(b - L p)/S, the sweep is
+// written p' = p - omega (b - L p)/S with L p in difference form, which in
+// FP32 avoids the cancellation of sum_nb c p_nb against S p.
+//
+// The solve is driven on the device: a residual-check kernel decides, once
+// per SRJ cycle, whether to run the cycle's M sweeps, and sets the graph
+// conditionals (WHILE over cycles, IF around the sweeps) -- see api.cu.
+#include <algorithm>
+
+#include "device_util.cuh"
+#include "stp_internal.cuh"
+
+namespace stp {
+
+namespace {
+
+// b - L p at one point, difference form (arithmetic in T)
+template <typename T>
+__device__ __forceinline__ T point_residual(const Geom<T>& g, const T* __restrict__ p, const T* __restrict__ b,
+                                            int i, int j, int k, T* pc_out) {
+  const int nx = g.nx, plane = g.nx * g.ny;
+  const int ip = i == nx - 1 ? 0 : i + 1, im = i == 0 ? nx - 1 : i - 1;
+  const int jp = j == g.ny - 1 ? 0 : j + 1, jm = j == 0 ? g.ny - 1 : j - 1;
+  const int row = k * plane;
+  const int q = row + j * nx + i;
+  const T pc = __ldg(p + q);
+  T lap = g.idx2 * ((__ldg(p + row + j * nx + ip) - pc) + (__ldg(p + row + j * nx + im) - pc)) +
+          g.idy2 * ((__ldg(p + row + jp * nx + i) - pc) + (__ldg(p + row + jm * nx + i) - pc));
+  if (k < g.nz - 1) lap += __ldg(g.cup + k) * (__ldg(p + q + plane) - pc);
+  if (k > 0) lap += __ldg(g.cdn + k) * (__ldg(p + q - plane) - pc);
+  *pc_out = pc;
+  return __ldg(b + q) - lap;
+}
+
+// FP32: difference form (no cancellation against S p).
+__global__ void __launch_bounds__(kBX* kBY) k_sweep_f32(Geom<float> g, const float* __restrict__ p,
+                                                         const float* __restrict__ b, float omega,
+                                                         float* __restrict__ out) {
+  const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y, k = blockIdx.z;
+  if (i >= g.nx || j >= g.ny) return;
+  float pc;
+  const float r = point_residual(g, p, b, i, j, k, &pc);
+  out[(k * g.ny + j) * g.nx + i] = pc - omega * r * __ldg(g.iS + k);
+}
+
+// FP64: the neighbour-sum form p + omega (p^J - p), p^J = (sum_nb c p_nb - b)/S,
+// which needs fewest FP64 operations (the FP64 sweep is bound by FP64
+// arithmetic on this part, not by memory).
+__global__ void __launch_bounds__(kBX* kBY) k_sweep_f64(Geom<double> g, const double* __restrict__ p,
+                                                         const double* __restrict__ b, double omega,
+                                                         double* __restrict__ out) {
+  const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y, k = blockIdx.z;
+  if (i >= g.nx || j >= g.ny) return;
+  const int nx = g.nx, plane = g.nx * g.ny;
+  const int ip = i == nx - 1 ? 0 : i + 1, im = i == 0 ? nx - 1 : i - 1;
+  const int jp = j == g.ny - 1 ? 0 : j + 1, jm = j == 0 ? g.ny - 1 : j - 1;
+  const int row = k * plane;
+  const int q = row + j * nx + i;
+  const double pc = __ldg(p + q);
+  double nb = g.idx2 * (__ldg(p + row + j * nx + ip) + __ldg(p + row + j * nx + im)) +
+              g.idy2 * (__ldg(p + row + jp * nx + i) + __ldg(p + row + jm * nx + i));
+  if (k < g.nz - 1) nb += __ldg(g.cup + k) * __ldg(p + q + plane);
+  if (k > 0) nb += __ldg(g.cdn + k) * __ldg(p + q - plane);
+  const double pj = (nb - __ldg(b + q)) * __ldg(g.iS + k);
+  out[q] = pc + omega * (pj - pc);
+}
+
+// arms the inner loop of a refinement pass and clears its correction
+__global__ void k_pass_begin(float* __restrict__ d, size_t n, cudaGraphConditionalHandle h_loop) {
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x)
+    d[q] = 0.f;
+  if (blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(h_loop, 1u);
+}
+
+// ||b - L p||_2 reduced in FP64, then the cycle decision in the last block.
+// mode 0: FP64 solve (tol * ||b||); mode 1: FP32 inner solve of the
+// refinement (target max(inner_tol ||r||, tol ||b|| / 2), stop on stall).
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kBX* kBY) k_check(Geom<T> g, const T* __restrict__ p, const T* __restrict__ b,
+                                                     SolveCtl* ctl, Red red, unsigned nblocks,
+                                                     cudaGraphConditionalHandle h_loop,
+                                                     cudaGraphConditionalHandle h_body) {
+  __shared__ double sh[32];
+  const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y, k = blockIdx.z;
+  double s = 0.0;
+  if (i < g.nx && j < g.ny) {
+    T pc;
+    const double r = (double)point_residual(g, p, b, i, j, k, &pc);
+    s = r * r;
+  }
+  s = block_sum(s, sh);
+  if (publish_partial(red, nblocks, s, 0.0, false)) {
+    const double tot = final_sum(red.partial, nblocks, sh);
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+      const double res = sqrt(tot);
+      const double nb = red.sc[SC_BNORM];
+      bool stop;
+      ctl->kernels += 1;
+      if (!(res == res) || isinf(res)) {
+        ctl->bad = 1;
+        stop = true;
+      } else if (MODE == 0) {
+        ctl->res = res;
+        ctl->converged = res <= ctl->tol * nb;
+        stop = ctl->converged || ctl->sweeps >= ctl->max_sweeps;
+      } else {
+        const double target = fmax(ctl->inner_tol * red.sc[SC_INNER_REF], 0.5 * ctl->tol * nb);
+        const bool stall = ctl->cycles_inner > 0 && res > 0.9 * ctl->prev;
+        ctl->res_inner = res;
+        stop = res <= target || stall || ctl->sweeps >= ctl->max_sweeps;
+        ctl->prev = res;
+      }
+      if (!stop) {
+        ctl->sweeps += ctl->M;
+        ctl->cycles_inner += 1;
+        ctl->kernels += ctl->M;
+      }
+      *red.counter = 0u;
+      cudaGraphSetConditional(h_loop, stop ? 0u : 1u);
+      cudaGraphSetConditional(h_body, stop ? 0u : 1u);
+    }
+  }
+}
+
+// Refinement residual: r = b - L p in FP64 (difference form), stored in FP32
+// for the inner solve; decides whether another refinement pass runs.
+__global__ void __launch_bounds__(kBX* kBY) k_outer(Geom<double> g, const double* __restrict__ p,
+                                                     const double* __restrict__ b, float* __restrict__ r32,
+                                                     SolveCtl* ctl, Red red, unsigned nblocks, int after_pass,
+                                                     cudaGraphConditionalHandle h_loop) {
+  __shared__ double sh[32];
+  const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y, k = blockIdx.z;
+  double s = 0.0;
+  if (i < g.nx && j < g.ny) {
+    double pc;
+    const double r = point_residual(g, p, b, i, j, k, &pc);
+    r32[(k * g.ny + j) * g.nx + i] = (float)r;
+    s = r * r;
+  }
+  s = block_sum(s, sh);
+  if (publish_partial(red, nblocks, s, 0.0, false)) {
+    const double tot = final_sum(red.partial, nblocks, sh);
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+      const double res = sqrt(tot);
+      const double nb = red.sc[SC_BNORM];
+      ctl->kernels += 1 + (after_pass ? 1 : 0);  // this kernel and the correction before it
+      if (after_pass) ctl->passes += 1;
+      ctl->res = res;
+      red.sc[SC_INNER_REF] = res;
+      ctl->cycles_inner = 0;
+      ctl->prev = 0.0;
+      bool stop;
+      if (!(res == res) || isinf(res)) {
+        ctl->bad = 1;
+        stop = true;
+      } else {
+        ctl->converged = res <= ctl->tol * nb;
+        stop = ctl->converged || ctl->sweeps >= ctl->max_sweeps || ctl->passes >= ctl->max_passes;
+      }
+      *red.counter = 0u;
+      cudaGraphSetConditional(h_loop, stop ? 0u : 1u);
+    }
+  }
+}
+
+__global__ void k_addcorr(double* __restrict__ p, const float* __restrict__ d, size_t n) {
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x)
+    p[q] += (double)d[q];
+}
+
+__global__ void k_begin(SolveCtl* ctl) {
+  if (ctl->solves > 0) {
+    ctl->tot_sweeps += ctl->sweeps;
+    ctl->tot_kernels += ctl->kernels;
+    ctl->nonconv += ctl->converged ? 0 : 1;
+  }
+  ctl->solves += 1;
+  ctl->sweeps = 0;
+  ctl->passes = 0;
+  ctl->cycles_inner = 0;
+  ctl->converged = 0;
+  ctl->prev = 0.0;
+  ctl->kernels = 1;
+}
+
+__global__ void __launch_bounds__(kBX* kBY) k_laplacian(Geom<double> g, const double* __restrict__ p,
+                                                         double* __restrict__ out) {
+  const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y, k = blockIdx.z;
+  if (i >= g.nx || j >= g.ny) return;
+  const int nx = g.nx, plane = g.nx * g.ny;
+  const int ip = i == nx - 1 ? 0 : i + 1, im = i == 0 ? nx - 1 : i - 1;
+  const int jp = j == g.ny - 1 ? 0 : j + 1, jm = j == 0 ? g.ny - 1 : j - 1;
+  const int row = k * plane, q = row + j * nx + i;
+  const double pc = p[q];
+  double lap = (p[row + j * nx + ip] - 2.0 * pc + p[row + j * nx + im]) * g.idx2 +
+               (p[row + jp * nx + i] - 2.0 * pc + p[row + jm * nx + i]) * g.idy2;
+  if (k < g.nz - 1) lap += g.cup[k] * (p[q + plane] - pc);
+  if (k > 0) lap -= g.cdn[k] * (pc - p[q - plane]);
+  out[q] = lap;
+}
+
+// ||a||_2 into sc[slot]
+__global__ void k_norm(const double* __restrict__ a, size_t n, int slot, Red red, unsigned nblocks) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
+    const double x = a[q];
+    s += x * x;
+  }
+  s = block_sum(s, sh);
+  if (publish_partial(red, nblocks, s, 0.0, false)) {
+    const double tot = final_sum(red.partial, nblocks, sh);
+    if (threadIdx.x == 0) {
+      red.sc[slot] = sqrt(tot);
+      *red.counter = 0u;
+    }
+  }
+}
+
+}  // namespace
+
+template <>
+cudaError_t launch_sweep<float>(const Geom<float>& g, const float* p, const float* b, float omega, float* out,
+                                cudaStream_t s) {
+  Launch l = plane_launch(g.nx, g.ny, g.nz);
+  k_sweep_f32<<<l.grid, l.block, 0, s>>>(g, p, b, omega, out);
+  return cudaGetLastError();
+}
+template <>
+cudaError_t launch_sweep<double>(const Geom<double>& g, const double* p, const double* b, double omega, double* out,
+                                 cudaStream_t s) {
+  Launch l = plane_launch(g.nx, g.ny, g.nz);
+  k_sweep_f64<<<l.grid, l.block, 0, s>>>(g, p, b, omega, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pass_begin(float* d, size_t n, cudaGraphConditionalHandle h_loop, cudaStream_t s) {
+  unsigned blocks = (unsigned)std::min<size_t>((n + 255) / 256, 152 * 16);
+  k_pass_begin<<<blocks ? blocks : 1, 256, 0, s>>>(d, n, h_loop);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_check(const Geom<T>& g, const T* p, const T* b, int mode, SolveCtl* ctl, Red red,
+                         cudaGraphConditionalHandle h_loop, cudaGraphConditionalHandle h_body, cudaStream_t s) {
+  Launch l = plane_launch(g.nx, g.ny, g.nz);
+  if (mode == 0)
+    k_check<T, 0><<<l.grid, l.block, 0, s>>>(g, p, b, ctl, red, l.nblocks, h_loop, h_body);
+  else
+    k_check<T, 1><<<l.grid, l.block, 0, s>>>(g, p, b, ctl, red, l.nblocks, h_loop, h_body);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_outer(const Geom<double>& g, const double* p, const double* b, float* r32, SolveCtl* ctl, Red red,
+                         int after_pass, cudaGraphConditionalHandle h_loop, cudaStream_t s) {
+  Launch l = plane_launch(g.nx, g.ny, g.nz);
+  k_outer<<<l.grid, l.block, 0, s>>>(g, p, b, r32, ctl, red, l.nblocks, after_pass, h_loop);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_addcorr(double* p, const float* d, size_t n, cudaStream_t s) {
+  unsigned blocks = (unsigned)std::min<size_t>((n + 255) / 256, 152 * 16);
+  k_addcorr<<<blocks ? blocks : 1, 256, 0, s>>>(p, d, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_begin(SolveCtl* ctl, cudaStream_t s) {
+  k_begin<<<1, 1, 0, s>>>(ctl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_laplacian(const Geom<double>& g, const double* p, double* out, cudaStream_t s) {
+  Launch l = plane_launch(g.nx, g.ny, g.nz);
+  k_laplacian<<<l.grid, l.block, 0, s>>>(g, p, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_norm(const double* a, size_t n, int slot, Red red, cudaStream_t s) {
+  unsigned blocks = (unsigned)((n + 255) / 256);
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  if (blocks == 0) blocks = 1;
+  k_norm<<<blocks, 256, 0, s>>>(a, n, slot, red, blocks);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_check<double>(const Geom<double>&, const double*, const double*, int, SolveCtl*, Red,
+                                          cudaGraphConditionalHandle, cudaGraphConditionalHandle, cudaStream_t);
+template cudaError_t launch_check<float>(const Geom<float>&, const float*, const float*, int, SolveCtl*, Red,
+                                         cudaGraphConditionalHandle, cudaGraphConditionalHandle, cudaStream_t);
+
+}  // namespace stp

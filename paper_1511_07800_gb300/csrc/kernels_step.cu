@@ -1,0 +1,561 @@
+// Velocity-side kernels of the projection step (arXiv 1511.07800, Sec. 2.2
+// and 3.1): eddy viscosity, explicit terms with the Adams-Bashforth
+// combination and the Crank-Nicolson right-hand side, Crank-Nicolson Jacobi
+// sweeps, divergence / Poisson right-hand side, velocity correction.
+//
+// Every kernel handles one output point per thread over an x-y tile of
+// 32 x 8 threads and one z level per block row of the grid, reading its
+// neighbours through the read-only cache.  x and y wrap periodically; at the
+// walls u and v take the mirror ghost (minus the first interior value) and
+// the wall planes of w are zero.
+#include "device_util.cuh"
+#include "stp_internal.cuh"
+
+namespace stp {
+
+namespace {
+
+template <typename T>
+struct Pt {
+  const Geom<T>& g;
+  int i, j, k, im, ip, jm, jp;
+  __device__ Pt(const Geom<T>& g_, int i_, int j_, int k_) : g(g_), i(i_), j(j_), k(k_) {
+    im = i == 0 ? g.nx - 1 : i - 1;
+    ip = i == g.nx - 1 ? 0 : i + 1;
+    jm = j == 0 ? g.ny - 1 : j - 1;
+    jp = j == g.ny - 1 ? 0 : j + 1;
+  }
+  __device__ int wx(int a) const { return a < 0 ? a + g.nx : (a >= g.nx ? a - g.nx : a); }
+  __device__ int wy(int b) const { return b < 0 ? b + g.ny : (b >= g.ny ? b - g.ny : b); }
+  // u or v with the no-slip ghost; a, b already wrapped; c in [-1, nz]
+  __device__ T vel(const T* f, int a, int b, int c) const {
+    if (c < 0) return -__ldg(f + at(g.nx, g.ny, a, b, 0));
+    if (c >= g.nz) return -__ldg(f + at(g.nx, g.ny, a, b, g.nz - 1));
+    return __ldg(f + at(g.nx, g.ny, a, b, c));
+  }
+  // w, c in [0, nz]
+  __device__ T wv(const T* f, int a, int b, int c) const { return __ldg(f + at(g.nx, g.ny, a, b, c)); }
+};
+
+// Viscosity lookups: constant nu0 without LES; with LES the cell-centred
+// field with even reflection at the walls, averaged to edges.
+template <typename T, bool LES>
+struct Visc {
+  const T* nu;
+  T nu0;
+  int nx, ny, nz;
+  __device__ T c(int a, int b, int k) const {
+    if (!LES) return nu0;
+    k = k < 0 ? 0 : (k >= nz ? nz - 1 : k);
+    return __ldg(nu + at(nx, ny, a, b, k));
+  }
+  // edge quantities; callers pass the two wrapped cell indices on each side
+  __device__ T e4(int a0, int a1, int b0, int b1, int k) const {  // xy-edge: cells a0,a1 x b0,b1 at level k
+    if (!LES) return nu0;
+    return T(0.25) * (c(a0, b0, k) + c(a1, b0, k) + c(a0, b1, k) + c(a1, b1, k));
+  }
+  __device__ T ez_x(int a0, int a1, int b, int cz) const {  // xz-edge at face cz: cells a0,a1 x cz-1,cz
+    if (!LES) return nu0;
+    return T(0.25) * (c(a0, b, cz - 1) + c(a1, b, cz - 1) + c(a0, b, cz) + c(a1, b, cz));
+  }
+  __device__ T ez_y(int a, int b0, int b1, int cz) const {  // yz-edge at face cz: cells b0,b1 x cz-1,cz
+    if (!LES) return nu0;
+    return T(0.25) * (c(a, b0, cz - 1) + c(a, b1, cz - 1) + c(a, b0, cz) + c(a, b1, cz));
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Sec. 2.2: nu_T = nu + (Cs Delta phi_w)^2 |S|, |S| = sqrt(2 S_ij S_ij);
+// off-diagonal strain on its edges, averaged from the four edges around the
+// centre.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kBX* kBY) k_viscosity(Geom<T> g, const T* __restrict__ u,
+                                                         const T* __restrict__ v, const T* __restrict__ w,
+                                                         T nu0, T* __restrict__ nu) {
+  const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y, k = blockIdx.z;
+  if (i >= g.nx || j >= g.ny) return;
+  Pt<T> P(g, i, j, k);
+  const int im = P.im, ip = P.ip, jm = P.jm, jp = P.jp;
+  const T s11 = (P.vel(u, ip, j, k) - P.vel(u, i, j, k)) * g.idx;
+  const T s22 = (P.vel(v, i, jp, k) - P.vel(v, i, j, k)) * g.idy;
+  const T s33 = (P.wv(w, i, j, k + 1) - P.wv(w, i, j, k)) * __ldg(g.idz + k);
+  auto e12 = [&](int a, int am, int b, int bm) {
+    return T(0.5) * ((P.vel(u, a, b, k) - P.vel(u, a, bm, k)) * g.idy + (P.vel(v, a, b, k) - P.vel(v, am, b, k)) * g.idx);
+  };
+  auto e13 = [&](int a, int am, int c) {
+    return T(0.5) * ((P.vel(u, a, j, c) - P.vel(u, a, j, c - 1)) * __ldg(g.idzf + c) +
+                     (P.wv(w, a, j, c) - P.wv(w, am, j, c)) * g.idx);
+  };
+  auto e23 = [&](int b, int bm, int c) {
+    return T(0.5) * ((P.vel(v, i, b, c) - P.vel(v, i, b, c - 1)) * __ldg(g.idzf + c) +
+                     (P.wv(w, i, b, c) - P.wv(w, i, bm, c)) * g.idy);
+  };
+  const T s12 = T(0.25) * (e12(i, im, j, jm) + e12(ip, i, j, jm) + e12(i, im, jp, j) + e12(ip, i, jp, j));
+  const T s13 = T(0.25) * (e13(i, im, k) + e13(ip, i, k) + e13(i, im, k + 1) + e13(ip, i, k + 1));
+  const T s23 = T(0.25) * (e23(j, jm, k) + e23(jp, j, k) + e23(j, jm, k + 1) + e23(jp, j, k + 1));
+  const T smag = sqrt(T(2) * (s11 * s11 + s22 * s22 + s33 * s33) + T(4) * (s12 * s12 + s13 * s13 + s23 * s23));
+  nu[at(g.nx, g.ny, i, j, k)] = nu0 + __ldg(g.lm2 + k) * smag;
+}
+
+// ---------------------------------------------------------------------------
+// Sec. 3.1 terms at one point.
+// ---------------------------------------------------------------------------
+
+// advective form u_j d_j u_i
+template <typename T>
+__device__ __forceinline__ T adv_u(const Pt<T>& P, const T* u, const T* v, const T* w) {
+  const Geom<T>& g = P.g;
+  const int i = P.i, j = P.j, k = P.k;
+  const T vb = T(0.25) * (P.vel(v, P.im, j, k) + P.vel(v, i, j, k) + P.vel(v, P.im, P.jp, k) + P.vel(v, i, P.jp, k));
+  const T wb = T(0.25) * (P.wv(w, P.im, j, k) + P.wv(w, i, j, k) + P.wv(w, P.im, j, k + 1) + P.wv(w, i, j, k + 1));
+  const T dudx = (P.vel(u, P.ip, j, k) - P.vel(u, P.im, j, k)) * g.hidx;
+  const T dudy = (P.vel(u, i, P.jp, k) - P.vel(u, i, P.jm, k)) * g.hidy;
+  const T dudz = (P.vel(u, i, j, k + 1) - P.vel(u, i, j, k - 1)) * __ldg(g.i2dzc + k);
+  return P.vel(u, i, j, k) * dudx + vb * dudy + wb * dudz;
+}
+template <typename T>
+__device__ __forceinline__ T adv_v(const Pt<T>& P, const T* u, const T* v, const T* w) {
+  const Geom<T>& g = P.g;
+  const int i = P.i, j = P.j, k = P.k;
+  const T ub = T(0.25) * (P.vel(u, i, P.jm, k) + P.vel(u, P.ip, P.jm, k) + P.vel(u, i, j, k) + P.vel(u, P.ip, j, k));
+  const T wb = T(0.25) * (P.wv(w, i, P.jm, k) + P.wv(w, i, j, k) + P.wv(w, i, P.jm, k + 1) + P.wv(w, i, j, k + 1));
+  const T dvdx = (P.vel(v, P.ip, j, k) - P.vel(v, P.im, j, k)) * g.hidx;
+  const T dvdy = (P.vel(v, i, P.jp, k) - P.vel(v, i, P.jm, k)) * g.hidy;
+  const T dvdz = (P.vel(v, i, j, k + 1) - P.vel(v, i, j, k - 1)) * __ldg(g.i2dzc + k);
+  return ub * dvdx + P.vel(v, i, j, k) * dvdy + wb * dvdz;
+}
+// w at an interior face c = P.k
+template <typename T>
+__device__ __forceinline__ T adv_w(const Pt<T>& P, const T* u, const T* v, const T* w) {
+  const Geom<T>& g = P.g;
+  const int i = P.i, j = P.j, c = P.k;
+  const T ub = T(0.25) * (P.vel(u, i, j, c - 1) + P.vel(u, P.ip, j, c - 1) + P.vel(u, i, j, c) + P.vel(u, P.ip, j, c));
+  const T vb = T(0.25) * (P.vel(v, i, j, c - 1) + P.vel(v, i, P.jp, c - 1) + P.vel(v, i, j, c) + P.vel(v, i, P.jp, c));
+  const T dwdx = (P.wv(w, P.ip, j, c) - P.wv(w, P.im, j, c)) * g.hidx;
+  const T dwdy = (P.wv(w, i, P.jp, c) - P.wv(w, i, P.jm, c)) * g.hidy;
+  const T dwdz = (P.wv(w, i, j, c + 1) - P.wv(w, i, j, c - 1)) * __ldg(g.idzw + c);
+  return ub * dwdx + vb * dwdy + P.wv(w, i, j, c) * dwdz;
+}
+
+// Viscous fluxes.  For each component the "diffusive-like" part
+// d_j(nu d_j u_i) (Crank-Nicolson) and the "convective-like" part
+// d_j(nu d_i u_j) (Adams-Bashforth) share the edge viscosities.
+template <typename T, bool LES>
+struct ViscU {
+  T diff, cross, diag;  // D u, C u, diagonal weight of D
+};
+
+template <typename T, bool LES>
+__device__ __forceinline__ ViscU<T, LES> visc_u(const Pt<T>& P, const Visc<T, LES>& N, const T* u, const T* v,
+                                                const T* w, bool need_cross) {
+  const Geom<T>& g = P.g;
+  const int i = P.i, j = P.j, k = P.k, im = P.im, ip = P.ip, jm = P.jm, jp = P.jp;
+  const T c = P.vel(u, i, j, k);
+  const T nxp = N.c(i, j, k), nxm = N.c(im, j, k);
+  const T nyp = N.e4(im, i, j, jp, k), nym = N.e4(im, i, jm, j, k);
+  const T nzp = N.ez_x(im, i, j, k + 1), nzm = N.ez_x(im, i, j, k);
+  const T idz = __ldg(g.idz + k), izp = __ldg(g.idzf + k + 1), izm = __ldg(g.idzf + k);
+  const T fx = (nxp * (P.vel(u, ip, j, k) - c) - nxm * (c - P.vel(u, im, j, k))) * g.idx2;
+  const T fy = (nyp * (P.vel(u, i, jp, k) - c) - nym * (c - P.vel(u, i, jm, k))) * g.idy2;
+  const T fz = (nzp * (P.vel(u, i, j, k + 1) - c) * izp - nzm * (c - P.vel(u, i, j, k - 1)) * izm) * idz;
+  ViscU<T, LES> r;
+  r.diff = fx + fy + fz;
+  const T gu = (k == g.nz - 1) ? T(2) : T(1), gd = (k == 0) ? T(2) : T(1);
+  r.diag = (nxp + nxm) * g.idx2 + (nyp + nym) * g.idy2 + (gu * nzp * izp + gd * nzm * izm) * idz;
+  r.cross = T(0);
+  if (need_cross) {
+    const T cy = (nyp * (P.vel(v, i, jp, k) - P.vel(v, im, jp, k)) - nym * (P.vel(v, i, j, k) - P.vel(v, im, j, k))) * g.idxdy;
+    const T cz = (nzp * (P.wv(w, i, j, k + 1) - P.wv(w, im, j, k + 1)) - nzm * (P.wv(w, i, j, k) - P.wv(w, im, j, k))) *
+                 g.idx * idz;
+    r.cross = fx + cy + cz;
+  }
+  return r;
+}
+
+template <typename T, bool LES>
+__device__ __forceinline__ ViscU<T, LES> visc_v(const Pt<T>& P, const Visc<T, LES>& N, const T* u, const T* v,
+                                                const T* w, bool need_cross) {
+  const Geom<T>& g = P.g;
+  const int i = P.i, j = P.j, k = P.k, im = P.im, ip = P.ip, jm = P.jm, jp = P.jp;
+  const T c = P.vel(v, i, j, k);
+  const T nxp = N.e4(i, ip, jm, j, k), nxm = N.e4(im, i, jm, j, k);
+  const T nyp = N.c(i, j, k), nym = N.c(i, jm, k);
+  const T nzp = N.ez_y(i, jm, j, k + 1), nzm = N.ez_y(i, jm, j, k);
+  const T idz = __ldg(g.idz + k), izp = __ldg(g.idzf + k + 1), izm = __ldg(g.idzf + k);
+  const T fx = (nxp * (P.vel(v, ip, j, k) - c) - nxm * (c - P.vel(v, im, j, k))) * g.idx2;
+  const T fy = (nyp * (P.vel(v, i, jp, k) - c) - nym * (c - P.vel(v, i, jm, k))) * g.idy2;
+  const T fz = (nzp * (P.vel(v, i, j, k + 1) - c) * izp - nzm * (c - P.vel(v, i, j, k - 1)) * izm) * idz;
+  ViscU<T, LES> r;
+  r.diff = fx + fy + fz;
+  const T gu = (k == g.nz - 1) ? T(2) : T(1), gd = (k == 0) ? T(2) : T(1);
+  r.diag = (nxp + nxm) * g.idx2 + (nyp + nym) * g.idy2 + (gu * nzp * izp + gd * nzm * izm) * idz;
+  r.cross = T(0);
+  if (need_cross) {
+    const T cx = (nxp * (P.vel(u, ip, j, k) - P.vel(u, ip, jm, k)) - nxm * (P.vel(u, i, j, k) - P.vel(u, i, jm, k))) * g.idxdy;
+    const T cz = (nzp * (P.wv(w, i, j, k + 1) - P.wv(w, i, jm, k + 1)) - nzm * (P.wv(w, i, j, k) - P.wv(w, i, jm, k))) *
+                 g.idy * idz;
+    r.cross = cx + fy + cz;
+  }
+  return r;
+}
+
+// w at interior face c
+template <typename T, bool LES>
+__device__ __forceinline__ ViscU<T, LES> visc_w(const Pt<T>& P, const Visc<T, LES>& N, const T* u, const T* v,
+                                                const T* w, bool need_cross) {
+  const Geom<T>& g = P.g;
+  const int i = P.i, j = P.j, c = P.k, im = P.im, ip = P.ip, jm = P.jm, jp = P.jp;
+  const T ctr = P.wv(w, i, j, c);
+  const T nxp = N.ez_x(i, ip, j, c), nxm = N.ez_x(im, i, j, c);
+  const T nyp = N.ez_y(i, j, jp, c), nym = N.ez_y(i, jm, j, c);
+  const T nzp = N.c(i, j, c), nzm = N.c(i, j, c - 1);
+  const T ih = __ldg(g.ihz + c), izp = __ldg(g.idz + c), izm = __ldg(g.idz + c - 1);
+  const T fx = (nxp * (P.wv(w, ip, j, c) - ctr) - nxm * (ctr - P.wv(w, im, j, c))) * g.idx2;
+  const T fy = (nyp * (P.wv(w, i, jp, c) - ctr) - nym * (ctr - P.wv(w, i, jm, c))) * g.idy2;
+  const T fz = (nzp * (P.wv(w, i, j, c + 1) - ctr) * izp - nzm * (ctr - P.wv(w, i, j, c - 1)) * izm) * ih;
+  ViscU<T, LES> r;
+  r.diff = fx + fy + fz;
+  r.diag = (nxp + nxm) * g.idx2 + (nyp + nym) * g.idy2 + (nzp * izp + nzm * izm) * ih;
+  r.cross = T(0);
+  if (need_cross) {
+    const T cx = (nxp * (P.vel(u, ip, j, c) - P.vel(u, ip, j, c - 1)) - nxm * (P.vel(u, i, j, c) - P.vel(u, i, j, c - 1))) *
+                 g.idx * ih;
+    const T cy = (nyp * (P.vel(v, i, jp, c) - P.vel(v, i, jp, c - 1)) - nym * (P.vel(v, i, j, c) - P.vel(v, i, j, c - 1))) *
+                 g.idy * ih;
+    r.cross = cx + cy + fz;
+  }
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// Explicit terms at time n, AB combination, CN right-hand side:
+//   N^n = -u.grad u + C(u) + f e_x
+//   rhs = u^n + dt (b0 N^n + b1 N^{n-1} + b2 N^{n-2}) + dt/2 D(u^n)
+// grid z covers levels 0..nz (the last level only carries w).
+// ---------------------------------------------------------------------------
+template <typename T, bool LES>
+__global__ void __launch_bounds__(kBX* kBY) k_momentum(Geom<T> g, const T* __restrict__ u, const T* __restrict__ v,
+                                                        const T* __restrict__ w, Visc<T, LES> N, T fx,
+                                                        T* __restrict__ Nu0, T* __restrict__ Nv0, T* __restrict__ Nw0,
+                                                        const T* __restrict__ Nu1, const T* __restrict__ Nv1,
+                                                        const T* __restrict__ Nw1, const T* __restrict__ Nu2,
+                                                        const T* __restrict__ Nv2, const T* __restrict__ Nw2, T b0,
+                                                        T b1, T b2, T dt, T* __restrict__ ru, T* __restrict__ rv,
+                                                        T* __restrict__ rw) {
+  const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y, k = blockIdx.z;
+  if (i >= g.nx || j >= g.ny) return;
+  Pt<T> P(g, i, j, k);
+  const int q = at(g.nx, g.ny, i, j, k);
+  const T hdt = T(0.5) * dt;
+  if (k < g.nz) {
+    const ViscU<T, LES> a = visc_u<T, LES>(P, N, u, v, w, true);
+    const T n0 = -adv_u(P, u, v, w) + a.cross + fx;
+    Nu0[q] = n0;
+    ru[q] = __ldg(u + q) + dt * (b0 * n0 + b1 * __ldg(Nu1 + q) + b2 * __ldg(Nu2 + q)) + hdt * a.diff;
+    const ViscU<T, LES> bb = visc_v<T, LES>(P, N, u, v, w, true);
+    const T m0 = -adv_v(P, u, v, w) + bb.cross;
+    Nv0[q] = m0;
+    rv[q] = __ldg(v + q) + dt * (b0 * m0 + b1 * __ldg(Nv1 + q) + b2 * __ldg(Nv2 + q)) + hdt * bb.diff;
+  }
+  if (k == 0 || k == g.nz) {
+    Nw0[q] = T(0);
+    rw[q] = T(0);
+  } else {
+    const ViscU<T, LES> c = visc_w<T, LES>(P, N, u, v, w, true);
+    const T l0 = -adv_w(P, u, v, w) + c.cross;
+    Nw0[q] = l0;
+    rw[q] = __ldg(w + q) + dt * (b0 * l0 + b1 * __ldg(Nw1 + q) + b2 * __ldg(Nw2 + q)) + hdt * c.diff;
+  }
+}
+
+// Explicit terms only (checks).
+template <typename T, bool LES>
+__global__ void k_explicit(Geom<T> g, const T* __restrict__ u, const T* __restrict__ v, const T* __restrict__ w,
+                           Visc<T, LES> N, T fx, T* Nu, T* Nv, T* Nw) {
+  const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y, k = blockIdx.z;
+  if (i >= g.nx || j >= g.ny) return;
+  Pt<T> P(g, i, j, k);
+  const int q = at(g.nx, g.ny, i, j, k);
+  if (k < g.nz) {
+    Nu[q] = -adv_u(P, u, v, w) + visc_u<T, LES>(P, N, u, v, w, true).cross + fx;
+    Nv[q] = -adv_v(P, u, v, w) + visc_v<T, LES>(P, N, u, v, w, true).cross;
+  }
+  Nw[q] = (k == 0 || k == g.nz) ? T(0) : -adv_w(P, u, v, w) + visc_w<T, LES>(P, N, u, v, w, true).cross;
+}
+
+template <typename T, bool LES>
+__global__ void k_diffusion(Geom<T> g, const T* __restrict__ u, const T* __restrict__ v, const T* __restrict__ w,
+                            Visc<T, LES> N, T* Du, T* Dv, T* Dw) {
+  const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y, k = blockIdx.z;
+  if (i >= g.nx || j >= g.ny) return;
+  Pt<T> P(g, i, j, k);
+  const int q = at(g.nx, g.ny, i, j, k);
+  if (k < g.nz) {
+    Du[q] = visc_u<T, LES>(P, N, u, v, w, false).diff;
+    Dv[q] = visc_v<T, LES>(P, N, u, v, w, false).diff;
+  }
+  Dw[q] = (k == 0 || k == g.nz) ? T(0) : visc_w<T, LES>(P, N, u, v, w, false).diff;
+}
+
+// ---------------------------------------------------------------------------
+// One Jacobi sweep of (I - dt/2 D) a = rhs for the three components:
+//   a_new = (rhs + dt/2 (D a + S_D a)) / (1 + dt/2 S_D)
+// ---------------------------------------------------------------------------
+template <typename T, bool LES>
+__global__ void __launch_bounds__(kBX* kBY) k_cn_sweep(Geom<T> g, Visc<T, LES> N, T hdt, const T* __restrict__ ru,
+                                                        const T* __restrict__ rv, const T* __restrict__ rw,
+                                                        const T* __restrict__ au, const T* __restrict__ av,
+                                                        const T* __restrict__ aw, T* __restrict__ ou,
+                                                        T* __restrict__ ov, T* __restrict__ ow) {
+  const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y, k = blockIdx.z;
+  if (i >= g.nx || j >= g.ny) return;
+  Pt<T> P(g, i, j, k);
+  const int q = at(g.nx, g.ny, i, j, k);
+  if (k < g.nz) {
+    const ViscU<T, LES> a = visc_u<T, LES>(P, N, au, av, aw, false);
+    ou[q] = (__ldg(ru + q) + hdt * (a.diff + a.diag * __ldg(au + q))) / (T(1) + hdt * a.diag);
+    const ViscU<T, LES> b = visc_v<T, LES>(P, N, au, av, aw, false);
+    ov[q] = (__ldg(rv + q) + hdt * (b.diff + b.diag * __ldg(av + q))) / (T(1) + hdt * b.diag);
+  }
+  if (k == 0 || k == g.nz) {
+    ow[q] = T(0);
+  } else {
+    const ViscU<T, LES> c = visc_w<T, LES>(P, N, au, av, aw, false);
+    ow[q] = (__ldg(rw + q) + hdt * (c.diff + c.diag * __ldg(aw + q))) / (T(1) + hdt * c.diag);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Eq. presdiv right-hand side b = D u* / dt, with ||b||_2 reduced in FP64.
+// Also clears the convergence flags of the coming solve.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kBX* kBY) k_divergence(Geom<T> g, const T* __restrict__ u, const T* __restrict__ v,
+                                                          const T* __restrict__ w, double idt, double* __restrict__ b,
+                                                          Red red, unsigned nblocks) {
+  __shared__ double sh[32];
+  const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y, k = blockIdx.z;
+  double s = 0.0;
+  if (i < g.nx && j < g.ny) {
+    const int ip = i == g.nx - 1 ? 0 : i + 1, jp = j == g.ny - 1 ? 0 : j + 1;
+    const int q = at(g.nx, g.ny, i, j, k);
+    // differences taken in FP64 (exact for FP32 inputs), so that the sum of b
+    // over the box telescopes to zero to FP64 rounding: the constant mode of
+    // b, which no Poisson iteration can remove, stays at that level
+    const double d = ((double)__ldg(u + at(g.nx, g.ny, ip, j, k)) - (double)__ldg(u + q)) * (double)g.idx +
+                     ((double)__ldg(v + at(g.nx, g.ny, i, jp, k)) - (double)__ldg(v + q)) * (double)g.idy +
+                     ((double)__ldg(w + q + g.nx * g.ny) - (double)__ldg(w + q)) * (double)__ldg(g.idz + k);
+    const double bt = d * idt;
+    b[q] = bt;
+    s = bt * bt;
+  }
+  s = block_sum(s, sh);
+  if (publish_partial(red, nblocks, s, 0.0, false)) {
+    const double tot = final_sum(red.partial, nblocks, sh);
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    if (tid == 0) {
+      red.sc[SC_BNORM] = sqrt(tot);
+      red.flag[FL_DONE] = 0;
+      red.flag[FL_INNER_DONE] = 0;
+      *red.counter = 0u;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Eq. project u_p_1: u = u* - dt G p with w = 0 on the walls; reduces the
+// volume-weighted mean of u and max |u| (FP64).  Grid z covers 0..nz.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kBX* kBY) k_correct(Geom<T> g, const double* __restrict__ p, double dt,
+                                                       T* __restrict__ u, T* __restrict__ v, T* __restrict__ w,
+                                                       const double* __restrict__ ihz64, const double* __restrict__ dz64,
+                                                       double inv_vol, Red red, unsigned nblocks) {
+  __shared__ double sh[32];
+  const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y, k = blockIdx.z;
+  double s = 0.0, m = 0.0;
+  if (i < g.nx && j < g.ny) {
+    const int im = i == 0 ? g.nx - 1 : i - 1, jm = j == 0 ? g.ny - 1 : j - 1;
+    const int q = at(g.nx, g.ny, i, j, k);
+    if (k < g.nz) {
+      const double pc = __ldg(p + q);
+      const double un = (double)u[q] - dt * (pc - __ldg(p + at(g.nx, g.ny, im, j, k))) * (double)g.idx;
+      const double vn = (double)v[q] - dt * (pc - __ldg(p + at(g.nx, g.ny, i, jm, k))) * (double)g.idy;
+      const T ut = (T)un;
+      u[q] = ut;
+      v[q] = (T)vn;
+      s = (double)ut * __ldg(dz64 + k);
+      m = fabs((double)ut);
+    }
+    if (k == 0 || k == g.nz) {
+      w[q] = T(0);
+    } else {
+      const double wn = (double)w[q] - dt * (__ldg(p + q) - __ldg(p + q - g.nx * g.ny)) * __ldg(ihz64 + k);
+      w[q] = (T)wn;
+    }
+  }
+  const double bs = block_sum(s, sh);
+  const double bm = block_max(m, sh);
+  if (publish_partial(red, nblocks, bs, bm, true)) {
+    const double tot = final_sum(red.partial, nblocks, sh);
+    const double mx = final_max(red.partial + nblocks, nblocks, sh);
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    if (tid == 0) {
+      red.sc[SC_BULK] = tot * inv_vol;
+      red.sc[SC_UMAX] = mx;
+      if (!(tot == tot) || !(mx == mx) || isinf(mx)) red.flag[FL_BAD] = 1;
+      *red.counter = 0u;
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_flux_shift(int n, T* __restrict__ u, double target, Red red) {
+  const double shift = target - __ldcg(red.sc + SC_BULK);
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x)
+    u[q] = (T)((double)u[q] + shift);
+  if (blockIdx.x == 0 && threadIdx.x == 0) red.sc[SC_SHIFT] = shift;
+}
+
+template <typename Td, typename Ts>
+__global__ void k_convert(Td* __restrict__ d, const Ts* __restrict__ s, size_t n) {
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x)
+    d[q] = (Td)s[q];
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+
+template <typename T>
+cudaError_t launch_viscosity(const Geom<T>& g, const T* u, const T* v, const T* w, T nu0, T* nu, cudaStream_t s) {
+  Launch l = plane_launch(g.nx, g.ny, g.nz);
+  k_viscosity<T><<<l.grid, l.block, 0, s>>>(g, u, v, w, nu0, nu);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_momentum(const Geom<T>& g, bool les, const T* u, const T* v, const T* w, const T* nu, T nu0,
+                            T fx, T* Nu0, T* Nv0, T* Nw0, const T* Nu1, const T* Nv1, const T* Nw1, const T* Nu2,
+                            const T* Nv2, const T* Nw2, T b0, T b1, T b2, T dt, T* ru, T* rv, T* rw,
+                            cudaStream_t s) {
+  Launch l = plane_launch(g.nx, g.ny, g.nz + 1);
+  if (les) {
+    Visc<T, true> N{nu, nu0, g.nx, g.ny, g.nz};
+    k_momentum<T, true><<<l.grid, l.block, 0, s>>>(g, u, v, w, N, fx, Nu0, Nv0, Nw0, Nu1, Nv1, Nw1, Nu2, Nv2, Nw2,
+                                                  b0, b1, b2, dt, ru, rv, rw);
+  } else {
+    Visc<T, false> N{nu, nu0, g.nx, g.ny, g.nz};
+    k_momentum<T, false><<<l.grid, l.block, 0, s>>>(g, u, v, w, N, fx, Nu0, Nv0, Nw0, Nu1, Nv1, Nw1, Nu2, Nv2, Nw2,
+                                                   b0, b1, b2, dt, ru, rv, rw);
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_cn_sweep(const Geom<T>& g, bool les, const T* nu, T nu0, T hdt, const T* ru, const T* rv,
+                            const T* rw, const T* au, const T* av, const T* aw, T* ou, T* ov, T* ow,
+                            cudaStream_t s) {
+  Launch l = plane_launch(g.nx, g.ny, g.nz + 1);
+  if (les) {
+    Visc<T, true> N{nu, nu0, g.nx, g.ny, g.nz};
+    k_cn_sweep<T, true><<<l.grid, l.block, 0, s>>>(g, N, hdt, ru, rv, rw, au, av, aw, ou, ov, ow);
+  } else {
+    Visc<T, false> N{nu, nu0, g.nx, g.ny, g.nz};
+    k_cn_sweep<T, false><<<l.grid, l.block, 0, s>>>(g, N, hdt, ru, rv, rw, au, av, aw, ou, ov, ow);
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_explicit_only(const Geom<T>& g, bool les, const T* u, const T* v, const T* w, const T* nu,
+                                 T nu0, T fx, T* Nu, T* Nv, T* Nw, cudaStream_t s) {
+  Launch l = plane_launch(g.nx, g.ny, g.nz + 1);
+  if (les) {
+    Visc<T, true> N{nu, nu0, g.nx, g.ny, g.nz};
+    k_explicit<T, true><<<l.grid, l.block, 0, s>>>(g, u, v, w, N, fx, Nu, Nv, Nw);
+  } else {
+    Visc<T, false> N{nu, nu0, g.nx, g.ny, g.nz};
+    k_explicit<T, false><<<l.grid, l.block, 0, s>>>(g, u, v, w, N, fx, Nu, Nv, Nw);
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_diffusion_only(const Geom<T>& g, bool les, const T* u, const T* v, const T* w, const T* nu,
+                                  T nu0, T* Du, T* Dv, T* Dw, cudaStream_t s) {
+  Launch l = plane_launch(g.nx, g.ny, g.nz + 1);
+  if (les) {
+    Visc<T, true> N{nu, nu0, g.nx, g.ny, g.nz};
+    k_diffusion<T, true><<<l.grid, l.block, 0, s>>>(g, u, v, w, N, Du, Dv, Dw);
+  } else {
+    Visc<T, false> N{nu, nu0, g.nx, g.ny, g.nz};
+    k_diffusion<T, false><<<l.grid, l.block, 0, s>>>(g, u, v, w, N, Du, Dv, Dw);
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_divergence_rhs(const Geom<T>& g, const T* u, const T* v, const T* w, double idt, double* b,
+                                  Red red, cudaStream_t s) {
+  Launch l = plane_launch(g.nx, g.ny, g.nz);
+  k_divergence<T><<<l.grid, l.block, 0, s>>>(g, u, v, w, idt, b, red, l.nblocks);
+  return cudaGetLastError();
+}
+
+// ihz64 / dz64 are FP64 copies of the metrics; they sit at fixed offsets of
+// the FP64 metric pack, passed in by the caller through Geom<double> below.
+template <typename T>
+cudaError_t launch_correct_impl(const Geom<T>& g, const double* p, double dt, T* u, T* v, T* w,
+                                const double* ihz64, const double* dz64, double inv_vol, Red red, cudaStream_t s) {
+  Launch l = plane_launch(g.nx, g.ny, g.nz + 1);
+  k_correct<T><<<l.grid, l.block, 0, s>>>(g, p, dt, u, v, w, ihz64, dz64, inv_vol, red, l.nblocks);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_flux_shift(const Geom<T>& g, T* u, double target, Red red, cudaStream_t s) {
+  const int n = g.nx * g.ny * g.nz;
+  int blocks = (n + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  k_flux_shift<T><<<blocks, 256, 0, s>>>(n, u, target, red);
+  return cudaGetLastError();
+}
+
+template <typename Td, typename Ts>
+cudaError_t launch_convert(Td* dst, const Ts* src, size_t n, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  size_t blocks = (n + 255) / 256;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  k_convert<Td, Ts><<<(unsigned)blocks, 256, 0, s>>>(dst, src, n);
+  return cudaGetLastError();
+}
+
+#define STP_INST(T)                                                                                                 \
+  template cudaError_t launch_viscosity<T>(const Geom<T>&, const T*, const T*, const T*, T, T*, cudaStream_t);      \
+  template cudaError_t launch_momentum<T>(const Geom<T>&, bool, const T*, const T*, const T*, const T*, T, T, T*, \
+                                          T*, T*, const T*, const T*, const T*, const T*, const T*, const T*, T, T, \
+                                          T, T, T*, T*, T*, cudaStream_t);                                          \
+  template cudaError_t launch_cn_sweep<T>(const Geom<T>&, bool, const T*, T, T, const T*, const T*, const T*,      \
+                                          const T*, const T*, const T*, T*, T*, T*, cudaStream_t);                  \
+  template cudaError_t launch_explicit_only<T>(const Geom<T>&, bool, const T*, const T*, const T*, const T*, T, T, \
+                                               T*, T*, T*, cudaStream_t);                                           \
+  template cudaError_t launch_diffusion_only<T>(const Geom<T>&, bool, const T*, const T*, const T*, const T*, T,   \
+                                                T*, T*, T*, cudaStream_t);                                          \
+  template cudaError_t launch_divergence_rhs<T>(const Geom<T>&, const T*, const T*, const T*, double, double*, Red,\
+                                                cudaStream_t);                                                      \
+  template cudaError_t launch_correct_impl<T>(const Geom<T>&, const double*, double, T*, T*, T*, const double*,    \
+                                              const double*, double, Red, cudaStream_t);                            \
+  template cudaError_t launch_flux_shift<T>(const Geom<T>&, T*, double, Red, cudaStream_t);
+
+STP_INST(double)
+STP_INST(float)
+
+template cudaError_t launch_convert<double, float>(double*, const float*, size_t, cudaStream_t);
+template cudaError_t launch_convert<float, double>(float*, const double*, size_t, cudaStream_t);
+template cudaError_t launch_convert<double, double>(double*, const double*, size_t, cudaStream_t);
+
+}  // namespace stp

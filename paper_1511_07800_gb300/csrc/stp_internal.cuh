@@ -1,0 +1,168 @@
+// Internal declarations of the GB300 projection-step library: device geometry,
+// the handle, deterministic reductions and the kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/stp.h"
+
+namespace stp {
+
+// ---------------------------------------------------------------------------
+// Grid metrics.  z is stretched or uniform; x and y are uniform.  Every 1-D
+// array lives in device memory (read through the read-only path).
+//   dz[k]   cell width            k < nz
+//   hz[c]   centre-to-centre distance across face c (c = 1..nz-1)
+//   dzf[c]  distance between the two u-values that straddle face c; at a wall
+//           the ghost is the mirror image of the first centre (dzf = dz)
+// ---------------------------------------------------------------------------
+template <typename T>
+struct Geom {
+  int nx, ny, nz;
+  T idx, idy;      // 1/dx, 1/dy
+  T idx2, idy2;    // 1/dx^2, 1/dy^2
+  T hidx, hidy;    // 1/(2dx), 1/(2dy)
+  T idxdy;         // 1/(dx dy)
+  const T* idz;    // [nz]    1/dz
+  const T* ihz;    // [nz+1]  1/hz (interior faces)
+  const T* idzf;   // [nz+1]  1/dzf
+  const T* i2dzc;  // [nz]    1/(distance between the centres (or ghosts) above and below)
+  const T* idzw;   // [nz+1]  1/(dz[c] + dz[c-1]) at interior faces
+  const T* cup;    // [nz]    Poisson coupling to k+1 (0 at the top wall)
+  const T* cdn;    // [nz]    Poisson coupling to k-1 (0 at the bottom wall)
+  const T* iS;     // [nz]    1/(2/dx^2 + 2/dy^2 + cup + cdn)
+  const T* S;      // [nz]    2/dx^2 + 2/dy^2 + cup + cdn
+  const T* lm2;    // [nz]    (Cs Delta phi_w)^2 per level (LES)
+  const T* dzv;    // [nz]    dz
+};
+
+// Number of metric arrays packed into one device allocation per precision.
+constexpr int kMetricArrays = 13;
+
+// Reduction workspace (device).  Every reducing kernel writes one partial per
+// block, then the last block to finish sums the partials in block order, so
+// results do not depend on scheduling.
+struct Red {
+  double* partial;    // [2 * max_blocks]
+  unsigned* counter;  // [1], returns to 0 after each reduction
+  double* sc;         // scalars, see SC_* below
+  int* flag;          // flags, see FL_* below
+};
+
+enum {
+  SC_BNORM = 0,     // ||b||_2 of the current Poisson right-hand side
+  SC_RES = 1,       // ||r||_2 at the last check
+  SC_INNER_REF = 2, // ||r||_2 of the outer residual (inner solve reference)
+  SC_BULK = 3,      // volume mean of u after the correction
+  SC_UMAX = 4,      // max |u| after the correction
+  SC_SHIFT = 5,     // flux fix-up added to u
+  SC_RES_INNER = 6, // inner residual at the last inner check
+  SC_COUNT = 8
+};
+enum { FL_DONE = 0, FL_INNER_DONE = 1, FL_BAD = 2, FL_COUNT = 4 };
+
+struct Launch {
+  dim3 grid, block;
+  unsigned nblocks;
+};
+
+// Device-resident control block of the pressure solves.  The host writes
+// the parameters once per call; the check kernels update the state and set
+// the graph conditionals; k_begin folds the previous solve into the totals.
+struct SolveCtl {
+  // parameters
+  double tol;        // ||b - L p|| <= tol ||b||
+  double inner_tol;  // FP32 inner solve: reduce the refinement residual by this
+  int max_sweeps;    // cap on SRJ sweeps per solve
+  int max_passes;    // cap on refinement passes per solve
+  int M;             // SRJ cycle length
+  int pad0;
+  // state of the current solve
+  int sweeps, passes, cycles_inner, converged, bad, pad1;
+  double prev, res, res_inner;
+  long long kernels;  // kernels run by the solve graph
+  // totals over the earlier solves of this call
+  long long tot_sweeps, tot_kernels;
+  int solves, nonconv;
+};
+
+// ---------------------------------------------------------------------------
+// Kernel launchers (kernels_step.cu, kernels_poisson.cu).  T is the storage
+// and arithmetic type of the velocity fields (double or float).
+// ---------------------------------------------------------------------------
+template <typename T>
+cudaError_t launch_viscosity(const Geom<T>& g, const T* u, const T* v, const T* w, T nu0, T* nu,
+                             cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_momentum(const Geom<T>& g, bool les, const T* u, const T* v, const T* w, const T* nu,
+                            T nu0, T fx, T* Nu0, T* Nv0, T* Nw0, const T* Nu1, const T* Nv1, const T* Nw1,
+                            const T* Nu2, const T* Nv2, const T* Nw2, T b0, T b1, T b2, T dt, T* ru, T* rv,
+                            T* rw, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_cn_sweep(const Geom<T>& g, bool les, const T* nu, T nu0, T hdt, const T* ru, const T* rv,
+                            const T* rw, const T* au, const T* av, const T* aw, T* ou, T* ov, T* ow,
+                            cudaStream_t s);
+
+// b = D u / dt, ||b||^2 reduced into sc[SC_BNORM] (as the norm), flags reset.
+template <typename T>
+cudaError_t launch_divergence_rhs(const Geom<T>& g, const T* u, const T* v, const T* w, double idt, double* b,
+                                  Red red, cudaStream_t s);
+
+// Terms for checks (stp_eval).
+template <typename T>
+cudaError_t launch_explicit_only(const Geom<T>& g, bool les, const T* u, const T* v, const T* w, const T* nu,
+                                 T nu0, T fx, T* Nu, T* Nv, T* Nw, cudaStream_t s);
+template <typename T>
+cudaError_t launch_diffusion_only(const Geom<T>& g, bool les, const T* u, const T* v, const T* w, const T* nu,
+                                  T nu0, T* Du, T* Dv, T* Dw, cudaStream_t s);
+
+// One Jacobi-SOR sweep of L p = b with factor omega: out = p - omega (b - Lp)/S.
+template <typename T>
+cudaError_t launch_sweep(const Geom<T>& g, const T* p, const T* b, T omega, T* out, cudaStream_t s);
+template <>
+cudaError_t launch_sweep<float>(const Geom<float>&, const float*, const float*, float, float*, cudaStream_t);
+template <>
+cudaError_t launch_sweep<double>(const Geom<double>&, const double*, const double*, double, double*, cudaStream_t);
+
+// ||b - L p|| and the once-per-cycle decision (mode 0: FP64 solve, mode 1:
+// FP32 inner solve); sets the WHILE (h_loop) and IF (h_body) conditionals.
+template <typename T>
+cudaError_t launch_check(const Geom<T>& g, const T* p, const T* b, int mode, SolveCtl* ctl, Red red,
+                         cudaGraphConditionalHandle h_loop, cudaGraphConditionalHandle h_body, cudaStream_t s);
+
+// Refinement residual r = b - L p (FP64, stored FP32) and the pass decision.
+cudaError_t launch_outer(const Geom<double>& g, const double* p, const double* b, float* r32, SolveCtl* ctl, Red red,
+                         int after_pass, cudaGraphConditionalHandle h_loop, cudaStream_t s);
+// start of a refinement pass: d = 0 and the inner loop armed
+cudaError_t launch_pass_begin(float* d, size_t n, cudaGraphConditionalHandle h_loop, cudaStream_t s);
+// p += d
+cudaError_t launch_addcorr(double* p, const float* d, size_t n, cudaStream_t s);
+// start of a solve: fold the previous solve into the totals, reset the state
+cudaError_t launch_begin(SolveCtl* ctl, cudaStream_t s);
+
+// Velocity correction (Eq. project u_p_1) with walls; reduces the volume
+// mean of u and max |u|.  The pressure is FP64 in both modes; ihz64 and dz64
+// are the FP64 metrics 1/hz and dz.
+template <typename T>
+cudaError_t launch_correct_impl(const Geom<T>& g, const double* p, double dt, T* u, T* v, T* w,
+                                const double* ihz64, const double* dz64, double inv_vol, Red red, cudaStream_t s);
+
+// u += target - sc[SC_BULK] (constant-flux fix-up).
+template <typename T>
+cudaError_t launch_flux_shift(const Geom<T>& g, T* u, double target, Red red, cudaStream_t s);
+
+cudaError_t launch_laplacian(const Geom<double>& g, const double* p, double* out, cudaStream_t s);
+
+template <typename Td, typename Ts>
+cudaError_t launch_convert(Td* dst, const Ts* src, size_t n, cudaStream_t s);
+
+// ||a||_2 of a double array into sc[slot].
+cudaError_t launch_norm(const double* a, size_t n, int slot, Red red, cudaStream_t s);
+
+}  // namespace stp

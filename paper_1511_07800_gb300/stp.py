@@ -1,0 +1,229 @@
+"""Python binding of the C ABI in include/stp.h (argument marshalling only).
+
+Every step of the method runs in the CUDA library libstp.so; this module
+converts dicts and arrays to the C structures and pointers.  It refuses to
+work when the library is missing: there is no CPU path.
+
+Arrays: numpy float64 arrays are passed as host memory (STP_HOST); objects
+with `data_ptr()` and `is_cuda` (torch CUDA float64 tensors) as device memory
+(STP_DEVICE).  Layouts are those of the header: u, v, p [nz][ny][nx],
+w [nz+1][ny][nx], x fastest.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libstp.so")
+
+STP_OK = 0
+STP_EINVAL = -1
+STP_ENOMEM = -2
+STP_ECUDA = -3
+STP_ENOTCONVERGED = -4
+STP_EDIVERGED = -5
+STP_ECFL = -6
+STP_HOST, STP_DEVICE = 0, 1
+STP_FP64, STP_FP32_REFINE = 0, 1
+TERMS = {"viscosity": 1, "explicit": 2, "diffusion": 3, "divergence": 4, "laplacian": 5}
+
+
+class StpError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("stp error %d: %s" % (code, msg))
+        self.code = code
+
+
+class Config(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("Lx", ctypes.c_double), ("Ly", ctypes.c_double), ("Lz", ctypes.c_double),
+        ("nu", ctypes.c_double), ("dt", ctypes.c_double),
+        ("forcing", ctypes.c_int), ("fx", ctypes.c_double), ("ubulk", ctypes.c_double),
+        ("les", ctypes.c_int), ("cs", ctypes.c_double), ("vd_a", ctypes.c_double),
+        ("re_tau", ctypes.c_double), ("stretch", ctypes.c_double),
+        ("precision", ctypes.c_int), ("ptol", ctypes.c_double), ("pmaxit", ctypes.c_int),
+        ("cn_sweeps", ctypes.c_int), ("srj_m", ctypes.c_int),
+        ("srj_omega", ctypes.POINTER(ctypes.c_double)),
+        ("inner_tol", ctypes.c_double), ("cfl_check", ctypes.c_int),
+        ("device", ctypes.c_int), ("stream", ctypes.c_void_p),
+    ]
+
+
+class StepStats(ctypes.Structure):
+    _fields_ = [("poisson_sweeps", ctypes.c_int), ("refine_passes", ctypes.c_int),
+                ("converged", ctypes.c_int), ("rel_residual", ctypes.c_double),
+                ("ubulk", ctypes.c_double), ("umax", ctypes.c_double), ("dpdx", ctypes.c_double),
+                ("step", ctypes.c_longlong), ("launches", ctypes.c_longlong),
+                ("solve_sweeps", ctypes.c_longlong), ("solve_ms", ctypes.c_double)]
+
+
+class SolveStats(ctypes.Structure):
+    _fields_ = [("sweeps", ctypes.c_int), ("refine_passes", ctypes.c_int),
+                ("converged", ctypes.c_int), ("rel_residual", ctypes.c_double)]
+
+
+EXPORTS = ("stp_config_defaults", "stp_init", "stp_destroy", "stp_last_error", "stp_set_fields",
+           "stp_get_fields", "stp_step", "stp_poisson_solve", "stp_eval", "stp_srj_schedule")
+
+_lib = None
+
+
+def lib():
+    """Load libstp.so (built by build.py).  Raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libstp.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+    L = ctypes.CDLL(LIB_PATH)
+    dp = ctypes.POINTER(ctypes.c_double)
+    vp = ctypes.c_void_p
+    L.stp_config_defaults.argtypes = [ctypes.POINTER(Config)]
+    L.stp_config_defaults.restype = None
+    L.stp_init.argtypes = [ctypes.POINTER(Config), ctypes.POINTER(vp)]
+    L.stp_destroy.argtypes = [vp]
+    L.stp_destroy.restype = None
+    L.stp_last_error.argtypes = [vp]
+    L.stp_last_error.restype = ctypes.c_char_p
+    L.stp_set_fields.argtypes = [vp, vp, vp, vp, vp, ctypes.c_int]
+    L.stp_get_fields.argtypes = [vp, vp, vp, vp, vp, vp, ctypes.c_int]
+    L.stp_step.argtypes = [vp, ctypes.c_int, ctypes.POINTER(StepStats)]
+    L.stp_poisson_solve.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                    ctypes.POINTER(SolveStats)]
+    L.stp_eval.argtypes = [vp, ctypes.c_int, vp, vp, vp, ctypes.c_int]
+    L.stp_srj_schedule.argtypes = [ctypes.POINTER(Config), ctypes.c_int, dp, ctypes.POINTER(ctypes.c_int),
+                                   dp, dp]
+    _lib = L
+    return L
+
+
+def make_config(cfg, precision="fp64", device=0, stream=None, omega=None):
+    """stp_config from a workload dict (keys as in inputs.preset)."""
+    c = Config()
+    lib().stp_config_defaults(ctypes.byref(c))
+    for k in ("nx", "ny", "nz", "Lx", "Ly", "Lz", "nu", "dt", "forcing", "fx", "ubulk", "les", "cs", "vd_a",
+              "re_tau", "stretch", "ptol", "pmaxit", "cn_sweeps", "srj_m", "inner_tol", "cfl_check"):
+        if k in cfg and cfg[k] is not None:
+            setattr(c, k, type(getattr(c, k))(cfg[k]))
+    c.precision = STP_FP64 if precision in ("fp64", 0) else STP_FP32_REFINE
+    c.device = int(device)
+    c.stream = stream
+    keep = None
+    if omega is not None:
+        keep = np.ascontiguousarray(omega, dtype=np.float64)
+        c.srj_m = len(keep)
+        c.srj_omega = keep.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    return c, keep
+
+
+def srj_schedule(cfg, M=0):
+    """(omega, mu_min, mu_max) of the library's Chebyshev SRJ schedule."""
+    c, _ = make_config(cfg)
+    om = np.zeros(1024)
+    m = ctypes.c_int(0)
+    mn, mx = ctypes.c_double(0), ctypes.c_double(0)
+    rc = lib().stp_srj_schedule(ctypes.byref(c), int(M), om.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                ctypes.byref(m), ctypes.byref(mn), ctypes.byref(mx))
+    if rc != STP_OK:
+        raise StpError(rc, lib().stp_last_error(None).decode())
+    return om[:m.value].copy(), mn.value, mx.value
+
+
+def _addr(a):
+    """(pointer, where) for a numpy array or a CUDA tensor."""
+    if a is None:
+        return None, None
+    if hasattr(a, "data_ptr"):
+        if not getattr(a, "is_cuda", False):
+            a = a.numpy()
+        else:
+            return ctypes.c_void_p(a.data_ptr()), STP_DEVICE
+    assert a.dtype == np.float64 and a.flags.c_contiguous, "need C-contiguous float64"
+    return ctypes.c_void_p(a.ctypes.data), STP_HOST
+
+
+class Channel:
+    """One channel on one GPU (a handle of the C ABI)."""
+
+    def __init__(self, cfg, precision="fp64", device=0, stream=None, omega=None):
+        self.cfg = dict(cfg)
+        self.nx, self.ny, self.nz = cfg["nx"], cfg["ny"], cfg["nz"]
+        c, self._omega = make_config(cfg, precision, device, stream, omega)
+        h = ctypes.c_void_p()
+        rc = lib().stp_init(ctypes.byref(c), ctypes.byref(h))
+        if rc != STP_OK:
+            raise StpError(rc, lib().stp_last_error(None).decode())
+        self._h = h
+
+    # ------------------------------------------------------------------
+    def _check(self, rc, allow=()):
+        if rc != STP_OK and rc not in allow:
+            raise StpError(rc, lib().stp_last_error(self._h).decode())
+        return rc
+
+    def _where(self, *arrays):
+        ws = {w for (p, w) in (_addr(a) for a in arrays if a is not None)}
+        if len(ws) != 1:
+            raise ValueError("mix of host and device arrays")
+        return ws.pop()
+
+    def set_fields(self, u, v, w, p=None):
+        where = self._where(u, v, w, p)
+        ptr = [_addr(a)[0] for a in (u, v, w, p)]
+        self._check(lib().stp_set_fields(self._h, ptr[0], ptr[1], ptr[2], ptr[3], where))
+
+    def get_fields(self, out=None):
+        """Copy the fields out: into `out` (dict of arrays/tensors) or new numpy arrays."""
+        if out is None:
+            sc, sw = (self.nz, self.ny, self.nx), (self.nz + 1, self.ny, self.nx)
+            out = dict(u=np.zeros(sc), v=np.zeros(sc), w=np.zeros(sw), p=np.zeros(sc), nu=np.zeros(sc))
+        where = self._where(*[out[k] for k in ("u", "v", "w", "p", "nu") if out.get(k) is not None])
+        ptr = [_addr(out.get(k))[0] for k in ("u", "v", "w", "p", "nu")]
+        self._check(lib().stp_get_fields(self._h, *ptr, where))
+        return out
+
+    def step(self, n=1):
+        st = StepStats()
+        rc = self._check(lib().stp_step(self._h, int(n), ctypes.byref(st)), allow=(STP_ENOTCONVERGED, STP_ECFL))
+        return dict(sweeps=st.poisson_sweeps, passes=st.refine_passes, converged=bool(st.converged),
+                    rel_res=st.rel_residual, ubulk=st.ubulk, umax=st.umax, dpdx=st.dpdx, step=st.step,
+                    launches=st.launches, solve_sweeps=st.solve_sweeps, solve_ms=st.solve_ms, status=rc)
+
+    def poisson_solve(self, rhs, p0, tol=1e-8, maxit=0):
+        """Solve L p = rhs from p0 (updated in place)."""
+        where = self._where(rhs, p0)
+        st = SolveStats()
+        rc = self._check(lib().stp_poisson_solve(self._h, _addr(rhs)[0], _addr(p0)[0], float(tol), int(maxit), where,
+                                                 ctypes.byref(st)), allow=(STP_ENOTCONVERGED,))
+        return dict(sweeps=st.sweeps, passes=st.refine_passes, converged=bool(st.converged),
+                    rel_res=st.rel_residual, status=rc)
+
+    def eval(self, term, out=None):
+        """A term of the step on the current fields (see stp_eval)."""
+        t = TERMS[term]
+        sc, sw = (self.nz, self.ny, self.nx), (self.nz + 1, self.ny, self.nx)
+        if out is None:
+            if t in (2, 3):
+                out = (np.zeros(sc), np.zeros(sc), np.zeros(sw))
+            else:
+                out = (np.zeros(sc),)
+        where = self._where(*out)
+        ptr = [_addr(a)[0] for a in out] + [None] * (3 - len(out))
+        self._check(lib().stp_eval(self._h, t, ptr[0], ptr[1], ptr[2], where))
+        return out if len(out) > 1 else out[0]
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and _lib is not None:
+            _lib.stp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -17,3 +17,19 @@ def orc():
     import oracle
     oracle.build()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def stp_lib():
+    """Build libstp.so if needed and return the binding module."""
+    from paper_1511_07800_gb300 import build, stp
+    build.build()
+    stp.lib()
+    return stp
+
+
+def rel_err(a, b):
+    import numpy as np
+    a, b = np.asarray(a), np.asarray(b)
+    den = max(float(np.abs(b).max()), 1e-300)
+    return float(np.abs(a - b).max()) / den
