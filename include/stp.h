@@ -22,6 +22,12 @@
  * handle's device.  The library never keeps a caller pointer after a call
  * returns; it owns all its device memory and frees it in stp_destroy.
  *
+ * The pressure solve runs as one CUDA graph steered from the device (graph
+ * conditional nodes).  With the environment variable STP_HOST_SOLVE=1 at
+ * stp_init the same kernels are driven from the host instead, one host
+ * round trip per SRJ cycle (for profilers that cannot see kernels inside
+ * conditional graphs).
+ *
  * Errors: every int-returning call returns STP_OK (0) or a negative STP_E*
  * code; stp_last_error gives a one-line message.  No call aborts the process.
  * Calls on one handle must not overlap (one handle per host thread).
@@ -166,6 +172,29 @@ int stp_eval(stp_handle *h, int term, double *a, double *b, double *c, int where
    mirror-pair order.  M = 0 picks the cycle length; omega needs room for
    1024 values.  Host only. */
 int stp_srj_schedule(const stp_config *cfg, int M, double *omega, int *M_out, double *mu_min, double *mu_max);
+
+/* ||b - L p||_2 of the pressure equation for caller-owned device arrays p
+   and b ([nz][ny][nx], FP64), without allocating anything.  The paper has
+   no counterpart: it is for callers that hold their own device buffers but
+   may not allocate device memory, for example a host program that has
+   handed all device memory to its own pool allocator, or a time-critical
+   loop that cannot accept the device-wide synchronisation cudaMalloc and
+   cudaFree can cause.  L is the operator of stp_poisson_solve on the grid
+   given by nx, ny, nz, Lx, Ly, Lz and stretch (as in stp_config).
+     r_out    optional device array [nz][ny][nx] that receives b - L p
+     norm_out host pointer that receives the norm
+     stream   cudaStream_t of the current device (NULL: the default stream);
+              the call synchronises it before returning
+   Scratch memory is one fixed device array inside the library (held by
+   every GPU that loads the library until the process exits), limited to
+   nz <= 4096 and ceil(nx/32) * ceil(ny/8) * nz <= 65536; larger grids are
+   rejected with STP_EINVAL.  The first call on a device looks up the
+   array's device address, so make it before any stream capture on that
+   device.  All calls share the array: calls whose work overlaps on the GPU
+   race and must be serialised by the caller.  Errors: STP_EINVAL,
+   STP_ECUDA; stp_last_error(NULL) gives the message. */
+int stp_poisson_residual_noalloc(int nx, int ny, int nz, double Lx, double Ly, double Lz, double stretch,
+                                 const double *p, const double *b, double *r_out, double *norm_out, void *stream);
 
 #ifdef __cplusplus
 }

@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -66,6 +67,7 @@ struct stp_handle {
   SolveCtl* h_ctl = nullptr;   // pinned
   cudaGraph_t solve_graph = nullptr;
   cudaGraphExec_t solve_exec = nullptr;
+  bool host_solve = false;     // STP_HOST_SOLVE=1: drive the solve from the host
 };
 
 namespace {
@@ -426,7 +428,7 @@ int build_cycle(stp_handle* h, const Geom<T>& g, cudaGraph_t wb, cudaGraphCondit
   CUDA_TRY(h, cudaGraphConditionalHandleCreate(&h_body, wb, 0, cudaGraphCondAssignDefault));
   int rc;
   if ((rc = begin_capture(h, wb, nullptr))) return rc;
-  CUDA_TRY(h, launch_check<T>(g, A, rhs, mode, h->ctl, h->red, h_loop, h_body, h->cap));
+  CUDA_TRY(h, launch_check<T>(g, A, rhs, mode, h->ctl, h->red, 1, h_loop, h_body, h->cap));
   if ((rc = end_capture(h, wb))) return rc;
   cudaGraph_t ib;
   cudaGraphNode_t ifn;
@@ -462,7 +464,7 @@ int build_solve_graph(stp_handle* h) {
     CUDA_TRY(h, cudaGraphConditionalHandleCreate(&h_pass, G, 0, cudaGraphCondAssignDefault));
     if ((rc = begin_capture(h, G, nullptr))) return rc;
     CUDA_TRY(h, launch_begin(h->ctl, h->cap));
-    CUDA_TRY(h, launch_outer(h->g64, h->p, h->b, h->r32, h->ctl, h->red, 0, h_pass, h->cap));
+    CUDA_TRY(h, launch_outer(h->g64, h->p, h->b, h->r32, h->ctl, h->red, 0, 1, h_pass, h->cap));
     if ((rc = end_capture(h, G))) return rc;
     if ((rc = add_conditional(h, G, leaf_node(G), h_pass, cudaGraphCondTypeWhile, &pb, &pn))) return rc;
     // pass body: d = 0, arm the loop -> WHILE(loop){cycle} -> p += d -> outer
@@ -470,13 +472,13 @@ int build_solve_graph(stp_handle* h) {
     // default value is applied only when the top-level graph launches.
     CUDA_TRY(h, cudaGraphConditionalHandleCreate(&h_loop, pb, 1, 0));
     if ((rc = begin_capture(h, pb, nullptr))) return rc;
-    CUDA_TRY(h, launch_pass_begin(h->d1, h->nc, h_loop, h->cap));
+    CUDA_TRY(h, launch_pass_begin(h->d1, h->nc, 1, h_loop, h->cap));
     if ((rc = end_capture(h, pb))) return rc;
     if ((rc = add_conditional(h, pb, leaf_node(pb), h_loop, cudaGraphCondTypeWhile, &wb, &wn))) return rc;
     if ((rc = build_cycle<float>(h, h->g32, wb, h_loop, h->d1, h->d2, h->r32, 1))) return rc;
     if ((rc = begin_capture(h, pb, wn))) return rc;
     CUDA_TRY(h, launch_addcorr(h->p, h->d1, h->nc, h->cap));
-    CUDA_TRY(h, launch_outer(h->g64, h->p, h->b, h->r32, h->ctl, h->red, 1, h_pass, h->cap));
+    CUDA_TRY(h, launch_outer(h->g64, h->p, h->b, h->r32, h->ctl, h->red, 1, 1, h_pass, h->cap));
     if ((rc = end_capture(h, pb))) return rc;
   }
   CUDA_TRY(h, cudaGraphInstantiate(&h->solve_exec, G, 0));
@@ -496,8 +498,54 @@ int arm_solves(stp_handle* h, double tol, int maxit) {
   return STP_OK;
 }
 
-// one solve on the stream; timed with events when `timed`
+// The same solve driven from the host: the check kernels write their
+// decision to ctl->go and the host reads it once per cycle.  Used when the
+// environment sets STP_HOST_SOLVE=1 at stp_init (profilers cannot see the
+// kernels inside graphs with conditional nodes).
+int read_go(stp_handle* h, int* go) {
+  CUDA_TRY(h, cudaMemcpyAsync(&h->h_ctl->go, &h->ctl->go, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  *go = h->h_ctl->go;
+  return STP_OK;
+}
+
+template <typename T>
+int host_cycles(stp_handle* h, const Geom<T>& g, T* A, T* B, const T* rhs, int mode) {
+  const int M = (int)h->omega.size();
+  for (;;) {
+    CUDA_TRY(h, launch_check<T>(g, A, rhs, mode, h->ctl, h->red, 0, 0, 0, h->st));
+    int go = 0, rc = read_go(h, &go);
+    if (rc) return rc;
+    if (!go) return STP_OK;
+    for (int m = 0; m < M; m++)
+      CUDA_TRY(h, launch_sweep<T>(g, (m % 2 == 0) ? A : B, rhs, (T)h->omega[m], (m % 2 == 0) ? B : A, h->st));
+  }
+}
+
+int host_solve(stp_handle* h) {
+  CUDA_TRY(h, launch_begin(h->ctl, h->st));
+  if (h->prec == STP_FP64) return host_cycles<double>(h, h->g64, h->p, h->p2, h->b, 0);
+  CUDA_TRY(h, launch_outer(h->g64, h->p, h->b, h->r32, h->ctl, h->red, 0, 0, 0, h->st));
+  for (;;) {
+    int go = 0, rc = read_go(h, &go);
+    if (rc) return rc;
+    if (!go) return STP_OK;
+    CUDA_TRY(h, launch_pass_begin(h->d1, h->nc, 0, 0, h->st));
+    if ((rc = host_cycles<float>(h, h->g32, h->d1, h->d2, h->r32, 1))) return rc;
+    CUDA_TRY(h, launch_addcorr(h->p, h->d1, h->nc, h->st));
+    CUDA_TRY(h, launch_outer(h->g64, h->p, h->b, h->r32, h->ctl, h->red, 1, 0, 0, h->st));
+  }
+}
+
+// one solve on the stream, bracketed by events
 int launch_solve(stp_handle* h) {
+  if (h->host_solve) {
+    CUDA_TRY(h, cudaEventRecord(h->ev0, h->st));
+    int rc = host_solve(h);
+    if (rc) return rc;
+    CUDA_TRY(h, cudaEventRecord(h->ev1, h->st));
+    return STP_OK;
+  }
   int rc = build_solve_graph(h);
   if (rc) return rc;
   CUDA_TRY(h, cudaEventRecord(h->ev0, h->st));
@@ -752,6 +800,10 @@ int stp_init(const stp_config* cfg, stp_handle** out) {
   h->cfg.srj_m = (int)h->omega.size();
   const ZGrid z = make_z(*cfg);
   h->cn_sweeps = cfg->cn_sweeps > 0 ? cfg->cn_sweeps : auto_cn_sweeps(*cfg, z);
+  {
+    const char* env = std::getenv("STP_HOST_SOLVE");
+    h->host_solve = env && env[0] == '1';
+  }
   // device memory
   const size_t es = h->esz, nc = h->nc, nw = h->nw;
   int rc = STP_OK;
@@ -1021,3 +1073,13 @@ int stp_eval(stp_handle* h, int term, double* a, double* b, double* c, int where
 }
 
 }  // extern "C"
+
+namespace stp {
+// z couplings of the Poisson operator for a channel configuration (used by
+// the allocation-free residual entry point)
+void poisson_couplings(const stp_config& c, std::vector<double>& cup, std::vector<double>& cdn) {
+  const ZGrid z = make_z(c);
+  poisson_z(c, z, cup, cdn);
+}
+void set_thread_error(const std::string& msg) { g_init_error = msg; }
+}  // namespace stp

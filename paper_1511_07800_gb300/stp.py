@@ -65,7 +65,8 @@ class SolveStats(ctypes.Structure):
 
 
 EXPORTS = ("stp_config_defaults", "stp_init", "stp_destroy", "stp_last_error", "stp_set_fields",
-           "stp_get_fields", "stp_step", "stp_poisson_solve", "stp_eval", "stp_srj_schedule")
+           "stp_get_fields", "stp_step", "stp_poisson_solve", "stp_eval", "stp_srj_schedule",
+           "stp_poisson_residual_noalloc")
 
 _lib = None
 
@@ -95,6 +96,9 @@ def lib():
     L.stp_eval.argtypes = [vp, ctypes.c_int, vp, vp, vp, ctypes.c_int]
     L.stp_srj_schedule.argtypes = [ctypes.POINTER(Config), ctypes.c_int, dp, ctypes.POINTER(ctypes.c_int),
                                    dp, dp]
+    L.stp_poisson_residual_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                               ctypes.c_double, ctypes.c_double, ctypes.c_double, vp, vp, vp,
+                                               ctypes.POINTER(ctypes.c_double), vp]
     _lib = L
     return L
 
@@ -129,6 +133,20 @@ def srj_schedule(cfg, M=0):
     if rc != STP_OK:
         raise StpError(rc, lib().stp_last_error(None).decode())
     return om[:m.value].copy(), mn.value, mx.value
+
+
+def poisson_residual_noalloc(cfg, p, b, r_out=None, stream=None):
+    """||b - L p||_2 for device arrays p, b (torch CUDA float64 tensors)
+    through the allocation-free entry point; r_out optionally receives b - Lp."""
+    norm = ctypes.c_double(0.0)
+    rc = lib().stp_poisson_residual_noalloc(int(cfg["nx"]), int(cfg["ny"]), int(cfg["nz"]), float(cfg["Lx"]),
+                                            float(cfg["Ly"]), float(cfg["Lz"]), float(cfg.get("stretch", 0.0)),
+                                            ctypes.c_void_p(p.data_ptr()), ctypes.c_void_p(b.data_ptr()),
+                                            ctypes.c_void_p(r_out.data_ptr()) if r_out is not None else None,
+                                            ctypes.byref(norm), stream)
+    if rc != STP_OK:
+        raise StpError(rc, lib().stp_last_error(None).decode())
+    return norm.value
 
 
 def _addr(a):
