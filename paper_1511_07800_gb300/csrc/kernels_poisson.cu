@@ -76,10 +76,10 @@ __global__ void __launch_bounds__(kBX* kBY) k_sweep_f64(Geom<double> g, const do
 }
 
 // arms the inner loop of a refinement pass and clears its correction
-__global__ void k_pass_begin(float* __restrict__ d, size_t n, cudaGraphConditionalHandle h_loop) {
+__global__ void k_pass_begin(float* __restrict__ d, size_t n, int graph, cudaGraphConditionalHandle h_loop) {
   for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x)
     d[q] = 0.f;
-  if (blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(h_loop, 1u);
+  if (graph && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(h_loop, 1u);
 }
 
 // ||b - L p||_2 reduced in FP64, then the cycle decision in the last block.
@@ -87,7 +87,7 @@ __global__ void k_pass_begin(float* __restrict__ d, size_t n, cudaGraphCondition
 // refinement (target max(inner_tol ||r||, tol ||b|| / 2), stop on stall).
 template <typename T, int MODE>
 __global__ void __launch_bounds__(kBX* kBY) k_check(Geom<T> g, const T* __restrict__ p, const T* __restrict__ b,
-                                                     SolveCtl* ctl, Red red, unsigned nblocks,
+                                                     SolveCtl* ctl, Red red, unsigned nblocks, int graph,
                                                      cudaGraphConditionalHandle h_loop,
                                                      cudaGraphConditionalHandle h_body) {
   __shared__ double sh[32];
@@ -126,8 +126,11 @@ __global__ void __launch_bounds__(kBX* kBY) k_check(Geom<T> g, const T* __restri
         ctl->kernels += ctl->M;
       }
       *red.counter = 0u;
-      cudaGraphSetConditional(h_loop, stop ? 0u : 1u);
-      cudaGraphSetConditional(h_body, stop ? 0u : 1u);
+      ctl->go = stop ? 0 : 1;
+      if (graph) {
+        cudaGraphSetConditional(h_loop, stop ? 0u : 1u);
+        cudaGraphSetConditional(h_body, stop ? 0u : 1u);
+      }
     }
   }
 }
@@ -137,7 +140,7 @@ __global__ void __launch_bounds__(kBX* kBY) k_check(Geom<T> g, const T* __restri
 __global__ void __launch_bounds__(kBX* kBY) k_outer(Geom<double> g, const double* __restrict__ p,
                                                      const double* __restrict__ b, float* __restrict__ r32,
                                                      SolveCtl* ctl, Red red, unsigned nblocks, int after_pass,
-                                                     cudaGraphConditionalHandle h_loop) {
+                                                     int graph, cudaGraphConditionalHandle h_loop) {
   __shared__ double sh[32];
   const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y, k = blockIdx.z;
   double s = 0.0;
@@ -168,7 +171,8 @@ __global__ void __launch_bounds__(kBX* kBY) k_outer(Geom<double> g, const double
         stop = ctl->converged || ctl->sweeps >= ctl->max_sweeps || ctl->passes >= ctl->max_passes;
       }
       *red.counter = 0u;
-      cudaGraphSetConditional(h_loop, stop ? 0u : 1u);
+      ctl->go = stop ? 0 : 1;
+      if (graph) cudaGraphSetConditional(h_loop, stop ? 0u : 1u);
     }
   }
 }
@@ -244,27 +248,27 @@ cudaError_t launch_sweep<double>(const Geom<double>& g, const double* p, const d
   return cudaGetLastError();
 }
 
-cudaError_t launch_pass_begin(float* d, size_t n, cudaGraphConditionalHandle h_loop, cudaStream_t s) {
+cudaError_t launch_pass_begin(float* d, size_t n, int graph, cudaGraphConditionalHandle h_loop, cudaStream_t s) {
   unsigned blocks = (unsigned)std::min<size_t>((n + 255) / 256, 152 * 16);
-  k_pass_begin<<<blocks ? blocks : 1, 256, 0, s>>>(d, n, h_loop);
+  k_pass_begin<<<blocks ? blocks : 1, 256, 0, s>>>(d, n, graph, h_loop);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_check(const Geom<T>& g, const T* p, const T* b, int mode, SolveCtl* ctl, Red red,
+cudaError_t launch_check(const Geom<T>& g, const T* p, const T* b, int mode, SolveCtl* ctl, Red red, int graph,
                          cudaGraphConditionalHandle h_loop, cudaGraphConditionalHandle h_body, cudaStream_t s) {
   Launch l = plane_launch(g.nx, g.ny, g.nz);
   if (mode == 0)
-    k_check<T, 0><<<l.grid, l.block, 0, s>>>(g, p, b, ctl, red, l.nblocks, h_loop, h_body);
+    k_check<T, 0><<<l.grid, l.block, 0, s>>>(g, p, b, ctl, red, l.nblocks, graph, h_loop, h_body);
   else
-    k_check<T, 1><<<l.grid, l.block, 0, s>>>(g, p, b, ctl, red, l.nblocks, h_loop, h_body);
+    k_check<T, 1><<<l.grid, l.block, 0, s>>>(g, p, b, ctl, red, l.nblocks, graph, h_loop, h_body);
   return cudaGetLastError();
 }
 
 cudaError_t launch_outer(const Geom<double>& g, const double* p, const double* b, float* r32, SolveCtl* ctl, Red red,
-                         int after_pass, cudaGraphConditionalHandle h_loop, cudaStream_t s) {
+                         int after_pass, int graph, cudaGraphConditionalHandle h_loop, cudaStream_t s) {
   Launch l = plane_launch(g.nx, g.ny, g.nz);
-  k_outer<<<l.grid, l.block, 0, s>>>(g, p, b, r32, ctl, red, l.nblocks, after_pass, h_loop);
+  k_outer<<<l.grid, l.block, 0, s>>>(g, p, b, r32, ctl, red, l.nblocks, after_pass, graph, h_loop);
   return cudaGetLastError();
 }
 
@@ -294,8 +298,8 @@ cudaError_t launch_norm(const double* a, size_t n, int slot, Red red, cudaStream
 }
 
 template cudaError_t launch_check<double>(const Geom<double>&, const double*, const double*, int, SolveCtl*, Red,
-                                          cudaGraphConditionalHandle, cudaGraphConditionalHandle, cudaStream_t);
-template cudaError_t launch_check<float>(const Geom<float>&, const float*, const float*, int, SolveCtl*, Red,
+                                          int, cudaGraphConditionalHandle, cudaGraphConditionalHandle, cudaStream_t);
+template cudaError_t launch_check<float>(const Geom<float>&, const float*, const float*, int, SolveCtl*, Red, int,
                                          cudaGraphConditionalHandle, cudaGraphConditionalHandle, cudaStream_t);
 
 }  // namespace stp

@@ -85,6 +85,8 @@ struct SolveCtl {
   int sweeps, passes, cycles_inner, converged, bad, pad1;
   double prev, res, res_inner;
   long long kernels;  // kernels run by the solve graph
+  int go;             // last decision of a check kernel (1: run the cycle / pass)
+  int pad2;
   // totals over the earlier solves of this call
   long long tot_sweeps, tot_kernels;
   int solves, nonconv;
@@ -132,15 +134,16 @@ cudaError_t launch_sweep<double>(const Geom<double>&, const double*, const doubl
 
 // ||b - L p|| and the once-per-cycle decision (mode 0: FP64 solve, mode 1:
 // FP32 inner solve); sets the WHILE (h_loop) and IF (h_body) conditionals.
+// Outside a graph (graph == 0) the decision is only written to ctl->go.
 template <typename T>
-cudaError_t launch_check(const Geom<T>& g, const T* p, const T* b, int mode, SolveCtl* ctl, Red red,
+cudaError_t launch_check(const Geom<T>& g, const T* p, const T* b, int mode, SolveCtl* ctl, Red red, int graph,
                          cudaGraphConditionalHandle h_loop, cudaGraphConditionalHandle h_body, cudaStream_t s);
 
 // Refinement residual r = b - L p (FP64, stored FP32) and the pass decision.
 cudaError_t launch_outer(const Geom<double>& g, const double* p, const double* b, float* r32, SolveCtl* ctl, Red red,
-                         int after_pass, cudaGraphConditionalHandle h_loop, cudaStream_t s);
+                         int after_pass, int graph, cudaGraphConditionalHandle h_loop, cudaStream_t s);
 // start of a refinement pass: d = 0 and the inner loop armed
-cudaError_t launch_pass_begin(float* d, size_t n, cudaGraphConditionalHandle h_loop, cudaStream_t s);
+cudaError_t launch_pass_begin(float* d, size_t n, int graph, cudaGraphConditionalHandle h_loop, cudaStream_t s);
 // p += d
 cudaError_t launch_addcorr(double* p, const float* d, size_t n, cudaStream_t s);
 // start of a solve: fold the previous solve into the totals, reset the state

@@ -211,3 +211,22 @@ def test_fp32_refine_error_vs_fp64_oracle(stp_lib, orc, stretch, les):
     for k, bd in bounds.items():
         e = rel_err(fg[k], fo[k]) if k != "p" else rel_err(fg[k] - fg[k].mean(), fo[k] - fo[k].mean())
         assert e < bd, (k, e)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_host_driven_solve_matches_graph(stp_lib, monkeypatch, precision):
+    """The host-driven solve (STP_HOST_SOLVE=1, for profilers) runs the same
+    kernels in the same order as the device-steered graph: identical fields."""
+    cfg = case(stretch=2.0, les=1, nu=1 / 500.0, cn_sweeps=4)
+    om = schedule(cfg, 16)
+    out = []
+    for mode in ("0", "1"):
+        monkeypatch.setenv("STP_HOST_SOLVE", mode)
+        with stp_lib.Channel(cfg, precision=precision, omega=om) as ch:
+            ch.set_fields(*turbulent_like(cfg, 8))
+            st = ch.step(3)
+            out.append((ch.get_fields(), st))
+    (fa, sa), (fb, sb) = out
+    assert sa["sweeps"] == sb["sweeps"] and sa["passes"] == sb["passes"]
+    for k in ("u", "v", "w", "p"):
+        assert np.array_equal(fa[k], fb[k]), k
