@@ -75,6 +75,99 @@ __global__ void __launch_bounds__(kBX* kBY) k_sweep_f64(Geom<double> g, const do
   out[q] = pc + omega * (pj - pc);
 }
 
+// Vectorised sweeps: each thread owns VW consecutive cells of a row (float4
+// in FP32, double2 in FP64); the x-neighbours across lanes come by warp
+// shuffle, so a cell costs one vector load per stencil direction instead
+// of eight scalar loads and their index arithmetic.  Lanes past the end of
+// a row (or rows past ny) read a clamped, in-bounds element, take part in
+// the shuffles and store nothing.  With PDL the kernel is launched as a
+// programmatic dependent of the previous sweep: its set-up overlaps the
+// previous kernel's tail and cudaGridDependencySynchronize waits for that
+// kernel's results before any read of p.
+template <bool PDL>
+__global__ void __launch_bounds__(kBX* kBY) k_sweep_f32_v4(Geom<float> g, const float* __restrict__ p,
+                                                            const float* __restrict__ b, float omega,
+                                                            float* __restrict__ out) {
+  const int lane = threadIdx.x;
+  const int nx = g.nx, ny = g.ny, nx4 = nx >> 2;
+  const int x4 = blockIdx.x * kBX + lane;
+  const int j = blockIdx.y * kBY + threadIdx.y, k = blockIdx.z;
+  const bool active = x4 < nx4 && j < ny;
+  const int xx = x4 < nx4 ? x4 : nx4 - 1;
+  const int jj = j < ny ? j : ny - 1;
+  const int jp = jj == ny - 1 ? 0 : jj + 1, jm = jj == 0 ? ny - 1 : jj - 1;
+  const size_t plane4 = (size_t)nx4 * ny;
+  const size_t rc = ((size_t)k * ny + jj) * nx4;
+  const float cup = __ldg(g.cup + k), cdn = __ldg(g.cdn + k), iS = __ldg(g.iS + k);
+  const float idx2 = g.idx2, idy2 = g.idy2;
+  const bool has_up = k < g.nz - 1, has_dn = k > 0;
+  if (PDL) cudaGridDependencySynchronize();
+  const float4* P = reinterpret_cast<const float4*>(p);
+  const float4 c = __ldg(P + rc + xx);
+  float left = __shfl_up_sync(0xffffffffu, c.w, 1);
+  float right = __shfl_down_sync(0xffffffffu, c.x, 1);
+  const float* prow = p + rc * 4;
+  if (lane == 0 || xx == 0) left = __ldg(prow + (4 * xx - 1 + nx) % nx);
+  if (lane == kBX - 1 || xx == nx4 - 1) right = __ldg(prow + (4 * xx + 4) % nx);
+  const float4 yn = __ldg(P + ((size_t)k * ny + jp) * nx4 + xx);
+  const float4 ys = __ldg(P + ((size_t)k * ny + jm) * nx4 + xx);
+  const float4 zu = has_up ? __ldg(P + rc + plane4 + xx) : c;
+  const float4 zd = has_dn ? __ldg(P + rc - plane4 + xx) : c;
+  const float4 bq = __ldg(reinterpret_cast<const float4*>(b) + rc + xx);
+  auto cell = [&](float pc, float xl, float xr, float nn, float ss, float uu, float dd, float bb) {
+    const float lap = idx2 * ((xr - pc) + (xl - pc)) + idy2 * ((nn - pc) + (ss - pc)) + cup * (uu - pc) +
+                      cdn * (dd - pc);
+    return pc - omega * (bb - lap) * iS;
+  };
+  float4 o;
+  o.x = cell(c.x, left, c.y, yn.x, ys.x, zu.x, zd.x, bq.x);
+  o.y = cell(c.y, c.x, c.z, yn.y, ys.y, zu.y, zd.y, bq.y);
+  o.z = cell(c.z, c.y, c.w, yn.z, ys.z, zu.z, zd.z, bq.z);
+  o.w = cell(c.w, c.z, right, yn.w, ys.w, zu.w, zd.w, bq.w);
+  if (active) reinterpret_cast<float4*>(out)[rc + x4] = o;
+}
+
+template <bool PDL>
+__global__ void __launch_bounds__(kBX* kBY) k_sweep_f64_v2(Geom<double> g, const double* __restrict__ p,
+                                                            const double* __restrict__ b, double omega,
+                                                            double* __restrict__ out) {
+  const int lane = threadIdx.x;
+  const int nx = g.nx, ny = g.ny, nx2 = nx >> 1;
+  const int x2 = blockIdx.x * kBX + lane;
+  const int j = blockIdx.y * kBY + threadIdx.y, k = blockIdx.z;
+  const bool active = x2 < nx2 && j < ny;
+  const int xx = x2 < nx2 ? x2 : nx2 - 1;
+  const int jj = j < ny ? j : ny - 1;
+  const int jp = jj == ny - 1 ? 0 : jj + 1, jm = jj == 0 ? ny - 1 : jj - 1;
+  const size_t plane2 = (size_t)nx2 * ny;
+  const size_t rc = ((size_t)k * ny + jj) * nx2;
+  const double cup = __ldg(g.cup + k), cdn = __ldg(g.cdn + k), iS = __ldg(g.iS + k);
+  const double idx2 = g.idx2, idy2 = g.idy2;
+  const bool has_up = k < g.nz - 1, has_dn = k > 0;
+  if (PDL) cudaGridDependencySynchronize();
+  const double2* P = reinterpret_cast<const double2*>(p);
+  const double2 c = __ldg(P + rc + xx);
+  double left = __shfl_up_sync(0xffffffffu, c.y, 1);
+  double right = __shfl_down_sync(0xffffffffu, c.x, 1);
+  const double* prow = p + rc * 2;
+  if (lane == 0 || xx == 0) left = __ldg(prow + (2 * xx - 1 + nx) % nx);
+  if (lane == kBX - 1 || xx == nx2 - 1) right = __ldg(prow + (2 * xx + 2) % nx);
+  const double2 yn = __ldg(P + ((size_t)k * ny + jp) * nx2 + xx);
+  const double2 ys = __ldg(P + ((size_t)k * ny + jm) * nx2 + xx);
+  const double2 zu = has_up ? __ldg(P + rc + plane2 + xx) : c;
+  const double2 zd = has_dn ? __ldg(P + rc - plane2 + xx) : c;
+  const double2 bq = __ldg(reinterpret_cast<const double2*>(b) + rc + xx);
+  auto cell = [&](double pc, double xl, double xr, double nn, double ss, double uu, double dd, double bb) {
+    const double nbs = idx2 * (xr + xl) + idy2 * (nn + ss) + cup * uu + cdn * dd;
+    const double pj = (nbs - bb) * iS;
+    return pc + omega * (pj - pc);
+  };
+  double2 o;
+  o.x = cell(c.x, left, c.y, yn.x, ys.x, zu.x, zd.x, bq.x);
+  o.y = cell(c.y, c.x, right, yn.y, ys.y, zu.y, zd.y, bq.y);
+  if (active) reinterpret_cast<double2*>(out)[rc + x2] = o;
+}
+
 // arms the inner loop of a refinement pass and clears its correction
 __global__ void k_pass_begin(float* __restrict__ d, size_t n, int graph, cudaGraphConditionalHandle h_loop) {
   for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x)
@@ -233,9 +326,33 @@ __global__ void k_norm(const double* __restrict__ a, size_t n, int slot, Red red
 
 }  // namespace
 
+// Vector kernels when the row length allows aligned vectors (nx a multiple
+// of 4 in FP32, of 2 in FP64), launched as programmatic dependents; the
+// one-cell-per-thread kernels otherwise.
+template <typename K, typename T>
+static cudaError_t launch_pdl(K kern, dim3 grid, dim3 block, cudaStream_t s, const Geom<T>& g, const T* p,
+                              const T* b, T omega, T* out) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, g, p, b, omega, out);
+}
+
 template <>
 cudaError_t launch_sweep<float>(const Geom<float>& g, const float* p, const float* b, float omega, float* out,
                                 cudaStream_t s) {
+  if (g.nx % 4 == 0) {
+    const dim3 grid((g.nx / 4 + kBX - 1) / kBX, (g.ny + kBY - 1) / kBY, g.nz), block(kBX, kBY, 1);
+    cudaError_t e = launch_pdl(k_sweep_f32_v4<true>, grid, block, s, g, p, b, omega, out);
+    return e != cudaSuccess ? e : cudaGetLastError();
+  }
   Launch l = plane_launch(g.nx, g.ny, g.nz);
   k_sweep_f32<<<l.grid, l.block, 0, s>>>(g, p, b, omega, out);
   return cudaGetLastError();
@@ -243,6 +360,11 @@ cudaError_t launch_sweep<float>(const Geom<float>& g, const float* p, const floa
 template <>
 cudaError_t launch_sweep<double>(const Geom<double>& g, const double* p, const double* b, double omega, double* out,
                                  cudaStream_t s) {
+  if (g.nx % 2 == 0) {
+    const dim3 grid((g.nx / 2 + kBX - 1) / kBX, (g.ny + kBY - 1) / kBY, g.nz), block(kBX, kBY, 1);
+    cudaError_t e = launch_pdl(k_sweep_f64_v2<true>, grid, block, s, g, p, b, omega, out);
+    return e != cudaSuccess ? e : cudaGetLastError();
+  }
   Launch l = plane_launch(g.nx, g.ny, g.nz);
   k_sweep_f64<<<l.grid, l.block, 0, s>>>(g, p, b, omega, out);
   return cudaGetLastError();
