@@ -173,6 +173,47 @@ int stp_eval(stp_handle *h, int term, double *a, double *b, double *c, int where
    1024 values.  Host only. */
 int stp_srj_schedule(const stp_config *cfg, int M, double *omega, int *M_out, double *mu_min, double *mu_max);
 
+/* ------------------------------------------------------------------------
+ * Learned pressure guess: a 3-D U-Net (4 levels of 16, 32, 64, 128
+ * channels, two 3x3x3 convolutions with ReLU per level, 2x2x2 mean pooling,
+ * nearest upsampling with skip concatenation, 1x1x1 linear output).
+ * Convolutions are periodic in x and y and zero-padded in z.  BF16 weights
+ * and activations on the tensor cores with FP32 accumulation; FP32 master
+ * weights, gradients and Adam state.  Inputs and outputs are FP32
+ * [n][nz][ny][nx] device arrays.  The paper's solver has no learned part:
+ * this follows the extension that asks for a learned initial guess of the
+ * SRJ pressure iteration, trained on (residual, correction) pairs that the
+ * solver itself produces.
+ * ------------------------------------------------------------------------ */
+typedef struct stp_unet stp_unet;
+
+/* Number of parameters (one flat FP32 vector: per layer, in the order
+   enc1a, enc1b, ..., enc4b, dec3a, dec3b, dec2a, dec2b, dec1a, dec1b, out,
+   weights [c_out][c_in][taps] (tap = (kz*3 + ky)*3 + kx) then bias). */
+long long stp_unet_param_count(void);
+
+/* Network for up to nmax samples of nz x ny x nx (each a multiple of 8, at
+   least 8) on the current device; stream NULL: its own stream.  Parameters
+   start at zero: set them with stp_unet_set_params. */
+int stp_unet_create(int nmax, int nz, int ny, int nx, void *stream, stp_unet **out);
+void stp_unet_destroy(stp_unet *net);
+const char *stp_unet_last_error(const stp_unet *net);
+
+/* Copy the FP32 parameters in (resets the Adam state) or out. */
+int stp_unet_set_params(stp_unet *net, const float *theta, int where);
+int stp_unet_get_params(stp_unet *net, float *theta, int where);
+
+/* y = U(x) for nb <= nmax samples (device arrays). */
+int stp_unet_forward(stp_unet *net, const float *x, float *y, int nb);
+
+/* Mean squared error of U(x) against target and its gradient with respect
+   to the parameters (grad: device FP32 [param_count], nullable). */
+int stp_unet_gradient(stp_unet *net, const float *x, const float *target, int nb, float *grad, float *loss);
+
+/* One Adam step (beta 0.9, 0.999, eps 1e-8) on the MSE loss; *loss gets the
+   loss before the step. */
+int stp_unet_train_step(stp_unet *net, const float *x, const float *target, int nb, float lr, float *loss);
+
 /* ||b - L p||_2 of the pressure equation for caller-owned device arrays p
    and b ([nz][ny][nx], FP64), without allocating anything.  The paper has
    no counterpart: it is for callers that hold their own device buffers but

@@ -55,6 +55,20 @@ def unpack(theta):
     return out
 
 
+def bf16(a):
+    """Round to the nearest bfloat16 (ties to even), returned as float64.
+    Used to state the CUDA path's storage points exactly: its activations,
+    weights and activation gradients are stored in bfloat16."""
+    f = np.ascontiguousarray(a, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def ident(a):
+    return a
+
+
 def init_params(seed):
     """He-normal weights (std sqrt(2 / fan_in)), zero bias; small output layer."""
     rng = np.random.default_rng(seed)
@@ -146,56 +160,60 @@ def upsample_backward(g):
 
 # ---------------------------------------------------------------- network
 
-def forward(theta, x, keep=False):
-    """y = U(x); with keep, also the activations needed for backward."""
-    P = unpack(theta)
+def forward(theta, x, keep=False, rnd=ident):
+    """y = U(x); with keep, also the activations needed for backward.
+    rnd is applied where a stored-precision copy is made (identity: exact
+    FP64; `bf16`: the CUDA path's storage points)."""
+    P = {k: (rnd(w), b) for k, (w, b) in unpack(theta).items()}
     acts = {}
-    h = x
+    h = rnd(x)
     skips = []
     for l in range(4):
         a_in = h
-        za = conv(a_in, *P["enc%d_a" % (l + 1)])
-        ha = relu(za)
-        zb = conv(ha, *P["enc%d_b" % (l + 1)])
-        e = relu(zb)
+        ha = rnd(relu(conv(a_in, *P["enc%d_a" % (l + 1)])))
+        e = rnd(relu(conv(ha, *P["enc%d_b" % (l + 1)])))
         acts["enc%d" % (l + 1)] = (a_in, ha, e)
         skips.append(e)
-        h = pool(e) if l < 3 else e
+        h = rnd(pool(e)) if l < 3 else e
     d = h
     for l in (2, 1, 0):
         u = np.concatenate([upsample(d), skips[l]], axis=-1)
-        ha = relu(conv(u, *P["dec%d_a" % (l + 1)]))
-        d = relu(conv(ha, *P["dec%d_b" % (l + 1)]))
+        ha = rnd(relu(conv(u, *P["dec%d_a" % (l + 1)])))
+        d = rnd(relu(conv(ha, *P["dec%d_b" % (l + 1)])))
         acts["dec%d" % (l + 1)] = (u, ha, d)
     y = conv(d, *P["out"])
     acts["out"] = d
+    acts["P"] = P
     return (y, acts) if keep else y
 
 
-def backward(theta, acts, gy):
-    """Gradient of sum(gy * U(x)) with respect to theta (flat vector)."""
-    P = unpack(theta)
+def backward(theta, acts, gy, rnd=ident):
+    """Gradient of sum(gy * U(x)) with respect to theta (flat vector); rnd
+    marks where the CUDA path stores activation gradients."""
+    P = acts["P"]
     G = {}
     gd, G["out_w"], G["out_b"] = conv_backward(acts["out"], P["out"][0], gy)
+    gd = rnd(gd * (acts["out"] > 0))
     gskip = [None] * 4
     for l in (0, 1, 2):
         u, ha, d = acts["dec%d" % (l + 1)]
-        g = gd * (d > 0)
+        g = gd
         gha, G["dec%d_b_w" % (l + 1)], G["dec%d_b_b" % (l + 1)] = conv_backward(ha, P["dec%d_b" % (l + 1)][0], g)
-        g = gha * (ha > 0)
+        g = rnd(gha * (ha > 0))
         gu, G["dec%d_a_w" % (l + 1)], G["dec%d_a_b" % (l + 1)] = conv_backward(u, P["dec%d_a" % (l + 1)][0], g)
+        gu = rnd(gu)
         cu = CH[l + 1]
         gskip[l] = gu[..., cu:]
-        gd = upsample_backward(gu[..., :cu])
-    ge = gd
+        deeper = acts["dec%d" % (l + 2)][2] if l < 2 else acts["enc4"][2]
+        gd = rnd(upsample_backward(gu[..., :cu]) * (deeper > 0))
+    gq = None
     for l in (3, 2, 1, 0):
         a_in, ha, e = acts["enc%d" % (l + 1)]
-        if l < 3:
-            ge = pool_backward(ge) + gskip[l]
-        g = ge * (e > 0)
+        g = gd if l == 3 else rnd((pool_backward(gq) + gskip[l]) * (e > 0))
         gha, G["enc%d_b_w" % (l + 1)], G["enc%d_b_b" % (l + 1)] = conv_backward(ha, P["enc%d_b" % (l + 1)][0], g)
-        g = gha * (ha > 0)
-        ge, G["enc%d_a_w" % (l + 1)], G["enc%d_a_b" % (l + 1)] = conv_backward(a_in, P["enc%d_a" % (l + 1)][0], g)
+        g = rnd(gha * (ha > 0))
+        gq, G["enc%d_a_w" % (l + 1)], G["enc%d_a_b" % (l + 1)] = conv_backward(a_in, P["enc%d_a" % (l + 1)][0], g)
+        gq = rnd(gq)
     parts = []
     for (name, ci, co, t) in layer_specs():
         parts.append(G[name + "_w"].ravel())
@@ -209,10 +227,10 @@ def mse(y, t):
     return float(np.mean(d * d)), 2.0 * d / d.size
 
 
-def loss_and_grad(theta, x, t):
-    y, acts = forward(theta, x, keep=True)
+def loss_and_grad(theta, x, t, rnd=ident):
+    y, acts = forward(theta, x, keep=True, rnd=rnd)
     L, gy = mse(y, t)
-    return L, backward(theta, acts, gy)
+    return L, backward(theta, acts, gy, rnd=rnd)
 
 
 def adam_step(theta, g, m, v, step, lr, b1=0.9, b2=0.999, eps=1e-8):

@@ -1,0 +1,890 @@
+// 3-D U-Net for the learned pressure guess: forward, backward and Adam, all
+// in hand-written kernels.  BF16 weights and activations, FP32 accumulation
+// on the tensor cores (mma.sync m16n8k16), FP32 master weights, gradients
+// and optimiser state.
+//
+// Network (channels-last [voxel][channel], voxel = ((n*D + z)*H + y)*W + x):
+//   encoder level l = 1..4 (16, 32, 64, 128 channels): two 3x3x3 conv+ReLU,
+//     then a 2x2x2 mean pool (not after level 4)
+//   decoder level l = 3, 2, 1: input = concat(upsample2(deeper), skip e_l),
+//     two 3x3x3 conv+ReLU
+//   output: 1x1x1 conv of the 16 channels, linear
+// Convolutions are periodic in x and y and zero-padded in z.  The skip of
+// level l is written straight into the channel slice of the decoder's
+// concat buffer, so no copy is needed.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "device_util.cuh"
+#include "stp_internal.cuh"
+
+namespace stp {
+namespace nn {
+
+typedef __nv_bfloat16 bf16;
+
+struct Dims {
+  int n, d, h, w;
+  __host__ __device__ long long vox() const { return (long long)n * d * h * w; }
+};
+
+__device__ __forceinline__ void mma16816(float* c, const unsigned* a, const unsigned* b) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__device__ __forceinline__ unsigned ld_u32(const bf16* p) { return *reinterpret_cast<const unsigned*>(p); }
+
+__device__ __forceinline__ unsigned pack2(bf16 lo, bf16 hi) {
+  return (unsigned)__bfloat16_as_ushort(lo) | ((unsigned)__bfloat16_as_ushort(hi) << 16);
+}
+
+// source voxel of v shifted by tap t (periodic y, x; -1 outside the walls)
+__device__ __forceinline__ long long tap_src(const Dims& dm, long long v, int t) {
+  const int x = (int)(v % dm.w);
+  long long r = v / dm.w;
+  const int y = (int)(r % dm.h);
+  r /= dm.h;
+  const int z = (int)(r % dm.d);
+  const long long n = r / dm.d;
+  const int z2 = z + t / 9 - 1;
+  if (z2 < 0 || z2 >= dm.d) return -1;
+  int y2 = y + (t / 3) % 3 - 1;
+  int x2 = x + t % 3 - 1;
+  y2 = y2 < 0 ? y2 + dm.h : (y2 >= dm.h ? y2 - dm.h : y2);
+  x2 = x2 < 0 ? x2 + dm.w : (x2 >= dm.w ? x2 - dm.w : x2);
+  return ((n * dm.d + z2) * dm.h + y2) * dm.w + x2;
+}
+
+// ---------------------------------------------------------------------------
+// 3x3x3 convolution as an implicit GEMM on the tensor cores:
+//   y[v][o] = b[o] + sum_{t, c} wt[t][o][c] x[v + off(t)][c]
+// M = voxels, N = output channels, K = 27 taps x input channels.  A warp
+// computes 32 voxels x 8*NT channels; a block has 4 warps (128 voxels).
+// Options: ReLU; multiply by (mask > 0) (the derivative of the ReLU that
+// produced this layer's input, used when the kernel runs the backward data
+// pass with transposed weights); no bias when bias is NULL.
+// ---------------------------------------------------------------------------
+template <int NT>
+__global__ void __launch_bounds__(128) k_conv3(Dims dm, const bf16* __restrict__ x, int ldx, int cin,
+                                               const bf16* __restrict__ wt, const float* __restrict__ bias, int cout,
+                                               bf16* __restrict__ y, int ldy, int relu, const bf16* __restrict__ mask,
+                                               int ldm) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
+  const long long V = dm.vox();
+  const long long vb = ((long long)blockIdx.x * 4 + warp) * 32;
+  const int cob = blockIdx.y * NT * 8;
+  float acc[2][NT][4];
+#pragma unroll
+  for (int m = 0; m < 2; m++)
+#pragma unroll
+    for (int n = 0; n < NT; n++) acc[m][n][0] = acc[m][n][1] = acc[m][n][2] = acc[m][n][3] = 0.f;
+  long long vrow[4];
+#pragma unroll
+  for (int r = 0; r < 4; r++) vrow[r] = vb + (r >> 1) * 16 + g + (r & 1) * 8;
+  const int kc = cin >> 4;
+  for (int t = 0; t < 27; t++) {
+    long long src[4];
+#pragma unroll
+    for (int r = 0; r < 4; r++) src[r] = vrow[r] < V ? tap_src(dm, vrow[r], t) : -1;
+    for (int c = 0; c < kc; c++) {
+      unsigned a[2][4];
+#pragma unroll
+      for (int m = 0; m < 2; m++) {
+        const long long s0 = src[2 * m], s1 = src[2 * m + 1];
+        const int col = c * 16 + 2 * q;
+        a[m][0] = s0 >= 0 ? ld_u32(x + s0 * ldx + col) : 0u;
+        a[m][1] = s1 >= 0 ? ld_u32(x + s1 * ldx + col) : 0u;
+        a[m][2] = s0 >= 0 ? ld_u32(x + s0 * ldx + col + 8) : 0u;
+        a[m][3] = s1 >= 0 ? ld_u32(x + s1 * ldx + col + 8) : 0u;
+      }
+#pragma unroll
+      for (int n = 0; n < NT; n++) {
+        const int co = cob + n * 8 + g;
+        unsigned b[2] = {0u, 0u};
+        if (co < cout) {
+          const bf16* wp = wt + ((long long)t * cout + co) * cin + c * 16 + 2 * q;
+          b[0] = ld_u32(wp);
+          b[1] = ld_u32(wp + 8);
+        }
+        mma16816(acc[0][n], a[0], b);
+        mma16816(acc[1][n], a[1], b);
+      }
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < 2; m++)
+#pragma unroll
+    for (int n = 0; n < NT; n++) {
+      const int co = cob + n * 8 + 2 * q;
+      if (co >= cout) continue;
+#pragma unroll
+      for (int h = 0; h < 2; h++) {
+        const long long v = vrow[2 * m + h];
+        if (v >= V) continue;
+        float v0 = acc[m][n][2 * h], v1 = acc[m][n][2 * h + 1];
+        if (bias) {
+          v0 += bias[co];
+          v1 += bias[co + 1];
+        }
+        if (relu) {
+          v0 = fmaxf(v0, 0.f);
+          v1 = fmaxf(v1, 0.f);
+        }
+        if (mask) {
+          const bf16* mp = mask + v * ldm + co;
+          if (!(__bfloat162float(mp[0]) > 0.f)) v0 = 0.f;
+          if (!(__bfloat162float(mp[1]) > 0.f)) v1 = 0.f;
+        }
+        *reinterpret_cast<unsigned*>(y + v * ldy + co) = pack2(__float2bfloat16(v0), __float2bfloat16(v1));
+      }
+    }
+}
+
+// First layer: 1 input channel (FP32 input rounded to BF16) -> 16 channels, ReLU.
+__global__ void k_conv_in(Dims dm, const float* __restrict__ x, const float* __restrict__ w /*[16][27]*/,
+                          const float* __restrict__ bias, bf16* __restrict__ y, int ldy) {
+  __shared__ float ws[16 * 27 + 16];
+  for (int i = threadIdx.x; i < 16 * 27; i += blockDim.x) ws[i] = __bfloat162float(__float2bfloat16(w[i]));
+  for (int i = threadIdx.x; i < 16; i += blockDim.x) ws[16 * 27 + i] = bias[i];
+  __syncthreads();
+  const long long V = dm.vox();
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x) {
+    float acc[16];
+#pragma unroll
+    for (int o = 0; o < 16; o++) acc[o] = ws[16 * 27 + o];
+    for (int t = 0; t < 27; t++) {
+      const long long s = tap_src(dm, v, t);
+      if (s < 0) continue;
+      const float xv = __bfloat162float(__float2bfloat16(x[s]));
+#pragma unroll
+      for (int o = 0; o < 16; o++) acc[o] = fmaf(ws[o * 27 + t], xv, acc[o]);
+    }
+#pragma unroll
+    for (int o = 0; o < 16; o += 2)
+      *reinterpret_cast<unsigned*>(y + v * ldy + o) =
+          pack2(__float2bfloat16(fmaxf(acc[o], 0.f)), __float2bfloat16(fmaxf(acc[o + 1], 0.f)));
+  }
+}
+
+// Output layer: 1x1x1, 16 channels -> 1, linear, FP32 output.
+__global__ void k_conv_out(long long V, const bf16* __restrict__ x, int ldx, const float* __restrict__ w,
+                           const float* __restrict__ bias, float* __restrict__ y) {
+  float ws[16];
+#pragma unroll
+  for (int c = 0; c < 16; c++) ws[c] = __bfloat162float(__float2bfloat16(w[c]));
+  const float b = bias[0];
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x) {
+    float s = b;
+#pragma unroll
+    for (int c = 0; c < 16; c++) s = fmaf(ws[c], __bfloat162float(x[v * ldx + c]), s);
+    y[v] = s;
+  }
+}
+
+// Backward of the output layer: g_d1[v][c] = gy[v] w[c] (d1 > 0);
+// dW[c] += sum_v gy[v] d1[v][c], db += sum_v gy[v].
+__global__ void k_conv_out_bwd(long long V, const float* __restrict__ gy, const bf16* __restrict__ d1, int ldx,
+                               const float* __restrict__ w, bf16* __restrict__ gd, int ldg, float* __restrict__ gw,
+                               float* __restrict__ gb) {
+  __shared__ float red[17][33];
+  float ws[16], acc[17];
+#pragma unroll
+  for (int c = 0; c < 16; c++) {
+    ws[c] = __bfloat162float(__float2bfloat16(w[c]));
+    acc[c] = 0.f;
+  }
+  acc[16] = 0.f;
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x) {
+    const float g = gy[v];
+    acc[16] += g;
+#pragma unroll
+    for (int c = 0; c < 16; c += 2) {
+      const float a0 = __bfloat162float(d1[v * ldx + c]), a1 = __bfloat162float(d1[v * ldx + c + 1]);
+      acc[c] += g * a0;
+      acc[c + 1] += g * a1;
+      *reinterpret_cast<unsigned*>(gd + v * ldg + c) =
+          pack2(__float2bfloat16(a0 > 0.f ? g * ws[c] : 0.f), __float2bfloat16(a1 > 0.f ? g * ws[c + 1] : 0.f));
+    }
+  }
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+#pragma unroll
+  for (int c = 0; c < 17; c++) {
+    float s = acc[c];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) red[c][wp] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x < 17) {
+    float s = 0.f;
+    for (int i = 0; i < (int)(blockDim.x >> 5); i++) s += red[threadIdx.x][i];
+    if (threadIdx.x < 16)
+      atomicAdd(gw + threadIdx.x, s);
+    else
+      atomicAdd(gb, s);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Weight gradient of a 3x3x3 layer on the tensor cores:
+//   gw[o][c][t] += sum_v gz[v][o] x[v + off(t)][c],   gb[o] += sum_v gz[v][o]
+// GEMM with M = output channels (16 per warp), N = input channels (32 per
+// warp, 4 n-tiles), K = voxels.  Block = 4 warps over consecutive voxel
+// chunks of one (tap, o-tile, c-tile); partial sums are reduced in shared
+// memory and added to the FP32 gradient with atomics.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_wgrad3(Dims dm, const bf16* __restrict__ x, int ldx, int cin,
+                                                const bf16* __restrict__ gz, int ldg, int cout,
+                                                float* __restrict__ gw, float* __restrict__ gb, long long vchunk) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, q = lane & 3;
+  const int ct = (cin + 31) / 32;
+  int idx = blockIdx.x;
+  const int t = idx % 27;
+  idx /= 27;
+  const int cti = idx % ct;
+  const int oti = idx / ct;
+  const int ob = oti * 16, cb = cti * 32;
+  const long long V = dm.vox();
+  const long long v0 = (long long)blockIdx.y * vchunk;
+  const long long v1 = V < v0 + vchunk ? V : v0 + vchunk;
+  float acc[4][4];
+#pragma unroll
+  for (int n = 0; n < 4; n++) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
+  const bf16 zero = __float2bfloat16(0.f);
+  for (long long vs = v0 + warp * 16; vs < v1; vs += 64) {
+    // the four voxels of this thread in the chunk: k = 2q, 2q+1, 2q+8, 2q+9
+    long long vk[4] = {vs + 2 * q, vs + 2 * q + 1, vs + 2 * q + 8, vs + 2 * q + 9};
+    long long sk[4];
+    bf16 gzv[2][4];
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+      const bool ok = vk[i] < v1;
+      sk[i] = ok ? tap_src(dm, vk[i], t) : -1;
+      gzv[0][i] = ok ? gz[vk[i] * ldg + ob + g] : zero;
+      gzv[1][i] = ok ? gz[vk[i] * ldg + ob + g + 8] : zero;
+    }
+    unsigned a[4];
+    a[0] = pack2(gzv[0][0], gzv[0][1]);
+    a[1] = pack2(gzv[1][0], gzv[1][1]);
+    a[2] = pack2(gzv[0][2], gzv[0][3]);
+    a[3] = pack2(gzv[1][2], gzv[1][3]);
+#pragma unroll
+    for (int n = 0; n < 4; n++) {
+      const int c = cb + n * 8 + g;
+      bf16 xv[4];
+#pragma unroll
+      for (int i = 0; i < 4; i++) xv[i] = (c < cin && sk[i] >= 0) ? x[sk[i] * ldx + c] : zero;
+      unsigned b[2] = {pack2(xv[0], xv[1]), pack2(xv[2], xv[3])};
+      mma16816(acc[n], a, b);
+    }
+  }
+  __shared__ float red[4][16][33];
+#pragma unroll
+  for (int n = 0; n < 4; n++) {
+    red[warp][g][n * 8 + 2 * q] = acc[n][0];
+    red[warp][g][n * 8 + 2 * q + 1] = acc[n][1];
+    red[warp][g + 8][n * 8 + 2 * q] = acc[n][2];
+    red[warp][g + 8][n * 8 + 2 * q + 1] = acc[n][3];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < 16 * 32; e += 128) {
+    const int o = e / 32, c = e % 32;
+    if (cb + c >= cin) continue;
+    const float s = red[0][o][c] + red[1][o][c] + red[2][o][c] + red[3][o][c];
+    atomicAdd(gw + ((long long)(ob + o) * cin + cb + c) * 27 + t, s);
+  }
+  (void)gb;
+}
+
+// bias gradient: gb[o] += sum_v gz[v][o]
+__global__ void k_bias_grad(long long V, const bf16* __restrict__ gz, int ldg, int cout, float* __restrict__ gb) {
+  const int o = blockIdx.y * blockDim.x + threadIdx.x;
+  if (o >= cout) return;
+  float s = 0.f;
+  for (long long v = blockIdx.x; v < V; v += gridDim.x) s += __bfloat162float(gz[v * ldg + o]);
+  atomicAdd(gb + o, s);
+}
+
+// first-layer weight gradient: gw[o][0][t] += sum_v gz[v][o] x[v + off(t)];
+// one tap per blockIdx.y
+__global__ void k_wgrad_in(Dims dm, const float* __restrict__ x, const bf16* __restrict__ gz, int ldg,
+                           float* __restrict__ gw) {
+  __shared__ float red[16];
+  if (threadIdx.x < 16) red[threadIdx.x] = 0.f;
+  __syncthreads();
+  const int t = blockIdx.y;
+  float acc[16];
+#pragma unroll
+  for (int o = 0; o < 16; o++) acc[o] = 0.f;
+  const long long V = dm.vox();
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x) {
+    const long long s = tap_src(dm, v, t);
+    if (s < 0) continue;
+    const float xv = __bfloat162float(__float2bfloat16(x[s]));
+#pragma unroll
+    for (int o = 0; o < 16; o++) acc[o] = fmaf(__bfloat162float(gz[v * ldg + o]), xv, acc[o]);
+  }
+#pragma unroll
+  for (int o = 0; o < 16; o++) {
+    float s = acc[o];
+    for (int k = 16; k > 0; k >>= 1) s += __shfl_xor_sync(0xffffffffu, s, k);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&red[o], s);
+  }
+  __syncthreads();
+  if (threadIdx.x < 16) atomicAdd(gw + threadIdx.x * 27 + t, red[threadIdx.x]);
+}
+
+// ---------------------------------------------------------------------------
+// pooling, upsampling and the gradient plumbing between levels
+// ---------------------------------------------------------------------------
+// out (coarse) = mean of the 2x2x2 fine block; fine dims dm
+__global__ void k_pool(Dims dm, const bf16* __restrict__ x, int ldx, int c, bf16* __restrict__ y, int ldy) {
+  const Dims cd{dm.n, dm.d / 2, dm.h / 2, dm.w / 2};
+  const long long total = cd.vox() * c;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    const int ch = (int)(e % c);
+    long long v = e / c;
+    const int xx = (int)(v % cd.w);
+    long long r = v / cd.w;
+    const int yy = (int)(r % cd.h);
+    r /= cd.h;
+    const int zz = (int)(r % cd.d);
+    const long long n = r / cd.d;
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+      const long long f = ((n * dm.d + 2 * zz + (k >> 2)) * dm.h + 2 * yy + ((k >> 1) & 1)) * dm.w + 2 * xx + (k & 1);
+      s += __bfloat162float(x[f * ldx + ch]);
+    }
+    y[v * ldy + ch] = __float2bfloat16(s * 0.125f);
+  }
+}
+
+// fine = coarse value (nearest); coarse dims cd
+__global__ void k_upsample(Dims cd, const bf16* __restrict__ x, int ldx, int c, bf16* __restrict__ y, int ldy) {
+  const Dims fd{cd.n, cd.d * 2, cd.h * 2, cd.w * 2};
+  const long long total = fd.vox() * c;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    const int ch = (int)(e % c);
+    long long v = e / c;
+    const int xx = (int)(v % fd.w);
+    long long r = v / fd.w;
+    const int yy = (int)(r % fd.h);
+    r /= fd.h;
+    const int zz = (int)(r % fd.d);
+    const long long n = r / fd.d;
+    const long long cv = ((n * cd.d + zz / 2) * cd.h + yy / 2) * cd.w + xx / 2;
+    y[v * ldy + ch] = x[cv * ldx + ch];
+  }
+}
+
+// coarse gradient of an upsample = sum over the fine block, times (act > 0)
+__global__ void k_upsample_bwd_mask(Dims cd, const bf16* __restrict__ gf, int ldg, int c, const bf16* __restrict__ act,
+                                    int lda, bf16* __restrict__ out, int ldo) {
+  const Dims fd{cd.n, cd.d * 2, cd.h * 2, cd.w * 2};
+  const long long total = cd.vox() * c;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    const int ch = (int)(e % c);
+    long long v = e / c;
+    const int xx = (int)(v % cd.w);
+    long long r = v / cd.w;
+    const int yy = (int)(r % cd.h);
+    r /= cd.h;
+    const int zz = (int)(r % cd.d);
+    const long long n = r / cd.d;
+    float s = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+      const long long f = ((n * fd.d + 2 * zz + (k >> 2)) * fd.h + 2 * yy + ((k >> 1) & 1)) * fd.w + 2 * xx + (k & 1);
+      s += __bfloat162float(gf[f * ldg + ch]);
+    }
+    out[v * ldo + ch] = __float2bfloat16(__bfloat162float(act[v * lda + ch]) > 0.f ? s : 0.f);
+  }
+}
+
+// fine gradient of a level's output: pool backward (coarse / 8) plus the skip
+// gradient, times (act > 0); fine dims fd
+__global__ void k_pool_bwd_add_mask(Dims fd, const bf16* __restrict__ gc, int ldc, const bf16* __restrict__ gskip,
+                                    int lds, int c, const bf16* __restrict__ act, int lda, bf16* __restrict__ out,
+                                    int ldo) {
+  const Dims cd{fd.n, fd.d / 2, fd.h / 2, fd.w / 2};
+  const long long total = fd.vox() * c;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    const int ch = (int)(e % c);
+    long long v = e / c;
+    const int xx = (int)(v % fd.w);
+    long long r = v / fd.w;
+    const int yy = (int)(r % fd.h);
+    r /= fd.h;
+    const int zz = (int)(r % fd.d);
+    const long long n = r / fd.d;
+    const long long cv = ((n * cd.d + zz / 2) * cd.h + yy / 2) * cd.w + xx / 2;
+    const float s = 0.125f * __bfloat162float(gc[cv * ldc + ch]) + __bfloat162float(gskip[v * lds + ch]);
+    out[v * ldo + ch] = __float2bfloat16(__bfloat162float(act[v * lda + ch]) > 0.f ? s : 0.f);
+  }
+}
+
+// weights: master W[o][c][t] (FP32) -> wt[t][o][c] (BF16) and, for the
+// backward data pass, wtt[26-t][c][o] (BF16)
+__global__ void k_pack_weights(const float* __restrict__ w, int cout, int cin, bf16* __restrict__ wt,
+                               bf16* __restrict__ wtt) {
+  const long long total = (long long)cout * cin * 27;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    const int t = (int)(e % 27);
+    const long long oc = e / 27;
+    const int c = (int)(oc % cin), o = (int)(oc / cin);
+    const bf16 v = __float2bfloat16(w[e]);
+    wt[((long long)t * cout + o) * cin + c] = v;
+    if (wtt) wtt[((long long)(26 - t) * cin + c) * cout + o] = v;
+  }
+}
+
+// mean((y - t)^2) (per-block partials, summed with atomics) and gy = 2(y - t)/n
+__global__ void k_mse(long long n, const float* __restrict__ y, const float* __restrict__ t, float* __restrict__ gy,
+                      float* __restrict__ loss) {
+  float s = 0.f;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float d = y[i] - t[i];
+    s += d * d;
+    gy[i] = 2.f * d / (float)n;
+  }
+  for (int k = 16; k > 0; k >>= 1) s += __shfl_xor_sync(0xffffffffu, s, k);
+  if ((threadIdx.x & 31) == 0) atomicAdd(loss, s / (float)n);
+}
+
+__global__ void k_adam(long long n, float* __restrict__ th, const float* __restrict__ g, float* __restrict__ m,
+                       float* __restrict__ v, float lr, float b1, float b2, float eps, float c1, float c2) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    th[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+  }
+}
+
+}  // namespace nn
+}  // namespace stp
+
+// ===========================================================================
+// the network object and its C ABI
+// ===========================================================================
+using namespace stp;
+using namespace stp::nn;
+
+namespace {
+
+const int kCh[4] = {16, 32, 64, 128};
+
+struct Layer {
+  int cin, cout, taps;
+  long long woff, boff;  // offsets of W and b in the flat parameter vector
+  bf16 *wt = nullptr, *wtt = nullptr;
+};
+
+int blocks_for(long long n, int threads = 256) {
+  long long b = (n + threads - 1) / threads;
+  return (int)std::max<long long>(1, std::min<long long>(b, 152LL * 32));
+}
+
+}  // namespace
+
+struct stp_unet {
+  Dims dm[4];  // level dims (batch included), level 0 = full resolution
+  int nmax;
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  std::vector<Layer> L;  // 15 layers in parameter order
+  long long np = 0;
+  float *theta = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
+  long long adam_step = 0;
+  // activations (BF16, channels-last)
+  bf16 *ha[4] = {}, *e4 = nullptr, *u[3] = {}, *q[3] = {}, *hd[3] = {}, *d[3] = {};
+  // gradients of activations
+  bf16 *ga[4] = {}, *gb[4] = {}, *gu[3] = {};
+  float *y = nullptr, *gy = nullptr, *loss = nullptr, *h_loss = nullptr;
+  std::vector<void*> allocs;
+  std::string err;
+};
+
+namespace {
+
+int ufail(stp_unet* n, int code, const std::string& m) {
+  if (n) n->err = m;
+  return code;
+}
+
+#define UTRY(n, call)                                                                                  \
+  do {                                                                                                 \
+    cudaError_t e_ = (call);                                                                           \
+    if (e_ != cudaSuccess) return ufail(n, STP_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+template <typename T>
+int ualloc(stp_unet* n, T** p, size_t count) {
+  cudaError_t e = cudaMalloc((void**)p, sizeof(T) * std::max<size_t>(count, 1));
+  if (e != cudaSuccess) return ufail(n, STP_ENOMEM, "cudaMalloc failed in the network");
+  n->allocs.push_back(*p);
+  return STP_OK;
+}
+
+// concat widths: decoder level l (0..2) input = kCh[l+1] + kCh[l]
+int cu_width(int l) { return kCh[l + 1] + kCh[l]; }
+
+// launch a 3x3x3 convolution (forward form)
+int conv3(stp_unet* n, const Dims& dm, const bf16* x, int ldx, int cin, const bf16* wt, const float* bias, int cout,
+          bf16* y, int ldy, int relu, const bf16* mask, int ldm) {
+  const long long V = dm.vox();
+  const unsigned gx = (unsigned)((V + 127) / 128);
+  if (cout % 64 == 0) {
+    k_conv3<8><<<dim3(gx, cout / 64), 128, 0, n->st>>>(dm, x, ldx, cin, wt, bias, cout, y, ldy, relu, mask, ldm);
+  } else if (cout == 32) {
+    k_conv3<4><<<dim3(gx, 1), 128, 0, n->st>>>(dm, x, ldx, cin, wt, bias, cout, y, ldy, relu, mask, ldm);
+  } else {
+    k_conv3<2><<<dim3(gx, (cout + 15) / 16), 128, 0, n->st>>>(dm, x, ldx, cin, wt, bias, cout, y, ldy, relu, mask,
+                                                               ldm);
+  }
+  UTRY(n, cudaGetLastError());
+  return STP_OK;
+}
+
+int wgrad3(stp_unet* n, const Dims& dm, const bf16* x, int ldx, int cin, const bf16* gz, int ldg, int cout,
+           const Layer& ly) {
+  const long long V = dm.vox();
+  const int tiles = 27 * ((cin + 31) / 32) * (cout / 16);
+  long long splits = std::max<long long>(1, std::min<long long>((152LL * 16) / tiles + 1, (V + 63) / 64));
+  long long chunk = (V + splits - 1) / splits;
+  chunk = ((chunk + 63) / 64) * 64;
+  splits = (V + chunk - 1) / chunk;
+  k_wgrad3<<<dim3(tiles, (unsigned)splits), 128, 0, n->st>>>(dm, x, ldx, cin, gz, ldg, cout, n->grad + ly.woff,
+                                                             nullptr, chunk);
+  UTRY(n, cudaGetLastError());
+  const int bx = (int)std::min<long long>(V, 1024);
+  k_bias_grad<<<dim3(bx, (cout + 127) / 128), 128, 0, n->st>>>(V, gz, ldg, cout, n->grad + ly.boff);
+  UTRY(n, cudaGetLastError());
+  return STP_OK;
+}
+
+int pack_all(stp_unet* n) {
+  for (size_t i = 0; i < n->L.size(); i++) {
+    Layer& ly = n->L[i];
+    if (ly.taps != 27 || ly.cin == 1) continue;
+    const long long tot = (long long)ly.cout * ly.cin * 27;
+    k_pack_weights<<<blocks_for(tot), 256, 0, n->st>>>(n->theta + ly.woff, ly.cout, ly.cin, ly.wt, ly.wtt);
+    UTRY(n, cudaGetLastError());
+  }
+  return STP_OK;
+}
+
+// forward of nb samples; x [nb][D][H][W] FP32 on the device
+int forward(stp_unet* n, const float* x, int nb) {
+  Dims dm[4];
+  for (int l = 0; l < 4; l++) dm[l] = Dims{nb, n->dm[l].d, n->dm[l].h, n->dm[l].w};
+  int rc;
+  // encoder
+  const Layer* P = n->L.data();
+  // level 1: input layer, second conv writes e1 into u[0][:, 32:48]
+  k_conv_in<<<blocks_for(dm[0].vox()), 256, 0, n->st>>>(dm[0], x, n->theta + P[0].woff, n->theta + P[0].boff, n->ha[0],
+                                                         16);
+  UTRY(n, cudaGetLastError());
+  const bf16* in = nullptr;
+  int ldin = 0;
+  for (int l = 0; l < 4; l++) {
+    const int c = kCh[l];
+    const Layer& la = P[2 * l];
+    const Layer& lb = P[2 * l + 1];
+    if (l > 0) {
+      if ((rc = conv3(n, dm[l], in, ldin, la.cin, la.wt, n->theta + la.boff, c, n->ha[l], c, 1, nullptr, 0))) return rc;
+    }
+    bf16* e = l < 3 ? n->u[l] + kCh[l + 1] : n->e4;
+    const int lde = l < 3 ? cu_width(l) : c;
+    if ((rc = conv3(n, dm[l], n->ha[l], c, c, lb.wt, n->theta + lb.boff, c, e, lde, 1, nullptr, 0))) return rc;
+    if (l < 3) {
+      k_pool<<<blocks_for(dm[l + 1].vox() * c), 256, 0, n->st>>>(dm[l], e, lde, c, n->q[l], c);
+      UTRY(n, cudaGetLastError());
+      in = n->q[l];
+      ldin = c;
+    }
+  }
+  // decoder
+  const bf16* deeper = n->e4;
+  int cdeep = kCh[3];
+  for (int l = 2; l >= 0; l--) {
+    const int c = kCh[l], cw = cu_width(l);
+    k_upsample<<<blocks_for(dm[l].vox() * cdeep), 256, 0, n->st>>>(dm[l + 1], deeper, cdeep, cdeep, n->u[l], cw);
+    UTRY(n, cudaGetLastError());
+    const Layer& la = P[8 + 2 * (2 - l)];
+    const Layer& lb = P[9 + 2 * (2 - l)];
+    if ((rc = conv3(n, dm[l], n->u[l], cw, cw, la.wt, n->theta + la.boff, c, n->hd[l], c, 1, nullptr, 0))) return rc;
+    if ((rc = conv3(n, dm[l], n->hd[l], c, c, lb.wt, n->theta + lb.boff, c, n->d[l], c, 1, nullptr, 0))) return rc;
+    deeper = n->d[l];
+    cdeep = c;
+  }
+  const Layer& lo = P[14];
+  k_conv_out<<<blocks_for(dm[0].vox()), 256, 0, n->st>>>(dm[0].vox(), n->d[0], 16, n->theta + lo.woff,
+                                                          n->theta + lo.boff, n->y);
+  UTRY(n, cudaGetLastError());
+  return STP_OK;
+}
+
+// backward from gy (FP32 [V0]) into n->grad (zeroed here)
+int backward(stp_unet* n, const float* x, int nb) {
+  Dims dm[4];
+  for (int l = 0; l < 4; l++) dm[l] = Dims{nb, n->dm[l].d, n->dm[l].h, n->dm[l].w};
+  const Layer* P = n->L.data();
+  int rc;
+  UTRY(n, cudaMemsetAsync(n->grad, 0, sizeof(float) * n->np, n->st));
+  // output layer -> gradient of the pre-activation of d1 (ga[0])
+  const Layer& lo = P[14];
+  k_conv_out_bwd<<<blocks_for(dm[0].vox()), 256, 0, n->st>>>(dm[0].vox(), n->gy, n->d[0], 16, n->theta + lo.woff,
+                                                              n->ga[0], 16, n->grad + lo.woff, n->grad + lo.boff);
+  UTRY(n, cudaGetLastError());
+  // decoder, level 0 up to 2; ga[l] holds the gradient of d_l's pre-activation
+  for (int l = 0; l <= 2; l++) {
+    const int c = kCh[l], cw = cu_width(l);
+    const Layer& la = P[8 + 2 * (2 - l)];
+    const Layer& lb = P[9 + 2 * (2 - l)];
+    // conv b: input hd[l], gradient ga[l]
+    if ((rc = wgrad3(n, dm[l], n->hd[l], c, c, n->ga[l], c, c, lb))) return rc;
+    if ((rc = conv3(n, dm[l], n->ga[l], c, c, lb.wtt, nullptr, c, n->gb[l], c, 0, n->hd[l], c))) return rc;
+    // conv a: input u[l], gradient gb[l]
+    if ((rc = wgrad3(n, dm[l], n->u[l], cw, cw, n->gb[l], c, c, la))) return rc;
+    if ((rc = conv3(n, dm[l], n->gb[l], c, c, la.wtt, nullptr, cw, n->gu[l], cw, 0, nullptr, 0))) return rc;
+    // upsample part -> gradient of the deeper level's output pre-activation
+    const int cd = kCh[l + 1];
+    const bf16* act = l < 2 ? n->d[l + 1] : n->e4;
+    bf16* out = l < 2 ? n->ga[l + 1] : n->ga[3];
+    k_upsample_bwd_mask<<<blocks_for(dm[l + 1].vox() * cd), 256, 0, n->st>>>(dm[l + 1], n->gu[l], cw, cd, act, cd, out,
+                                                                              cd);
+    UTRY(n, cudaGetLastError());
+  }
+  // encoder, level 3 down to 0.  Buffers at level l: gz (gradient of e_l's
+  // pre-activation), gha (of ha_l's), gq (of q_{l-1}, handed to level l-1).
+  //   l = 3: gz = ga[3] (from the decoder), gha = gb[3], gq = ga[3]
+  //   l < 3: gz = gb[l], gha = ga[l], gq = gb[l]
+  // each is overwritten only after its last reader has run.
+  const bf16* gq_in = nullptr;
+  for (int l = 3; l >= 0; l--) {
+    const int c = kCh[l];
+    const Layer& la = P[2 * l];
+    const Layer& lb = P[2 * l + 1];
+    bf16* gz = l == 3 ? n->ga[3] : n->gb[l];
+    if (l < 3) {
+      // gz = (pool backward of the gradient of q_l + skip gradient) * (e_l > 0)
+      const bf16* e = n->u[l] + kCh[l + 1];
+      k_pool_bwd_add_mask<<<blocks_for(dm[l].vox() * c), 256, 0, n->st>>>(dm[l], gq_in, c, n->gu[l] + kCh[l + 1],
+                                                                            cu_width(l), c, e, cu_width(l), gz, c);
+      UTRY(n, cudaGetLastError());
+    }
+    // conv b: input ha[l]
+    if ((rc = wgrad3(n, dm[l], n->ha[l], c, c, gz, c, c, lb))) return rc;
+    bf16* gha = l == 3 ? n->gb[3] : n->ga[l];
+    if ((rc = conv3(n, dm[l], gz, c, c, lb.wtt, nullptr, c, gha, c, 0, n->ha[l], c))) return rc;
+    if (l > 0) {
+      // conv a: input q[l-1]
+      const int cp = kCh[l - 1];
+      if ((rc = wgrad3(n, dm[l], n->q[l - 1], cp, cp, gha, c, c, la))) return rc;
+      bf16* gq = l == 3 ? n->ga[3] : n->gb[l];
+      if ((rc = conv3(n, dm[l], gha, c, c, la.wtt, nullptr, cp, gq, cp, 0, nullptr, 0))) return rc;
+      gq_in = gq;
+    } else {
+      // conv a of level 1: the network input (1 channel)
+      k_wgrad_in<<<dim3((unsigned)std::min<long long>(152 * 2, (dm[0].vox() + 255) / 256), 27), 256, 0, n->st>>>(
+          dm[0], x, gha, c, n->grad + la.woff);
+      UTRY(n, cudaGetLastError());
+      const int bx = (int)std::min<long long>(dm[0].vox(), 1024);
+      k_bias_grad<<<dim3(bx, 1), 128, 0, n->st>>>(dm[0].vox(), gha, c, c, n->grad + la.boff);
+      UTRY(n, cudaGetLastError());
+    }
+  }
+  return STP_OK;
+}
+
+int check_n(stp_unet* n, int nb) {
+  if (nb < 1 || nb > n->nmax) return ufail(n, STP_EINVAL, "batch size out of range");
+  return STP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+long long stp_unet_param_count(void) {
+  long long np = 0;
+  int cin = 1;
+  for (int l = 0; l < 4; l++) {
+    np += 27LL * cin * kCh[l] + kCh[l] + 27LL * kCh[l] * kCh[l] + kCh[l];
+    cin = kCh[l];
+  }
+  for (int l = 2; l >= 0; l--) np += 27LL * cu_width(l) * kCh[l] + kCh[l] + 27LL * kCh[l] * kCh[l] + kCh[l];
+  return np + 16 + 1;
+}
+
+int stp_unet_create(int nmax, int nz, int ny, int nx, void* stream, stp_unet** out) {
+  if (!out) return STP_EINVAL;
+  *out = nullptr;
+  if (nmax < 1 || nz < 8 || ny < 8 || nx < 8 || nz % 8 || ny % 8 || nx % 8) return STP_EINVAL;
+  stp_unet* n = new stp_unet();
+  n->nmax = nmax;
+  for (int l = 0; l < 4; l++) n->dm[l] = Dims{nmax, nz >> l, ny >> l, nx >> l};
+  if (stream) {
+    n->st = (cudaStream_t)stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&n->st, cudaStreamNonBlocking) != cudaSuccess) {
+      delete n;
+      return STP_ECUDA;
+    }
+    n->own_stream = true;
+  }
+  // layers in parameter order
+  long long q = 0;
+  auto add = [&](int ci, int co, int taps) {
+    Layer ly;
+    ly.cin = ci;
+    ly.cout = co;
+    ly.taps = taps;
+    ly.woff = q;
+    q += (long long)co * ci * taps;
+    ly.boff = q;
+    q += co;
+    n->L.push_back(ly);
+  };
+  int cin = 1;
+  for (int l = 0; l < 4; l++) {
+    add(cin, kCh[l], 27);
+    add(kCh[l], kCh[l], 27);
+    cin = kCh[l];
+  }
+  for (int l = 2; l >= 0; l--) {
+    add(cu_width(l), kCh[l], 27);
+    add(kCh[l], kCh[l], 27);
+  }
+  add(16, 1, 1);
+  n->np = q;
+  int rc = STP_OK;
+  auto A = [&](auto** p, size_t count) {
+    if (rc == STP_OK) rc = ualloc(n, p, count);
+  };
+  A(&n->theta, n->np);
+  A(&n->grad, n->np);
+  A(&n->m, n->np);
+  A(&n->v, n->np);
+  for (Layer& ly : n->L) {
+    if (ly.taps == 27 && ly.cin > 1) {
+      A(&ly.wt, (size_t)ly.cout * ly.cin * 27);
+      A(&ly.wtt, (size_t)ly.cout * ly.cin * 27);
+    }
+  }
+  const long long V[4] = {n->dm[0].vox(), n->dm[1].vox(), n->dm[2].vox(), n->dm[3].vox()};
+  for (int l = 0; l < 4; l++) {
+    A(&n->ha[l], (size_t)V[l] * kCh[l]);
+    A(&n->ga[l], (size_t)V[l] * kCh[l]);
+    A(&n->gb[l], (size_t)V[l] * kCh[l]);
+  }
+  A(&n->e4, (size_t)V[3] * kCh[3]);
+  for (int l = 0; l < 3; l++) {
+    A(&n->u[l], (size_t)V[l] * cu_width(l));
+    A(&n->gu[l], (size_t)V[l] * cu_width(l));
+    A(&n->q[l], (size_t)V[l + 1] * kCh[l]);
+    A(&n->hd[l], (size_t)V[l] * kCh[l]);
+    A(&n->d[l], (size_t)V[l] * kCh[l]);
+  }
+  A(&n->y, (size_t)V[0]);
+  A(&n->gy, (size_t)V[0]);
+  A(&n->loss, 1);
+  if (rc == STP_OK && cudaMallocHost((void**)&n->h_loss, sizeof(float)) != cudaSuccess) rc = STP_ENOMEM;
+  if (rc == STP_OK) {
+    cudaMemsetAsync(n->theta, 0, sizeof(float) * n->np, n->st);
+    cudaMemsetAsync(n->m, 0, sizeof(float) * n->np, n->st);
+    cudaMemsetAsync(n->v, 0, sizeof(float) * n->np, n->st);
+    if (cudaStreamSynchronize(n->st) != cudaSuccess) rc = STP_ECUDA;
+  }
+  if (rc != STP_OK) {
+    stp_unet_destroy(n);
+    return rc;
+  }
+  *out = n;
+  return STP_OK;
+}
+
+void stp_unet_destroy(stp_unet* n) {
+  if (!n) return;
+  if (n->st) cudaStreamSynchronize(n->st);
+  for (void* p : n->allocs) cudaFree(p);
+  if (n->h_loss) cudaFreeHost(n->h_loss);
+  if (n->own_stream && n->st) cudaStreamDestroy(n->st);
+  delete n;
+}
+
+const char* stp_unet_last_error(const stp_unet* n) { return n ? n->err.c_str() : ""; }
+
+int stp_unet_set_params(stp_unet* n, const float* theta, int where) {
+  if (!n || !theta) return STP_EINVAL;
+  UTRY(n, cudaMemcpyAsync(n->theta, theta, sizeof(float) * n->np,
+                          where == STP_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, n->st));
+  UTRY(n, cudaMemsetAsync(n->m, 0, sizeof(float) * n->np, n->st));
+  UTRY(n, cudaMemsetAsync(n->v, 0, sizeof(float) * n->np, n->st));
+  n->adam_step = 0;
+  int rc = pack_all(n);
+  if (rc) return rc;
+  UTRY(n, cudaStreamSynchronize(n->st));
+  return STP_OK;
+}
+
+int stp_unet_get_params(stp_unet* n, float* theta, int where) {
+  if (!n || !theta) return STP_EINVAL;
+  UTRY(n, cudaMemcpyAsync(theta, n->theta, sizeof(float) * n->np,
+                          where == STP_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, n->st));
+  UTRY(n, cudaStreamSynchronize(n->st));
+  return STP_OK;
+}
+
+int stp_unet_forward(stp_unet* n, const float* x, float* y, int nb) {
+  if (!n || !x || !y) return STP_EINVAL;
+  if (int rc = check_n(n, nb)) return rc;
+  int rc = forward(n, x, nb);
+  if (rc) return rc;
+  UTRY(n, cudaMemcpyAsync(y, n->y, sizeof(float) * n->dm[0].vox() / n->nmax * nb, cudaMemcpyDeviceToDevice, n->st));
+  UTRY(n, cudaStreamSynchronize(n->st));
+  return STP_OK;
+}
+
+int stp_unet_gradient(stp_unet* n, const float* x, const float* target, int nb, float* grad, float* loss) {
+  if (!n || !x || !target) return STP_EINVAL;
+  if (int rc = check_n(n, nb)) return rc;
+  int rc = forward(n, x, nb);
+  if (rc) return rc;
+  const long long V = n->dm[0].vox() / n->nmax * nb;
+  UTRY(n, cudaMemsetAsync(n->loss, 0, sizeof(float), n->st));
+  k_mse<<<blocks_for(V), 256, 0, n->st>>>(V, n->y, target, n->gy, n->loss);
+  UTRY(n, cudaGetLastError());
+  if ((rc = backward(n, x, nb))) return rc;
+  if (grad) UTRY(n, cudaMemcpyAsync(grad, n->grad, sizeof(float) * n->np, cudaMemcpyDeviceToDevice, n->st));
+  UTRY(n, cudaMemcpyAsync(n->h_loss, n->loss, sizeof(float), cudaMemcpyDeviceToHost, n->st));
+  UTRY(n, cudaStreamSynchronize(n->st));
+  if (loss) *loss = *n->h_loss;
+  return STP_OK;
+}
+
+int stp_unet_train_step(stp_unet* n, const float* x, const float* target, int nb, float lr, float* loss) {
+  int rc = stp_unet_gradient(n, x, target, nb, nullptr, loss);
+  if (rc) return rc;
+  n->adam_step++;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.f - std::pow(b1, (float)n->adam_step), c2 = 1.f - std::pow(b2, (float)n->adam_step);
+  k_adam<<<blocks_for(n->np), 256, 0, n->st>>>(n->np, n->theta, n->grad, n->m, n->v, lr, b1, b2, 1e-8f, c1, c2);
+  UTRY(n, cudaGetLastError());
+  if ((rc = pack_all(n))) return rc;
+  UTRY(n, cudaStreamSynchronize(n->st));
+  return STP_OK;
+}
+
+}  // extern "C"

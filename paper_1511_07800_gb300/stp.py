@@ -66,7 +66,9 @@ class SolveStats(ctypes.Structure):
 
 EXPORTS = ("stp_config_defaults", "stp_init", "stp_destroy", "stp_last_error", "stp_set_fields",
            "stp_get_fields", "stp_step", "stp_poisson_solve", "stp_eval", "stp_srj_schedule",
-           "stp_poisson_residual_noalloc")
+           "stp_poisson_residual_noalloc", "stp_unet_param_count", "stp_unet_create", "stp_unet_destroy",
+           "stp_unet_last_error", "stp_unet_set_params", "stp_unet_get_params", "stp_unet_forward",
+           "stp_unet_gradient", "stp_unet_train_step")
 
 _lib = None
 
@@ -99,6 +101,17 @@ def lib():
     L.stp_poisson_residual_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                                ctypes.c_double, ctypes.c_double, ctypes.c_double, vp, vp, vp,
                                                ctypes.POINTER(ctypes.c_double), vp]
+    L.stp_unet_param_count.restype = ctypes.c_longlong
+    L.stp_unet_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, ctypes.POINTER(vp)]
+    L.stp_unet_destroy.argtypes = [vp]
+    L.stp_unet_destroy.restype = None
+    L.stp_unet_last_error.argtypes = [vp]
+    L.stp_unet_last_error.restype = ctypes.c_char_p
+    L.stp_unet_set_params.argtypes = [vp, vp, ctypes.c_int]
+    L.stp_unet_get_params.argtypes = [vp, vp, ctypes.c_int]
+    L.stp_unet_forward.argtypes = [vp, vp, vp, ctypes.c_int]
+    L.stp_unet_gradient.argtypes = [vp, vp, vp, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_float)]
+    L.stp_unet_train_step.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_float, ctypes.POINTER(ctypes.c_float)]
     _lib = L
     return L
 
@@ -244,4 +257,64 @@ class Channel:
         return self
 
     def __exit__(self, *a):
+        self.close()
+
+
+class UNet:
+    """The learned-guess network (see stp_unet_* in the header).  Arrays are
+    torch CUDA float32 tensors [n][nz][ny][nx]; parameters a flat float32
+    vector (numpy for host, tensor for device)."""
+
+    def __init__(self, nmax, nz, ny, nx, stream=None):
+        h = ctypes.c_void_p()
+        rc = lib().stp_unet_create(int(nmax), int(nz), int(ny), int(nx), stream, ctypes.byref(h))
+        if rc != STP_OK:
+            raise StpError(rc, "stp_unet_create failed (sizes must be multiples of 8)")
+        self._h = h
+        self.shape = (nz, ny, nx)
+        self.nmax = nmax
+
+    @staticmethod
+    def param_count():
+        return int(lib().stp_unet_param_count())
+
+    def _check(self, rc):
+        if rc != STP_OK:
+            raise StpError(rc, lib().stp_unet_last_error(self._h).decode())
+
+    def set_params(self, theta):
+        if hasattr(theta, "data_ptr"):
+            self._check(lib().stp_unet_set_params(self._h, ctypes.c_void_p(theta.data_ptr()), STP_DEVICE))
+        else:
+            a = np.ascontiguousarray(theta, dtype=np.float32)
+            self._check(lib().stp_unet_set_params(self._h, ctypes.c_void_p(a.ctypes.data), STP_HOST))
+
+    def get_params(self):
+        a = np.zeros(self.param_count(), dtype=np.float32)
+        self._check(lib().stp_unet_get_params(self._h, ctypes.c_void_p(a.ctypes.data), STP_HOST))
+        return a
+
+    def forward(self, x, y):
+        self._check(lib().stp_unet_forward(self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                                           int(x.shape[0])))
+
+    def gradient(self, x, t, grad=None):
+        loss = ctypes.c_float(0)
+        g = ctypes.c_void_p(grad.data_ptr()) if grad is not None else None
+        self._check(lib().stp_unet_gradient(self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(t.data_ptr()),
+                                            int(x.shape[0]), g, ctypes.byref(loss)))
+        return loss.value
+
+    def train_step(self, x, t, lr):
+        loss = ctypes.c_float(0)
+        self._check(lib().stp_unet_train_step(self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(t.data_ptr()),
+                                              int(x.shape[0]), float(lr), ctypes.byref(loss)))
+        return loss.value
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and _lib is not None:
+            _lib.stp_unet_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
         self.close()

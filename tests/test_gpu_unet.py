@@ -1,0 +1,104 @@
+"""The learned-guess U-Net on the GPU (BF16 tensor-core kernels) against
+the FP64 oracle, with the oracle's storage points rounded to bfloat16 where
+the CUDA path stores in bfloat16: forward pass, the gradient of the MSE
+loss, and one Adam step."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+def _setup(seed, shape=(2, 8, 8, 16)):
+    from oracle import unet
+    rng = np.random.default_rng(seed)
+    theta = unet.init_params(seed).astype(np.float32).astype(np.float64)
+    x = rng.standard_normal(shape)
+    t = rng.standard_normal(shape) * 0.1
+    return unet, theta, x, t
+
+
+def test_unet_param_count(stp_lib, orc):
+    from oracle import unet
+    assert stp_lib.UNet.param_count() == unet.n_params()
+
+
+def test_unet_forward_parity(stp_lib, orc):
+    torch = pytest.importorskip("torch")
+    unet, theta, x, t = _setup(1)
+    n, d, h, w = x.shape
+    net = stp_lib.UNet(n, d, h, w)
+    net.set_params(theta.astype(np.float32))
+    tx = torch.from_numpy(x.astype(np.float32)).cuda()
+    ty = torch.zeros_like(tx)
+    net.forward(tx, ty)
+    y = ty.cpu().numpy().astype(np.float64)
+    y_b = unet.forward(theta, x[..., None], rnd=unet.bf16)[..., 0]
+    y_e = unet.forward(theta, x[..., None])[..., 0]
+    scale = np.abs(y_b).max()
+    # against the bfloat16-storage oracle: FP32 accumulation order only
+    assert np.abs(y - y_b).max() < 2e-2 * scale
+    # against exact FP64: the size of bfloat16 storage itself
+    assert np.abs(y - y_e).max() < 6e-2 * np.abs(y_e).max()
+    net.close()
+
+
+def test_unet_gradient_parity(stp_lib, orc):
+    torch = pytest.importorskip("torch")
+    unet, theta, x, t = _setup(2)
+    n, d, h, w = x.shape
+    net = stp_lib.UNet(n, d, h, w)
+    net.set_params(theta.astype(np.float32))
+    tx = torch.from_numpy(x.astype(np.float32)).cuda()
+    tt = torch.from_numpy(t.astype(np.float32)).cuda()
+    g = torch.zeros(stp_lib.UNet.param_count(), dtype=torch.float32, device="cuda")
+    loss = net.gradient(tx, tt, g)
+    L_o, g_o = unet.loss_and_grad(theta, x[..., None], t[..., None], rnd=unet.bf16)
+    gg = g.cpu().numpy().astype(np.float64)
+    assert abs(loss - L_o) < 1e-2 * L_o
+    rel = np.linalg.norm(gg - g_o) / np.linalg.norm(g_o)
+    cos = gg @ g_o / (np.linalg.norm(gg) * np.linalg.norm(g_o))
+    assert rel < 5e-2 and cos > 0.998, (rel, cos)
+    # per layer: every layer's gradient block agrees
+    q = 0
+    for (name, ci, co, taps) in unet.layer_specs():
+        m = co * ci * taps + co
+        a, b = gg[q:q + m], g_o[q:q + m]
+        assert np.linalg.norm(a - b) < 0.1 * np.linalg.norm(b) + 1e-9, name
+        q += m
+    net.close()
+
+
+def test_unet_adam_step(stp_lib, orc):
+    torch = pytest.importorskip("torch")
+    unet, theta, x, t = _setup(3)
+    n, d, h, w = x.shape
+    net = stp_lib.UNet(n, d, h, w)
+    net.set_params(theta.astype(np.float32))
+    tx = torch.from_numpy(x.astype(np.float32)).cuda()
+    tt = torch.from_numpy(t.astype(np.float32)).cuda()
+    lr = 1e-3
+    net.train_step(tx, tt, lr)
+    th1 = net.get_params().astype(np.float64)
+    _, g_o = unet.loss_and_grad(theta, x[..., None], t[..., None], rnd=unet.bf16)
+    t_o, _, _ = unet.adam_step(theta, g_o, np.zeros_like(theta), np.zeros_like(theta), 1, lr)
+    big = np.abs(g_o) > 1e-3 * np.abs(g_o).max()
+    # the first Adam step moves each parameter by about lr * sign(g)
+    agree = np.mean(np.sign(th1 - theta)[big] == np.sign(t_o - theta)[big])
+    assert agree > 0.98, agree
+    assert np.abs(th1 - theta).max() <= lr * 1.001
+    net.close()
+
+
+def test_unet_training_reduces_loss(stp_lib, orc):
+    torch = pytest.importorskip("torch")
+    unet, theta, x, t = _setup(4)
+    n, d, h, w = x.shape
+    net = stp_lib.UNet(n, d, h, w)
+    net.set_params(theta.astype(np.float32))
+    tx = torch.from_numpy(x.astype(np.float32)).cuda()
+    tt = torch.from_numpy(t.astype(np.float32)).cuda()
+    l0 = net.train_step(tx, tt, 1e-3)
+    for _ in range(30):
+        l1 = net.train_step(tx, tt, 1e-3)
+    assert l1 < 0.5 * l0
+    net.close()
