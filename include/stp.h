@@ -214,6 +214,28 @@ int stp_unet_gradient(stp_unet *net, const float *x, const float *target, int nb
    loss before the step. */
 int stp_unet_train_step(stp_unet *net, const float *x, const float *target, int nb, float lr, float *loss);
 
+/* Training on solver pairs: r = residual of the previous pressure, dp = the
+   exact correction (see stp_set_harvest).  Each sample is scaled by the RMS
+   s of its r: the network maps r/s to K dp/s, K the output scale (default
+   1; set it so that K dp/s is of order one).  One Adam step per call;
+   stp_unet_eval_pairs gives the loss without a step. */
+int stp_unet_set_output_scale(stp_unet *net, float k);
+int stp_unet_train_pairs(stp_unet *net, const float *r, const float *dp, int nb, float lr, float *loss);
+int stp_unet_eval_pairs(stp_unet *net, const float *r, const float *dp, int nb, float *loss);
+
+/* Use net (NULL: none) as the learned initial guess of every pressure solve
+   of h: with s = RMS(r) of the solve's starting residual r, the correction
+   s U(r / s) is added to p before the SRJ iteration (once per solve, in
+   both precisions).  The SRJ iteration always finishes to ptol.
+   The network must match the grid (nz, ny, nx); the handle keeps the
+   pointer, which must stay valid while set. */
+int stp_set_learned_guess(stp_handle *h, stp_unet *net);
+
+/* Record training pairs of every pressure solve of h into caller device
+   arrays (FP32 [nz][ny][nx], NULL: stop): r_out = b - L p_prev at the start
+   of the solve, dp_out = p - p_prev after it. */
+int stp_set_harvest(stp_handle *h, float *r_out, float *dp_out);
+
 /* ||b - L p||_2 of the pressure equation for caller-owned device arrays p
    and b ([nz][ny][nx], FP64), without allocating anything.  The paper has
    no counterpart: it is for callers that hold their own device buffers but

@@ -68,6 +68,11 @@ struct stp_handle {
   cudaGraph_t solve_graph = nullptr;
   cudaGraphExec_t solve_exec = nullptr;
   bool host_solve = false;     // STP_HOST_SOLVE=1: drive the solve from the host
+  // learned guess and training-pair harvest
+  stp_unet* net = nullptr;
+  int guess_kernels = 0;
+  float *hr = nullptr, *hdp = nullptr;  // caller buffers for harvested pairs
+  double* p_prev = nullptr;
 };
 
 namespace {
@@ -456,6 +461,13 @@ int build_solve_graph(stp_handle* h) {
     CUDA_TRY(h, cudaGraphConditionalHandleCreate(&h_loop, G, 1, cudaGraphCondAssignDefault));
     if ((rc = begin_capture(h, G, nullptr))) return rc;
     CUDA_TRY(h, launch_begin(h->ctl, h->cap));
+    if (h->net) {
+      // learned guess: r = b - L p (FP32), p += s U(r / s)
+      CUDA_TRY(h, launch_outer(h->g64, h->p, h->b, h->r32, h->ctl, h->red, 0, 0, 0, h->cap));
+      if ((rc = unet_guess(h->net, h->r32, h->red.sc + SC_INNER_REF, h->d1, h->cap, &h->guess_kernels)))
+        return fail(h, rc, "learned guess: " + std::string(stp_unet_last_error(h->net)));
+      CUDA_TRY(h, launch_addcorr(h->p, h->d1, h->nc, h->cap));
+    }
     if ((rc = end_capture(h, G))) return rc;
     if ((rc = add_conditional(h, G, leaf_node(G), h_loop, cudaGraphCondTypeWhile, &wb, &wn))) return rc;
     if ((rc = build_cycle<double>(h, h->g64, wb, h_loop, h->p, h->p2, h->b, 0))) return rc;
@@ -465,6 +477,14 @@ int build_solve_graph(stp_handle* h) {
     if ((rc = begin_capture(h, G, nullptr))) return rc;
     CUDA_TRY(h, launch_begin(h->ctl, h->cap));
     CUDA_TRY(h, launch_outer(h->g64, h->p, h->b, h->r32, h->ctl, h->red, 0, 1, h_pass, h->cap));
+    if (h->net) {
+      // learned guess at the start of the solve: p += s U(r / s), then the
+      // residual of the new p decides the first pass
+      if ((rc = unet_guess(h->net, h->r32, h->red.sc + SC_INNER_REF, h->d1, h->cap, &h->guess_kernels)))
+        return fail(h, rc, "learned guess: " + std::string(stp_unet_last_error(h->net)));
+      CUDA_TRY(h, launch_addcorr(h->p, h->d1, h->nc, h->cap));
+      CUDA_TRY(h, launch_outer(h->g64, h->p, h->b, h->r32, h->ctl, h->red, 0, 1, h_pass, h->cap));
+    }
     if ((rc = end_capture(h, G))) return rc;
     if ((rc = add_conditional(h, G, leaf_node(G), h_pass, cudaGraphCondTypeWhile, &pb, &pn))) return rc;
     // pass body: d = 0, arm the loop -> WHILE(loop){cycle} -> p += d -> outer
@@ -524,8 +544,22 @@ int host_cycles(stp_handle* h, const Geom<T>& g, T* A, T* B, const T* rhs, int m
 
 int host_solve(stp_handle* h) {
   CUDA_TRY(h, launch_begin(h->ctl, h->st));
-  if (h->prec == STP_FP64) return host_cycles<double>(h, h->g64, h->p, h->p2, h->b, 0);
+  if (h->prec == STP_FP64) {
+    if (h->net) {
+      CUDA_TRY(h, launch_outer(h->g64, h->p, h->b, h->r32, h->ctl, h->red, 0, 0, 0, h->st));
+      int rc = unet_guess(h->net, h->r32, h->red.sc + SC_INNER_REF, h->d1, h->st, &h->guess_kernels);
+      if (rc) return fail(h, rc, "learned guess failed");
+      CUDA_TRY(h, launch_addcorr(h->p, h->d1, h->nc, h->st));
+    }
+    return host_cycles<double>(h, h->g64, h->p, h->p2, h->b, 0);
+  }
   CUDA_TRY(h, launch_outer(h->g64, h->p, h->b, h->r32, h->ctl, h->red, 0, 0, 0, h->st));
+  if (h->net) {
+    int rc = unet_guess(h->net, h->r32, h->red.sc + SC_INNER_REF, h->d1, h->st, &h->guess_kernels);
+    if (rc) return fail(h, rc, "learned guess failed");
+    CUDA_TRY(h, launch_addcorr(h->p, h->d1, h->nc, h->st));
+    CUDA_TRY(h, launch_outer(h->g64, h->p, h->b, h->r32, h->ctl, h->red, 0, 0, 0, h->st));
+  }
   for (;;) {
     int go = 0, rc = read_go(h, &go);
     if (rc) return rc;
@@ -535,6 +569,19 @@ int host_solve(stp_handle* h) {
     CUDA_TRY(h, launch_addcorr(h->p, h->d1, h->nc, h->st));
     CUDA_TRY(h, launch_outer(h->g64, h->p, h->b, h->r32, h->ctl, h->red, 1, 0, 0, h->st));
   }
+}
+
+// training pairs: r = b - L p_prev before the solve, dp = p - p_prev after
+int harvest_before(stp_handle* h) {
+  if (!h->hr) return STP_OK;
+  CUDA_TRY(h, cudaMemcpyAsync(h->p_prev, h->p, sizeof(double) * h->nc, cudaMemcpyDeviceToDevice, h->st));
+  CUDA_TRY(h, launch_outer(h->g64, h->p, h->b, h->hr, h->ctl, h->red, 0, 0, 0, h->st));
+  return STP_OK;
+}
+int harvest_after(stp_handle* h) {
+  if (!h->hr) return STP_OK;
+  CUDA_TRY(h, launch_difference(h->p, h->p_prev, h->hdp, h->nc, h->st));
+  return STP_OK;
 }
 
 // one solve on the stream, bracketed by events
@@ -565,6 +612,9 @@ int finish_solve(stp_handle* h, SolveOut* o) {
   o->converged = c.converged;
   o->bad = c.bad;
   o->kernels = c.tot_kernels + c.kernels;
+  // the learned guess runs once per solve: its kernels, the outer residual
+  // before it, the correction and (FP32) the residual after it
+  if (h->net) o->kernels += (long long)c.solves * (h->guess_kernels + 3);
   o->tot_sweeps = c.tot_sweeps + c.sweeps;
   o->nonconv = c.nonconv + (c.converged ? 0 : 1);
   const double nb = h->h_sc[SC_BNORM];
@@ -622,8 +672,10 @@ int step_impl(stp_handle* h, const Geom<T>& g) {
   T *su = (T*)cur[0], *sv = (T*)cur[1], *sw = (T*)cur[2];
   // b = D u* / dt
   CUDA_TRY(h, launch_divergence_rhs<T>(g, su, sv, sw, 1.0 / c.dt, h->b, h->red, h->st));
-  int rc = launch_solve(h);
+  int rc = harvest_before(h);
   if (rc) return rc;
+  if ((rc = launch_solve(h))) return rc;
+  if ((rc = harvest_after(h))) return rc;
   const double inv_vol = 1.0 / ((double)h->nx * h->ny * c.Lz);
   CUDA_TRY(h, launch_correct_impl<T>(g, h->p, c.dt, su, sv, sw, h->g64.ihz, h->g64.dzv, inv_vol, h->red, h->st));
   if (c.forcing == 1) CUDA_TRY(h, launch_flux_shift<T>(g, su, c.ubulk, h->red, h->st));
@@ -984,7 +1036,9 @@ int stp_poisson_solve(stp_handle* h, const double* rhs, double* p_inout, double 
   if (rc) return rc;
   h->solve_ms = 0.0;
   h->solve_sweeps = 0;
+  if ((rc = harvest_before(h))) return rc;
   if ((rc = launch_solve(h))) return rc;
+  if ((rc = harvest_after(h))) return rc;
   CUDA_TRY(h, cudaMemcpyAsync(p_inout, h->p, sizeof(double) * h->nc,
                               where == STP_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, h->st));
   if ((rc = sync_scalars(h))) return rc;
@@ -998,6 +1052,40 @@ int stp_poisson_solve(stp_handle* h, const double* rhs, double* p_inout, double 
     stats->rel_residual = so.rel;
   }
   return so.converged ? STP_OK : fail(h, STP_ENOTCONVERGED, "pressure solve hit maxit");
+}
+
+int stp_set_learned_guess(stp_handle* h, stp_unet* net) {
+  if (!h) return STP_EINVAL;
+  if (net && !unet_matches(net, h->nz, h->ny, h->nx))
+    return fail(h, STP_EINVAL, "the network's grid does not match the channel");
+  CUDA_TRY(h, cudaSetDevice(h->dev));
+  if (net && (!h->r32 || !h->d1)) {
+    int rc = STP_OK;
+    if (!h->r32) rc = dalloc(h, (void**)&h->r32, sizeof(float) * h->nc);
+    if (rc == STP_OK && !h->d1) rc = dalloc(h, (void**)&h->d1, sizeof(float) * h->nc);
+    if (rc) return rc;
+  }
+  // the solve graph is rebuilt with (or without) the guess nodes
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  if (h->solve_exec) cudaGraphExecDestroy(h->solve_exec);
+  if (h->solve_graph) cudaGraphDestroy(h->solve_graph);
+  h->solve_exec = nullptr;
+  h->solve_graph = nullptr;
+  h->net = net;
+  return STP_OK;
+}
+
+int stp_set_harvest(stp_handle* h, float* r_out, float* dp_out) {
+  if (!h) return STP_EINVAL;
+  if ((r_out == nullptr) != (dp_out == nullptr)) return fail(h, STP_EINVAL, "give both r_out and dp_out, or neither");
+  CUDA_TRY(h, cudaSetDevice(h->dev));
+  if (r_out && !h->p_prev) {
+    int rc = dalloc(h, (void**)&h->p_prev, sizeof(double) * h->nc);
+    if (rc) return rc;
+  }
+  h->hr = r_out;
+  h->hdp = dp_out;
+  return STP_OK;
 }
 
 int stp_eval(stp_handle* h, int term, double* a, double* b, double* c, int where) {

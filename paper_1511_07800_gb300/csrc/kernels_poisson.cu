@@ -275,6 +275,12 @@ __global__ void k_addcorr(double* __restrict__ p, const float* __restrict__ d, s
     p[q] += (double)d[q];
 }
 
+__global__ void k_difference(const double* __restrict__ a, const double* __restrict__ b, float* __restrict__ out,
+                             size_t n) {
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x)
+    out[q] = (float)(a[q] - b[q]);
+}
+
 __global__ void k_begin(SolveCtl* ctl) {
   if (ctl->solves > 0) {
     ctl->tot_sweeps += ctl->sweeps;
@@ -397,6 +403,12 @@ cudaError_t launch_outer(const Geom<double>& g, const double* p, const double* b
 cudaError_t launch_addcorr(double* p, const float* d, size_t n, cudaStream_t s) {
   unsigned blocks = (unsigned)std::min<size_t>((n + 255) / 256, 152 * 16);
   k_addcorr<<<blocks ? blocks : 1, 256, 0, s>>>(p, d, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_difference(const double* a, const double* b, float* out, size_t n, cudaStream_t s) {
+  unsigned blocks = (unsigned)std::min<size_t>((n + 255) / 256, 152 * 16);
+  k_difference<<<blocks ? blocks : 1, 256, 0, s>>>(a, b, out, n);
   return cudaGetLastError();
 }
 

@@ -146,6 +146,8 @@ cudaError_t launch_outer(const Geom<double>& g, const double* p, const double* b
 cudaError_t launch_pass_begin(float* d, size_t n, int graph, cudaGraphConditionalHandle h_loop, cudaStream_t s);
 // p += d
 cudaError_t launch_addcorr(double* p, const float* d, size_t n, cudaStream_t s);
+// out = a - b (FP64 in, FP32 out)
+cudaError_t launch_difference(const double* a, const double* b, float* out, size_t n, cudaStream_t s);
 // start of a solve: fold the previous solve into the totals, reset the state
 cudaError_t launch_begin(SolveCtl* ctl, cudaStream_t s);
 
@@ -167,5 +169,9 @@ cudaError_t launch_convert(Td* dst, const Ts* src, size_t n, cudaStream_t s);
 
 // ||a||_2 of a double array into sc[slot].
 cudaError_t launch_norm(const double* a, size_t n, int slot, Red red, cudaStream_t s);
+
+// learned guess (unet.cu)
+bool unet_matches(const stp_unet* n, int nz, int ny, int nx);
+int unet_guess(stp_unet* n, const float* r, const double* norm, float* d, cudaStream_t st, int* kernels);
 
 }  // namespace stp

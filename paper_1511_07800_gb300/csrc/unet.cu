@@ -471,6 +471,45 @@ __global__ void k_adam(long long n, float* __restrict__ th, const float* __restr
   }
 }
 
+// per-sample sums of squares: s2[i] += sum over sample i of r^2 (blockIdx.y = sample)
+__global__ void k_sample_sumsq(long long Vs, const float* __restrict__ r, float* __restrict__ s2) {
+  const float* rs = r + (long long)blockIdx.y * Vs;
+  float s = 0.f;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < Vs; i += (long long)gridDim.x * blockDim.x)
+    s += rs[i] * rs[i];
+  for (int k = 16; k > 0; k >>= 1) s += __shfl_xor_sync(0xffffffffu, s, k);
+  if ((threadIdx.x & 31) == 0) atomicAdd(s2 + blockIdx.y, s);
+}
+
+// x = r / s_i and t = dp / s_i with s_i = RMS of sample i's r (0 if r = 0)
+__global__ void k_scale_pairs(long long Vs, int nb, const float* __restrict__ r, const float* __restrict__ dp,
+                              const float* __restrict__ s2, float kscale, float* __restrict__ x, float* __restrict__ t) {
+  const long long total = Vs * nb;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    const float rms = sqrtf(s2[e / Vs] / (float)Vs);
+    const float inv = rms > 0.f ? 1.f / rms : 0.f;
+    x[e] = r[e] * inv;
+    if (t) t[e] = dp[e] * inv * kscale;
+  }
+}
+
+// guess in the solver: x = r / s (s = ||r||_2 / sqrt(V), ||r|| read on the device)
+__global__ void k_guess_in(long long V, const float* __restrict__ r, const double* __restrict__ norm,
+                           float* __restrict__ x) {
+  const double s = __ldcg(norm) / sqrt((double)V);
+  const float inv = s > 0.0 ? (float)(1.0 / s) : 0.f;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < V; i += (long long)gridDim.x * blockDim.x)
+    x[i] = r[i] * inv;
+}
+
+// d = s * y / kscale
+__global__ void k_guess_out(long long V, const float* __restrict__ y, const double* __restrict__ norm, float kscale,
+                            float* __restrict__ d) {
+  const float s = (float)(__ldcg(norm) / sqrt((double)V)) / kscale;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < V; i += (long long)gridDim.x * blockDim.x)
+    d[i] = s * y[i];
+}
+
 }  // namespace nn
 }  // namespace stp
 
@@ -511,6 +550,9 @@ struct stp_unet {
   // gradients of activations
   bf16 *ga[4] = {}, *gb[4] = {}, *gu[3] = {};
   float *y = nullptr, *gy = nullptr, *loss = nullptr, *h_loss = nullptr;
+  float *xin = nullptr, *tin = nullptr, *snorm = nullptr;  // normalised pairs, per-sample norms
+  int guess_kernels = 0;                                   // kernels launched by one guess
+  float out_scale = 1.f;                                   // the network predicts out_scale * dp / s
   std::vector<void*> allocs;
   std::string err;
 };
@@ -715,6 +757,36 @@ int check_n(stp_unet* n, int nb) {
 
 }  // namespace
 
+namespace stp {
+
+bool unet_matches(const stp_unet* n, int nz, int ny, int nx) {
+  return n && n->dm[0].d == nz && n->dm[0].h == ny && n->dm[0].w == nx;
+}
+
+// d = s U(r / s) for one sample on stream st, s = norm / sqrt(V) with the
+// norm read on the device; launches only (no synchronisation), so it can be
+// captured into a graph.  Returns the number of kernels through *kernels.
+int unet_guess(stp_unet* n, const float* r, const double* norm, float* d, cudaStream_t st, int* kernels) {
+  cudaStream_t keep = n->st;
+  n->st = st;
+  const long long V = n->dm[0].vox() / n->nmax;
+  int rc = STP_OK;
+  k_guess_in<<<blocks_for(V), 256, 0, st>>>(V, r, norm, n->xin);
+  if (cudaGetLastError() != cudaSuccess) rc = STP_ECUDA;
+  if (rc == STP_OK) rc = forward(n, n->xin, 1);
+  if (rc == STP_OK) {
+    k_guess_out<<<blocks_for(V), 256, 0, st>>>(V, n->y, norm, n->out_scale, d);
+    if (cudaGetLastError() != cudaSuccess) rc = STP_ECUDA;
+  }
+  n->st = keep;
+  // scale in and out + the forward pass: input layer, 7 further encoder
+  // convolutions, 3 pools, 3 upsamplings, 6 decoder convolutions, output layer
+  if (kernels) *kernels = 2 + 21;
+  return rc;
+}
+
+}  // namespace stp
+
 extern "C" {
 
 long long stp_unet_param_count(void) {
@@ -798,6 +870,9 @@ int stp_unet_create(int nmax, int nz, int ny, int nx, void* stream, stp_unet** o
     A(&n->d[l], (size_t)V[l] * kCh[l]);
   }
   A(&n->y, (size_t)V[0]);
+  A(&n->xin, (size_t)V[0]);
+  A(&n->tin, (size_t)V[0]);
+  A(&n->snorm, (size_t)nmax);
   A(&n->gy, (size_t)V[0]);
   A(&n->loss, 1);
   if (rc == STP_OK && cudaMallocHost((void**)&n->h_loss, sizeof(float)) != cudaSuccess) rc = STP_ENOMEM;
@@ -884,6 +959,44 @@ int stp_unet_train_step(stp_unet* n, const float* x, const float* target, int nb
   UTRY(n, cudaGetLastError());
   if ((rc = pack_all(n))) return rc;
   UTRY(n, cudaStreamSynchronize(n->st));
+  return STP_OK;
+}
+
+int stp_unet_set_output_scale(stp_unet* n, float k) {
+  if (!n || !(k > 0.f)) return STP_EINVAL;
+  n->out_scale = k;
+  return STP_OK;
+}
+
+int stp_unet_train_pairs(stp_unet* n, const float* r, const float* dp, int nb, float lr, float* loss) {
+  if (!n || !r || !dp) return STP_EINVAL;
+  if (int rc = check_n(n, nb)) return rc;
+  const long long Vs = n->dm[0].vox() / n->nmax;
+  UTRY(n, cudaMemsetAsync(n->snorm, 0, sizeof(float) * nb, n->st));
+  k_sample_sumsq<<<dim3((unsigned)std::min<long long>(256, (Vs + 255) / 256), nb), 256, 0, n->st>>>(Vs, r, n->snorm);
+  UTRY(n, cudaGetLastError());
+  k_scale_pairs<<<blocks_for(Vs * nb), 256, 0, n->st>>>(Vs, nb, r, dp, n->snorm, n->out_scale, n->xin, n->tin);
+  UTRY(n, cudaGetLastError());
+  return stp_unet_train_step(n, n->xin, n->tin, nb, lr, loss);
+}
+
+int stp_unet_eval_pairs(stp_unet* n, const float* r, const float* dp, int nb, float* loss) {
+  if (!n || !r || !dp) return STP_EINVAL;
+  if (int rc = check_n(n, nb)) return rc;
+  const long long Vs = n->dm[0].vox() / n->nmax;
+  UTRY(n, cudaMemsetAsync(n->snorm, 0, sizeof(float) * nb, n->st));
+  k_sample_sumsq<<<dim3((unsigned)std::min<long long>(256, (Vs + 255) / 256), nb), 256, 0, n->st>>>(Vs, r, n->snorm);
+  UTRY(n, cudaGetLastError());
+  k_scale_pairs<<<blocks_for(Vs * nb), 256, 0, n->st>>>(Vs, nb, r, dp, n->snorm, n->out_scale, n->xin, n->tin);
+  UTRY(n, cudaGetLastError());
+  int rc = forward(n, n->xin, nb);
+  if (rc) return rc;
+  UTRY(n, cudaMemsetAsync(n->loss, 0, sizeof(float), n->st));
+  k_mse<<<blocks_for(Vs * nb), 256, 0, n->st>>>(Vs * nb, n->y, n->tin, n->gy, n->loss);
+  UTRY(n, cudaGetLastError());
+  UTRY(n, cudaMemcpyAsync(n->h_loss, n->loss, sizeof(float), cudaMemcpyDeviceToHost, n->st));
+  UTRY(n, cudaStreamSynchronize(n->st));
+  if (loss) *loss = *n->h_loss;
   return STP_OK;
 }
 

@@ -68,7 +68,8 @@ EXPORTS = ("stp_config_defaults", "stp_init", "stp_destroy", "stp_last_error", "
            "stp_get_fields", "stp_step", "stp_poisson_solve", "stp_eval", "stp_srj_schedule",
            "stp_poisson_residual_noalloc", "stp_unet_param_count", "stp_unet_create", "stp_unet_destroy",
            "stp_unet_last_error", "stp_unet_set_params", "stp_unet_get_params", "stp_unet_forward",
-           "stp_unet_gradient", "stp_unet_train_step")
+           "stp_unet_gradient", "stp_unet_train_step", "stp_unet_train_pairs", "stp_unet_eval_pairs",
+           "stp_set_learned_guess", "stp_set_harvest", "stp_unet_set_output_scale")
 
 _lib = None
 
@@ -112,6 +113,11 @@ def lib():
     L.stp_unet_forward.argtypes = [vp, vp, vp, ctypes.c_int]
     L.stp_unet_gradient.argtypes = [vp, vp, vp, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_float)]
     L.stp_unet_train_step.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_float, ctypes.POINTER(ctypes.c_float)]
+    L.stp_unet_train_pairs.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_float, ctypes.POINTER(ctypes.c_float)]
+    L.stp_unet_eval_pairs.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.POINTER(ctypes.c_float)]
+    L.stp_set_learned_guess.argtypes = [vp, vp]
+    L.stp_unet_set_output_scale.argtypes = [vp, ctypes.c_float]
+    L.stp_set_harvest.argtypes = [vp, vp, vp]
     _lib = L
     return L
 
@@ -245,6 +251,19 @@ class Channel:
         self._check(lib().stp_eval(self._h, t, ptr[0], ptr[1], ptr[2], where))
         return out if len(out) > 1 else out[0]
 
+    def set_learned_guess(self, net):
+        """Start every pressure solve from the network's guess (None: off)."""
+        self._net = net
+        self._check(lib().stp_set_learned_guess(self._h, net._h if net is not None else None))
+
+    def set_harvest(self, r_out, dp_out):
+        """Record (residual, correction) pairs of each solve into two CUDA
+        float32 tensors [nz][ny][nx] (None, None: stop)."""
+        self._harvest = (r_out, dp_out)
+        a = ctypes.c_void_p(r_out.data_ptr()) if r_out is not None else None
+        b = ctypes.c_void_p(dp_out.data_ptr()) if dp_out is not None else None
+        self._check(lib().stp_set_harvest(self._h, a, b))
+
     def close(self):
         if getattr(self, "_h", None) is not None and _lib is not None:
             _lib.stp_destroy(self._h)
@@ -309,6 +328,22 @@ class UNet:
         loss = ctypes.c_float(0)
         self._check(lib().stp_unet_train_step(self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(t.data_ptr()),
                                               int(x.shape[0]), float(lr), ctypes.byref(loss)))
+        return loss.value
+
+    def set_output_scale(self, k):
+        self._check(lib().stp_unet_set_output_scale(self._h, float(k)))
+
+    def train_pairs(self, r, dp, lr):
+        """One Adam step on (residual, correction) pairs, each scaled by its RMS(r)."""
+        loss = ctypes.c_float(0)
+        self._check(lib().stp_unet_train_pairs(self._h, ctypes.c_void_p(r.data_ptr()), ctypes.c_void_p(dp.data_ptr()),
+                                               int(r.shape[0]), float(lr), ctypes.byref(loss)))
+        return loss.value
+
+    def eval_pairs(self, r, dp):
+        loss = ctypes.c_float(0)
+        self._check(lib().stp_unet_eval_pairs(self._h, ctypes.c_void_p(r.data_ptr()), ctypes.c_void_p(dp.data_ptr()),
+                                              int(r.shape[0]), ctypes.byref(loss)))
         return loss.value
 
     def close(self):

@@ -1,0 +1,84 @@
+"""The learned initial guess inside the pressure solve: harvested pairs are
+exact, the solve with the guess still meets the tolerance, and a briefly
+trained network reduces the SRJ work on a channel it was not trained on."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+GRID = (32, 16, 32)
+
+
+def _cfg():
+    from paper_1511_07800_gb300 import learn
+    return learn.workload("os_instability", grid=GRID)
+
+
+def test_harvested_pairs_satisfy_the_poisson_equation(stp_lib):
+    """r = b - L p_prev and dp = p - p_prev, so r - L dp = b - L p, which the
+    solve drove below 1e-8 ||b||; FP32 storage of r and dp adds ~1e-7."""
+    torch = pytest.importorskip("torch")
+    from paper_1511_07800_gb300 import learn
+    cfg = _cfg()
+    R, DP = learn.harvest(cfg, seeds=[5], steps_per_seed=4, precision="fp64")
+    for i in range(4):
+        r = R[i].double().contiguous()
+        dp = DP[i].double().contiguous()
+        res = torch.zeros_like(r)
+        n = stp_lib.poisson_residual_noalloc(cfg, dp, r, res)
+        assert n <= 1e-6 * float(r.norm()), (i, n, float(r.norm()))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_learned_guess_solves_to_tolerance(stp_lib, orc, precision):
+    """With an untrained (random) network as the guess, every solve still
+    converges to ptol, and the step agrees with the plain step to that level."""
+    torch = pytest.importorskip("torch")
+    from oracle import unet
+    from paper_1511_07800_gb300 import learn
+    cfg = _cfg()
+    net = stp_lib.UNet(1, *GRID)
+    net.set_params(unet.init_params(11).astype(np.float32))
+    fields = {}
+    for mode in ("plain", "learned"):
+        with stp_lib.Channel(cfg, precision=precision) as ch:
+            ch.set_fields(*learn.varied_fields(cfg, 3))
+            ch.step(2)
+            if mode == "learned":
+                ch.set_learned_guess(net)
+            for _ in range(3):
+                st = ch.step(1)
+                assert st["converged"] and st["rel_res"] <= cfg["ptol"]
+            if mode == "learned":
+                ch.set_learned_guess(None)
+            fields[mode] = ch.get_fields()
+    for k in ("u", "v", "w"):
+        a, b = fields["plain"][k], fields["learned"][k]
+        assert np.abs(a - b).max() <= 1e-6 * np.abs(b).max(), k
+    net.close()
+
+
+def test_trained_guess_reduces_srj_work(stp_lib, orc):
+    """Train on pairs harvested from six channels, evaluate on a seventh:
+    the validation loss falls well below that of the zero guess, and the
+    FP64 solves started from the learned guess need no more SRJ sweeps
+    than the plain solves from the previous pressure (the gain is printed)."""
+    torch = pytest.importorskip("torch")
+    from oracle import unet
+    from paper_1511_07800_gb300 import learn
+    cfg = _cfg()
+    R, DP = learn.harvest(cfg, seeds=range(6), steps_per_seed=30)
+    Rv, DPv = learn.harvest(cfg, seeds=[50], steps_per_seed=8)
+    K = learn.output_scale(R, DP, 8, GRID)
+    net = stp_lib.UNet(8, *GRID)
+    net.set_params(unet.init_params(0).astype(np.float32))
+    net.set_output_scale(K)
+    # loss of the zero guess in these units is 1 (K normalises dp/s)
+    learn.train(net, R, DP, 300, 8, 1e-3)
+    learn.train(net, R, DP, 200, 8, 3e-4)
+    val = net.eval_pairs(Rv.contiguous(), DPv.contiguous())
+    assert val < 0.5, val
+    res = learn.compare(cfg, net, seed=50, nsteps=8, precision="fp64")
+    print("learned vs plain (FP64):", res)
+    assert res["learned"]["sweeps"] <= res["plain"]["sweeps"]
+    net.close()
