@@ -23,7 +23,12 @@
  * returns; it owns all its device memory and frees it in stp_destroy.
  *
  * The pressure solve runs as one CUDA graph steered from the device (graph
- * conditional nodes).  With the environment variable STP_HOST_SOLVE=1 at
+ * conditional nodes), one kernel per SRJ sweep.  With STP_PERSISTENT=1 at
+ * stp_init an FP32 cycle instead runs as one persistent cooperative kernel
+ * with bounded grid barriers between its sweeps (slower on GB300: kept as an
+ * option).  The FP32 sweep kernel's tile shape (z levels per thread, rows
+ * per block) is picked on first use by timing the variants on the grid
+ * (STP_SWEEP_VARIANT=<0..5> forces one).  With the environment variable STP_HOST_SOLVE=1 at
  * stp_init the same kernels are driven from the host instead, one host
  * round trip per SRJ cycle (for profilers that cannot see kernels inside
  * conditional graphs).
@@ -46,6 +51,7 @@ extern "C" {
 #define STP_ENOTCONVERGED (-4) /* pressure solve hit its sweep cap              */
 #define STP_EDIVERGED (-5)     /* NaN/Inf in a residual or the velocity         */
 #define STP_ECFL (-6)          /* U_max dt > 0.1 dx (Eq. cfl_cond), if checked   */
+#define STP_ETIMEOUT (-7)      /* a bounded device-side wait ran out              */
 
 #define STP_HOST 0
 #define STP_DEVICE 1

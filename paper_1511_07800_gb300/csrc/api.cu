@@ -5,6 +5,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <cstring>
 #include <new>
 #include <string>
@@ -68,6 +71,11 @@ struct stp_handle {
   cudaGraph_t solve_graph = nullptr;
   cudaGraphExec_t solve_exec = nullptr;
   bool host_solve = false;     // STP_HOST_SOLVE=1: drive the solve from the host
+  int cycle_blocks = 0;        // >0: FP32 cycles run as one persistent cooperative kernel
+  int sweep_variant = -1;      // FP32 sweep kernel variant chosen by the autotuner (-1: not yet)
+  float sweep_us = 0.f;        // its measured time per sweep
+  float* d_omega32 = nullptr;  // the schedule on the device (FP32)
+  GridBar bar{};
   // learned guess and training-pair harvest
   stp_unet* net = nullptr;
   int guess_kernels = 0;
@@ -440,6 +448,12 @@ int build_cycle(stp_handle* h, const Geom<T>& g, cudaGraph_t wb, cudaGraphCondit
   if ((rc = add_conditional(h, wb, leaf_node(wb), h_body, cudaGraphCondTypeIf, &ib, &ifn))) return rc;
   if ((rc = begin_capture(h, ib, nullptr))) return rc;
   const int M = (int)h->omega.size();
+  if (sizeof(T) == sizeof(float) && h->cycle_blocks > 0) {
+    // the whole cycle in one persistent kernel
+    CUDA_TRY(h, launch_cycle_f32(h->g32, (float*)A, (float*)B, (const float*)rhs, h->d_omega32, M, h->bar, h->ctl,
+                                 h->cycle_blocks, h->cap));
+    return end_capture(h, ib);
+  }
   for (int m = 0; m < M; m++) {
     const T* src = (m % 2 == 0) ? A : B;
     T* dst = (m % 2 == 0) ? B : A;
@@ -448,8 +462,63 @@ int build_cycle(stp_handle* h, const Geom<T>& g, cudaGraph_t wb, cudaGraphCondit
   return end_capture(h, ib);
 }
 
+// Autotuner of the FP32 sweep kernel: times every variant valid for this
+// grid (3 warm-up and 20 timed launches each, CUDA events on the handle's
+// stream, on the handle's own scratch buffers) and keeps the fastest; the
+// choice is cached per (device, nx, ny, nz).  STP_SWEEP_VARIANT=<v> forces a
+// variant.  All variants compute the same values.
+int tune_sweep(stp_handle* h) {
+  if (h->sweep_variant >= 0) return STP_OK;
+  h->sweep_variant = 0;
+  if (h->prec != STP_FP32_REFINE || h->nx % 4) return STP_OK;
+  if (const char* env = std::getenv("STP_SWEEP_VARIANT")) {
+    const int v = std::atoi(env);
+    if (sweep_variant_ok(v, h->nz)) h->sweep_variant = v;
+    return STP_OK;
+  }
+  static std::mutex mu;
+  static std::map<std::tuple<int, int, int, int>, std::pair<int, float>> cache;
+  const auto key = std::make_tuple(h->dev, h->nx, h->ny, h->nz);
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+      h->sweep_variant = it->second.first;
+      h->sweep_us = it->second.second;
+      return STP_OK;
+    }
+  }
+  CUDA_TRY(h, cudaMemsetAsync(h->d1, 0, sizeof(float) * h->nc, h->st));
+  CUDA_TRY(h, cudaMemsetAsync(h->r32, 0, sizeof(float) * h->nc, h->st));
+  float best = 1e30f;
+  int bv = 0;
+  for (int v = 0; v < sweep_variant_count(); v++) {
+    if (!sweep_variant_ok(v, h->nz)) continue;
+    set_sweep_variant(v);
+    for (int w = 0; w < 3; w++) CUDA_TRY(h, launch_sweep<float>(h->g32, h->d1, h->r32, 1.0f, h->d2, h->st));
+    CUDA_TRY(h, cudaEventRecord(h->ev0, h->st));
+    for (int w = 0; w < 20; w++)
+      CUDA_TRY(h, launch_sweep<float>(h->g32, (w & 1) ? h->d2 : h->d1, h->r32, 1.0f, (w & 1) ? h->d1 : h->d2, h->st));
+    CUDA_TRY(h, cudaEventRecord(h->ev1, h->st));
+    CUDA_TRY(h, cudaEventSynchronize(h->ev1));
+    float ms = 0.f;
+    CUDA_TRY(h, cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+    if (ms < best) {
+      best = ms;
+      bv = v;
+    }
+  }
+  h->sweep_variant = bv;
+  h->sweep_us = best * 1e3f / 20.f;
+  std::lock_guard<std::mutex> lock(mu);
+  cache[key] = std::make_pair(bv, h->sweep_us);
+  return STP_OK;
+}
+
 int build_solve_graph(stp_handle* h) {
   if (h->solve_exec) return STP_OK;
+  if (int rc = tune_sweep(h)) return rc;
+  set_sweep_variant(h->sweep_variant);
   cudaGraph_t G;
   CUDA_TRY(h, cudaGraphCreate(&G, 0));
   h->solve_graph = G;
@@ -537,12 +606,19 @@ int host_cycles(stp_handle* h, const Geom<T>& g, T* A, T* B, const T* rhs, int m
     int go = 0, rc = read_go(h, &go);
     if (rc) return rc;
     if (!go) return STP_OK;
+    if (sizeof(T) == sizeof(float) && h->cycle_blocks > 0) {
+      CUDA_TRY(h, launch_cycle_f32(h->g32, (float*)A, (float*)B, (const float*)rhs, h->d_omega32, M, h->bar, h->ctl,
+                                   h->cycle_blocks, h->st));
+      continue;
+    }
     for (int m = 0; m < M; m++)
       CUDA_TRY(h, launch_sweep<T>(g, (m % 2 == 0) ? A : B, rhs, (T)h->omega[m], (m % 2 == 0) ? B : A, h->st));
   }
 }
 
 int host_solve(stp_handle* h) {
+  if (int rc = tune_sweep(h)) return rc;
+  set_sweep_variant(h->sweep_variant);
   CUDA_TRY(h, launch_begin(h->ctl, h->st));
   if (h->prec == STP_FP64) {
     if (h->net) {
@@ -896,7 +972,19 @@ int stp_init(const stp_config* cfg, stp_handle** out) {
   A((void**)&h->red.sc, sizeof(double) * SC_COUNT);
   A((void**)&h->red.flag, sizeof(int) * FL_COUNT);
   A((void**)&h->ctl, sizeof(SolveCtl));
+  A((void**)&h->d_omega32, sizeof(float) * h->omega.size());
+  A((void**)&h->bar.count, sizeof(unsigned) * 4);
   if (rc) return bail(rc);
+  h->bar.gen = h->bar.count + 1;
+  h->bar.err = (int*)(h->bar.count + 2);
+  {
+    // persistent FP32 cycles (STP_PERSISTENT=1) need rows of whole float4
+    // units; off by default: on GB300 a grid barrier between sweeps costs
+    // more than a graph-launched kernel boundary
+    const char* env = std::getenv("STP_PERSISTENT");
+    const bool allow = env && env[0] == '1';
+    if (allow && h->prec == STP_FP32_REFINE && h->nx % 4 == 0) h->cycle_blocks = cycle_grid_f32(h->dev);
+  }
   if (cudaMallocHost((void**)&h->h_sc, sizeof(double) * SC_COUNT) != cudaSuccess ||
       cudaMallocHost((void**)&h->h_flag, sizeof(int) * FL_COUNT) != cudaSuccess ||
       cudaMallocHost((void**)&h->h_ctl, sizeof(SolveCtl)) != cudaSuccess)
@@ -924,6 +1012,12 @@ int stp_init(const stp_config* cfg, stp_handle** out) {
   if (e == cudaSuccess) e = cudaMemsetAsync(h->red.sc, 0, sizeof(double) * SC_COUNT, h->st);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->red.flag, 0, sizeof(int) * FL_COUNT, h->st);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->ctl, 0, sizeof(SolveCtl), h->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->bar.count, 0, sizeof(unsigned) * 4, h->st);
+  if (e == cudaSuccess) {
+    std::vector<float> om32(h->omega.begin(), h->omega.end());
+    e = cudaMemcpyAsync(h->d_omega32, om32.data(), sizeof(float) * om32.size(), cudaMemcpyHostToDevice, h->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
   if (e != cudaSuccess) return bail(fail(h, STP_ECUDA, std::string("init copies: ") + cudaGetErrorString(e)));
   *out = h;
@@ -998,6 +1092,7 @@ int stp_step(stp_handle* h, int nsteps, stp_step_stats* stats) {
     if (rc) return rc;
     if ((rc = sync_scalars(h))) return rc;
     if ((rc = finish_solve(h, &so))) return rc;
+    if (so.bad == 2) return fail(h, STP_ETIMEOUT, "a grid barrier of the persistent SRJ cycle timed out");
     if (so.bad) return fail(h, STP_EDIVERGED, "NaN or Inf in the pressure residual");
     if (h->h_flag[FL_BAD]) return fail(h, STP_EDIVERGED, "NaN or Inf in the velocity");
   }
@@ -1044,6 +1139,7 @@ int stp_poisson_solve(stp_handle* h, const double* rhs, double* p_inout, double 
   if ((rc = sync_scalars(h))) return rc;
   SolveOut so;
   if ((rc = finish_solve(h, &so))) return rc;
+  if (so.bad == 2) return fail(h, STP_ETIMEOUT, "a grid barrier of the persistent SRJ cycle timed out");
   if (so.bad) return fail(h, STP_EDIVERGED, "NaN or Inf in the pressure residual");
   if (stats) {
     stats->sweeps = so.sweeps;

@@ -42,15 +42,34 @@ __device__ __forceinline__ T point_residual(const Geom<T>& g, const T* __restric
   return __ldg(b + q) - lap;
 }
 
+// One FP32 SRJ update in difference form with a fixed rounding sequence
+// (explicit round-to-nearest operations), shared by every FP32 sweep kernel
+// so that all of them produce bitwise the same values.
+__device__ __forceinline__ float srj_cell_f32(float pc, float xl, float xr, float nn, float ss, float uu, float dd,
+                                              float bb, float idx2, float idy2, float cup, float cdn, float iS,
+                                              float om) {
+  float lap = __fmul_rn(idx2, __fadd_rn(__fsub_rn(xr, pc), __fsub_rn(xl, pc)));
+  lap = __fmaf_rn(idy2, __fadd_rn(__fsub_rn(nn, pc), __fsub_rn(ss, pc)), lap);
+  lap = __fmaf_rn(cup, __fsub_rn(uu, pc), lap);
+  lap = __fmaf_rn(cdn, __fsub_rn(dd, pc), lap);
+  return __fmaf_rn(-om, __fmul_rn(__fsub_rn(bb, lap), iS), pc);
+}
+
 // FP32: difference form (no cancellation against S p).
 __global__ void __launch_bounds__(kBX* kBY) k_sweep_f32(Geom<float> g, const float* __restrict__ p,
                                                          const float* __restrict__ b, float omega,
                                                          float* __restrict__ out) {
   const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y, k = blockIdx.z;
   if (i >= g.nx || j >= g.ny) return;
-  float pc;
-  const float r = point_residual(g, p, b, i, j, k, &pc);
-  out[(k * g.ny + j) * g.nx + i] = pc - omega * r * __ldg(g.iS + k);
+  const int nx = g.nx, plane = g.nx * g.ny;
+  const int ip = i == nx - 1 ? 0 : i + 1, im = i == 0 ? nx - 1 : i - 1;
+  const int jp = j == g.ny - 1 ? 0 : j + 1, jm = j == 0 ? g.ny - 1 : j - 1;
+  const int row = k * plane, q = row + j * nx + i;
+  const float pc = __ldg(p + q);
+  const float uu = k < g.nz - 1 ? __ldg(p + q + plane) : pc, dd = k > 0 ? __ldg(p + q - plane) : pc;
+  out[q] = srj_cell_f32(pc, __ldg(p + row + j * nx + im), __ldg(p + row + j * nx + ip), __ldg(p + row + jp * nx + i),
+                        __ldg(p + row + jm * nx + i), uu, dd, __ldg(b + q), g.idx2, g.idy2, __ldg(g.cup + k),
+                        __ldg(g.cdn + k), __ldg(g.iS + k), omega);
 }
 
 // FP64: the neighbour-sum form p + omega (p^J - p), p^J = (sum_nb c p_nb - b)/S,
@@ -115,9 +134,7 @@ __global__ void __launch_bounds__(kBX* kBY) k_sweep_f32_v4(Geom<float> g, const 
   const float4 zd = has_dn ? __ldg(P + rc - plane4 + xx) : c;
   const float4 bq = __ldg(reinterpret_cast<const float4*>(b) + rc + xx);
   auto cell = [&](float pc, float xl, float xr, float nn, float ss, float uu, float dd, float bb) {
-    const float lap = idx2 * ((xr - pc) + (xl - pc)) + idy2 * ((nn - pc) + (ss - pc)) + cup * (uu - pc) +
-                      cdn * (dd - pc);
-    return pc - omega * (bb - lap) * iS;
+    return srj_cell_f32(pc, xl, xr, nn, ss, uu, dd, bb, idx2, idy2, cup, cdn, iS, omega);
   };
   float4 o;
   o.x = cell(c.x, left, c.y, yn.x, ys.x, zu.x, zd.x, bq.x);
@@ -125,6 +142,59 @@ __global__ void __launch_bounds__(kBX* kBY) k_sweep_f32_v4(Geom<float> g, const 
   o.z = cell(c.z, c.y, c.w, yn.z, ys.z, zu.z, zd.z, bq.z);
   o.w = cell(c.w, c.z, right, yn.w, ys.w, zu.w, zd.w, bq.w);
   if (active) reinterpret_cast<float4*>(out)[rc + x4] = o;
+}
+
+// The same FP32 sweep with KZ consecutive z levels per thread (the z
+// neighbours inside the column come from registers, and a thread has KZ
+// rows of loads in flight) and BY rows per block.  nz must be a multiple of
+// KZ.  Identical arithmetic per cell for every (KZ, BY).
+template <int KZ, int BY>
+__global__ void __launch_bounds__(kBX* BY) k_sweep_f32_z(Geom<float> g, const float* __restrict__ p,
+                                                          const float* __restrict__ b, float omega,
+                                                          float* __restrict__ out) {
+  const int lane = threadIdx.x;
+  const int nx = g.nx, ny = g.ny, nx4 = nx >> 2;
+  const int x4 = blockIdx.x * kBX + lane;
+  const int j = blockIdx.y * BY + threadIdx.y, k0 = blockIdx.z * KZ;
+  const bool active = x4 < nx4 && j < ny;
+  const int xx = x4 < nx4 ? x4 : nx4 - 1;
+  const int jj = j < ny ? j : ny - 1;
+  const int jp = jj == ny - 1 ? 0 : jj + 1, jm = jj == 0 ? ny - 1 : jj - 1;
+  const size_t plane4 = (size_t)nx4 * ny;
+  const size_t r0 = ((size_t)k0 * ny + jj) * nx4 + xx;  // this thread's unit at level k0
+  const float idx2 = g.idx2, idy2 = g.idy2;
+  cudaGridDependencySynchronize();
+  const float4* P = reinterpret_cast<const float4*>(p);
+  float4 c[KZ + 2];
+#pragma unroll
+  for (int q = 0; q < KZ; q++) c[q + 1] = __ldg(P + r0 + q * plane4);
+  c[0] = k0 > 0 ? __ldg(P + r0 - plane4) : c[1];
+  c[KZ + 1] = k0 + KZ < g.nz ? __ldg(P + r0 + KZ * plane4) : c[KZ];
+#pragma unroll
+  for (int q = 0; q < KZ; q++) {
+    const int k = k0 + q;
+    const size_t rc = r0 + q * plane4;
+    const size_t rowbase = ((size_t)k * ny + jj) * nx4;
+    const float cup = __ldg(g.cup + k), cdn = __ldg(g.cdn + k), iS = __ldg(g.iS + k);
+    const float4 cc = c[q + 1], zu = c[q + 2], zd = c[q];
+    float left = __shfl_up_sync(0xffffffffu, cc.w, 1);
+    float right = __shfl_down_sync(0xffffffffu, cc.x, 1);
+    const float* prow = p + rowbase * 4;
+    if (lane == 0 || xx == 0) left = __ldg(prow + (4 * xx - 1 + nx) % nx);
+    if (lane == kBX - 1 || xx == nx4 - 1) right = __ldg(prow + (4 * xx + 4) % nx);
+    const float4 yn = __ldg(P + ((size_t)k * ny + jp) * nx4 + xx);
+    const float4 ys = __ldg(P + ((size_t)k * ny + jm) * nx4 + xx);
+    const float4 bq = __ldg(reinterpret_cast<const float4*>(b) + rc);
+    auto cell = [&](float pc, float xl, float xr, float nn, float ss, float uu, float dd, float bb) {
+      return srj_cell_f32(pc, xl, xr, nn, ss, uu, dd, bb, idx2, idy2, cup, cdn, iS, omega);
+    };
+    float4 o;
+    o.x = cell(cc.x, left, cc.y, yn.x, ys.x, zu.x, zd.x, bq.x);
+    o.y = cell(cc.y, cc.x, cc.z, yn.y, ys.y, zu.y, zd.y, bq.y);
+    o.z = cell(cc.z, cc.y, cc.w, yn.z, ys.z, zu.z, zd.z, bq.z);
+    o.w = cell(cc.w, cc.z, right, yn.w, ys.w, zu.w, zd.w, bq.w);
+    if (active) reinterpret_cast<float4*>(out)[rc] = o;
+  }
 }
 
 template <bool PDL>
@@ -166,6 +236,102 @@ __global__ void __launch_bounds__(kBX* kBY) k_sweep_f64_v2(Geom<double> g, const
   o.x = cell(c.x, left, c.y, yn.x, ys.x, zu.x, zd.x, bq.x);
   o.y = cell(c.y, c.x, right, yn.y, ys.y, zu.y, zd.y, bq.y);
   if (active) reinterpret_cast<double2*>(out)[rc + x2] = o;
+}
+
+// ---------------------------------------------------------------------------
+// One whole SRJ cycle in a single cooperative launch (FP32): the M sweeps
+// ping-pong between A and B with a grid barrier between consecutive sweeps,
+// so the cycle costs one launch instead of M.  The grid is exactly the
+// co-resident size (cooperative launch guarantees co-residency).  p is read
+// with L2-coherent loads (__ldcg): another SM wrote it in the previous
+// sweep.  Work: warps take chunks of 32 consecutive float4 units (4 cells of
+// a row each) in a grid-stride loop; a unit's x-neighbours come from the
+// adjacent lanes when they hold the same row, else by a scalar load.
+// Every barrier wait is bounded (about one second of clock); on time-out
+// the kernel sets ctl->bad = 2 and returns.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool grid_barrier(GridBar bar, unsigned nblocks) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    volatile unsigned* vgen = bar.gen;
+    const unsigned g0 = *vgen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(bar.count, 1u);
+    if (arrived == nblocks - 1) {
+      atomicExch(bar.count, 0u);
+      __threadfence();
+      atomicAdd(bar.gen, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*vgen == g0) {
+        if (clock64() - t0 > 2000000000LL) {
+          atomicExch(bar.err, 1);
+          break;
+        }
+      }
+    }
+    __threadfence();
+    if (*(volatile int*)bar.err) ok = 0;
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+__global__ void __launch_bounds__(1024, 1) k_cycle_f32(Geom<float> g, float* A, float* B, const float* __restrict__ b,
+                                                       const float* __restrict__ omega, int M, GridBar bar,
+                                                       SolveCtl* ctl) {
+  const int nx = g.nx, ny = g.ny, nx4 = nx >> 2;
+  const long long nunits = (long long)nx4 * ny * g.nz;
+  const long long nchunks = (nunits + 31) / 32;
+  const int lane = threadIdx.x & 31;
+  const long long warp0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  const size_t plane4 = (size_t)nx4 * ny;
+  const float idx2 = g.idx2, idy2 = g.idy2;
+  for (int m = 0; m < M; m++) {
+    const float* src = (m & 1) ? B : A;
+    float* dst = (m & 1) ? A : B;
+    const float om = __ldg(omega + m);
+    const float4* P = reinterpret_cast<const float4*>(src);
+    for (long long ch = warp0; ch < nchunks; ch += nwarps) {
+      const long long u0 = ch * 32 + lane;
+      const bool active = u0 < nunits;
+      const long long u = active ? u0 : nunits - 1;
+      const int x4 = (int)(u % nx4);
+      const long long rr = u / nx4;
+      const int j = (int)(rr % ny), k = (int)(rr / ny);
+      const int jp = j == ny - 1 ? 0 : j + 1, jm = j == 0 ? ny - 1 : j - 1;
+      const size_t rc = ((size_t)k * ny + j) * nx4;
+      const float cup = __ldg(g.cup + k), cdn = __ldg(g.cdn + k), iS = __ldg(g.iS + k);
+      const float4 c = __ldcg(P + rc + x4);
+      float left = __shfl_up_sync(0xffffffffu, c.w, 1);
+      float right = __shfl_down_sync(0xffffffffu, c.x, 1);
+      const float* prow = src + rc * 4;
+      if (lane == 0 || x4 == 0) left = __ldcg(prow + (4 * x4 - 1 + nx) % nx);
+      if (lane == 31 || x4 == nx4 - 1) right = __ldcg(prow + (4 * x4 + 4) % nx);
+      const float4 yn = __ldcg(P + ((size_t)k * ny + jp) * nx4 + x4);
+      const float4 ys = __ldcg(P + ((size_t)k * ny + jm) * nx4 + x4);
+      const float4 zu = k < g.nz - 1 ? __ldcg(P + rc + plane4 + x4) : c;
+      const float4 zd = k > 0 ? __ldcg(P + rc - plane4 + x4) : c;
+      const float4 bq = __ldg(reinterpret_cast<const float4*>(b) + rc + x4);
+      auto cell = [&](float pc, float xl, float xr, float nn, float ss, float uu, float dd, float bb) {
+        return srj_cell_f32(pc, xl, xr, nn, ss, uu, dd, bb, idx2, idy2, cup, cdn, iS, om);
+      };
+      float4 o;
+      o.x = cell(c.x, left, c.y, yn.x, ys.x, zu.x, zd.x, bq.x);
+      o.y = cell(c.y, c.x, c.z, yn.y, ys.y, zu.y, zd.y, bq.y);
+      o.z = cell(c.z, c.y, c.w, yn.z, ys.z, zu.z, zd.z, bq.z);
+      o.w = cell(c.w, c.z, right, yn.w, ys.w, zu.w, zd.w, bq.w);
+      if (active) reinterpret_cast<float4*>(dst)[rc + x4] = o;
+    }
+    if (m + 1 < M && !grid_barrier(bar, gridDim.x)) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) ctl->bad = 2;
+      return;
+    }
+  }
 }
 
 // arms the inner loop of a refinement pass and clears its correction
@@ -351,10 +517,46 @@ static cudaError_t launch_pdl(K kern, dim3 grid, dim3 block, cudaStream_t s, con
   return cudaLaunchKernelEx(&cfg, kern, g, p, b, omega, out);
 }
 
+// FP32 sweep variants: 0 = one level per thread, 32 x 8 block (k_sweep_f32_v4);
+// 1..5 = (KZ, BY) in {(2,8), (4,8), (2,4), (4,4), (8,4)} (k_sweep_f32_z).
+static thread_local int t_sweep_variant = 0;
+void set_sweep_variant(int v) { t_sweep_variant = v; }
+int sweep_variant_count() { return 6; }
+bool sweep_variant_ok(int v, int nz) {
+  static const int kz[6] = {1, 2, 4, 2, 4, 8};
+  return v >= 0 && v < 6 && nz % kz[v] == 0;
+}
+
+template <int KZ, int BY>
+static cudaError_t launch_z(const Geom<float>& g, const float* p, const float* b, float omega, float* out,
+                            cudaStream_t s) {
+  const dim3 grid((g.nx / 4 + kBX - 1) / kBX, (g.ny + BY - 1) / BY, g.nz / KZ), block(kBX, BY, 1);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, k_sweep_f32_z<KZ, BY>, g, p, b, omega, out);
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
+
 template <>
 cudaError_t launch_sweep<float>(const Geom<float>& g, const float* p, const float* b, float omega, float* out,
                                 cudaStream_t s) {
   if (g.nx % 4 == 0) {
+    const int v = sweep_variant_ok(t_sweep_variant, g.nz) ? t_sweep_variant : 0;
+    switch (v) {
+      case 1: return launch_z<2, 8>(g, p, b, omega, out, s);
+      case 2: return launch_z<4, 8>(g, p, b, omega, out, s);
+      case 3: return launch_z<2, 4>(g, p, b, omega, out, s);
+      case 4: return launch_z<4, 4>(g, p, b, omega, out, s);
+      case 5: return launch_z<8, 4>(g, p, b, omega, out, s);
+      default: break;
+    }
     const dim3 grid((g.nx / 4 + kBX - 1) / kBX, (g.ny + kBY - 1) / kBY, g.nz), block(kBX, kBY, 1);
     cudaError_t e = launch_pdl(k_sweep_f32_v4<true>, grid, block, s, g, p, b, omega, out);
     return e != cudaSuccess ? e : cudaGetLastError();
@@ -374,6 +576,29 @@ cudaError_t launch_sweep<double>(const Geom<double>& g, const double* p, const d
   Launch l = plane_launch(g.nx, g.ny, g.nz);
   k_sweep_f64<<<l.grid, l.block, 0, s>>>(g, p, b, omega, out);
   return cudaGetLastError();
+}
+
+int cycle_grid_f32(int device) {
+  int per_sm = 0, sms = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cycle_f32, 1024, 0) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
+  return per_sm * sms;
+}
+
+cudaError_t launch_cycle_f32(const Geom<float>& g, float* A, float* B, const float* b, const float* omega, int M,
+                             GridBar bar, SolveCtl* ctl, int nblocks, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nblocks);
+  cfg.blockDim = dim3(1024);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, k_cycle_f32, g, A, B, b, omega, M, bar, ctl);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_pass_begin(float* d, size_t n, int graph, cudaGraphConditionalHandle h_loop, cudaStream_t s) {

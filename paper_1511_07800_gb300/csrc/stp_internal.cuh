@@ -65,6 +65,13 @@ enum {
 };
 enum { FL_DONE = 0, FL_INNER_DONE = 1, FL_BAD = 2, FL_COUNT = 4 };
 
+// grid-wide barrier state of the persistent SRJ cycle kernel (device)
+struct GridBar {
+  unsigned* count;  // arrivals in the current barrier
+  unsigned* gen;    // completed barriers
+  int* err;         // set when a wait timed out
+};
+
 struct Launch {
   dim3 grid, block;
   unsigned nblocks;
@@ -132,6 +139,12 @@ cudaError_t launch_sweep<float>(const Geom<float>&, const float*, const float*, 
 template <>
 cudaError_t launch_sweep<double>(const Geom<double>&, const double*, const double*, double, double*, cudaStream_t);
 
+// FP32 sweep variant used by launch_sweep<float> on this host thread
+// (chosen by the autotuner in api.cu).
+void set_sweep_variant(int v);
+int sweep_variant_count();
+bool sweep_variant_ok(int v, int nz);
+
 // ||b - L p|| and the once-per-cycle decision (mode 0: FP64 solve, mode 1:
 // FP32 inner solve); sets the WHILE (h_loop) and IF (h_body) conditionals.
 // Outside a graph (graph == 0) the decision is only written to ctl->go.
@@ -142,6 +155,11 @@ cudaError_t launch_check(const Geom<T>& g, const T* p, const T* b, int mode, Sol
 // Refinement residual r = b - L p (FP64, stored FP32) and the pass decision.
 cudaError_t launch_outer(const Geom<double>& g, const double* p, const double* b, float* r32, SolveCtl* ctl, Red red,
                          int after_pass, int graph, cudaGraphConditionalHandle h_loop, cudaStream_t s);
+// One SRJ cycle of M FP32 sweeps (A -> B -> A ...) in one cooperative
+// launch of nblocks x 1024 threads (nblocks from cycle_grid_f32).
+int cycle_grid_f32(int device);
+cudaError_t launch_cycle_f32(const Geom<float>& g, float* A, float* B, const float* b, const float* omega, int M,
+                             GridBar bar, SolveCtl* ctl, int nblocks, cudaStream_t s);
 // start of a refinement pass: d = 0 and the inner loop armed
 cudaError_t launch_pass_begin(float* d, size_t n, int graph, cudaGraphConditionalHandle h_loop, cudaStream_t s);
 // p += d

@@ -24,6 +24,7 @@ STP_ECUDA = -3
 STP_ENOTCONVERGED = -4
 STP_EDIVERGED = -5
 STP_ECFL = -6
+STP_ETIMEOUT = -7
 STP_HOST, STP_DEVICE = 0, 1
 STP_FP64, STP_FP32_REFINE = 0, 1
 TERMS = {"viscosity": 1, "explicit": 2, "diffusion": 3, "divergence": 4, "laplacian": 5}

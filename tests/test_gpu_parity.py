@@ -230,3 +230,41 @@ def test_host_driven_solve_matches_graph(stp_lib, monkeypatch, precision):
     assert sa["sweeps"] == sb["sweeps"] and sa["passes"] == sb["passes"]
     for k in ("u", "v", "w", "p"):
         assert np.array_equal(fa[k], fb[k]), k
+
+
+def test_persistent_cycle_matches_per_sweep_kernels(stp_lib, monkeypatch):
+    """FP32 SRJ cycles as one persistent cooperative kernel (grid barriers
+    between sweeps) give the fields of the one-kernel-per-sweep path."""
+    cfg = case(nx=64, ny=20, nz=24, stretch=2.0, les=1, nu=1 / 500.0, cn_sweeps=4)
+    om = schedule(cfg, 32)
+    out = []
+    for mode in ("0", "1"):
+        monkeypatch.setenv("STP_PERSISTENT", mode)
+        with stp_lib.Channel(cfg, precision="fp32", omega=om) as ch:
+            ch.set_fields(*turbulent_like(cfg, 12))
+            st = ch.step(3)
+            assert st["converged"]
+            out.append((ch.get_fields(), st))
+    (fa, sa), (fb, sb) = out
+    assert sa["sweeps"] == sb["sweeps"]
+    for k in ("u", "v", "w", "p"):
+        assert rel_err(fb[k] - fb[k].mean() * (k == "p"), fa[k] - fa[k].mean() * (k == "p")) < 1e-6, k
+
+
+def test_sweep_variants_identical(stp_lib, monkeypatch):
+    """Every FP32 sweep tile shape the autotuner may pick computes the same
+    values (z levels per thread and rows per block only change the mapping)."""
+    cfg = case(nx=64, ny=24, nz=32, stretch=2.0, les=0, nu=1 / 500.0, cn_sweeps=4)
+    om = schedule(cfg, 32)
+    ref = None
+    for v in range(6):
+        monkeypatch.setenv("STP_SWEEP_VARIANT", str(v))
+        with stp_lib.Channel(cfg, precision="fp32", omega=om) as ch:
+            ch.set_fields(*turbulent_like(cfg, 13))
+            ch.step(2)
+            f = ch.get_fields()
+        if ref is None:
+            ref = f
+        else:
+            for k in ("u", "v", "w", "p"):
+                assert np.array_equal(f[k], ref[k]), (v, k)
