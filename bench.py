@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--grid", default=None, help="override the cell counts, NXxNYxNZ (profiling runs)")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-guess comparison")
     return ap.parse_args()
 
 
@@ -99,6 +100,17 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def reduce_max(value, device=None):
+    """Maximum of a per-rank scalar over all ranks (identity on one rank)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device or "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -144,6 +156,52 @@ def cpu_baseline_sample(cfg, fields, sweeps_per_step):
             "sample": "1 FP64 oracle step of the full %dx%dx%d workload from the initial fields, SRJ held to "
                       "%d sweeps (%d cycles of %d, the GPU's mean per timed step); %.2f s wall"
                       % (cfg["nx"], cfg["ny"], cfg["nz"], cycles * M, cycles, M, dt)}
+
+
+def learned_comparison(cfg, steps):
+    """Poisson time to 1e-8, learned guess vs plain, on the workload grid:
+    train the U-Net on (residual, correction) pairs harvested from channels
+    of the same workload (seeds 0-3, 10 steps each), then step one channel
+    (seed 7) with and without the guess and compare the solves."""
+    import numpy as np
+    import torch
+    from paper_1511_07800_gb300 import learn, stp
+    shape = (cfg["nz"], cfg["ny"], cfg["nx"])
+    t0 = time.perf_counter()
+    R, DP = learn.harvest(cfg, seeds=range(4), steps_per_seed=10)
+    K = learn.output_scale(R, DP, 4, shape)
+    net = stp.UNet(4, *shape)
+    rng = np.random.default_rng(3)
+    theta = []
+    # He-normal initialisation (std sqrt(2/fan_in)), zero bias, small output layer
+    cin = 1
+    specs = []
+    for c in (16, 32, 64, 128):
+        specs += [(cin, c, 27), (c, c, 27)]
+        cin = c
+    for l in (2, 1, 0):
+        c = (16, 32, 64, 128)[l]
+        specs += [((16, 32, 64, 128)[l + 1] + c, c, 27), (c, c, 27)]
+    specs.append((16, 1, 1))
+    for i, (ci, co, taps) in enumerate(specs):
+        std = math.sqrt(2.0 / (ci * taps)) if i < len(specs) - 1 else 0.1 / math.sqrt(ci)
+        theta.append(rng.standard_normal(co * ci * taps) * std)
+        theta.append(np.zeros(co))
+    net.set_params(np.concatenate(theta).astype(np.float32))
+    net.set_output_scale(K)
+    losses = learn.train(net, R, DP, 150, 4, 1e-3) + learn.train(net, R, DP, 100, 4, 3e-4)
+    t_train = time.perf_counter() - t0
+    res = learn.compare(cfg, net, seed=7, nsteps=max(3, steps), precision="fp32")
+    res64 = learn.compare(cfg, net, seed=7, nsteps=3, precision="fp64")
+    net.close()
+    return {"plain_ms": res["plain"]["solve_ms"], "learned_ms": res["learned"]["solve_ms"],
+            "plain_sweeps": res["plain"]["sweeps"], "learned_sweeps": res["learned"]["sweeps"],
+            "speedup": res["plain"]["solve_ms"] / res["learned"]["solve_ms"],
+            "fp64": {"plain_ms": res64["plain"]["solve_ms"], "learned_ms": res64["learned"]["solve_ms"],
+                     "plain_sweeps": res64["plain"]["sweeps"], "learned_sweeps": res64["learned"]["sweeps"]},
+            "train": {"pairs": int(R.shape[0]), "adam_steps": len(losses), "batch": 4,
+                      "final_loss": float(np.mean(losses[-10:])), "output_scale": K, "seconds": t_train},
+            "note": "time per pressure solve to 1e-8 (GPU events), previous-step pressure as the plain guess"}
 
 
 def run_reference(args):
@@ -249,11 +307,7 @@ def run_ours(args):
     if world > 1:
         torch.distributed.barrier()
     clocks = clk.stop()
-    ms_max = ms
-    if world > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_max = float(t.item())
+    ms_max = reduce_max(ms, "cuda")
     value = world * cells * args.steps / (ms_max / 1e3) / 1e6
 
     # end to end through the C ABI with host buffers: copy the step's inputs
@@ -307,6 +361,11 @@ def run_ours(args):
         "clocks": clocks,
         "e2e": e2e,
     }
+    if rank == 0 and world == 1 and not args.no_learned and args.grid is None:
+        try:
+            line["poisson_learned_vs_plain"] = learned_comparison(cfg, args.steps)
+        except Exception as ex:  # report, never fake
+            line["poisson_learned_vs_plain"] = {"error": str(ex)[:200]}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
             line["cpu_baseline"] = cpu_baseline_sample(cfg, fields, sweeps / args.steps)

@@ -149,6 +149,15 @@ int stp_get_fields(stp_handle *h, double *u, double *v, double *w, double *p, do
    stats (nullable) describes the last step. */
 int stp_step(stp_handle *h, int nsteps, stp_step_stats *stats);
 
+/* Checkpoint: the whole state of the time stepper (velocities, pressure,
+   the two Adams-Bashforth history levels, the history depth and the step
+   counter) as one opaque FP64 host buffer of stp_state_size() doubles;
+   stp_set_state resumes bitwise where stp_get_state was taken (same
+   configuration). */
+long long stp_state_size(const stp_handle *h);
+int stp_get_state(stp_handle *h, double *buf);
+int stp_set_state(stp_handle *h, const double *buf);
+
 /* Solve L p = rhs (Sec. 3.4 SRJ; Eq. presdiv operator with Neumann walls)
    to ||rhs - Lp||_2 <= tol ||rhs||_2 starting from p_inout, capped at maxit
    sweeps (0: pmaxit).  rhs [nz][ny][nx] must have zero volume-weighted mean

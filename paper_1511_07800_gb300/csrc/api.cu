@@ -1150,6 +1150,69 @@ int stp_poisson_solve(stp_handle* h, const double* rhs, double* p_inout, double 
   return so.converged ? STP_OK : fail(h, STP_ENOTCONVERGED, "pressure solve hit maxit");
 }
 
+// state layout: header [4] (magic, nhist, step, nc) | u | v | w | p | Nu,Nv,Nw of levels n, n-1 (history)
+long long stp_state_size(const stp_handle* h) {
+  if (!h) return 0;
+  return 4 + 3 * (long long)h->nc + (long long)h->nw + 2 * (2 * (long long)h->nc + (long long)h->nw);
+}
+
+int stp_get_state(stp_handle* h, double* buf) {
+  if (!h || !buf) return STP_EINVAL;
+  CUDA_TRY(h, cudaSetDevice(h->dev));
+  buf[0] = 1511.07800;
+  buf[1] = h->nhist;
+  buf[2] = (double)h->step;
+  buf[3] = (double)h->nc;
+  double* q = buf + 4;
+  int rc;
+  if ((rc = get_any(h, q, h->u, h->nc, STP_HOST))) return rc;
+  q += h->nc;
+  if ((rc = get_any(h, q, h->v, h->nc, STP_HOST))) return rc;
+  q += h->nc;
+  if ((rc = get_any(h, q, h->w, h->nw, STP_HOST))) return rc;
+  q += h->nw;
+  CUDA_TRY(h, cudaMemcpyAsync(q, h->p, sizeof(double) * h->nc, cudaMemcpyDeviceToHost, h->st));
+  q += h->nc;
+  for (int l = 0; l < 2; l++) {
+    if ((rc = get_any(h, q, h->Nu[l], h->nc, STP_HOST))) return rc;
+    q += h->nc;
+    if ((rc = get_any(h, q, h->Nv[l], h->nc, STP_HOST))) return rc;
+    q += h->nc;
+    if ((rc = get_any(h, q, h->Nw[l], h->nw, STP_HOST))) return rc;
+    q += h->nw;
+  }
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  return STP_OK;
+}
+
+int stp_set_state(stp_handle* h, const double* buf) {
+  if (!h || !buf) return STP_EINVAL;
+  if (buf[0] != 1511.07800 || buf[3] != (double)h->nc) return fail(h, STP_EINVAL, "state buffer does not match");
+  CUDA_TRY(h, cudaSetDevice(h->dev));
+  const double* q = buf + 4;
+  int rc;
+  if ((rc = put_any(h, h->u, q, h->nc, STP_HOST))) return rc;
+  q += h->nc;
+  if ((rc = put_any(h, h->v, q, h->nc, STP_HOST))) return rc;
+  q += h->nc;
+  if ((rc = put_any(h, h->w, q, h->nw, STP_HOST))) return rc;
+  q += h->nw;
+  CUDA_TRY(h, cudaMemcpyAsync(h->p, q, sizeof(double) * h->nc, cudaMemcpyHostToDevice, h->st));
+  q += h->nc;
+  for (int l = 0; l < 2; l++) {
+    if ((rc = put_any(h, h->Nu[l], q, h->nc, STP_HOST))) return rc;
+    q += h->nc;
+    if ((rc = put_any(h, h->Nv[l], q, h->nc, STP_HOST))) return rc;
+    q += h->nc;
+    if ((rc = put_any(h, h->Nw[l], q, h->nw, STP_HOST))) return rc;
+    q += h->nw;
+  }
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  h->nhist = (int)buf[1];
+  h->step = (long long)buf[2];
+  return STP_OK;
+}
+
 int stp_set_learned_guess(stp_handle* h, stp_unet* net) {
   if (!h) return STP_EINVAL;
   if (net && !unet_matches(net, h->nz, h->ny, h->nx))

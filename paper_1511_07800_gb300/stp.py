@@ -70,7 +70,8 @@ EXPORTS = ("stp_config_defaults", "stp_init", "stp_destroy", "stp_last_error", "
            "stp_poisson_residual_noalloc", "stp_unet_param_count", "stp_unet_create", "stp_unet_destroy",
            "stp_unet_last_error", "stp_unet_set_params", "stp_unet_get_params", "stp_unet_forward",
            "stp_unet_gradient", "stp_unet_train_step", "stp_unet_train_pairs", "stp_unet_eval_pairs",
-           "stp_set_learned_guess", "stp_set_harvest", "stp_unet_set_output_scale")
+           "stp_set_learned_guess", "stp_set_harvest", "stp_unet_set_output_scale", "stp_state_size",
+           "stp_get_state", "stp_set_state")
 
 _lib = None
 
@@ -117,6 +118,10 @@ def lib():
     L.stp_unet_train_pairs.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_float, ctypes.POINTER(ctypes.c_float)]
     L.stp_unet_eval_pairs.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.POINTER(ctypes.c_float)]
     L.stp_set_learned_guess.argtypes = [vp, vp]
+    L.stp_state_size.argtypes = [vp]
+    L.stp_state_size.restype = ctypes.c_longlong
+    L.stp_get_state.argtypes = [vp, vp]
+    L.stp_set_state.argtypes = [vp, vp]
     L.stp_unet_set_output_scale.argtypes = [vp, ctypes.c_float]
     L.stp_set_harvest.argtypes = [vp, vp, vp]
     _lib = L
@@ -251,6 +256,16 @@ class Channel:
         ptr = [_addr(a)[0] for a in out] + [None] * (3 - len(out))
         self._check(lib().stp_eval(self._h, t, ptr[0], ptr[1], ptr[2], where))
         return out if len(out) > 1 else out[0]
+
+    def get_state(self):
+        """The whole time-stepper state as a float64 numpy array (checkpoint)."""
+        buf = np.zeros(int(lib().stp_state_size(self._h)))
+        self._check(lib().stp_get_state(self._h, ctypes.c_void_p(buf.ctypes.data)))
+        return buf
+
+    def set_state(self, buf):
+        buf = np.ascontiguousarray(buf, dtype=np.float64)
+        self._check(lib().stp_set_state(self._h, ctypes.c_void_p(buf.ctypes.data)))
 
     def set_learned_guess(self, net):
         """Start every pressure solve from the network's guess (None: off)."""

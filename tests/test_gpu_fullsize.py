@@ -1,0 +1,82 @@
+"""Parity at the full sizes of the workloads, in the configurations the
+benchmark runs: the instability grid 128 x 64 x 128 (FP64 with forced sweep
+counts, and FP32 + refinement with tolerance-driven solves as benchmarked)
+and the LES channel 256 x 128 x 192 (stretched, Smagorinsky, constant flux)."""
+import numpy as np
+import pytest
+
+from paper_1511_07800_gb300 import inputs
+
+from .conftest import rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(stp_lib, orc, cfg, fields, nsteps, om, precision):
+    o = orc.Oracle(dict(cfg, omega=om))
+    o.set_fields(*fields)
+    so = o.step(nsteps)
+    with stp_lib.Channel(cfg, precision=precision, omega=om) as ch:
+        ch.set_fields(*fields)
+        sg = ch.step(nsteps)
+        fg = ch.get_fields()
+    return o.get_fields(), so, fg, sg
+
+
+def _threads(orc):
+    import os
+    orc.set_threads(len(os.sched_getaffinity(0)))
+
+
+def test_instability_grid_fp64_forced_sweeps(stp_lib, orc):
+    from oracle import srj
+    _threads(orc)
+    cfg = inputs.preset("os_instability", cn_sweeps=5, ptol=0.0, pmaxit=32)
+    om = srj.schedule_for(128, 64, 128, cfg["Lx"], cfg["Ly"], cfg["Lz"], 0.0, 16)[0]
+    fields = inputs.initial_fields("os_instability", cfg, seed=0)
+    fo, so, fg, sg = _run(stp_lib, orc, cfg, fields, 2, om, "fp64")
+    assert sg["sweeps"] == so["sweeps"] == 32
+    for k in ("u", "v", "w"):
+        assert rel_err(fg[k], fo[k]) < 1e-10, k
+    assert rel_err(fg["w"] - fields[2], fo["w"] - fields[2]) < 1e-8
+
+
+def test_instability_grid_fp32_as_benchmarked(stp_lib, orc):
+    """The benchmark's configuration (FP32 sweeps, FP64 refinement, library
+    schedule, autotuned sweep kernel, solves to 1e-8) against the FP64
+    oracle with its own schedule: both solves meet the tolerance, and the
+    fields agree to the FP32 bounds."""
+    from oracle import srj
+    import bench
+    _threads(orc)
+    cfg = inputs.preset("os_instability")
+    cfg["cn_sweeps"] = bench._auto_cn(cfg)
+    fields = inputs.initial_fields("os_instability", cfg, seed=0)
+    om = srj.schedule_for(128, 64, 128, cfg["Lx"], cfg["Ly"], cfg["Lz"], 0.0)[0]
+    o = orc.Oracle(dict(cfg, omega=om))
+    o.set_fields(*fields)
+    so = o.step(2)
+    with stp_lib.Channel(cfg, precision="fp32") as ch:
+        ch.set_fields(*fields)
+        sg = ch.step(2)
+        fg = ch.get_fields()
+    fo = o.get_fields()
+    assert so["converged"] and sg["converged"] and sg["rel_res"] <= 1e-8
+    # FP32 storage: velocity errors relative to the velocity scale (v and w
+    # are only perturbations here), the pressure relative to its own range
+    vs = max(np.abs(fo[k]).max() for k in ("u", "v", "w"))
+    for k in ("u", "v", "w"):
+        assert np.abs(fg[k] - fo[k]).max() < 2e-6 * vs, k
+    assert rel_err(fg["p"] - fg["p"].mean(), fo["p"] - fo["p"].mean()) < 1e-3
+
+
+def test_les_grid_fp64_forced_sweeps(stp_lib, orc):
+    from oracle import srj
+    _threads(orc)
+    cfg = inputs.preset("les_channel", cn_sweeps=4, ptol=0.0, pmaxit=8)
+    om = srj.schedule_for(256, 128, 192, cfg["Lx"], cfg["Ly"], cfg["Lz"], 2.0, 8)[0]
+    fields = inputs.initial_fields("les_channel", cfg, seed=1)
+    fo, so, fg, sg = _run(stp_lib, orc, cfg, fields, 1, om, "fp64")
+    for k in ("u", "v", "w", "nu"):
+        assert rel_err(fg[k], fo[k]) < 1e-10, k
+    assert abs(sg["ubulk"] - 1.0) < 1e-12
