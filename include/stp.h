@@ -149,6 +149,36 @@ int stp_get_fields(stp_handle *h, double *u, double *v, double *w, double *p, do
    stats (nullable) describes the last step. */
 int stp_step(stp_handle *h, int nsteps, stp_step_stats *stats);
 
+/* ------------------------------------------------------------------------
+ * Batched channels: many independent channels (each its own stp_handle,
+ * of any size and configuration, all on one device) advanced together by
+ * one CUDA graph launch.  The graph holds a device-side WHILE loop over the
+ * steps; its body has one branch per channel (velocity kernels, the
+ * channel's own device-steered pressure solve, the correction), so the
+ * channels run concurrently and the host neither launches nor waits
+ * between steps.  Every pressure solve still meets its channel's ptol.
+ * ------------------------------------------------------------------------ */
+typedef struct stp_batch stp_batch;
+
+typedef struct stp_batch_stats {
+    long long steps;         /* steps taken by every channel in this call      */
+    long long cells;         /* total cells over the channels                  */
+    long long sweeps;        /* SRJ sweeps over all channels and steps         */
+    int converged;           /* 1 if every solve of every channel met its ptol  */
+    double gpu_ms;           /* GPU time of the launch (CUDA events)           */
+} stp_batch_stats;
+
+/* The handles stay owned by the caller and must outlive the batch; they
+   must not be stepped on their own while the batch runs.  stream NULL: the
+   batch's own stream. */
+int stp_batch_create(stp_handle *const *handles, int n, void *stream, stp_batch **out);
+void stp_batch_destroy(stp_batch *b);
+const char *stp_batch_last_error(const stp_batch *b);
+
+/* Advance every channel nsteps steps in one graph launch; per_channel
+   (nullable, n entries) receives each channel's stats of its last step. */
+int stp_batch_step(stp_batch *b, int nsteps, stp_batch_stats *stats, stp_step_stats *per_channel);
+
 /* Checkpoint: the whole state of the time stepper (velocities, pressure,
    the two Adams-Bashforth history levels, the history depth and the step
    counter) as one opaque FP64 host buffer of stp_state_size() doubles;

@@ -64,6 +64,7 @@ struct stp_handle {
   long long solve_sweeps = 0;
   double solve_ms = 0.0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  int* d_step = nullptr;       // steps since the fields were set (device copy)
   // device-steered pressure solve
   cudaStream_t cap = nullptr;  // private stream used only for graph capture
   SolveCtl* ctl = nullptr;
@@ -515,21 +516,31 @@ int tune_sweep(stp_handle* h) {
   return STP_OK;
 }
 
-int build_solve_graph(stp_handle* h) {
-  if (h->solve_exec) return STP_OK;
+// end the capture on h->cap, returning the node the capture ended on
+int end_capture_tail(stp_handle* h, cudaGraph_t g, cudaGraphNode_t* tail) {
+  cudaStreamCaptureStatus st;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  CUDA_TRY(h, cudaStreamGetCaptureInfo(h->cap, &st, nullptr, nullptr, &deps, nullptr, &nd));
+  *tail = nd ? deps[nd - 1] : nullptr;
+  return end_capture(h, g);
+}
+
+// Append the pressure solve of h to graph G after node dep (nullptr: a
+// root); *last receives its final node.  Conditional handles are created on
+// G and armed explicitly every time the solve runs, so the solve can also sit
+// inside another WHILE body (the batched step).
+int append_solve(stp_handle* h, cudaGraph_t G, cudaGraphNode_t dep, cudaGraphNode_t* last) {
   if (int rc = tune_sweep(h)) return rc;
   set_sweep_variant(h->sweep_variant);
-  cudaGraph_t G;
-  CUDA_TRY(h, cudaGraphCreate(&G, 0));
-  h->solve_graph = G;
   int rc;
   cudaGraph_t wb, pb;
-  cudaGraphNode_t wn, pn;
+  cudaGraphNode_t wn, pn, tail;
   if (h->prec == STP_FP64) {
     cudaGraphConditionalHandle h_loop;
     CUDA_TRY(h, cudaGraphConditionalHandleCreate(&h_loop, G, 1, cudaGraphCondAssignDefault));
-    if ((rc = begin_capture(h, G, nullptr))) return rc;
-    CUDA_TRY(h, launch_begin(h->ctl, h->cap));
+    if ((rc = begin_capture(h, G, dep))) return rc;
+    CUDA_TRY(h, launch_begin(h->ctl, 1, h_loop, h->cap));
     if (h->net) {
       // learned guess: r = b - L p (FP32), p += s U(r / s)
       CUDA_TRY(h, launch_outer(h->g64, h->p, h->b, h->r32, h->ctl, h->red, 0, 0, 0, h->cap));
@@ -537,14 +548,15 @@ int build_solve_graph(stp_handle* h) {
         return fail(h, rc, "learned guess: " + std::string(stp_unet_last_error(h->net)));
       CUDA_TRY(h, launch_addcorr(h->p, h->d1, h->nc, h->cap));
     }
-    if ((rc = end_capture(h, G))) return rc;
-    if ((rc = add_conditional(h, G, leaf_node(G), h_loop, cudaGraphCondTypeWhile, &wb, &wn))) return rc;
+    if ((rc = end_capture_tail(h, G, &tail))) return rc;
+    if ((rc = add_conditional(h, G, tail, h_loop, cudaGraphCondTypeWhile, &wb, &wn))) return rc;
     if ((rc = build_cycle<double>(h, h->g64, wb, h_loop, h->p, h->p2, h->b, 0))) return rc;
+    *last = wn;
   } else {
     cudaGraphConditionalHandle h_pass, h_loop;
     CUDA_TRY(h, cudaGraphConditionalHandleCreate(&h_pass, G, 0, cudaGraphCondAssignDefault));
-    if ((rc = begin_capture(h, G, nullptr))) return rc;
-    CUDA_TRY(h, launch_begin(h->ctl, h->cap));
+    if ((rc = begin_capture(h, G, dep))) return rc;
+    CUDA_TRY(h, launch_begin(h->ctl, 0, 0, h->cap));
     CUDA_TRY(h, launch_outer(h->g64, h->p, h->b, h->r32, h->ctl, h->red, 0, 1, h_pass, h->cap));
     if (h->net) {
       // learned guess at the start of the solve: p += s U(r / s), then the
@@ -554,8 +566,8 @@ int build_solve_graph(stp_handle* h) {
       CUDA_TRY(h, launch_addcorr(h->p, h->d1, h->nc, h->cap));
       CUDA_TRY(h, launch_outer(h->g64, h->p, h->b, h->r32, h->ctl, h->red, 0, 1, h_pass, h->cap));
     }
-    if ((rc = end_capture(h, G))) return rc;
-    if ((rc = add_conditional(h, G, leaf_node(G), h_pass, cudaGraphCondTypeWhile, &pb, &pn))) return rc;
+    if ((rc = end_capture_tail(h, G, &tail))) return rc;
+    if ((rc = add_conditional(h, G, tail, h_pass, cudaGraphCondTypeWhile, &pb, &pn))) return rc;
     // pass body: d = 0, arm the loop -> WHILE(loop){cycle} -> p += d -> outer
     // residual.  The loop handle is set explicitly each pass: a handle's
     // default value is applied only when the top-level graph launches.
@@ -569,7 +581,18 @@ int build_solve_graph(stp_handle* h) {
     CUDA_TRY(h, launch_addcorr(h->p, h->d1, h->nc, h->cap));
     CUDA_TRY(h, launch_outer(h->g64, h->p, h->b, h->r32, h->ctl, h->red, 1, 1, h_pass, h->cap));
     if ((rc = end_capture(h, pb))) return rc;
+    *last = pn;
   }
+  return STP_OK;
+}
+
+int build_solve_graph(stp_handle* h) {
+  if (h->solve_exec) return STP_OK;
+  cudaGraph_t G;
+  CUDA_TRY(h, cudaGraphCreate(&G, 0));
+  h->solve_graph = G;
+  cudaGraphNode_t last;
+  if (int rc = append_solve(h, G, nullptr, &last)) return rc;
   CUDA_TRY(h, cudaGraphInstantiate(&h->solve_exec, G, 0));
   return STP_OK;
 }
@@ -619,7 +642,7 @@ int host_cycles(stp_handle* h, const Geom<T>& g, T* A, T* B, const T* rhs, int m
 int host_solve(stp_handle* h) {
   if (int rc = tune_sweep(h)) return rc;
   set_sweep_variant(h->sweep_variant);
-  CUDA_TRY(h, launch_begin(h->ctl, h->st));
+  CUDA_TRY(h, launch_begin(h->ctl, 0, 0, h->st));
   if (h->prec == STP_FP64) {
     if (h->net) {
       CUDA_TRY(h, launch_outer(h->g64, h->p, h->b, h->r32, h->ctl, h->red, 0, 0, 0, h->st));
@@ -701,71 +724,74 @@ int finish_solve(stp_handle* h, SolveOut* o) {
 }
 
 // ---------------------------------------------------------------------------
-// one projection step (Sec. 3.1)
+// one projection step (Sec. 3.1).  Every pointer is fixed across steps (the
+// Adams-Bashforth slot and coefficients come from the device step counter,
+// and the Crank-Nicolson ping-pong always ends in the u buffer), so the
+// launches of a step can be captured once into a graph.
 // ---------------------------------------------------------------------------
+// velocity part up to the Poisson right-hand side, on stream s
 template <typename T>
-int step_impl(stp_handle* h, const Geom<T>& g) {
+int step_pre(stp_handle* h, const Geom<T>& g, cudaStream_t s) {
   const stp_config& c = h->cfg;
-  // history ring: slot 0 becomes level n
-  std::swap(h->Nu[2], h->Nu[1]);
-  std::swap(h->Nv[2], h->Nv[1]);
-  std::swap(h->Nw[2], h->Nw[1]);
-  std::swap(h->Nu[1], h->Nu[0]);
-  std::swap(h->Nv[1], h->Nv[0]);
-  std::swap(h->Nw[1], h->Nw[0]);
-  if (h->nhist < 3) h->nhist++;
-  double b0 = 1, b1 = 0, b2 = 0;
-  if (h->nhist == 2) {
-    b0 = 1.5;
-    b1 = -0.5;
-  } else if (h->nhist == 3) {
-    b0 = 23.0 / 12.0;
-    b1 = -16.0 / 12.0;
-    b2 = 5.0 / 12.0;
-  }
   T *u = (T*)h->u, *v = (T*)h->v, *w = (T*)h->w;
   T* nu = (T*)h->nu;
   const T nu0 = (T)c.nu;
-  if (c.les) CUDA_TRY(h, launch_viscosity<T>(g, u, v, w, nu0, nu, h->st));
+  if (c.les) CUDA_TRY(h, launch_viscosity<T>(g, u, v, w, nu0, nu, s));
   const T fx = (T)(c.forcing == 0 ? c.fx : 0.0);
-  CUDA_TRY(h, launch_momentum<T>(g, c.les != 0, u, v, w, nu, nu0, fx, (T*)h->Nu[0], (T*)h->Nv[0], (T*)h->Nw[0],
-                                 (const T*)h->Nu[1], (const T*)h->Nv[1], (const T*)h->Nw[1], (const T*)h->Nu[2],
-                                 (const T*)h->Nv[2], (const T*)h->Nw[2], (T)b0, (T)b1, (T)b2, (T)c.dt, (T*)h->ru,
-                                 (T*)h->rv, (T*)h->rw, h->st));
-  // Crank-Nicolson Jacobi sweeps: rhs is the first iterate; buffers rotate
-  // over (t, u) so that the rhs stays intact.
-  void* in[3] = {h->ru, h->rv, h->rw};
-  void* bufA[3] = {h->tu, h->tv, h->tw};
-  void* bufB[3] = {h->u, h->v, h->w};
-  void** cur = in;
-  for (int s = 0; s < h->cn_sweeps; s++) {
-    void** out = (s % 2 == 0) ? bufA : bufB;
+  Hist<T> H;
+  for (int l = 0; l < 3; l++) {
+    H.u[l] = (T*)h->Nu[l];
+    H.v[l] = (T*)h->Nv[l];
+    H.w[l] = (T*)h->Nw[l];
+  }
+  H.step = h->d_step;
+  CUDA_TRY(h, launch_momentum<T>(g, c.les != 0, u, v, w, nu, nu0, fx, H, (T)c.dt, (T*)h->ru, (T*)h->rv, (T*)h->rw, s));
+  // Crank-Nicolson Jacobi sweeps from the rhs, alternating between the t and
+  // u buffers so that the last sweep writes u (u^n is no longer needed)
+  void* R[3] = {h->ru, h->rv, h->rw};
+  void* U[3] = {h->u, h->v, h->w};
+  void* Tb[3] = {h->tu, h->tv, h->tw};
+  void** cur = R;
+  const int n = h->cn_sweeps;
+  for (int k = 0; k < n; k++) {
+    void** out = ((n - 1 - k) % 2 == 0) ? U : Tb;
     CUDA_TRY(h, launch_cn_sweep<T>(g, c.les != 0, nu, nu0, (T)(0.5 * c.dt), (const T*)h->ru, (const T*)h->rv,
                                    (const T*)h->rw, (const T*)cur[0], (const T*)cur[1], (const T*)cur[2],
-                                   (T*)out[0], (T*)out[1], (T*)out[2], h->st));
+                                   (T*)out[0], (T*)out[1], (T*)out[2], s));
     cur = out;
   }
-  T *su = (T*)cur[0], *sv = (T*)cur[1], *sw = (T*)cur[2];
+  if (n == 0) {
+    CUDA_TRY(h, cudaMemcpyAsync(h->u, h->ru, h->esz * h->nc, cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(h, cudaMemcpyAsync(h->v, h->rv, h->esz * h->nc, cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(h, cudaMemcpyAsync(h->w, h->rw, h->esz * h->nw, cudaMemcpyDeviceToDevice, s));
+  }
   // b = D u* / dt
-  CUDA_TRY(h, launch_divergence_rhs<T>(g, su, sv, sw, 1.0 / c.dt, h->b, h->red, h->st));
-  int rc = harvest_before(h);
+  CUDA_TRY(h, launch_divergence_rhs<T>(g, u, v, w, 1.0 / c.dt, h->b, h->red, s));
+  return STP_OK;
+}
+
+// projection, wall conditions, flux fix-up and the step counter, on stream s
+template <typename T>
+int step_post(stp_handle* h, const Geom<T>& g, cudaStream_t s) {
+  const stp_config& c = h->cfg;
+  T *u = (T*)h->u, *v = (T*)h->v, *w = (T*)h->w;
+  const double inv_vol = 1.0 / ((double)h->nx * h->ny * c.Lz);
+  CUDA_TRY(h, launch_correct_impl<T>(g, h->p, c.dt, u, v, w, h->g64.ihz, h->g64.dzv, inv_vol, h->red, s));
+  if (c.forcing == 1) CUDA_TRY(h, launch_flux_shift<T>(g, u, c.ubulk, h->red, s));
+  CUDA_TRY(h, launch_step_end(h->d_step, s));
+  return STP_OK;
+}
+
+template <typename T>
+int step_impl(stp_handle* h, const Geom<T>& g) {
+  int rc = step_pre<T>(h, g, h->st);
   if (rc) return rc;
+  if ((rc = harvest_before(h))) return rc;
   if ((rc = launch_solve(h))) return rc;
   if ((rc = harvest_after(h))) return rc;
-  const double inv_vol = 1.0 / ((double)h->nx * h->ny * c.Lz);
-  CUDA_TRY(h, launch_correct_impl<T>(g, h->p, c.dt, su, sv, sw, h->g64.ihz, h->g64.dzv, inv_vol, h->red, h->st));
-  if (c.forcing == 1) CUDA_TRY(h, launch_flux_shift<T>(g, su, c.ubulk, h->red, h->st));
-  // the buffer holding u^{n+1} becomes the current field
-  if (cur == bufA) {
-    std::swap(h->u, h->tu);
-    std::swap(h->v, h->tv);
-    std::swap(h->w, h->tw);
-  } else if (cur == in) {
-    std::swap(h->u, h->ru);
-    std::swap(h->v, h->rv);
-    std::swap(h->w, h->rw);
-  }
+  if ((rc = step_post<T>(h, g, h->st))) return rc;
   h->step++;
+  if (h->nhist < 3) h->nhist++;
   return STP_OK;
 }
 
@@ -972,6 +998,7 @@ int stp_init(const stp_config* cfg, stp_handle** out) {
   A((void**)&h->red.sc, sizeof(double) * SC_COUNT);
   A((void**)&h->red.flag, sizeof(int) * FL_COUNT);
   A((void**)&h->ctl, sizeof(SolveCtl));
+  A((void**)&h->d_step, sizeof(int) * 4);
   A((void**)&h->d_omega32, sizeof(float) * h->omega.size());
   A((void**)&h->bar.count, sizeof(unsigned) * 4);
   if (rc) return bail(rc);
@@ -1013,6 +1040,7 @@ int stp_init(const stp_config* cfg, stp_handle** out) {
   if (e == cudaSuccess) e = cudaMemsetAsync(h->red.flag, 0, sizeof(int) * FL_COUNT, h->st);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->ctl, 0, sizeof(SolveCtl), h->st);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->bar.count, 0, sizeof(unsigned) * 4, h->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->d_step, 0, sizeof(int) * 4, h->st);
   if (e == cudaSuccess) {
     std::vector<float> om32(h->omega.begin(), h->omega.end());
     e = cudaMemcpyAsync(h->d_omega32, om32.data(), sizeof(float) * om32.size(), cudaMemcpyHostToDevice, h->st);
@@ -1047,6 +1075,7 @@ int stp_set_fields(stp_handle* h, const double* u, const double* v, const double
   } else {
     CUDA_TRY(h, cudaMemsetAsync(h->p, 0, sizeof(double) * h->nc, h->st));
   }
+  CUDA_TRY(h, cudaMemsetAsync(h->d_step, 0, sizeof(int), h->st));
   CUDA_TRY(h, cudaStreamSynchronize(h->st));
   h->nhist = 0;
   h->step = 0;
@@ -1165,6 +1194,8 @@ int stp_get_state(stp_handle* h, double* buf) {
   buf[3] = (double)h->nc;
   double* q = buf + 4;
   int rc;
+  // the latest history level is in slot (step - 1) % 3, the one before in (step - 2) % 3
+  const int sl[2] = {(int)((h->step + 2) % 3), (int)((h->step + 1) % 3)};
   if ((rc = get_any(h, q, h->u, h->nc, STP_HOST))) return rc;
   q += h->nc;
   if ((rc = get_any(h, q, h->v, h->nc, STP_HOST))) return rc;
@@ -1173,7 +1204,8 @@ int stp_get_state(stp_handle* h, double* buf) {
   q += h->nw;
   CUDA_TRY(h, cudaMemcpyAsync(q, h->p, sizeof(double) * h->nc, cudaMemcpyDeviceToHost, h->st));
   q += h->nc;
-  for (int l = 0; l < 2; l++) {
+  for (int i = 0; i < 2; i++) {
+    const int l = sl[i];
     if ((rc = get_any(h, q, h->Nu[l], h->nc, STP_HOST))) return rc;
     q += h->nc;
     if ((rc = get_any(h, q, h->Nv[l], h->nc, STP_HOST))) return rc;
@@ -1191,6 +1223,8 @@ int stp_set_state(stp_handle* h, const double* buf) {
   CUDA_TRY(h, cudaSetDevice(h->dev));
   const double* q = buf + 4;
   int rc;
+  const long long step = (long long)buf[2];
+  const int sl[2] = {(int)((step + 2) % 3), (int)((step + 1) % 3)};
   if ((rc = put_any(h, h->u, q, h->nc, STP_HOST))) return rc;
   q += h->nc;
   if ((rc = put_any(h, h->v, q, h->nc, STP_HOST))) return rc;
@@ -1199,7 +1233,8 @@ int stp_set_state(stp_handle* h, const double* buf) {
   q += h->nw;
   CUDA_TRY(h, cudaMemcpyAsync(h->p, q, sizeof(double) * h->nc, cudaMemcpyHostToDevice, h->st));
   q += h->nc;
-  for (int l = 0; l < 2; l++) {
+  for (int i = 0; i < 2; i++) {
+    const int l = sl[i];
     if ((rc = put_any(h, h->Nu[l], q, h->nc, STP_HOST))) return rc;
     q += h->nc;
     if ((rc = put_any(h, h->Nv[l], q, h->nc, STP_HOST))) return rc;
@@ -1207,9 +1242,11 @@ int stp_set_state(stp_handle* h, const double* buf) {
     if ((rc = put_any(h, h->Nw[l], q, h->nw, STP_HOST))) return rc;
     q += h->nw;
   }
+  const int dstep = (int)step;
+  CUDA_TRY(h, cudaMemcpyAsync(h->d_step, &dstep, sizeof(int), cudaMemcpyHostToDevice, h->st));
   CUDA_TRY(h, cudaStreamSynchronize(h->st));
   h->nhist = (int)buf[1];
-  h->step = (long long)buf[2];
+  h->step = step;
   return STP_OK;
 }
 
@@ -1316,6 +1353,198 @@ int stp_eval(stp_handle* h, int term, double* a, double* b, double* c, int where
       return fail(h, STP_EINVAL, "unknown term");
   }
   CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  return STP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// batched channels
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+struct stp_batch {
+  std::vector<stp_handle*> hs;
+  int dev = 0;
+  cudaStream_t st = nullptr, cap = nullptr;
+  bool own = false;
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t x = nullptr;
+  int* d_ctr = nullptr;
+  int* h_ctr = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  std::string err;
+};
+
+namespace {
+
+int bfail(stp_batch* b, int code, const std::string& m) {
+  b->err = m;
+  return code;
+}
+
+#define BTRY(b, call)                                                                                  \
+  do {                                                                                                 \
+    cudaError_t e_ = (call);                                                                           \
+    if (e_ != cudaSuccess) return bfail(b, STP_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+int build_batch_graph(stp_batch* b) {
+  cudaGraph_t G;
+  BTRY(b, cudaGraphCreate(&G, 0));
+  b->g = G;
+  cudaGraphConditionalHandle h_steps;
+  BTRY(b, cudaGraphConditionalHandleCreate(&h_steps, G, 0, cudaGraphCondAssignDefault));
+  BTRY(b, cudaStreamBeginCaptureToGraph(b->cap, G, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+  BTRY(b, launch_batch_begin(b->d_ctr, h_steps, b->cap));
+  cudaGraph_t out = G;
+  BTRY(b, cudaStreamEndCapture(b->cap, &out));
+  cudaGraphNodeParams prm = {};
+  prm.type = cudaGraphNodeTypeConditional;
+  prm.conditional.handle = h_steps;
+  prm.conditional.type = cudaGraphCondTypeWhile;
+  prm.conditional.size = 1;
+  cudaGraphNode_t root = leaf_node(G), wn;
+  BTRY(b, cudaGraphAddNode(&wn, G, &root, nullptr, 1, &prm));
+  cudaGraph_t body = prm.conditional.phGraph_out[0];
+  std::vector<cudaGraphNode_t> tails;
+  for (stp_handle* h : b->hs) {
+    cudaGraphNode_t pre, solved, post;
+    int rc;
+    if ((rc = begin_capture(h, body, nullptr))) return bfail(b, rc, h->err);
+    rc = h->prec == STP_FP64 ? step_pre<double>(h, h->g64, h->cap) : step_pre<float>(h, h->g32, h->cap);
+    if (rc) return bfail(b, rc, h->err);
+    if ((rc = end_capture_tail(h, body, &pre))) return bfail(b, rc, h->err);
+    if ((rc = append_solve(h, body, pre, &solved))) return bfail(b, rc, h->err);
+    if ((rc = begin_capture(h, body, solved))) return bfail(b, rc, h->err);
+    rc = h->prec == STP_FP64 ? step_post<double>(h, h->g64, h->cap) : step_post<float>(h, h->g32, h->cap);
+    if (rc) return bfail(b, rc, h->err);
+    if ((rc = end_capture_tail(h, body, &post))) return bfail(b, rc, h->err);
+    tails.push_back(post);
+  }
+  BTRY(b, cudaStreamBeginCaptureToGraph(b->cap, body, tails.data(), nullptr, tails.size(),
+                                        cudaStreamCaptureModeRelaxed));
+  BTRY(b, launch_batch_end(b->d_ctr, h_steps, b->cap));
+  out = body;
+  BTRY(b, cudaStreamEndCapture(b->cap, &out));
+  BTRY(b, cudaGraphInstantiate(&b->x, G, 0));
+  return STP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int stp_batch_create(stp_handle* const* hs, int n, void* stream, stp_batch** out) {
+  if (!out || !hs || n < 1) return fail(nullptr, STP_EINVAL, "need at least one handle");
+  *out = nullptr;
+  for (int i = 0; i < n; i++) {
+    if (!hs[i]) return fail(nullptr, STP_EINVAL, "NULL handle");
+    if (hs[i]->dev != hs[0]->dev) return fail(nullptr, STP_EINVAL, "all channels must be on one device");
+    if (hs[i]->host_solve) return fail(nullptr, STP_EINVAL, "host-driven solves cannot be batched");
+    for (int j = 0; j < i; j++)
+      if (hs[j] == hs[i]) return fail(nullptr, STP_EINVAL, "a handle appears twice");
+  }
+  stp_batch* b = new stp_batch();
+  b->hs.assign(hs, hs + n);
+  b->dev = hs[0]->dev;
+  cudaSetDevice(b->dev);
+  cudaError_t e = cudaSuccess;
+  if (stream) {
+    b->st = (cudaStream_t)stream;
+  } else {
+    e = cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking);
+    b->own = true;
+  }
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_ctr, sizeof(int) * 4);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_ctr, sizeof(int) * 4);
+  if (e == cudaSuccess) e = cudaEventCreate(&b->e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&b->e1);
+  if (e != cudaSuccess) {
+    g_init_error = std::string("batch set-up: ") + cudaGetErrorString(e);
+    stp_batch_destroy(b);
+    return STP_ECUDA;
+  }
+  *out = b;
+  return STP_OK;
+}
+
+void stp_batch_destroy(stp_batch* b) {
+  if (!b) return;
+  cudaSetDevice(b->dev);
+  if (b->st) cudaStreamSynchronize(b->st);
+  if (b->x) cudaGraphExecDestroy(b->x);
+  if (b->g) cudaGraphDestroy(b->g);
+  if (b->d_ctr) cudaFree(b->d_ctr);
+  if (b->h_ctr) cudaFreeHost(b->h_ctr);
+  if (b->e0) cudaEventDestroy(b->e0);
+  if (b->e1) cudaEventDestroy(b->e1);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  if (b->own && b->st) cudaStreamDestroy(b->st);
+  delete b;
+}
+
+const char* stp_batch_last_error(const stp_batch* b) { return b ? b->err.c_str() : ""; }
+
+int stp_batch_step(stp_batch* b, int nsteps, stp_batch_stats* stats, stp_step_stats* per_channel) {
+  if (!b || nsteps < 0) return STP_EINVAL;
+  BTRY(b, cudaSetDevice(b->dev));
+  if (!b->x) {
+    if (int rc = build_batch_graph(b)) return rc;
+  }
+  for (stp_handle* h : b->hs) {
+    h->launches = 0;
+    if (int rc = arm_solves(h, h->cfg.ptol, h->cfg.pmaxit)) return bfail(b, rc, h->err);
+    BTRY(b, cudaStreamSynchronize(h->st));
+  }
+  b->h_ctr[0] = 0;
+  b->h_ctr[1] = nsteps;
+  BTRY(b, cudaMemcpyAsync(b->d_ctr, b->h_ctr, sizeof(int) * 2, cudaMemcpyHostToDevice, b->st));
+  BTRY(b, cudaEventRecord(b->e0, b->st));
+  BTRY(b, cudaGraphLaunch(b->x, b->st));
+  BTRY(b, cudaEventRecord(b->e1, b->st));
+  BTRY(b, cudaStreamSynchronize(b->st));
+  float ms = 0.f;
+  BTRY(b, cudaEventElapsedTime(&ms, b->e0, b->e1));
+  stp_batch_stats out{};
+  out.steps = nsteps;
+  out.converged = 1;
+  out.gpu_ms = ms;
+  int status = STP_OK;
+  for (size_t i = 0; i < b->hs.size(); i++) {
+    stp_handle* h = b->hs[i];
+    int rc = sync_scalars(h);
+    if (rc) return bfail(b, rc, h->err);
+    BTRY(b, cudaMemcpy(h->h_ctl, h->ctl, sizeof(SolveCtl), cudaMemcpyDeviceToHost));
+    const SolveCtl& c = *h->h_ctl;
+    h->step += nsteps;
+    h->nhist = (int)std::min<long long>(3, h->nhist + nsteps);
+    const int nonconv = nsteps > 0 ? c.nonconv + (c.converged ? 0 : 1) : 0;
+    if (nonconv) {
+      out.converged = 0;
+      status = STP_ENOTCONVERGED;
+    }
+    if (c.bad || h->h_flag[FL_BAD]) status = STP_EDIVERGED;
+    out.cells += (long long)h->nc;
+    out.sweeps += nsteps > 0 ? c.tot_sweeps + c.sweeps : 0;
+    if (per_channel) {
+      stp_step_stats& st = per_channel[i];
+      st.poisson_sweeps = c.sweeps;
+      st.refine_passes = c.passes;
+      st.converged = nonconv == 0;
+      const double nb = h->h_sc[SC_BNORM];
+      st.rel_residual = nb > 0 ? c.res / nb : c.res;
+      st.ubulk = h->h_sc[SC_BULK] + (h->cfg.forcing == 1 ? h->h_sc[SC_SHIFT] : 0.0);
+      st.umax = h->h_sc[SC_UMAX];
+      st.dpdx = h->cfg.forcing == 1 ? h->h_sc[SC_SHIFT] / h->cfg.dt : 0.0;
+      st.step = h->step;
+      st.launches = 0;
+      st.solve_sweeps = nsteps > 0 ? c.tot_sweeps + c.sweeps : 0;
+      st.solve_ms = 0.0;
+    }
+  }
+  if (stats) *stats = out;
+  if (status == STP_EDIVERGED) return bfail(b, status, "NaN or Inf in a channel");
+  if (status == STP_ENOTCONVERGED) return bfail(b, status, "a pressure solve hit pmaxit");
   return STP_OK;
 }
 

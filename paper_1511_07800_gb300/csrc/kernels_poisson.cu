@@ -447,7 +447,8 @@ __global__ void k_difference(const double* __restrict__ a, const double* __restr
     out[q] = (float)(a[q] - b[q]);
 }
 
-__global__ void k_begin(SolveCtl* ctl) {
+__global__ void k_begin(SolveCtl* ctl, int graph, cudaGraphConditionalHandle h_loop) {
+  if (graph) cudaGraphSetConditional(h_loop, 1u);
   if (ctl->solves > 0) {
     ctl->tot_sweeps += ctl->sweeps;
     ctl->tot_kernels += ctl->kernels;
@@ -637,8 +638,8 @@ cudaError_t launch_difference(const double* a, const double* b, float* out, size
   return cudaGetLastError();
 }
 
-cudaError_t launch_begin(SolveCtl* ctl, cudaStream_t s) {
-  k_begin<<<1, 1, 0, s>>>(ctl);
+cudaError_t launch_begin(SolveCtl* ctl, int graph, cudaGraphConditionalHandle h_loop, cudaStream_t s) {
+  k_begin<<<1, 1, 0, s>>>(ctl, graph, h_loop);
   return cudaGetLastError();
 }
 

@@ -236,15 +236,32 @@ __device__ __forceinline__ ViscU<T, LES> visc_w(const Pt<T>& P, const Visc<T, LE
 // ---------------------------------------------------------------------------
 template <typename T, bool LES>
 __global__ void __launch_bounds__(kBX* kBY) k_momentum(Geom<T> g, const T* __restrict__ u, const T* __restrict__ v,
-                                                        const T* __restrict__ w, Visc<T, LES> N, T fx,
-                                                        T* __restrict__ Nu0, T* __restrict__ Nv0, T* __restrict__ Nw0,
-                                                        const T* __restrict__ Nu1, const T* __restrict__ Nv1,
-                                                        const T* __restrict__ Nw1, const T* __restrict__ Nu2,
-                                                        const T* __restrict__ Nv2, const T* __restrict__ Nw2, T b0,
-                                                        T b1, T b2, T dt, T* __restrict__ ru, T* __restrict__ rv,
+                                                        const T* __restrict__ w, Visc<T, LES> N, T fx, Hist<T> H,
+                                                        T dt, T* __restrict__ ru, T* __restrict__ rv,
                                                         T* __restrict__ rw) {
   const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y, k = blockIdx.z;
   if (i >= g.nx || j >= g.ny) return;
+  // history slots and Adams-Bashforth coefficients of step n
+  const int n = __ldg(H.step);
+  const int s0 = n % 3, s1 = (n + 2) % 3, s2 = (n + 1) % 3;
+  T b0 = T(1), b1 = T(0), b2 = T(0);
+  if (n == 1) {
+    b0 = T(1.5);
+    b1 = T(-0.5);
+  } else if (n >= 2) {
+    b0 = T(23.0 / 12.0);
+    b1 = T(-16.0 / 12.0);
+    b2 = T(5.0 / 12.0);
+  }
+  T* __restrict__ Nu0 = H.u[s0];
+  T* __restrict__ Nv0 = H.v[s0];
+  T* __restrict__ Nw0 = H.w[s0];
+  const T* __restrict__ Nu1 = H.u[s1];
+  const T* __restrict__ Nv1 = H.v[s1];
+  const T* __restrict__ Nw1 = H.w[s1];
+  const T* __restrict__ Nu2 = H.u[s2];
+  const T* __restrict__ Nv2 = H.v[s2];
+  const T* __restrict__ Nw2 = H.w[s2];
   Pt<T> P(g, i, j, k);
   const int q = at(g.nx, g.ny, i, j, k);
   const T hdt = T(0.5) * dt;
@@ -439,19 +456,40 @@ cudaError_t launch_viscosity(const Geom<T>& g, const T* u, const T* v, const T* 
 
 template <typename T>
 cudaError_t launch_momentum(const Geom<T>& g, bool les, const T* u, const T* v, const T* w, const T* nu, T nu0,
-                            T fx, T* Nu0, T* Nv0, T* Nw0, const T* Nu1, const T* Nv1, const T* Nw1, const T* Nu2,
-                            const T* Nv2, const T* Nw2, T b0, T b1, T b2, T dt, T* ru, T* rv, T* rw,
-                            cudaStream_t s) {
+                            T fx, Hist<T> H, T dt, T* ru, T* rv, T* rw, cudaStream_t s) {
   Launch l = plane_launch(g.nx, g.ny, g.nz + 1);
   if (les) {
     Visc<T, true> N{nu, nu0, g.nx, g.ny, g.nz};
-    k_momentum<T, true><<<l.grid, l.block, 0, s>>>(g, u, v, w, N, fx, Nu0, Nv0, Nw0, Nu1, Nv1, Nw1, Nu2, Nv2, Nw2,
-                                                  b0, b1, b2, dt, ru, rv, rw);
+    k_momentum<T, true><<<l.grid, l.block, 0, s>>>(g, u, v, w, N, fx, H, dt, ru, rv, rw);
   } else {
     Visc<T, false> N{nu, nu0, g.nx, g.ny, g.nz};
-    k_momentum<T, false><<<l.grid, l.block, 0, s>>>(g, u, v, w, N, fx, Nu0, Nv0, Nw0, Nu1, Nv1, Nw1, Nu2, Nv2, Nw2,
-                                                   b0, b1, b2, dt, ru, rv, rw);
+    k_momentum<T, false><<<l.grid, l.block, 0, s>>>(g, u, v, w, N, fx, H, dt, ru, rv, rw);
   }
+  return cudaGetLastError();
+}
+
+__global__ void k_step_end(int* step) { *step += 1; }
+
+__global__ void k_batch_begin(int* c, cudaGraphConditionalHandle h) {
+  c[0] = 0;
+  cudaGraphSetConditional(h, c[1] > 0 ? 1u : 0u);
+}
+__global__ void k_batch_end(int* c, cudaGraphConditionalHandle h) {
+  c[0] += 1;
+  cudaGraphSetConditional(h, c[0] < c[1] ? 1u : 0u);
+}
+
+cudaError_t launch_batch_begin(int* counter, cudaGraphConditionalHandle h_steps, cudaStream_t s) {
+  k_batch_begin<<<1, 1, 0, s>>>(counter, h_steps);
+  return cudaGetLastError();
+}
+cudaError_t launch_batch_end(int* counter, cudaGraphConditionalHandle h_steps, cudaStream_t s) {
+  k_batch_end<<<1, 1, 0, s>>>(counter, h_steps);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_step_end(int* step, cudaStream_t s) {
+  k_step_end<<<1, 1, 0, s>>>(step);
   return cudaGetLastError();
 }
 
@@ -536,9 +574,8 @@ cudaError_t launch_convert(Td* dst, const Ts* src, size_t n, cudaStream_t s) {
 
 #define STP_INST(T)                                                                                                 \
   template cudaError_t launch_viscosity<T>(const Geom<T>&, const T*, const T*, const T*, T, T*, cudaStream_t);      \
-  template cudaError_t launch_momentum<T>(const Geom<T>&, bool, const T*, const T*, const T*, const T*, T, T, T*, \
-                                          T*, T*, const T*, const T*, const T*, const T*, const T*, const T*, T, T, \
-                                          T, T, T*, T*, T*, cudaStream_t);                                          \
+  template cudaError_t launch_momentum<T>(const Geom<T>&, bool, const T*, const T*, const T*, const T*, T, T,     \
+                                          Hist<T>, T, T*, T*, T*, cudaStream_t);                                    \
   template cudaError_t launch_cn_sweep<T>(const Geom<T>&, bool, const T*, T, T, const T*, const T*, const T*,      \
                                           const T*, const T*, const T*, T*, T*, T*, cudaStream_t);                  \
   template cudaError_t launch_explicit_only<T>(const Geom<T>&, bool, const T*, const T*, const T*, const T*, T, T, \

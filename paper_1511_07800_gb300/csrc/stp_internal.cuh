@@ -107,11 +107,24 @@ template <typename T>
 cudaError_t launch_viscosity(const Geom<T>& g, const T* u, const T* v, const T* w, T nu0, T* nu,
                              cudaStream_t s);
 
+// Adams-Bashforth history: three slots per component; step n (the number
+// of steps taken since the fields were set, read on the device) writes
+// N^n into slot n % 3 and reads N^{n-1}, N^{n-2} from the others, with
+// forward Euler at n = 0, AB2 at n = 1 and AB3 after.
+template <typename T>
+struct Hist {
+  T* u[3];
+  T* v[3];
+  T* w[3];
+  const int* step;
+};
+
 template <typename T>
 cudaError_t launch_momentum(const Geom<T>& g, bool les, const T* u, const T* v, const T* w, const T* nu,
-                            T nu0, T fx, T* Nu0, T* Nv0, T* Nw0, const T* Nu1, const T* Nv1, const T* Nw1,
-                            const T* Nu2, const T* Nv2, const T* Nw2, T b0, T b1, T b2, T dt, T* ru, T* rv,
-                            T* rw, cudaStream_t s);
+                            T nu0, T fx, Hist<T> H, T dt, T* ru, T* rv, T* rw, cudaStream_t s);
+
+// end of a step: (*step)++
+cudaError_t launch_step_end(int* step, cudaStream_t s);
 
 template <typename T>
 cudaError_t launch_cn_sweep(const Geom<T>& g, bool les, const T* nu, T nu0, T hdt, const T* ru, const T* rv,
@@ -167,7 +180,12 @@ cudaError_t launch_addcorr(double* p, const float* d, size_t n, cudaStream_t s);
 // out = a - b (FP64 in, FP32 out)
 cudaError_t launch_difference(const double* a, const double* b, float* out, size_t n, cudaStream_t s);
 // start of a solve: fold the previous solve into the totals, reset the state
-cudaError_t launch_begin(SolveCtl* ctl, cudaStream_t s);
+// (in a graph it also arms the WHILE handle h_loop of an FP64 solve)
+cudaError_t launch_begin(SolveCtl* ctl, int graph, cudaGraphConditionalHandle h_loop, cudaStream_t s);
+
+// batched step: counter[0] = steps done, counter[1] = steps wanted
+cudaError_t launch_batch_begin(int* counter, cudaGraphConditionalHandle h_steps, cudaStream_t s);
+cudaError_t launch_batch_end(int* counter, cudaGraphConditionalHandle h_steps, cudaStream_t s);
 
 // Velocity correction (Eq. project u_p_1) with walls; reduces the volume
 // mean of u and max |u|.  The pressure is FP64 in both modes; ihz64 and dz64

@@ -159,6 +159,24 @@ def os_mode(cfg, amp, Re, alpha):
     return u, np.zeros_like(u), w, lam
 
 
+def batched_instances(count=64, seed=2, sizes=(32, 48, 64, 96, 128)):
+    """Uneven-channel batch (sizes drawn per dimension from `sizes`, Re
+    uniform in [5000, 10000], Orr-Sommerfeld amplitude log-uniform in
+    [1e-5, 1e-3]); box 2 pi x pi x 2, dt 2e-3.  Instance i uses seed 1000 + i
+    for its noise.  Returns a list of (cfg, (u, v, w))."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        nx, ny, nz = (int(rng.choice(sizes)) for _ in range(3))
+        Re = float(rng.uniform(5000.0, 10000.0))
+        amp = float(10 ** rng.uniform(-5, -3))
+        cfg = preset("os_instability", nx=nx, ny=ny, nz=nz, nu=1.0 / Re, fx=2.0 / Re)
+        u0, v0, w0 = poiseuille(cfg, 1.0)
+        du, dv, dw, _ = os_mode(cfg, amp, Re, 1.0)
+        out.append((cfg, noise(cfg, 1e-6, 1000 + i, (u0 + du, v0 + dv, w0 + dw))))
+    return out
+
+
 def initial_fields(name, cfg=None, seed=0):
     """Initial (u, v, w) of a named workload."""
     cfg = cfg or preset(name)

@@ -60,6 +60,11 @@ class StepStats(ctypes.Structure):
                 ("solve_sweeps", ctypes.c_longlong), ("solve_ms", ctypes.c_double)]
 
 
+class BatchStats(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_longlong), ("cells", ctypes.c_longlong), ("sweeps", ctypes.c_longlong),
+                ("converged", ctypes.c_int), ("gpu_ms", ctypes.c_double)]
+
+
 class SolveStats(ctypes.Structure):
     _fields_ = [("sweeps", ctypes.c_int), ("refine_passes", ctypes.c_int),
                 ("converged", ctypes.c_int), ("rel_residual", ctypes.c_double)]
@@ -71,7 +76,8 @@ EXPORTS = ("stp_config_defaults", "stp_init", "stp_destroy", "stp_last_error", "
            "stp_unet_last_error", "stp_unet_set_params", "stp_unet_get_params", "stp_unet_forward",
            "stp_unet_gradient", "stp_unet_train_step", "stp_unet_train_pairs", "stp_unet_eval_pairs",
            "stp_set_learned_guess", "stp_set_harvest", "stp_unet_set_output_scale", "stp_state_size",
-           "stp_get_state", "stp_set_state")
+           "stp_get_state", "stp_set_state", "stp_batch_create", "stp_batch_destroy", "stp_batch_last_error",
+           "stp_batch_step")
 
 _lib = None
 
@@ -118,6 +124,12 @@ def lib():
     L.stp_unet_train_pairs.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_float, ctypes.POINTER(ctypes.c_float)]
     L.stp_unet_eval_pairs.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.POINTER(ctypes.c_float)]
     L.stp_set_learned_guess.argtypes = [vp, vp]
+    L.stp_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, vp, ctypes.POINTER(vp)]
+    L.stp_batch_destroy.argtypes = [vp]
+    L.stp_batch_destroy.restype = None
+    L.stp_batch_last_error.argtypes = [vp]
+    L.stp_batch_last_error.restype = ctypes.c_char_p
+    L.stp_batch_step.argtypes = [vp, ctypes.c_int, ctypes.POINTER(BatchStats), ctypes.POINTER(StepStats)]
     L.stp_state_size.argtypes = [vp]
     L.stp_state_size.restype = ctypes.c_longlong
     L.stp_get_state.argtypes = [vp, vp]
@@ -365,6 +377,38 @@ class UNet:
     def close(self):
         if getattr(self, "_h", None) is not None and _lib is not None:
             _lib.stp_unet_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+
+class Batch:
+    """Many channels advanced together by one graph launch (stp_batch_*)."""
+
+    def __init__(self, channels, stream=None):
+        self.channels = list(channels)
+        arr = (ctypes.c_void_p * len(self.channels))(*[c._h.value for c in self.channels])
+        h = ctypes.c_void_p()
+        rc = lib().stp_batch_create(arr, len(self.channels), stream, ctypes.byref(h))
+        if rc != STP_OK:
+            raise StpError(rc, lib().stp_last_error(None).decode())
+        self._h = h
+
+    def step(self, n=1):
+        st = BatchStats()
+        per = (StepStats * len(self.channels))()
+        rc = lib().stp_batch_step(self._h, int(n), ctypes.byref(st), per)
+        if rc not in (STP_OK, STP_ENOTCONVERGED):
+            raise StpError(rc, lib().stp_batch_last_error(self._h).decode())
+        return dict(steps=st.steps, cells=st.cells, sweeps=st.sweeps, converged=bool(st.converged),
+                    gpu_ms=st.gpu_ms, status=rc,
+                    channels=[dict(sweeps=p.poisson_sweeps, converged=bool(p.converged), rel_res=p.rel_residual,
+                                   ubulk=p.ubulk, umax=p.umax, step=p.step) for p in per])
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and _lib is not None:
+            _lib.stp_batch_destroy(self._h)
             self._h = None
 
     def __del__(self):
