@@ -28,7 +28,8 @@
  * with bounded grid barriers between its sweeps (slower on GB300: kept as an
  * option).  The FP32 sweep kernel's tile shape (z levels per thread, rows
  * per block) is picked on first use by timing the variants on the grid
- * (STP_SWEEP_VARIANT=<0..5> forces one).  With the environment variable STP_HOST_SOLVE=1 at
+ * (STP_SWEEP_VARIANT=<0..8> forces one; variants 6..8 pack warps along the
+ * plane for rows shorter than 128 cells).  With STP_HOST_SOLVE=1 at
  * stp_init the same kernels are driven from the host instead, one host
  * round trip per SRJ cycle (for profilers that cannot see kernels inside
  * conditional graphs).
@@ -166,6 +167,7 @@ typedef struct stp_batch_stats {
     long long sweeps;        /* SRJ sweeps over all channels and steps         */
     int converged;           /* 1 if every solve of every channel met its ptol  */
     double gpu_ms;           /* GPU time of the launch (CUDA events)           */
+    long long kernels;       /* kernels the launch ran                         */
 } stp_batch_stats;
 
 /* The handles stay owned by the caller and must outlive the batch; they
@@ -174,6 +176,28 @@ typedef struct stp_batch_stats {
 int stp_batch_create(stp_handle *const *handles, int n, void *stream, stp_batch **out);
 void stp_batch_destroy(stp_batch *b);
 const char *stp_batch_last_error(const stp_batch *b);
+
+/* Lock-step groups of the batch (built at the first stp_batch_step).
+   Channels in FP32 with refinement that share the SRJ cycle length M (at
+   least two of them, rows a multiple of 4 cells, no learned guess) are
+   solved together: every kernel of their pressure solve covers all of them
+   in one launch, each channel keeping its own schedule, residuals and
+   stopping decisions, so its results are bitwise those of its own solve.
+   Environment, read when the graph is built: STP_BATCH_GROUPS=0 keeps every
+   channel on its own solve; groups are split into parts whose inner
+   working set (12 bytes a cell) fills at most half the L2, or at most n
+   cells with STP_BATCH_GROUP_CELLS=<n> (0: no split);
+   STP_BATCH_GROUP_CHAIN=1 runs the groups' solves one after another
+   instead of side by side. */
+typedef struct stp_batch_group {
+    int channels, M;
+    int variant;        /* FP32 sweep tile variant picked by timing the group   */
+    long long cells;
+    float sweep_us;     /* measured grouped sweep, every channel active (0: not timed) */
+} stp_batch_group;
+
+/* Number of groups; fills out[0 .. min(n, max_groups)) when out is not NULL. */
+int stp_batch_groups(const stp_batch *b, int max_groups, stp_batch_group *out);
 
 /* Advance every channel nsteps steps in one graph launch; per_channel
    (nullable, n entries) receives each channel's stats of its last step. */

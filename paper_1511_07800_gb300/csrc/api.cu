@@ -474,7 +474,7 @@ int tune_sweep(stp_handle* h) {
   if (h->prec != STP_FP32_REFINE || h->nx % 4) return STP_OK;
   if (const char* env = std::getenv("STP_SWEEP_VARIANT")) {
     const int v = std::atoi(env);
-    if (sweep_variant_ok(v, h->nz)) h->sweep_variant = v;
+    if (sweep_variant_ok(v, h->nx, h->ny, h->nz)) h->sweep_variant = v;
     return STP_OK;
   }
   static std::mutex mu;
@@ -494,7 +494,7 @@ int tune_sweep(stp_handle* h) {
   float best = 1e30f;
   int bv = 0;
   for (int v = 0; v < sweep_variant_count(); v++) {
-    if (!sweep_variant_ok(v, h->nz)) continue;
+    if (!sweep_variant_ok(v, h->nx, h->ny, h->nz)) continue;
     set_sweep_variant(v);
     for (int w = 0; w < 3; w++) CUDA_TRY(h, launch_sweep<float>(h->g32, h->d1, h->r32, 1.0f, h->d2, h->st));
     CUDA_TRY(h, cudaEventRecord(h->ev0, h->st));
@@ -1361,6 +1361,15 @@ int stp_eval(stp_handle* h, int term, double* a, double* b, double* c, int where
 // ---------------------------------------------------------------------------
 }  // extern "C"
 
+// channels of a batch solved in lock step (same SRJ cycle length, FP32)
+struct BatchGroup {
+  std::vector<stp_handle*> hs;
+  std::vector<int> idx;  // positions in the batch
+  Group G{};
+  void* mem = nullptr;   // device: GState | GChan[n] | soff | voff | pass_on | inner_on
+  float sweep_us = 0.f;  // measured time of one grouped sweep over all channels
+};
+
 struct stp_batch {
   std::vector<stp_handle*> hs;
   int dev = 0;
@@ -1371,6 +1380,9 @@ struct stp_batch {
   int* d_ctr = nullptr;
   int* h_ctr = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
+  std::vector<BatchGroup> groups;
+  std::vector<int> in_group;   // per channel: its group, or -1 (own solve)
+  long long step_kernels = 0;  // kernels per step outside the pressure solves
   std::string err;
 };
 
@@ -1387,7 +1399,235 @@ int bfail(stp_batch* b, int code, const std::string& m) {
     if (e_ != cudaSuccess) return bfail(b, STP_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
   } while (0)
 
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Channels eligible for a lock-step group: FP32 with refinement, rows of
+// float4, no learned guess, no persistent-cycle kernel.  Groups are formed
+// per SRJ cycle length when at least two channels share it;
+// STP_BATCH_GROUPS=0 keeps every channel on its own solve.
+void plan_groups(stp_batch* b) {
+  b->in_group.assign(b->hs.size(), -1);
+  const char* env = std::getenv("STP_BATCH_GROUPS");
+  if (env && std::atoi(env) == 0) return;
+  std::map<int, std::vector<int>> byM;
+  for (size_t i = 0; i < b->hs.size(); i++) {
+    stp_handle* h = b->hs[i];
+    if (h->prec != STP_FP32_REFINE || h->nx % 4 || h->net || h->cycle_blocks > 0) continue;
+    byM[(int)h->omega.size()].push_back((int)i);
+  }
+  // A group's inner solve touches d, d' and r of all its channels every
+  // sweep (12 bytes a cell).  Groups are split into parts whose inner
+  // working set fills at most half the L2, so that consecutive sweeps of a
+  // part hit in L2 (STP_BATCH_GROUP_CELLS=<n> sets the cap in cells, 0: no
+  // split); largest channels first, each into the part with the fewest
+  // cells that still has room.
+  int l2 = 0;
+  cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, b->dev);
+  long long cap = l2 > 0 ? (long long)l2 / 2 / 12 : 0;
+  if (const char* e = std::getenv("STP_BATCH_GROUP_CELLS")) cap = std::atoll(e);
+  for (auto& kv : byM) {
+    if (kv.second.size() < 2) continue;
+    std::vector<int> order = kv.second;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return b->hs[a]->nc > b->hs[c]->nc; });
+    std::vector<std::vector<int>> parts;
+    std::vector<long long> cells;
+    for (int i : order) {
+      const long long nc = (long long)b->hs[i]->nc;
+      int best = -1;
+      for (size_t q = 0; q < parts.size(); q++)
+        if ((cap <= 0 || cells[q] + nc <= cap) && (best < 0 || cells[q] < cells[best])) best = (int)q;
+      if (best < 0) {
+        parts.emplace_back();
+        cells.push_back(0);
+        best = (int)parts.size() - 1;
+      }
+      parts[best].push_back(i);
+      cells[best] += nc;
+    }
+    for (auto& part : parts) {
+      if (part.size() < 2) continue;
+      std::sort(part.begin(), part.end());
+      BatchGroup grp;
+      grp.idx = part;
+      for (int i : part) {
+        grp.hs.push_back(b->hs[i]);
+        b->in_group[i] = (int)b->groups.size();
+      }
+      grp.G.M = kv.first;
+      b->groups.push_back(grp);
+    }
+  }
+}
+
+// voff and the tile total of sweep variant v for the group's channels
+bool group_voff(const BatchGroup& grp, int v, std::vector<int>& voff) {
+  voff.assign(grp.hs.size() + 1, 0);
+  for (size_t c = 0; c < grp.hs.size(); c++) {
+    const stp_handle* h = grp.hs[c];
+    const int t = group_sweep_tiles(v, h->nx, h->ny, h->nz);
+    if (t < 0) return false;
+    voff[c + 1] = voff[c] + t;
+  }
+  return true;
+}
+
+// Device tables of a group, and its sweep tile variant: every variant valid
+// for all its channels is timed on the whole group (3 warm-up and 20 timed
+// grouped sweeps, every channel active, CUDA events) and the fastest kept.
+// STP_SWEEP_VARIANT=<v> forces a variant.  All variants compute the same values.
+int setup_group(stp_batch* b, BatchGroup& grp) {
+  const int n = (int)grp.hs.size();
+  const size_t o_ch = align256(sizeof(GState));
+  const size_t o_soff = o_ch + align256(sizeof(GChan) * n);
+  const size_t o_voff = o_soff + align256(sizeof(int) * (n + 1));
+  const size_t o_pass = o_voff + align256(sizeof(int) * (n + 1));
+  const size_t o_inner = o_pass + align256(sizeof(int) * n);
+  const size_t total = o_inner + align256(sizeof(int) * n);
+  BTRY(b, cudaMalloc(&grp.mem, total));
+  char* base = (char*)grp.mem;
+  Group& G = grp.G;
+  G.gs = (GState*)base;
+  G.ch = (const GChan*)(base + o_ch);
+  G.soff = (const int*)(base + o_soff);
+  G.voff = (const int*)(base + o_voff);
+  G.pass_on = (int*)(base + o_pass);
+  G.inner_on = (int*)(base + o_inner);
+  G.n = n;
+  std::vector<GChan> ch(n);
+  std::vector<int> soff(n + 1, 0);
+  for (int c = 0; c < n; c++) {
+    stp_handle* h = grp.hs[c];
+    GChan& x = ch[c];
+    x.g32 = h->g32;
+    x.g64 = h->g64;
+    x.p = h->p;
+    x.b = h->b;
+    x.d1 = h->d1;
+    x.d2 = h->d2;
+    x.r32 = h->r32;
+    x.omega = h->d_omega32;
+    x.ctl = h->ctl;
+    x.red = h->red;
+    soff[c + 1] = soff[c] + group_scalar_tiles(h->nx, h->ny, h->nz);
+  }
+  G.stiles = soff[n];
+  BTRY(b, cudaMemcpy(base + o_ch, ch.data(), sizeof(GChan) * n, cudaMemcpyHostToDevice));
+  BTRY(b, cudaMemcpy(base + o_soff, soff.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice));
+  BTRY(b, cudaMemset(base, 0, o_ch));
+  BTRY(b, cudaMemset(base + o_pass, 0, total - o_pass));
+  std::vector<int> voff;
+  int forced = -1;
+  if (const char* env = std::getenv("STP_SWEEP_VARIANT")) forced = std::atoi(env);
+  std::vector<int> cand;
+  for (int v = 0; v < sweep_variant_count(); v++)
+    if (group_voff(grp, v, voff) && (forced < 0 || v == forced)) cand.push_back(v);
+  if (cand.empty()) cand.push_back(0);  // every member has nx % 4 == 0: variant 0 always fits
+  int best_v = cand[0];
+  float best = 1e30f;
+  if (cand.size() > 1) {
+    // scratch contents for timing: d = 0, r = 0, every channel active
+    for (stp_handle* h : grp.hs) {
+      BTRY(b, cudaMemsetAsync(h->d1, 0, sizeof(float) * h->nc, b->st));
+      BTRY(b, cudaMemsetAsync(h->r32, 0, sizeof(float) * h->nc, b->st));
+    }
+    BTRY(b, cudaMemsetAsync(G.inner_on, 1, sizeof(int) * n, b->st));
+    for (int v : cand) {
+      group_voff(grp, v, voff);
+      BTRY(b, cudaMemcpyAsync(base + o_voff, voff.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, b->st));
+      G.variant = v;
+      G.vtiles = voff[n];
+      for (int w = 0; w < 3; w++) BTRY(b, launch_group_sweep(G, w % G.M, b->st));
+      BTRY(b, cudaEventRecord(b->e0, b->st));
+      for (int w = 0; w < 20; w++) BTRY(b, launch_group_sweep(G, w % G.M, b->st));
+      BTRY(b, cudaEventRecord(b->e1, b->st));
+      BTRY(b, cudaEventSynchronize(b->e1));
+      float ms = 0.f;
+      BTRY(b, cudaEventElapsedTime(&ms, b->e0, b->e1));
+      if (ms < best) {
+        best = ms;
+        best_v = v;
+      }
+    }
+    BTRY(b, cudaMemsetAsync(G.inner_on, 0, sizeof(int) * n, b->st));
+    grp.sweep_us = best * 1e3f / 20.f;
+  }
+  group_voff(grp, best_v, voff);
+  BTRY(b, cudaMemcpyAsync(base + o_voff, voff.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, b->st));
+  BTRY(b, cudaStreamSynchronize(b->st));
+  G.variant = best_v;
+  G.vtiles = voff[n];
+  return STP_OK;
+}
+
+// graph pieces of the batch, captured on b->cap
+int bcap_begin(stp_batch* b, cudaGraph_t g, const cudaGraphNode_t* deps, size_t nd) {
+  BTRY(b, cudaStreamBeginCaptureToGraph(b->cap, g, nd ? deps : nullptr, nullptr, nd, cudaStreamCaptureModeRelaxed));
+  return STP_OK;
+}
+int bcap_end(stp_batch* b, cudaGraph_t g, cudaGraphNode_t* tail) {
+  cudaStreamCaptureStatus st;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  if (tail) {
+    BTRY(b, cudaStreamGetCaptureInfo(b->cap, &st, nullptr, nullptr, &deps, nullptr, &nd));
+    *tail = nd ? deps[nd - 1] : nullptr;
+  }
+  cudaGraph_t out = g;
+  BTRY(b, cudaStreamEndCapture(b->cap, &out));
+  return STP_OK;
+}
+int badd_cond(stp_batch* b, cudaGraph_t g, cudaGraphNode_t dep, cudaGraphConditionalHandle hc,
+              cudaGraphConditionalNodeType type, cudaGraph_t* body, cudaGraphNode_t* node) {
+  cudaGraphNodeParams prm = {};
+  prm.type = cudaGraphNodeTypeConditional;
+  prm.conditional.handle = hc;
+  prm.conditional.type = type;
+  prm.conditional.size = 1;
+  BTRY(b, cudaGraphAddNode(node, g, dep ? &dep : nullptr, nullptr, dep ? 1 : 0, &prm));
+  *body = prm.conditional.phGraph_out[0];
+  return STP_OK;
+}
+
+// The lock-step solve of a group after the nodes deps (the end of every
+// member's velocity part); *last receives its final node.  Same loop
+// structure as one channel's FP32 solve, with grouped kernels.
+int append_group_solve(stp_batch* b, BatchGroup& grp, cudaGraph_t G, const std::vector<cudaGraphNode_t>& deps,
+                       cudaGraphNode_t* last) {
+  int rc;
+  cudaGraphConditionalHandle h_pass, h_loop, h_body;
+  cudaGraph_t pb, wb, ib;
+  cudaGraphNode_t tail, pn, wn, ifn;
+  BTRY(b, cudaGraphConditionalHandleCreate(&h_pass, G, 0, cudaGraphCondAssignDefault));
+  if ((rc = bcap_begin(b, G, deps.data(), deps.size()))) return rc;
+  BTRY(b, launch_group_begin(grp.G, b->cap));
+  BTRY(b, launch_group_outer(grp.G, 0, h_pass, b->cap));
+  if ((rc = bcap_end(b, G, &tail))) return rc;
+  if ((rc = badd_cond(b, G, tail, h_pass, cudaGraphCondTypeWhile, &pb, &pn))) return rc;
+  BTRY(b, cudaGraphConditionalHandleCreate(&h_loop, pb, 1, 0));
+  if ((rc = bcap_begin(b, pb, nullptr, 0))) return rc;
+  BTRY(b, launch_group_pass_begin(grp.G, h_loop, b->cap));
+  if ((rc = bcap_end(b, pb, nullptr))) return rc;
+  if ((rc = badd_cond(b, pb, leaf_node(pb), h_loop, cudaGraphCondTypeWhile, &wb, &wn))) return rc;
+  BTRY(b, cudaGraphConditionalHandleCreate(&h_body, wb, 0, cudaGraphCondAssignDefault));
+  if ((rc = bcap_begin(b, wb, nullptr, 0))) return rc;
+  BTRY(b, launch_group_check(grp.G, h_loop, h_body, b->cap));
+  if ((rc = bcap_end(b, wb, nullptr))) return rc;
+  if ((rc = badd_cond(b, wb, leaf_node(wb), h_body, cudaGraphCondTypeIf, &ib, &ifn))) return rc;
+  if ((rc = bcap_begin(b, ib, nullptr, 0))) return rc;
+  for (int m = 0; m < grp.G.M; m++) BTRY(b, launch_group_sweep(grp.G, m, b->cap));
+  if ((rc = bcap_end(b, ib, nullptr))) return rc;
+  if ((rc = bcap_begin(b, pb, &wn, 1))) return rc;
+  BTRY(b, launch_group_addcorr(grp.G, b->cap));
+  BTRY(b, launch_group_outer(grp.G, 1, h_pass, b->cap));
+  if ((rc = bcap_end(b, pb, nullptr))) return rc;
+  *last = pn;
+  return STP_OK;
+}
+
 int build_batch_graph(stp_batch* b) {
+  plan_groups(b);
+  for (BatchGroup& grp : b->groups)
+    if (int rc = setup_group(b, grp)) return rc;
   cudaGraph_t G;
   BTRY(b, cudaGraphCreate(&G, 0));
   b->g = G;
@@ -1405,19 +1645,45 @@ int build_batch_graph(stp_batch* b) {
   cudaGraphNode_t root = leaf_node(G), wn;
   BTRY(b, cudaGraphAddNode(&wn, G, &root, nullptr, 1, &prm));
   cudaGraph_t body = prm.conditional.phGraph_out[0];
-  std::vector<cudaGraphNode_t> tails;
-  for (stp_handle* h : b->hs) {
-    cudaGraphNode_t pre, solved, post;
+  // per channel: velocity part -> its own solve, or its group's -> projection
+  const size_t n = b->hs.size();
+  std::vector<cudaGraphNode_t> pre(n), solved(n), tails;
+  b->step_kernels = 0;
+  for (size_t i = 0; i < n; i++) {
+    stp_handle* h = b->hs[i];
     int rc;
+    const long long l0 = h->launches;
     if ((rc = begin_capture(h, body, nullptr))) return bfail(b, rc, h->err);
     rc = h->prec == STP_FP64 ? step_pre<double>(h, h->g64, h->cap) : step_pre<float>(h, h->g32, h->cap);
     if (rc) return bfail(b, rc, h->err);
-    if ((rc = end_capture_tail(h, body, &pre))) return bfail(b, rc, h->err);
-    if ((rc = append_solve(h, body, pre, &solved))) return bfail(b, rc, h->err);
-    if ((rc = begin_capture(h, body, solved))) return bfail(b, rc, h->err);
+    if ((rc = end_capture_tail(h, body, &pre[i]))) return bfail(b, rc, h->err);
+    b->step_kernels += h->launches - l0;
+    if (b->in_group[i] < 0 && (rc = append_solve(h, body, pre[i], &solved[i]))) return bfail(b, rc, h->err);
+  }
+  // STP_BATCH_GROUP_CHAIN=1: one group's solve after another (each has the
+  // L2 to itself); otherwise the groups' solves are independent branches
+  const char* chain_env = std::getenv("STP_BATCH_GROUP_CHAIN");
+  const bool chain = chain_env && std::atoi(chain_env) != 0;
+  cudaGraphNode_t prev_group = nullptr;
+  for (BatchGroup& grp : b->groups) {
+    std::vector<cudaGraphNode_t> deps;
+    for (int i : grp.idx) deps.push_back(pre[i]);
+    if (chain && prev_group) deps.push_back(prev_group);
+    cudaGraphNode_t last;
+    if (int rc = append_group_solve(b, grp, body, deps, &last)) return rc;
+    for (int i : grp.idx) solved[i] = last;
+    prev_group = last;
+  }
+  for (size_t i = 0; i < n; i++) {
+    stp_handle* h = b->hs[i];
+    int rc;
+    cudaGraphNode_t post;
+    const long long l0 = h->launches;
+    if ((rc = begin_capture(h, body, solved[i]))) return bfail(b, rc, h->err);
     rc = h->prec == STP_FP64 ? step_post<double>(h, h->g64, h->cap) : step_post<float>(h, h->g32, h->cap);
     if (rc) return bfail(b, rc, h->err);
     if ((rc = end_capture_tail(h, body, &post))) return bfail(b, rc, h->err);
+    b->step_kernels += h->launches - l0;
     tails.push_back(post);
   }
   BTRY(b, cudaStreamBeginCaptureToGraph(b->cap, body, tails.data(), nullptr, tails.size(),
@@ -1478,12 +1744,30 @@ void stp_batch_destroy(stp_batch* b) {
   if (b->h_ctr) cudaFreeHost(b->h_ctr);
   if (b->e0) cudaEventDestroy(b->e0);
   if (b->e1) cudaEventDestroy(b->e1);
+  for (BatchGroup& grp : b->groups)
+    if (grp.mem) cudaFree(grp.mem);
   if (b->cap) cudaStreamDestroy(b->cap);
   if (b->own && b->st) cudaStreamDestroy(b->st);
   delete b;
 }
 
 const char* stp_batch_last_error(const stp_batch* b) { return b ? b->err.c_str() : ""; }
+
+int stp_batch_groups(const stp_batch* b, int max_groups, stp_batch_group* out) {
+  if (!b) return STP_EINVAL;
+  const int n = (int)b->groups.size();
+  for (int i = 0; i < n && i < max_groups && out; i++) {
+    const BatchGroup& grp = b->groups[i];
+    stp_batch_group& o = out[i];
+    o.channels = grp.G.n;
+    o.M = grp.G.M;
+    o.variant = grp.G.variant;
+    o.cells = 0;
+    for (const stp_handle* h : grp.hs) o.cells += (long long)h->nc;
+    o.sweep_us = grp.sweep_us;
+  }
+  return n;
+}
 
 int stp_batch_step(stp_batch* b, int nsteps, stp_batch_stats* stats, stp_step_stats* per_channel) {
   if (!b || nsteps < 0) return STP_EINVAL;
@@ -1496,6 +1780,7 @@ int stp_batch_step(stp_batch* b, int nsteps, stp_batch_stats* stats, stp_step_st
     if (int rc = arm_solves(h, h->cfg.ptol, h->cfg.pmaxit)) return bfail(b, rc, h->err);
     BTRY(b, cudaStreamSynchronize(h->st));
   }
+  for (BatchGroup& grp : b->groups) BTRY(b, cudaMemsetAsync(grp.G.gs, 0, sizeof(GState), b->st));
   b->h_ctr[0] = 0;
   b->h_ctr[1] = nsteps;
   BTRY(b, cudaMemcpyAsync(b->d_ctr, b->h_ctr, sizeof(int) * 2, cudaMemcpyHostToDevice, b->st));
@@ -1509,6 +1794,14 @@ int stp_batch_step(stp_batch* b, int nsteps, stp_batch_stats* stats, stp_step_st
   out.steps = nsteps;
   out.converged = 1;
   out.gpu_ms = ms;
+  // kernels run: the velocity parts and projections, the step counter's
+  // begin and per-step end, the channels' own solves and the grouped solves
+  out.kernels = 1 + nsteps * (b->step_kernels + 1);
+  for (BatchGroup& grp : b->groups) {
+    GState gs;
+    BTRY(b, cudaMemcpy(&gs, grp.G.gs, sizeof(GState), cudaMemcpyDeviceToHost));
+    out.kernels += gs.kernels;
+  }
   int status = STP_OK;
   for (size_t i = 0; i < b->hs.size(); i++) {
     stp_handle* h = b->hs[i];
@@ -1526,6 +1819,7 @@ int stp_batch_step(stp_batch* b, int nsteps, stp_batch_stats* stats, stp_step_st
     if (c.bad || h->h_flag[FL_BAD]) status = STP_EDIVERGED;
     out.cells += (long long)h->nc;
     out.sweeps += nsteps > 0 ? c.tot_sweeps + c.sweeps : 0;
+    if (b->in_group[i] < 0 && nsteps > 0) out.kernels += c.tot_kernels + c.kernels;
     if (per_channel) {
       stp_step_stats& st = per_channel[i];
       st.poisson_sweeps = c.sweeps;

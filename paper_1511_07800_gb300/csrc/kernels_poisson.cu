@@ -18,43 +18,12 @@
 #include <algorithm>
 
 #include "device_util.cuh"
+#include "poisson_common.cuh"
 #include "stp_internal.cuh"
 
 namespace stp {
 
 namespace {
-
-// b - L p at one point, difference form (arithmetic in T)
-template <typename T>
-__device__ __forceinline__ T point_residual(const Geom<T>& g, const T* __restrict__ p, const T* __restrict__ b,
-                                            int i, int j, int k, T* pc_out) {
-  const int nx = g.nx, plane = g.nx * g.ny;
-  const int ip = i == nx - 1 ? 0 : i + 1, im = i == 0 ? nx - 1 : i - 1;
-  const int jp = j == g.ny - 1 ? 0 : j + 1, jm = j == 0 ? g.ny - 1 : j - 1;
-  const int row = k * plane;
-  const int q = row + j * nx + i;
-  const T pc = __ldg(p + q);
-  T lap = g.idx2 * ((__ldg(p + row + j * nx + ip) - pc) + (__ldg(p + row + j * nx + im) - pc)) +
-          g.idy2 * ((__ldg(p + row + jp * nx + i) - pc) + (__ldg(p + row + jm * nx + i) - pc));
-  if (k < g.nz - 1) lap += __ldg(g.cup + k) * (__ldg(p + q + plane) - pc);
-  if (k > 0) lap += __ldg(g.cdn + k) * (__ldg(p + q - plane) - pc);
-  *pc_out = pc;
-  return __ldg(b + q) - lap;
-}
-
-// One FP32 SRJ update in difference form with a fixed rounding sequence
-// (explicit round-to-nearest operations), shared by every FP32 sweep kernel
-// so that all of them produce bitwise the same values.
-__device__ __forceinline__ float srj_cell_f32(float pc, float xl, float xr, float nn, float ss, float uu, float dd,
-                                              float bb, float idx2, float idy2, float cup, float cdn, float iS,
-                                              float om) {
-  float lap = __fmul_rn(idx2, __fadd_rn(__fsub_rn(xr, pc), __fsub_rn(xl, pc)));
-  lap = __fmaf_rn(idy2, __fadd_rn(__fsub_rn(nn, pc), __fsub_rn(ss, pc)), lap);
-  lap = __fmaf_rn(cup, __fsub_rn(uu, pc), lap);
-  lap = __fmaf_rn(cdn, __fsub_rn(dd, pc), lap);
-  return __fmaf_rn(-om, __fmul_rn(__fsub_rn(bb, lap), iS), pc);
-}
-
 // FP32: difference form (no cancellation against S p).
 __global__ void __launch_bounds__(kBX* kBY) k_sweep_f32(Geom<float> g, const float* __restrict__ p,
                                                          const float* __restrict__ b, float omega,
@@ -152,49 +121,14 @@ template <int KZ, int BY>
 __global__ void __launch_bounds__(kBX* BY) k_sweep_f32_z(Geom<float> g, const float* __restrict__ p,
                                                           const float* __restrict__ b, float omega,
                                                           float* __restrict__ out) {
-  const int lane = threadIdx.x;
-  const int nx = g.nx, ny = g.ny, nx4 = nx >> 2;
-  const int x4 = blockIdx.x * kBX + lane;
-  const int j = blockIdx.y * BY + threadIdx.y, k0 = blockIdx.z * KZ;
-  const bool active = x4 < nx4 && j < ny;
-  const int xx = x4 < nx4 ? x4 : nx4 - 1;
-  const int jj = j < ny ? j : ny - 1;
-  const int jp = jj == ny - 1 ? 0 : jj + 1, jm = jj == 0 ? ny - 1 : jj - 1;
-  const size_t plane4 = (size_t)nx4 * ny;
-  const size_t r0 = ((size_t)k0 * ny + jj) * nx4 + xx;  // this thread's unit at level k0
-  const float idx2 = g.idx2, idy2 = g.idy2;
-  cudaGridDependencySynchronize();
-  const float4* P = reinterpret_cast<const float4*>(p);
-  float4 c[KZ + 2];
-#pragma unroll
-  for (int q = 0; q < KZ; q++) c[q + 1] = __ldg(P + r0 + q * plane4);
-  c[0] = k0 > 0 ? __ldg(P + r0 - plane4) : c[1];
-  c[KZ + 1] = k0 + KZ < g.nz ? __ldg(P + r0 + KZ * plane4) : c[KZ];
-#pragma unroll
-  for (int q = 0; q < KZ; q++) {
-    const int k = k0 + q;
-    const size_t rc = r0 + q * plane4;
-    const size_t rowbase = ((size_t)k * ny + jj) * nx4;
-    const float cup = __ldg(g.cup + k), cdn = __ldg(g.cdn + k), iS = __ldg(g.iS + k);
-    const float4 cc = c[q + 1], zu = c[q + 2], zd = c[q];
-    float left = __shfl_up_sync(0xffffffffu, cc.w, 1);
-    float right = __shfl_down_sync(0xffffffffu, cc.x, 1);
-    const float* prow = p + rowbase * 4;
-    if (lane == 0 || xx == 0) left = __ldg(prow + (4 * xx - 1 + nx) % nx);
-    if (lane == kBX - 1 || xx == nx4 - 1) right = __ldg(prow + (4 * xx + 4) % nx);
-    const float4 yn = __ldg(P + ((size_t)k * ny + jp) * nx4 + xx);
-    const float4 ys = __ldg(P + ((size_t)k * ny + jm) * nx4 + xx);
-    const float4 bq = __ldg(reinterpret_cast<const float4*>(b) + rc);
-    auto cell = [&](float pc, float xl, float xr, float nn, float ss, float uu, float dd, float bb) {
-      return srj_cell_f32(pc, xl, xr, nn, ss, uu, dd, bb, idx2, idy2, cup, cdn, iS, omega);
-    };
-    float4 o;
-    o.x = cell(cc.x, left, cc.y, yn.x, ys.x, zu.x, zd.x, bq.x);
-    o.y = cell(cc.y, cc.x, cc.z, yn.y, ys.y, zu.y, zd.y, bq.y);
-    o.z = cell(cc.z, cc.y, cc.w, yn.z, ys.z, zu.z, zd.z, bq.z);
-    o.w = cell(cc.w, cc.z, right, yn.w, ys.w, zu.w, zd.w, bq.w);
-    if (active) reinterpret_cast<float4*>(out)[rc] = o;
-  }
+  sweep_z_tile<KZ, BY>(g, p, b, omega, out, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+template <int KZ>
+__global__ void __launch_bounds__(kBX* kBY) k_sweep_f32_flat(Geom<float> g, const float* __restrict__ p,
+                                                             const float* __restrict__ b, float omega,
+                                                             float* __restrict__ out) {
+  sweep_flat_tile<KZ>(g, p, b, omega, out, blockIdx.x);
 }
 
 template <bool PDL>
@@ -361,34 +295,10 @@ __global__ void __launch_bounds__(kBX* kBY) k_check(Geom<T> g, const T* __restri
   if (publish_partial(red, nblocks, s, 0.0, false)) {
     const double tot = final_sum(red.partial, nblocks, sh);
     if (threadIdx.x == 0 && threadIdx.y == 0) {
-      const double res = sqrt(tot);
-      const double nb = red.sc[SC_BNORM];
-      bool stop;
-      ctl->kernels += 1;
-      if (!(res == res) || isinf(res)) {
-        ctl->bad = 1;
-        stop = true;
-      } else if (MODE == 0) {
-        ctl->res = res;
-        ctl->converged = res <= ctl->tol * nb;
-        stop = ctl->converged || ctl->sweeps >= ctl->max_sweeps;
-      } else {
-        const double target = fmax(ctl->inner_tol * red.sc[SC_INNER_REF], 0.5 * ctl->tol * nb);
-        const bool stall = ctl->cycles_inner > 0 && res > 0.9 * ctl->prev;
-        ctl->res_inner = res;
-        stop = res <= target || stall || ctl->sweeps >= ctl->max_sweeps;
-        ctl->prev = res;
-      }
-      if (!stop) {
-        ctl->sweeps += ctl->M;
-        ctl->cycles_inner += 1;
-        ctl->kernels += ctl->M;
-      }
-      *red.counter = 0u;
-      ctl->go = stop ? 0 : 1;
+      const bool go = cycle_decide<MODE>(ctl, red, sqrt(tot));
       if (graph) {
-        cudaGraphSetConditional(h_loop, stop ? 0u : 1u);
-        cudaGraphSetConditional(h_body, stop ? 0u : 1u);
+        cudaGraphSetConditional(h_loop, go ? 1u : 0u);
+        cudaGraphSetConditional(h_body, go ? 1u : 0u);
       }
     }
   }
@@ -413,25 +323,8 @@ __global__ void __launch_bounds__(kBX* kBY) k_outer(Geom<double> g, const double
   if (publish_partial(red, nblocks, s, 0.0, false)) {
     const double tot = final_sum(red.partial, nblocks, sh);
     if (threadIdx.x == 0 && threadIdx.y == 0) {
-      const double res = sqrt(tot);
-      const double nb = red.sc[SC_BNORM];
-      ctl->kernels += 1 + (after_pass ? 1 : 0);  // this kernel and the correction before it
-      if (after_pass) ctl->passes += 1;
-      ctl->res = res;
-      red.sc[SC_INNER_REF] = res;
-      ctl->cycles_inner = 0;
-      ctl->prev = 0.0;
-      bool stop;
-      if (!(res == res) || isinf(res)) {
-        ctl->bad = 1;
-        stop = true;
-      } else {
-        ctl->converged = res <= ctl->tol * nb;
-        stop = ctl->converged || ctl->sweeps >= ctl->max_sweeps || ctl->passes >= ctl->max_passes;
-      }
-      *red.counter = 0u;
-      ctl->go = stop ? 0 : 1;
-      if (graph) cudaGraphSetConditional(h_loop, stop ? 0u : 1u);
+      const bool go = pass_decide(ctl, red, sqrt(tot), after_pass);
+      if (graph) cudaGraphSetConditional(h_loop, go ? 1u : 0u);
     }
   }
 }
@@ -449,18 +342,7 @@ __global__ void k_difference(const double* __restrict__ a, const double* __restr
 
 __global__ void k_begin(SolveCtl* ctl, int graph, cudaGraphConditionalHandle h_loop) {
   if (graph) cudaGraphSetConditional(h_loop, 1u);
-  if (ctl->solves > 0) {
-    ctl->tot_sweeps += ctl->sweeps;
-    ctl->tot_kernels += ctl->kernels;
-    ctl->nonconv += ctl->converged ? 0 : 1;
-  }
-  ctl->solves += 1;
-  ctl->sweeps = 0;
-  ctl->passes = 0;
-  ctl->cycles_inner = 0;
-  ctl->converged = 0;
-  ctl->prev = 0.0;
-  ctl->kernels = 1;
+  begin_solve_state(ctl);
 }
 
 __global__ void __launch_bounds__(kBX* kBY) k_laplacian(Geom<double> g, const double* __restrict__ p,
@@ -518,14 +400,37 @@ static cudaError_t launch_pdl(K kern, dim3 grid, dim3 block, cudaStream_t s, con
   return cudaLaunchKernelEx(&cfg, kern, g, p, b, omega, out);
 }
 
-// FP32 sweep variants: 0 = one level per thread, 32 x 8 block (k_sweep_f32_v4);
-// 1..5 = (KZ, BY) in {(2,8), (4,8), (2,4), (4,4), (8,4)} (k_sweep_f32_z).
+// FP32 sweep variant per host thread (poisson_common.cuh numbers them)
 static thread_local int t_sweep_variant = 0;
 void set_sweep_variant(int v) { t_sweep_variant = v; }
-int sweep_variant_count() { return 6; }
-bool sweep_variant_ok(int v, int nz) {
-  static const int kz[6] = {1, 2, 4, 2, 4, 8};
-  return v >= 0 && v < 6 && nz % kz[v] == 0;
+int sweep_variant_count() { return kSweepVariants; }
+bool sweep_variant_ok(int v, int nx, int ny, int nz) {
+  if (v < 0 || v >= kSweepVariants || nx % 4 || nz % sweep_kz(v)) return false;
+  return !sweep_flat(v) || ((nx / 4) * ny) % 32 == 0;
+}
+
+static cudaError_t launch_sweep_cfg(const void* kern, dim3 grid, dim3 block, cudaStream_t s, void** args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaLaunchKernelExC(&cfg, kern, args);
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+template <int KZ>
+static cudaError_t launch_flat(const Geom<float>& g, const float* p, const float* b, float omega, float* out,
+                               cudaStream_t s) {
+  const long long units = (long long)(g.nz / KZ) * (g.nx / 4) * g.ny;
+  const dim3 grid((unsigned)((units + kBX * kBY - 1) / (kBX * kBY))), block(kBX, kBY, 1);
+  Geom<float> gg = g;
+  void* args[] = {&gg, &p, &b, &omega, &out};
+  return launch_sweep_cfg((const void*)k_sweep_f32_flat<KZ>, grid, block, s, args);
 }
 
 template <int KZ, int BY>
@@ -549,8 +454,11 @@ template <>
 cudaError_t launch_sweep<float>(const Geom<float>& g, const float* p, const float* b, float omega, float* out,
                                 cudaStream_t s) {
   if (g.nx % 4 == 0) {
-    const int v = sweep_variant_ok(t_sweep_variant, g.nz) ? t_sweep_variant : 0;
+    const int v = sweep_variant_ok(t_sweep_variant, g.nx, g.ny, g.nz) ? t_sweep_variant : 0;
     switch (v) {
+      case 6: return launch_flat<2>(g, p, b, omega, out, s);
+      case 7: return launch_flat<4>(g, p, b, omega, out, s);
+      case 8: return launch_flat<8>(g, p, b, omega, out, s);
       case 1: return launch_z<2, 8>(g, p, b, omega, out, s);
       case 2: return launch_z<4, 8>(g, p, b, omega, out, s);
       case 3: return launch_z<2, 4>(g, p, b, omega, out, s);

@@ -156,7 +156,7 @@ cudaError_t launch_sweep<double>(const Geom<double>&, const double*, const doubl
 // (chosen by the autotuner in api.cu).
 void set_sweep_variant(int v);
 int sweep_variant_count();
-bool sweep_variant_ok(int v, int nz);
+bool sweep_variant_ok(int v, int nx, int ny, int nz);
 
 // ||b - L p|| and the once-per-cycle decision (mode 0: FP64 solve, mode 1:
 // FP32 inner solve); sets the WHILE (h_loop) and IF (h_body) conditionals.
@@ -182,6 +182,60 @@ cudaError_t launch_difference(const double* a, const double* b, float* out, size
 // start of a solve: fold the previous solve into the totals, reset the state
 // (in a graph it also arms the WHILE handle h_loop of an FP64 solve)
 cudaError_t launch_begin(SolveCtl* ctl, int graph, cudaGraphConditionalHandle h_loop, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Grouped FP32 pressure solves (kernels_group.cu).  In the batched step the
+// channels that share an SRJ cycle length M are solved in lock step: each
+// kernel of the solve covers the tiles of every channel of the group in one
+// launch (block -> channel by a search over the channels' first tiles), and
+// each channel keeps its own schedule, residuals, counters and stopping
+// decisions, so it computes exactly what its own solve computes.  A channel
+// that has stopped skips its tiles.  The channel deciding last in a kernel
+// sets the graph conditionals: the loops run while any channel continues.
+// ---------------------------------------------------------------------------
+struct GChan {
+  Geom<float> g32;
+  Geom<double> g64;
+  double* p;
+  const double* b;
+  float* d1;           // inner correction (cycle input and output)
+  float* d2;           // its ping-pong partner
+  float* r32;          // refinement residual (inner right-hand side)
+  const float* omega;  // [M] FP32 schedule
+  SolveCtl* ctl;
+  Red red;
+};
+
+struct GState {
+  unsigned arrived;     // channels that have decided in the current kernel
+  unsigned n_go;        // of those, the ones that continue
+  unsigned part_pass;   // channels in the current refinement pass
+  unsigned part_inner;  // channels in the current inner SRJ loop
+  long long kernels;    // grouped kernels run (all solves since the counter was cleared)
+};
+
+struct Group {
+  const GChan* ch;  // [n]
+  const int* soff;  // [n+1] first 32 x 8 one-level tile of each channel (residuals, element-wise work)
+  const int* voff;  // [n+1] first sweep tile of each channel (sweep variant kz x by)
+  int* pass_on;     // [n] channel in the current refinement pass
+  int* inner_on;    // [n] channel in the current inner SRJ loop
+  GState* gs;
+  int n, M;
+  int stiles, vtiles;
+  int variant;      // FP32 sweep tile variant (as set_sweep_variant numbers them)
+};
+
+// tile counts of one channel: one-level 32 x 8 tiles, and sweep tiles of a variant
+int group_scalar_tiles(int nx, int ny, int nz);
+int group_sweep_tiles(int variant, int nx, int ny, int nz);
+cudaError_t launch_group_begin(const Group& G, cudaStream_t s);
+cudaError_t launch_group_outer(const Group& G, int after_pass, cudaGraphConditionalHandle h_pass, cudaStream_t s);
+cudaError_t launch_group_pass_begin(const Group& G, cudaGraphConditionalHandle h_loop, cudaStream_t s);
+cudaError_t launch_group_check(const Group& G, cudaGraphConditionalHandle h_loop, cudaGraphConditionalHandle h_body,
+                               cudaStream_t s);
+cudaError_t launch_group_sweep(const Group& G, int m, cudaStream_t s);
+cudaError_t launch_group_addcorr(const Group& G, cudaStream_t s);
 
 // batched step: counter[0] = steps done, counter[1] = steps wanted
 cudaError_t launch_batch_begin(int* counter, cudaGraphConditionalHandle h_steps, cudaStream_t s);

@@ -62,7 +62,12 @@ class StepStats(ctypes.Structure):
 
 class BatchStats(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_longlong), ("cells", ctypes.c_longlong), ("sweeps", ctypes.c_longlong),
-                ("converged", ctypes.c_int), ("gpu_ms", ctypes.c_double)]
+                ("converged", ctypes.c_int), ("gpu_ms", ctypes.c_double), ("kernels", ctypes.c_longlong)]
+
+
+class BatchGroup(ctypes.Structure):
+    _fields_ = [("channels", ctypes.c_int), ("M", ctypes.c_int), ("variant", ctypes.c_int),
+                ("cells", ctypes.c_longlong), ("sweep_us", ctypes.c_float)]
 
 
 class SolveStats(ctypes.Structure):
@@ -77,7 +82,7 @@ EXPORTS = ("stp_config_defaults", "stp_init", "stp_destroy", "stp_last_error", "
            "stp_unet_gradient", "stp_unet_train_step", "stp_unet_train_pairs", "stp_unet_eval_pairs",
            "stp_set_learned_guess", "stp_set_harvest", "stp_unet_set_output_scale", "stp_state_size",
            "stp_get_state", "stp_set_state", "stp_batch_create", "stp_batch_destroy", "stp_batch_last_error",
-           "stp_batch_step")
+           "stp_batch_step", "stp_batch_groups")
 
 _lib = None
 
@@ -130,6 +135,7 @@ def lib():
     L.stp_batch_last_error.argtypes = [vp]
     L.stp_batch_last_error.restype = ctypes.c_char_p
     L.stp_batch_step.argtypes = [vp, ctypes.c_int, ctypes.POINTER(BatchStats), ctypes.POINTER(StepStats)]
+    L.stp_batch_groups.argtypes = [vp, ctypes.c_int, ctypes.POINTER(BatchGroup)]
     L.stp_state_size.argtypes = [vp]
     L.stp_state_size.restype = ctypes.c_longlong
     L.stp_get_state.argtypes = [vp, vp]
@@ -402,9 +408,18 @@ class Batch:
         if rc not in (STP_OK, STP_ENOTCONVERGED):
             raise StpError(rc, lib().stp_batch_last_error(self._h).decode())
         return dict(steps=st.steps, cells=st.cells, sweeps=st.sweeps, converged=bool(st.converged),
-                    gpu_ms=st.gpu_ms, status=rc,
+                    gpu_ms=st.gpu_ms, kernels=st.kernels, status=rc,
                     channels=[dict(sweeps=p.poisson_sweeps, converged=bool(p.converged), rel_res=p.rel_residual,
                                    ubulk=p.ubulk, umax=p.umax, step=p.step) for p in per])
+
+    def groups(self):
+        """Lock-step groups (known after the first step): channels, M, sweep
+        variant, cells and the measured grouped sweep time."""
+        n = lib().stp_batch_groups(self._h, 0, None)
+        arr = (BatchGroup * max(1, n))()
+        lib().stp_batch_groups(self._h, n, arr)
+        return [dict(channels=g.channels, M=g.M, variant=g.variant, cells=g.cells, sweep_us=g.sweep_us)
+                for g in arr[:n]]
 
     def close(self):
         if getattr(self, "_h", None) is not None and _lib is not None:

@@ -65,3 +65,46 @@ def test_batch_uneven_instability_channels(stp_lib):
     b.close()
     for ch in chans:
         ch.close()
+
+
+@pytest.mark.parametrize("env", [{"STP_SWEEP_VARIANT": "0"}, {"STP_SWEEP_VARIANT": "7"},
+                                 {"STP_SWEEP_VARIANT": "5", "STP_BATCH_GROUP_CELLS": "60000"},
+                                 {"STP_BATCH_GROUP_CHAIN": "1"}])
+def test_grouped_solves_match_own_solves(stp_lib, monkeypatch, env):
+    """Lock-step groups (one launch per solve kernel over all channels of a
+    group), with a forced sweep tile, split into parts, or chained, leave
+    every channel bitwise where its own solve leaves it.  The channels share
+    M = 32 but differ in size, stretching and LES, so their solves stop after
+    different numbers of cycles and passes."""
+    specs = [case(nx=32, ny=16, nz=32, nu=1 / 500.0),
+             case(nx=48, ny=24, nz=32, stretch=2.0, les=1, forcing=1, nu=1 / 500.0),
+             case(nx=64, ny=32, nz=48, nu=1 / 800.0, cn_sweeps=3),
+             case(nx=32, ny=32, nz=16, nu=1 / 300.0)]
+    res = []
+    for groups in ("0", "1"):
+        monkeypatch.setenv("STP_BATCH_GROUPS", groups)
+        for k, v in env.items():
+            monkeypatch.setenv(k, v)
+        chans = []
+        for i, cfg in enumerate(specs):
+            ch = stp_lib.Channel(cfg, precision="fp32", omega=schedule(cfg, 32))
+            ch.set_fields(*turbulent_like(cfg, 50 + i))
+            chans.append(ch)
+        b = stp_lib.Batch(chans)
+        st = b.step(4)
+        assert st["converged"] and st["kernels"] > 0
+        grp = b.groups()
+        if groups == "1":
+            assert sum(g["channels"] for g in grp) >= 2
+            assert all(g["M"] == 32 for g in grp)
+        else:
+            assert grp == []
+        res.append(([ch.get_fields() for ch in chans], [c["sweeps"] for c in st["channels"]]))
+        b.close()
+        for ch in chans:
+            ch.close()
+    (fa, sa), (fb, sb) = res
+    assert sa == sb
+    for i in range(len(specs)):
+        for k in ("u", "v", "w", "p"):
+            assert np.array_equal(fa[i][k], fb[i][k]), (env, i, k)

@@ -251,13 +251,17 @@ def test_persistent_cycle_matches_per_sweep_kernels(stp_lib, monkeypatch):
         assert rel_err(fb[k] - fb[k].mean() * (k == "p"), fa[k] - fa[k].mean() * (k == "p")) < 1e-6, k
 
 
-def test_sweep_variants_identical(stp_lib, monkeypatch):
+@pytest.mark.parametrize("shape", [(64, 24, 32), (32, 12, 16)])
+def test_sweep_variants_identical(stp_lib, monkeypatch, shape):
     """Every FP32 sweep tile shape the autotuner may pick computes the same
-    values (z levels per thread and rows per block only change the mapping)."""
-    cfg = case(nx=64, ny=24, nz=32, stretch=2.0, les=0, nu=1 / 500.0, cn_sweeps=4)
+    values (z levels per thread, rows per block and warps packed along the
+    plane only change the mapping).  The second grid has rows of 8 float4
+    units, so a packed warp holds four rows and wraps x inside the warp."""
+    nx, ny, nz = shape
+    cfg = case(nx=nx, ny=ny, nz=nz, stretch=2.0, les=0, nu=1 / 500.0, cn_sweeps=4)
     om = schedule(cfg, 32)
     ref = None
-    for v in range(6):
+    for v in range(9):
         monkeypatch.setenv("STP_SWEEP_VARIANT", str(v))
         with stp_lib.Channel(cfg, precision="fp32", omega=om) as ch:
             ch.set_fields(*turbulent_like(cfg, 13))
