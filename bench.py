@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--grid", default=None, help="override the cell counts, NXxNYxNZ (profiling runs)")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-guess comparison")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched uneven-channel measurement")
     return ap.parse_args()
 
 
@@ -204,6 +205,66 @@ def learned_comparison(cfg, steps):
             "note": "time per pressure solve to 1e-8 (GPU events), previous-step pressure as the plain guess"}
 
 
+def batched_channels(steps, warmup, peak):
+    """Uneven-channel batch: 64 instances with sizes drawn from
+    {32, 48, 64, 96, 128}^3 (seed 2), Re uniform in [5000, 10000],
+    Orr-Sommerfeld amplitude log-uniform in [1e-5, 1e-3], FP32 with FP64
+    refinement, all advanced by one graph launch per call.  Measured grouped
+    (lock-step solves, the default), with every channel on its own solve,
+    and with the channels stepped one after another; GPU time by CUDA events
+    around the launch."""
+    import torch
+    from paper_1511_07800_gb300 import inputs, stp
+    inst = inputs.batched_instances(count=64, seed=2)
+    cells = sum(c["nx"] * c["ny"] * c["nz"] for c, _ in inst)
+    chans = []
+    for cfg, f in inst:
+        ch = stp.Channel(cfg, precision="fp32")
+        ch.set_fields(*f)
+        chans.append(ch)
+    out = {"instances": len(chans), "cells": cells, "precision": "fp32", "steps": steps,
+           "warmup": max(3, warmup), "l2": "working set of the 64 channels (about 3 GB) far above L2",
+           "data": "synthetic (seeded)"}
+    saved = os.environ.get("STP_BATCH_GROUPS")
+    try:
+        for mode, env in (("ungrouped", "0"), ("grouped", "1")):
+            os.environ["STP_BATCH_GROUPS"] = env
+            b = stp.Batch(chans)
+            b.step(max(3, warmup))
+            st = b.step(steps)
+            r = {"value": cells * steps / (st["gpu_ms"] / 1e3) / 1e6, "unit": "Mcell*steps/s",
+                 "ms_per_step": st["gpu_ms"] / steps, "gpu_launches": st["kernels"],
+                 "sweeps_per_step": st["sweeps"] / steps, "converged": st["converged"]}
+            if mode == "grouped":
+                groups = b.groups()
+                r["groups"] = groups
+                g = max(groups, key=lambda x: x["cells"]) if groups else None
+                if g and g["sweep_us"] > 0:
+                    ach = 12.0 * g["cells"] / (g["sweep_us"] * 1e-6) / 1e9
+                    r["roofline"] = {"bound": "hbm", "kernel": "kg_sweep (grouped FP32 SRJ sweep, largest group)",
+                                     "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                                     "traffic": None, "bytes_per_launch": 12 * g["cells"],
+                                     "mean_launch_us": g["sweep_us"],
+                                     "note": "autotuner's timing: 20 back-to-back grouped sweeps, all channels active"}
+            out[mode] = r
+            b.close()
+    finally:
+        if saved is None:
+            os.environ.pop("STP_BATCH_GROUPS", None)
+        else:
+            os.environ["STP_BATCH_GROUPS"] = saved
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for ch in chans:
+        ch.step(steps)
+    ts = time.perf_counter() - t0
+    out["sequential"] = {"value": cells * steps / ts / 1e6, "unit": "Mcell*steps/s",
+                         "note": "each channel stepped on its own, one after another (wall clock)"}
+    for ch in chans:
+        ch.close()
+    return out
+
+
 def run_reference(args):
     """The oracle (plain FP64 C, OpenMP over z) time-stepping the workload with
     its own tolerance-driven pressure solves, on rank 0's host cores."""
@@ -338,6 +399,12 @@ def run_ours(args):
     t_sweep = solve_ms / max(1, sweeps) / 1e3
     achieved = bytes_per_sweep / t_sweep / 1e9 if sweeps else None
     peak = peaks.get("hbm_gbs", 6800.0)
+    variant, _ = ch.sweep_tile()
+    names = {0: "k_sweep_f32_v4", 1: "k_sweep_f32_z<2,8>", 2: "k_sweep_f32_z<4,8>", 3: "k_sweep_f32_z<2,4>",
+             4: "k_sweep_f32_z<4,4>", 5: "k_sweep_f32_z<8,4>", 6: "k_sweep_f32_flat<2>", 7: "k_sweep_f32_flat<4>",
+             8: "k_sweep_f32_flat<8>"}
+    sweep_kernel = (names.get(variant, "k_sweep_f32") if args.precision == "fp32" else "k_sweep_f64_v2") + \
+        " (SRJ sweep, autotuned tile variant %d)" % variant
     kern = os.path.join(ROOT, "paper_1511_07800_gb300", "csrc", "kernels_poisson.cu")
     traffic = traffic_for(kern, args.precision)
     line = {
@@ -352,7 +419,7 @@ def run_ours(args):
                    "srj_M": len(stp.srj_schedule(cfg)[0])},
         "poisson": {"sweeps_per_step": sweeps / args.steps, "refine_passes_per_step": passes / args.steps,
                     "all_converged": conv, "ms_per_step": solve_ms / args.steps},
-        "roofline": {"bound": "hbm", "kernel": "k_sweep<%s> (SRJ sweep)" % ("float" if word == 4 else "double"),
+        "roofline": {"bound": "hbm", "kernel": sweep_kernel,
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                      "bytes_per_launch": bytes_per_sweep, "mean_launch_us": t_sweep * 1e6,
@@ -366,6 +433,11 @@ def run_ours(args):
             line["poisson_learned_vs_plain"] = learned_comparison(cfg, args.steps)
         except Exception as ex:  # report, never fake
             line["poisson_learned_vs_plain"] = {"error": str(ex)[:200]}
+    if rank == 0 and world == 1 and not args.no_batch and args.grid is None:
+        try:
+            line["batched_channels"] = batched_channels(max(3, min(args.steps, 10)), args.warmup, peak)
+        except Exception as ex:  # report, never fake
+            line["batched_channels"] = {"error": str(ex)[:200]}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
             line["cpu_baseline"] = cpu_baseline_sample(cfg, fields, sweeps / args.steps)

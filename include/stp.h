@@ -177,6 +177,11 @@ int stp_batch_create(stp_handle *const *handles, int n, void *stream, stp_batch 
 void stp_batch_destroy(stp_batch *b);
 const char *stp_batch_last_error(const stp_batch *b);
 
+/* The FP32 sweep tile variant the autotuner picked for this handle's grid
+   (0..8, see above; -1 before the first solve, 0 in FP64) and, when it was
+   timed, its time per sweep in microseconds (*us may be NULL). */
+int stp_sweep_tile(const stp_handle *h, float *us);
+
 /* Lock-step groups of the batch (built at the first stp_batch_step).
    Channels in FP32 with refinement that share the SRJ cycle length M (at
    least two of them, rows a multiple of 4 cells, no learned guess) are

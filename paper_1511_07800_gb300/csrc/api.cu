@@ -463,11 +463,58 @@ int build_cycle(stp_handle* h, const Geom<T>& g, cudaGraph_t wb, cudaGraphCondit
   return end_capture(h, ib);
 }
 
+// Time of one sweep of the FP32 variant currently set on this host thread,
+// as the solve runs it: 20 sweeps captured into a graph (programmatic
+// dependent launches between them), best of three launches after a warm-up
+// launch, CUDA events on the handle's stream.
+int time_sweeps(stp_handle* h, float* us) {
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t x = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeRelaxed);
+  const bool capturing = e == cudaSuccess;
+  for (int w = 0; w < 20 && e == cudaSuccess; w++)
+    e = launch_sweep<float>(h->g32, (w & 1) ? h->d2 : h->d1, h->r32, 1.0f, (w & 1) ? h->d1 : h->d2, h->cap);
+  if (capturing) {
+    const cudaError_t e2 = cudaStreamEndCapture(h->cap, &g);
+    if (e == cudaSuccess) e = e2;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&x, g, 0);
+  float best = 1e30f;
+  for (int r = 0; r < 4 && e == cudaSuccess; r++) {
+    float ms = 0.f;
+    e = cudaEventRecord(h->ev0, h->st);
+    if (e == cudaSuccess) e = cudaGraphLaunch(x, h->st);
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev1, h->st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(h->ev1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+    if (e == cudaSuccess && r > 0 && ms < best) best = ms;
+  }
+  if (x) cudaGraphExecDestroy(x);
+  if (g) cudaGraphDestroy(g);
+  if (e != cudaSuccess) return fail(h, STP_ECUDA, std::string("sweep autotuner: ") + cudaGetErrorString(e));
+  *us = best * 1e3f / 20.f;
+  return STP_OK;
+}
+
+// Pick among timed variants: the lowest-numbered one within 2 % of the
+// fastest (timing noise then does not flip the choice between near-equal
+// tiles from run to run).
+int pick_variant(const std::vector<std::pair<int, float>>& timed, float* us) {
+  float best = 1e30f;
+  for (const auto& t : timed) best = std::min(best, t.second);
+  for (const auto& t : timed)
+    if (t.second <= 1.02f * best) {
+      *us = t.second;
+      return t.first;
+    }
+  *us = 0.f;
+  return 0;
+}
+
 // Autotuner of the FP32 sweep kernel: times every variant valid for this
-// grid (3 warm-up and 20 timed launches each, CUDA events on the handle's
-// stream, on the handle's own scratch buffers) and keeps the fastest; the
-// choice is cached per (device, nx, ny, nz).  STP_SWEEP_VARIANT=<v> forces a
-// variant.  All variants compute the same values.
+// grid (time_sweeps, on the handle's own scratch buffers) and keeps the
+// choice of pick_variant; cached per (device, nx, ny, nz).
+// STP_SWEEP_VARIANT=<v> forces a variant.  All variants compute the same values.
 int tune_sweep(stp_handle* h) {
   if (h->sweep_variant >= 0) return STP_OK;
   h->sweep_variant = 0;
@@ -491,26 +538,16 @@ int tune_sweep(stp_handle* h) {
   }
   CUDA_TRY(h, cudaMemsetAsync(h->d1, 0, sizeof(float) * h->nc, h->st));
   CUDA_TRY(h, cudaMemsetAsync(h->r32, 0, sizeof(float) * h->nc, h->st));
-  float best = 1e30f;
-  int bv = 0;
+  std::vector<std::pair<int, float>> timed;
   for (int v = 0; v < sweep_variant_count(); v++) {
     if (!sweep_variant_ok(v, h->nx, h->ny, h->nz)) continue;
     set_sweep_variant(v);
-    for (int w = 0; w < 3; w++) CUDA_TRY(h, launch_sweep<float>(h->g32, h->d1, h->r32, 1.0f, h->d2, h->st));
-    CUDA_TRY(h, cudaEventRecord(h->ev0, h->st));
-    for (int w = 0; w < 20; w++)
-      CUDA_TRY(h, launch_sweep<float>(h->g32, (w & 1) ? h->d2 : h->d1, h->r32, 1.0f, (w & 1) ? h->d1 : h->d2, h->st));
-    CUDA_TRY(h, cudaEventRecord(h->ev1, h->st));
-    CUDA_TRY(h, cudaEventSynchronize(h->ev1));
-    float ms = 0.f;
-    CUDA_TRY(h, cudaEventElapsedTime(&ms, h->ev0, h->ev1));
-    if (ms < best) {
-      best = ms;
-      bv = v;
-    }
+    float us = 0.f;
+    if (int rc = time_sweeps(h, &us)) return rc;
+    timed.emplace_back(v, us);
   }
+  const int bv = pick_variant(timed, &h->sweep_us);
   h->sweep_variant = bv;
-  h->sweep_us = best * 1e3f / 20.f;
   std::lock_guard<std::mutex> lock(mu);
   cache[key] = std::make_pair(bv, h->sweep_us);
   return STP_OK;
@@ -1523,7 +1560,6 @@ int setup_group(stp_batch* b, BatchGroup& grp) {
     if (group_voff(grp, v, voff) && (forced < 0 || v == forced)) cand.push_back(v);
   if (cand.empty()) cand.push_back(0);  // every member has nx % 4 == 0: variant 0 always fits
   int best_v = cand[0];
-  float best = 1e30f;
   if (cand.size() > 1) {
     // scratch contents for timing: d = 0, r = 0, every channel active
     for (stp_handle* h : grp.hs) {
@@ -1531,25 +1567,39 @@ int setup_group(stp_batch* b, BatchGroup& grp) {
       BTRY(b, cudaMemsetAsync(h->r32, 0, sizeof(float) * h->nc, b->st));
     }
     BTRY(b, cudaMemsetAsync(G.inner_on, 1, sizeof(int) * n, b->st));
+    std::vector<std::pair<int, float>> timed;
     for (int v : cand) {
       group_voff(grp, v, voff);
       BTRY(b, cudaMemcpyAsync(base + o_voff, voff.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, b->st));
+      BTRY(b, cudaStreamSynchronize(b->st));
       G.variant = v;
       G.vtiles = voff[n];
-      for (int w = 0; w < 3; w++) BTRY(b, launch_group_sweep(G, w % G.M, b->st));
-      BTRY(b, cudaEventRecord(b->e0, b->st));
-      for (int w = 0; w < 20; w++) BTRY(b, launch_group_sweep(G, w % G.M, b->st));
-      BTRY(b, cudaEventRecord(b->e1, b->st));
-      BTRY(b, cudaEventSynchronize(b->e1));
-      float ms = 0.f;
-      BTRY(b, cudaEventElapsedTime(&ms, b->e0, b->e1));
-      if (ms < best) {
-        best = ms;
-        best_v = v;
+      // 20 grouped sweeps captured into a graph, best of three launches after a warm-up
+      cudaGraph_t gr = nullptr;
+      cudaGraphExec_t gx = nullptr;
+      BTRY(b, cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeRelaxed));
+      cudaError_t e = cudaSuccess;
+      for (int w = 0; w < 20 && e == cudaSuccess; w++) e = launch_group_sweep(G, w % G.M, b->cap);
+      const cudaError_t e2 = cudaStreamEndCapture(b->cap, &gr);
+      if (e == cudaSuccess) e = e2;
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&gx, gr, 0);
+      float vbest = 1e30f;
+      for (int r = 0; r < 4 && e == cudaSuccess; r++) {
+        float ms = 0.f;
+        e = cudaEventRecord(b->e0, b->st);
+        if (e == cudaSuccess) e = cudaGraphLaunch(gx, b->st);
+        if (e == cudaSuccess) e = cudaEventRecord(b->e1, b->st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(b->e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, b->e0, b->e1);
+        if (e == cudaSuccess && r > 0) vbest = std::min(vbest, ms);
       }
+      if (gx) cudaGraphExecDestroy(gx);
+      if (gr) cudaGraphDestroy(gr);
+      if (e != cudaSuccess) return bfail(b, STP_ECUDA, std::string("group sweep autotuner: ") + cudaGetErrorString(e));
+      timed.emplace_back(v, vbest * 1e3f / 20.f);
     }
     BTRY(b, cudaMemsetAsync(G.inner_on, 0, sizeof(int) * n, b->st));
-    grp.sweep_us = best * 1e3f / 20.f;
+    best_v = pick_variant(timed, &grp.sweep_us);
   }
   group_voff(grp, best_v, voff);
   BTRY(b, cudaMemcpyAsync(base + o_voff, voff.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, b->st));
@@ -1752,6 +1802,12 @@ void stp_batch_destroy(stp_batch* b) {
 }
 
 const char* stp_batch_last_error(const stp_batch* b) { return b ? b->err.c_str() : ""; }
+
+int stp_sweep_tile(const stp_handle* h, float* us) {
+  if (!h) return STP_EINVAL;
+  if (us) *us = h->sweep_us;
+  return h->sweep_variant;
+}
 
 int stp_batch_groups(const stp_batch* b, int max_groups, stp_batch_group* out) {
   if (!b) return STP_EINVAL;

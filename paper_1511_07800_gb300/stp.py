@@ -82,7 +82,7 @@ EXPORTS = ("stp_config_defaults", "stp_init", "stp_destroy", "stp_last_error", "
            "stp_unet_gradient", "stp_unet_train_step", "stp_unet_train_pairs", "stp_unet_eval_pairs",
            "stp_set_learned_guess", "stp_set_harvest", "stp_unet_set_output_scale", "stp_state_size",
            "stp_get_state", "stp_set_state", "stp_batch_create", "stp_batch_destroy", "stp_batch_last_error",
-           "stp_batch_step", "stp_batch_groups")
+           "stp_batch_step", "stp_batch_groups", "stp_sweep_tile")
 
 _lib = None
 
@@ -136,6 +136,7 @@ def lib():
     L.stp_batch_last_error.restype = ctypes.c_char_p
     L.stp_batch_step.argtypes = [vp, ctypes.c_int, ctypes.POINTER(BatchStats), ctypes.POINTER(StepStats)]
     L.stp_batch_groups.argtypes = [vp, ctypes.c_int, ctypes.POINTER(BatchGroup)]
+    L.stp_sweep_tile.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
     L.stp_state_size.argtypes = [vp]
     L.stp_state_size.restype = ctypes.c_longlong
     L.stp_get_state.argtypes = [vp, vp]
@@ -297,6 +298,12 @@ class Channel:
         a = ctypes.c_void_p(r_out.data_ptr()) if r_out is not None else None
         b = ctypes.c_void_p(dp_out.data_ptr()) if dp_out is not None else None
         self._check(lib().stp_set_harvest(self._h, a, b))
+
+    def sweep_tile(self):
+        """(variant, microseconds per sweep) picked by the FP32 sweep autotuner."""
+        us = ctypes.c_float()
+        v = lib().stp_sweep_tile(self._h, ctypes.byref(us))
+        return v, us.value
 
     def close(self):
         if getattr(self, "_h", None) is not None and _lib is not None:
