@@ -28,8 +28,9 @@
  * with bounded grid barriers between its sweeps (slower on GB300: kept as an
  * option).  The FP32 sweep kernel's tile shape (z levels per thread, rows
  * per block) is picked on first use by timing the variants on the grid
- * (STP_SWEEP_VARIANT=<0..8> forces one; variants 6..8 pack warps along the
- * plane for rows shorter than 128 cells).  With STP_HOST_SOLVE=1 at
+ * (STP_SWEEP_VARIANT=<0..11> forces one; variants 6..8 pack warps along the
+ * plane for rows shorter than 128 cells, 9..11 run two sweeps per launch on
+ * a shared-memory tile; STP_TUNE_LOG=1 prints the timings to stderr).  With STP_HOST_SOLVE=1 at
  * stp_init the same kernels are driven from the host instead, one host
  * round trip per SRJ cycle (for profilers that cannot see kernels inside
  * conditional graphs).
@@ -183,13 +184,14 @@ const char *stp_batch_last_error(const stp_batch *b);
 int stp_sweep_tile(const stp_handle *h, float *us);
 
 /* Lock-step groups of the batch (built at the first stp_batch_step).
-   Channels in FP32 with refinement that share the SRJ cycle length M (at
-   least two of them, rows a multiple of 4 cells, no learned guess) are
-   solved together: every kernel of their pressure solve covers all of them
+   Channels of at most 2^17 cells in FP32 with refinement that share the SRJ
+   cycle length M (at least two of them, rows a multiple of 4 cells, no
+   learned guess) are solved together: every kernel of their pressure solve covers all of them
    in one launch, each channel keeping its own schedule, residuals and
    stopping decisions, so its results are bitwise those of its own solve.
    Environment, read when the graph is built: STP_BATCH_GROUPS=0 keeps every
-   channel on its own solve; groups are split into parts whose inner
+   channel on its own solve; STP_BATCH_GROUP_MAX_CHANNEL=<n> sets the channel
+   size limit (-1: none); groups are split into parts whose inner
    working set (12 bytes a cell) fills at most half the L2, or at most n
    cells with STP_BATCH_GROUP_CELLS=<n> (0: no split);
    STP_BATCH_GROUP_CHAIN=1 runs the groups' solves one after another

@@ -434,6 +434,12 @@ int end_capture(stp_handle* h, cudaGraph_t g) {
   return STP_OK;
 }
 
+// FP32 cycles run as pair launches (two sweeps each) with the tuned variant
+bool uses_pairs(const stp_handle* h) {
+  return h->prec == STP_FP32_REFINE && h->cycle_blocks == 0 && sweep_variant_is_pair(h->sweep_variant) &&
+         h->omega.size() % 4 == 0;
+}
+
 // the cycle: check -> IF { M sweeps }, inside the WHILE body `wb`
 template <typename T>
 int build_cycle(stp_handle* h, const Geom<T>& g, cudaGraph_t wb, cudaGraphConditionalHandle h_loop, T* A, T* B,
@@ -455,6 +461,16 @@ int build_cycle(stp_handle* h, const Geom<T>& g, cudaGraph_t wb, cudaGraphCondit
                                  h->cycle_blocks, h->cap));
     return end_capture(h, ib);
   }
+  if (sizeof(T) == sizeof(float) && uses_pairs(h)) {
+    // two sweeps per launch: A -> B, B -> A, ... (M / 2 even: ends in A)
+    for (int m = 0; m < M; m += 2) {
+      const float* src = (const float*)((m % 4 == 0) ? A : B);
+      float* dst = (float*)((m % 4 == 0) ? B : A);
+      CUDA_TRY(h, launch_sweep_pair(h->g32, src, (const float*)rhs, (float)h->omega[m], (float)h->omega[m + 1], dst,
+                                    h->cap));
+    }
+    return end_capture(h, ib);
+  }
   for (int m = 0; m < M; m++) {
     const T* src = (m % 2 == 0) ? A : B;
     T* dst = (m % 2 == 0) ? B : A;
@@ -464,16 +480,21 @@ int build_cycle(stp_handle* h, const Geom<T>& g, cudaGraph_t wb, cudaGraphCondit
 }
 
 // Time of one sweep of the FP32 variant currently set on this host thread,
-// as the solve runs it: 20 sweeps captured into a graph (programmatic
-// dependent launches between them), best of three launches after a warm-up
-// launch, CUDA events on the handle's stream.
-int time_sweeps(stp_handle* h, float* us) {
+// as the solve runs it: 20 sweeps (10 launches of a pair variant) captured
+// into a graph (programmatic dependent launches between them), best of
+// three launches after a warm-up launch, CUDA events on the handle's stream.
+int time_sweeps(stp_handle* h, bool pair, float* us) {
   cudaGraph_t g = nullptr;
   cudaGraphExec_t x = nullptr;
   cudaError_t e = cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeRelaxed);
   const bool capturing = e == cudaSuccess;
-  for (int w = 0; w < 20 && e == cudaSuccess; w++)
-    e = launch_sweep<float>(h->g32, (w & 1) ? h->d2 : h->d1, h->r32, 1.0f, (w & 1) ? h->d1 : h->d2, h->cap);
+  if (pair) {
+    for (int w = 0; w < 10 && e == cudaSuccess; w++)
+      e = launch_sweep_pair(h->g32, (w & 1) ? h->d2 : h->d1, h->r32, 1.0f, 1.0f, (w & 1) ? h->d1 : h->d2, h->cap);
+  } else {
+    for (int w = 0; w < 20 && e == cudaSuccess; w++)
+      e = launch_sweep<float>(h->g32, (w & 1) ? h->d2 : h->d1, h->r32, 1.0f, (w & 1) ? h->d1 : h->d2, h->cap);
+  }
   if (capturing) {
     const cudaError_t e2 = cudaStreamEndCapture(h->cap, &g);
     if (e == cudaSuccess) e = e2;
@@ -541,13 +562,27 @@ int tune_sweep(stp_handle* h) {
   std::vector<std::pair<int, float>> timed;
   for (int v = 0; v < sweep_variant_count(); v++) {
     if (!sweep_variant_ok(v, h->nx, h->ny, h->nz)) continue;
+    const bool pair = sweep_variant_is_pair(v);
+    if (pair && (h->omega.size() % 4 != 0 || h->cycle_blocks > 0)) continue;
     set_sweep_variant(v);
     float us = 0.f;
-    if (int rc = time_sweeps(h, &us)) return rc;
+    if (int rc = time_sweeps(h, pair, &us)) {
+      if (!pair) return rc;
+      cudaGetLastError();  // a pair tile this device cannot launch: not a candidate
+      h->err.clear();
+      continue;
+    }
     timed.emplace_back(v, us);
   }
   const int bv = pick_variant(timed, &h->sweep_us);
   h->sweep_variant = bv;
+  if (const char* lg = std::getenv("STP_TUNE_LOG")) {
+    if (std::atoi(lg)) {
+      std::fprintf(stderr, "stp: FP32 sweep tiles at %dx%dx%d (us per sweep):", h->nx, h->ny, h->nz);
+      for (const auto& t : timed) std::fprintf(stderr, " %d=%.3f", t.first, t.second);
+      std::fprintf(stderr, " -> %d\n", bv);
+    }
+  }
   std::lock_guard<std::mutex> lock(mu);
   cache[key] = std::make_pair(bv, h->sweep_us);
   return STP_OK;
@@ -636,12 +671,14 @@ int build_solve_graph(stp_handle* h) {
 
 // write the solve parameters and clear the totals (once per API call)
 int arm_solves(stp_handle* h, double tol, int maxit) {
+  if (int rc = tune_sweep(h)) return rc;
   SolveCtl c = {};
   c.tol = tol;
   c.inner_tol = h->cfg.inner_tol > 0 ? h->cfg.inner_tol : 1e-3;
   c.max_sweeps = maxit;
   c.max_passes = 64;
   c.M = (int)h->omega.size();
+  c.kpc = h->cycle_blocks > 0 ? 1 : uses_pairs(h) ? c.M / 2 : c.M;
   *h->h_ctl = c;
   CUDA_TRY(h, cudaMemcpyAsync(h->ctl, h->h_ctl, sizeof(SolveCtl), cudaMemcpyHostToDevice, h->st));
   return STP_OK;
@@ -669,6 +706,13 @@ int host_cycles(stp_handle* h, const Geom<T>& g, T* A, T* B, const T* rhs, int m
     if (sizeof(T) == sizeof(float) && h->cycle_blocks > 0) {
       CUDA_TRY(h, launch_cycle_f32(h->g32, (float*)A, (float*)B, (const float*)rhs, h->d_omega32, M, h->bar, h->ctl,
                                    h->cycle_blocks, h->st));
+      continue;
+    }
+    if (sizeof(T) == sizeof(float) && uses_pairs(h)) {
+      for (int m = 0; m < M; m += 2)
+        CUDA_TRY(h, launch_sweep_pair(h->g32, (const float*)((m % 4 == 0) ? A : B), (const float*)rhs,
+                                      (float)h->omega[m], (float)h->omega[m + 1], (float*)((m % 4 == 0) ? B : A),
+                                      h->st));
       continue;
     }
     for (int m = 0; m < M; m++)
@@ -1446,10 +1490,17 @@ void plan_groups(stp_batch* b) {
   b->in_group.assign(b->hs.size(), -1);
   const char* env = std::getenv("STP_BATCH_GROUPS");
   if (env && std::atoi(env) == 0) return;
+  // Size class: only channels of at most 2^17 cells are grouped (their own
+  // sweeps are launch-bound; larger channels sweep near the copy rate on
+  // their own and would only wait for their group's slowest member);
+  // STP_BATCH_GROUP_MAX_CHANNEL=<n> sets the limit (-1: no limit).
+  long long max_ch = 1 << 17;
+  if (const char* e = std::getenv("STP_BATCH_GROUP_MAX_CHANNEL")) max_ch = std::atoll(e);
   std::map<int, std::vector<int>> byM;
   for (size_t i = 0; i < b->hs.size(); i++) {
     stp_handle* h = b->hs[i];
     if (h->prec != STP_FP32_REFINE || h->nx % 4 || h->net || h->cycle_blocks > 0) continue;
+    if (max_ch >= 0 && (long long)h->nc > max_ch) continue;
     byM[(int)h->omega.size()].push_back((int)i);
   }
   // A group's inner solve touches d, d' and r of all its channels every
@@ -1600,6 +1651,15 @@ int setup_group(stp_batch* b, BatchGroup& grp) {
     }
     BTRY(b, cudaMemsetAsync(G.inner_on, 0, sizeof(int) * n, b->st));
     best_v = pick_variant(timed, &grp.sweep_us);
+    if (const char* lg = std::getenv("STP_TUNE_LOG")) {
+      if (std::atoi(lg)) {
+        long long cells = 0;
+        for (const stp_handle* h : grp.hs) cells += (long long)h->nc;
+        std::fprintf(stderr, "stp: grouped sweep tiles, %d channels, %lld cells (us per sweep):", n, cells);
+        for (const auto& t : timed) std::fprintf(stderr, " %d=%.3f", t.first, t.second);
+        std::fprintf(stderr, " -> %d\n", best_v);
+      }
+    }
   }
   group_voff(grp, best_v, voff);
   BTRY(b, cudaMemcpyAsync(base + o_voff, voff.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, b->st));

@@ -253,7 +253,7 @@ cudaError_t launch_gf(const Group& G, int m, cudaStream_t s) {
 int group_scalar_tiles(int nx, int ny, int nz) { return ((nx + kBX - 1) / kBX) * ((ny + kBY - 1) / kBY) * nz; }
 
 int group_sweep_tiles(int variant, int nx, int ny, int nz) {
-  if (!sweep_variant_ok(variant, nx, ny, nz)) return -1;
+  if (!sweep_variant_ok(variant, nx, ny, nz) || sweep_pair(variant)) return -1;
   const int kz = sweep_kz(variant), nx4 = nx / 4;
   if (sweep_flat(variant)) return ((nz / kz) * nx4 * ny + kBX * kBY - 1) / (kBX * kBY);
   const int by = sweep_by(variant);

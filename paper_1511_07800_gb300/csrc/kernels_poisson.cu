@@ -63,59 +63,17 @@ __global__ void __launch_bounds__(kBX* kBY) k_sweep_f64(Geom<double> g, const do
   out[q] = pc + omega * (pj - pc);
 }
 
-// Vectorised sweeps: each thread owns VW consecutive cells of a row (float4
-// in FP32, double2 in FP64); the x-neighbours across lanes come by warp
-// shuffle, so a cell costs one vector load per stencil direction instead
-// of eight scalar loads and their index arithmetic.  Lanes past the end of
-// a row (or rows past ny) read a clamped, in-bounds element, take part in
-// the shuffles and store nothing.  With PDL the kernel is launched as a
-// programmatic dependent of the previous sweep: its set-up overlaps the
-// previous kernel's tail and cudaGridDependencySynchronize waits for that
-// kernel's results before any read of p.
-template <bool PDL>
-__global__ void __launch_bounds__(kBX* kBY) k_sweep_f32_v4(Geom<float> g, const float* __restrict__ p,
-                                                            const float* __restrict__ b, float omega,
-                                                            float* __restrict__ out) {
-  const int lane = threadIdx.x;
-  const int nx = g.nx, ny = g.ny, nx4 = nx >> 2;
-  const int x4 = blockIdx.x * kBX + lane;
-  const int j = blockIdx.y * kBY + threadIdx.y, k = blockIdx.z;
-  const bool active = x4 < nx4 && j < ny;
-  const int xx = x4 < nx4 ? x4 : nx4 - 1;
-  const int jj = j < ny ? j : ny - 1;
-  const int jp = jj == ny - 1 ? 0 : jj + 1, jm = jj == 0 ? ny - 1 : jj - 1;
-  const size_t plane4 = (size_t)nx4 * ny;
-  const size_t rc = ((size_t)k * ny + jj) * nx4;
-  const float cup = __ldg(g.cup + k), cdn = __ldg(g.cdn + k), iS = __ldg(g.iS + k);
-  const float idx2 = g.idx2, idy2 = g.idy2;
-  const bool has_up = k < g.nz - 1, has_dn = k > 0;
-  if (PDL) cudaGridDependencySynchronize();
-  const float4* P = reinterpret_cast<const float4*>(p);
-  const float4 c = __ldg(P + rc + xx);
-  float left = __shfl_up_sync(0xffffffffu, c.w, 1);
-  float right = __shfl_down_sync(0xffffffffu, c.x, 1);
-  const float* prow = p + rc * 4;
-  if (lane == 0 || xx == 0) left = __ldg(prow + (4 * xx - 1 + nx) % nx);
-  if (lane == kBX - 1 || xx == nx4 - 1) right = __ldg(prow + (4 * xx + 4) % nx);
-  const float4 yn = __ldg(P + ((size_t)k * ny + jp) * nx4 + xx);
-  const float4 ys = __ldg(P + ((size_t)k * ny + jm) * nx4 + xx);
-  const float4 zu = has_up ? __ldg(P + rc + plane4 + xx) : c;
-  const float4 zd = has_dn ? __ldg(P + rc - plane4 + xx) : c;
-  const float4 bq = __ldg(reinterpret_cast<const float4*>(b) + rc + xx);
-  auto cell = [&](float pc, float xl, float xr, float nn, float ss, float uu, float dd, float bb) {
-    return srj_cell_f32(pc, xl, xr, nn, ss, uu, dd, bb, idx2, idy2, cup, cdn, iS, omega);
-  };
-  float4 o;
-  o.x = cell(c.x, left, c.y, yn.x, ys.x, zu.x, zd.x, bq.x);
-  o.y = cell(c.y, c.x, c.z, yn.y, ys.y, zu.y, zd.y, bq.y);
-  o.z = cell(c.z, c.y, c.w, yn.z, ys.z, zu.z, zd.z, bq.z);
-  o.w = cell(c.w, c.z, right, yn.w, ys.w, zu.w, zd.w, bq.w);
-  if (active) reinterpret_cast<float4*>(out)[rc + x4] = o;
-}
-
-// The same FP32 sweep with KZ consecutive z levels per thread (the z
-// neighbours inside the column come from registers, and a thread has KZ
-// rows of loads in flight) and BY rows per block.  nz must be a multiple of
+// Vectorised sweeps: each thread owns 4 consecutive cells of a row (float4
+// in FP32, double2 pairs in FP64); the x-neighbours across lanes come by
+// warp shuffle, so a cell costs one vector load per stencil direction
+// instead of eight scalar loads and their index arithmetic.  Lanes past the
+// end of a row (or rows past ny) read a clamped, in-bounds element, take
+// part in the shuffles and store nothing.  Launched as programmatic
+// dependents: set-up overlaps the previous kernel's tail, and
+// cudaGridDependencySynchronize waits for its results before any read of p.
+// FP32 sweep with KZ consecutive z levels per thread (the z neighbours
+// inside the column come from registers, and a thread has KZ rows of loads
+// in flight) and BY rows per block (sweep_z_tile).  nz must be a multiple of
 // KZ.  Identical arithmetic per cell for every (KZ, BY).
 template <int KZ, int BY>
 __global__ void __launch_bounds__(kBX* BY) k_sweep_f32_z(Geom<float> g, const float* __restrict__ p,
@@ -129,6 +87,107 @@ __global__ void __launch_bounds__(kBX* kBY) k_sweep_f32_flat(Geom<float> g, cons
                                                              const float* __restrict__ b, float omega,
                                                              float* __restrict__ out) {
   sweep_flat_tile<KZ>(g, p, b, omega, out, blockIdx.x);
+}
+
+// 16-byte asynchronous copy global -> shared, and the wait for all of them
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+// Two consecutive SRJ sweeps (omega_a, then omega_b) in one launch.  A block
+// owns TY rows x TZ levels x all of x of the output.  It stages p on its
+// tile widened by two rows and two levels on each side (rows wrap
+// periodically; levels past a wall are not needed: the wall cell uses its
+// own value, as in every sweep kernel) and b widened by one, computes the
+// first sweep on the tile widened by one into shared memory, then the
+// second sweep on the tile itself into global memory.  The widened part of
+// the first sweep repeats what the neighbouring blocks compute, with the
+// same inputs and the same cell function, so the result is bitwise that of
+// two single sweeps.  b is constant over a cycle and is copied before the
+// wait for the previous launch; p after it.
+template <int TY, int TZ>
+__global__ void __launch_bounds__(256) k_sweep_f32_pair(Geom<float> g, const float* __restrict__ p,
+                                                         const float* __restrict__ b, float om_a, float om_b,
+                                                         float* __restrict__ out) {
+  extern __shared__ float4 sm[];
+  constexpr int RY0 = TY + 4, RZ0 = TZ + 4, RY1 = TY + 2, RZ1 = TZ + 2;
+  const int nx = g.nx, ny = g.ny, nz = g.nz, nx4 = nx >> 2;
+  float4* P0 = sm;                    // [RZ0][RY0][nx4]  p, levels k0-2.., rows j0-2..
+  float4* B1 = P0 + RZ0 * RY0 * nx4;  // [RZ1][RY1][nx4]  b, levels k0-1.., rows j0-1..
+  float4* P1 = B1 + RZ1 * RY1 * nx4;  // [RZ1][RY1][nx4]  first sweep, same region as B1
+  const int j0 = blockIdx.x * TY, k0 = blockIdx.y * TZ;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const float4* Pg = reinterpret_cast<const float4*>(p);
+  const float4* Bg = reinterpret_cast<const float4*>(b);
+  const float idx2 = g.idx2, idy2 = g.idy2;
+  const int n1 = RZ1 * RY1 * nx4;
+  for (int q = tid; q < n1; q += nthr) {
+    const int x4 = q % nx4, r = q / nx4, yt = r % RY1, zt = r / RY1;
+    const int k = k0 - 1 + zt;
+    if (k < 0 || k >= nz) continue;
+    const int j = ((j0 - 1 + yt) % ny + ny) % ny;
+    cp_async16(B1 + q, Bg + ((size_t)k * ny + j) * nx4 + x4);
+  }
+  cudaGridDependencySynchronize();
+  const int n0 = RZ0 * RY0 * nx4;
+  for (int q = tid; q < n0; q += nthr) {
+    const int x4 = q % nx4, r = q / nx4, yt = r % RY0, zt = r / RY0;
+    const int k = k0 - 2 + zt;
+    if (k < 0 || k >= nz) continue;
+    const int j = ((j0 - 2 + yt) % ny + ny) % ny;
+    cp_async16(P0 + q, Pg + ((size_t)k * ny + j) * nx4 + x4);
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  // first sweep: levels k0-1 .. k0+TZ (inside the walls), rows j0-1 .. j0+TY
+  for (int q = tid; q < n1; q += nthr) {
+    const int x4 = q % nx4, r = q / nx4, yt = r % RY1, zt = r / RY1;
+    const int k = k0 - 1 + zt;
+    if (k < 0 || k >= nz) continue;
+    const float4* row = P0 + ((zt + 1) * RY0 + (yt + 1)) * nx4;
+    const float4 c = row[x4];
+    const float left = reinterpret_cast<const float*>(row + (x4 == 0 ? nx4 - 1 : x4 - 1))[3];
+    const float right = reinterpret_cast<const float*>(row + (x4 == nx4 - 1 ? 0 : x4 + 1))[0];
+    const float4 yn = row[nx4 + x4], ys = row[x4 - nx4];
+    const float4 zu = k < nz - 1 ? row[RY0 * nx4 + x4] : c;
+    const float4 zd = k > 0 ? row[x4 - RY0 * nx4] : c;
+    const float4 bq = B1[q];
+    const float cup = __ldg(g.cup + k), cdn = __ldg(g.cdn + k), iS = __ldg(g.iS + k);
+    float4 o;
+    o.x = srj_cell_f32(c.x, left, c.y, yn.x, ys.x, zu.x, zd.x, bq.x, idx2, idy2, cup, cdn, iS, om_a);
+    o.y = srj_cell_f32(c.y, c.x, c.z, yn.y, ys.y, zu.y, zd.y, bq.y, idx2, idy2, cup, cdn, iS, om_a);
+    o.z = srj_cell_f32(c.z, c.y, c.w, yn.z, ys.z, zu.z, zd.z, bq.z, idx2, idy2, cup, cdn, iS, om_a);
+    o.w = srj_cell_f32(c.w, c.z, right, yn.w, ys.w, zu.w, zd.w, bq.w, idx2, idy2, cup, cdn, iS, om_a);
+    P1[q] = o;
+  }
+  __syncthreads();
+  // second sweep: the tile itself
+  const int n2 = TZ * TY * nx4;
+  for (int q = tid; q < n2; q += nthr) {
+    const int x4 = q % nx4, r = q / nx4, yt = r % TY, zt = r / TY;
+    const int k = k0 + zt;
+    const int i1 = ((zt + 1) * RY1 + (yt + 1)) * nx4;
+    const float4* row = P1 + i1;
+    const float4 c = row[x4];
+    const float left = reinterpret_cast<const float*>(row + (x4 == 0 ? nx4 - 1 : x4 - 1))[3];
+    const float right = reinterpret_cast<const float*>(row + (x4 == nx4 - 1 ? 0 : x4 + 1))[0];
+    const float4 yn = row[nx4 + x4], ys = row[x4 - nx4];
+    const float4 zu = k < nz - 1 ? row[RY1 * nx4 + x4] : c;
+    const float4 zd = k > 0 ? row[x4 - RY1 * nx4] : c;
+    const float4 bq = B1[i1 + x4];
+    const float cup = __ldg(g.cup + k), cdn = __ldg(g.cdn + k), iS = __ldg(g.iS + k);
+    float4 o;
+    o.x = srj_cell_f32(c.x, left, c.y, yn.x, ys.x, zu.x, zd.x, bq.x, idx2, idy2, cup, cdn, iS, om_b);
+    o.y = srj_cell_f32(c.y, c.x, c.z, yn.y, ys.y, zu.y, zd.y, bq.y, idx2, idy2, cup, cdn, iS, om_b);
+    o.z = srj_cell_f32(c.z, c.y, c.w, yn.z, ys.z, zu.z, zd.z, bq.z, idx2, idy2, cup, cdn, iS, om_b);
+    o.w = srj_cell_f32(c.w, c.z, right, yn.w, ys.w, zu.w, zd.w, bq.w, idx2, idy2, cup, cdn, iS, om_b);
+    reinterpret_cast<float4*>(out)[((size_t)k * ny + j0 + yt) * nx4 + x4] = o;
+  }
 }
 
 template <bool PDL>
@@ -406,7 +465,50 @@ void set_sweep_variant(int v) { t_sweep_variant = v; }
 int sweep_variant_count() { return kSweepVariants; }
 bool sweep_variant_ok(int v, int nx, int ny, int nz) {
   if (v < 0 || v >= kSweepVariants || nx % 4 || nz % sweep_kz(v)) return false;
+  if (sweep_pair(v)) return ny % sweep_by(v) == 0 && pair_smem_bytes(sweep_by(v), sweep_kz(v), nx) <= kPairSmemMax;
   return !sweep_flat(v) || ((nx / 4) * ny) % 32 == 0;
+}
+bool sweep_variant_is_pair(int v) { return v >= 0 && v < kSweepVariants && sweep_pair(v); }
+
+template <int TY, int TZ>
+static cudaError_t launch_pair(const Geom<float>& g, const float* p, const float* b, float om_a, float om_b,
+                               float* out, cudaStream_t s) {
+  const size_t smem = pair_smem_bytes(TY, TZ, g.nx);
+  static size_t attr_bytes = 0;  // the kernel's shared-memory limit, raised as needed
+  if (smem > attr_bytes) {
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    if (smem > (size_t)optin) return cudaErrorInvalidConfiguration;
+    e = cudaFuncSetAttribute(k_sweep_f32_pair<TY, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    if (e != cudaSuccess) return e;
+    attr_bytes = (size_t)optin;
+  }
+  const dim3 grid(g.ny / TY, g.nz / TZ), block(256);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, k_sweep_f32_pair<TY, TZ>, g, p, b, om_a, om_b, out);
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+cudaError_t launch_sweep_pair(const Geom<float>& g, const float* p, const float* b, float om_a, float om_b,
+                              float* out, cudaStream_t s) {
+  const int v = sweep_variant_ok(t_sweep_variant, g.nx, g.ny, g.nz) ? t_sweep_variant : -1;
+  switch (v) {
+    case 9: return launch_pair<8, 4>(g, p, b, om_a, om_b, out, s);
+    case 10: return launch_pair<4, 4>(g, p, b, om_a, om_b, out, s);
+    case 11: return launch_pair<4, 8>(g, p, b, om_a, om_b, out, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 static cudaError_t launch_sweep_cfg(const void* kern, dim3 grid, dim3 block, cudaStream_t s, void** args) {
@@ -464,11 +566,8 @@ cudaError_t launch_sweep<float>(const Geom<float>& g, const float* p, const floa
       case 3: return launch_z<2, 4>(g, p, b, omega, out, s);
       case 4: return launch_z<4, 4>(g, p, b, omega, out, s);
       case 5: return launch_z<8, 4>(g, p, b, omega, out, s);
-      default: break;
+      default: return launch_z<1, 8>(g, p, b, omega, out, s);
     }
-    const dim3 grid((g.nx / 4 + kBX - 1) / kBX, (g.ny + kBY - 1) / kBY, g.nz), block(kBX, kBY, 1);
-    cudaError_t e = launch_pdl(k_sweep_f32_v4<true>, grid, block, s, g, p, b, omega, out);
-    return e != cudaSuccess ? e : cudaGetLastError();
   }
   Launch l = plane_launch(g.nx, g.ny, g.nz);
   k_sweep_f32<<<l.grid, l.block, 0, s>>>(g, p, b, omega, out);

@@ -65,41 +65,45 @@ __device__ __forceinline__ void sweep_z_tile(const Geom<float>& g, const float* 
   const bool active = x4 < nx4 && j < ny;
   const int xx = x4 < nx4 ? x4 : nx4 - 1;
   const int jj = j < ny ? j : ny - 1;
-  const int jp = jj == ny - 1 ? 0 : jj + 1, jm = jj == 0 ? ny - 1 : jj - 1;
-  const size_t plane4 = (size_t)nx4 * ny;
-  const size_t r0 = ((size_t)k0 * ny + jj) * nx4 + xx;  // this thread's unit at level k0
+  // 32-bit float4-unit offsets (fields of fewer than 2^32 cells)
+  const unsigned plane4 = (unsigned)nx4 * ny;
+  const unsigned rc = (unsigned)jj * nx4 + xx;                             // unit within a level
+  const unsigned rn = (unsigned)(jj == ny - 1 ? 0 : jj + 1) * nx4 + xx;    // row j+1
+  const unsigned rs = (unsigned)(jj == 0 ? ny - 1 : jj - 1) * nx4 + xx;    // row j-1
+  const int xl = xx == 0 ? nx - 1 - 4 * xx : -1, xr = xx == nx4 - 1 ? 4 - nx : 4;  // x-neighbour cells, wrapped
+  const unsigned u0 = (unsigned)k0 * plane4;
   const float idx2 = g.idx2, idy2 = g.idy2;
   cudaGridDependencySynchronize();
   const float4* P = reinterpret_cast<const float4*>(p);
+  const float4* Bq = reinterpret_cast<const float4*>(b);
   float4 c[KZ + 2];
 #pragma unroll
-  for (int q = 0; q < KZ; q++) c[q + 1] = __ldg(P + r0 + q * plane4);
-  c[0] = k0 > 0 ? __ldg(P + r0 - plane4) : c[1];
-  c[KZ + 1] = k0 + KZ < g.nz ? __ldg(P + r0 + KZ * plane4) : c[KZ];
+  for (int q = 0; q < KZ; q++) c[q + 1] = __ldg(P + (u0 + q * plane4 + rc));
+  c[0] = k0 > 0 ? __ldg(P + (u0 - plane4 + rc)) : c[1];
+  c[KZ + 1] = k0 + KZ < g.nz ? __ldg(P + (u0 + KZ * plane4 + rc)) : c[KZ];
 #pragma unroll
   for (int q = 0; q < KZ; q++) {
     const int k = k0 + q;
-    const size_t rc = r0 + q * plane4;
-    const size_t rowbase = ((size_t)k * ny + jj) * nx4;
+    const unsigned lev = u0 + q * plane4;
     const float cup = __ldg(g.cup + k), cdn = __ldg(g.cdn + k), iS = __ldg(g.iS + k);
     const float4 cc = c[q + 1], zu = c[q + 2], zd = c[q];
     float left = __shfl_up_sync(0xffffffffu, cc.w, 1);
     float right = __shfl_down_sync(0xffffffffu, cc.x, 1);
-    const float* prow = p + rowbase * 4;
-    if (lane == 0 || xx == 0) left = __ldg(prow + (4 * xx - 1 + nx) % nx);
-    if (lane == kBX - 1 || xx == nx4 - 1) right = __ldg(prow + (4 * xx + 4) % nx);
-    const float4 yn = __ldg(P + ((size_t)k * ny + jp) * nx4 + xx);
-    const float4 ys = __ldg(P + ((size_t)k * ny + jm) * nx4 + xx);
-    const float4 bq = __ldg(reinterpret_cast<const float4*>(b) + rc);
-    auto cell = [&](float pc, float xl, float xr, float nn, float ss, float uu, float dd, float bb) {
-      return srj_cell_f32(pc, xl, xr, nn, ss, uu, dd, bb, idx2, idy2, cup, cdn, iS, omega);
+    const float* pc = p + 4 * (lev + rc);  // first cell of this thread's unit
+    if (lane == 0 || xx == 0) left = __ldg(pc + xl);
+    if (lane == kBX - 1 || xx == nx4 - 1) right = __ldg(pc + xr);
+    const float4 yn = __ldg(P + (lev + rn));
+    const float4 ys = __ldg(P + (lev + rs));
+    const float4 bq = __ldg(Bq + (lev + rc));
+    auto cell = [&](float pcv, float xlv, float xrv, float nn, float ss, float uu, float dd, float bb) {
+      return srj_cell_f32(pcv, xlv, xrv, nn, ss, uu, dd, bb, idx2, idy2, cup, cdn, iS, omega);
     };
     float4 o;
     o.x = cell(cc.x, left, cc.y, yn.x, ys.x, zu.x, zd.x, bq.x);
     o.y = cell(cc.y, cc.x, cc.z, yn.y, ys.y, zu.y, zd.y, bq.y);
     o.z = cell(cc.z, cc.y, cc.w, yn.z, ys.z, zu.z, zd.z, bq.z);
     o.w = cell(cc.w, cc.z, right, yn.w, ys.w, zu.w, zd.w, bq.w);
-    if (active) reinterpret_cast<float4*>(out)[rc] = o;
+    if (active) reinterpret_cast<float4*>(out)[lev + rc] = o;
   }
 }
 
@@ -126,40 +130,43 @@ __device__ __forceinline__ void sweep_flat_tile(const Geom<float>& g, const floa
   const int slab = f / plane4, pi = f - slab * plane4;
   const int j = pi / nx4, x4 = pi - j * nx4;
   const int k0 = slab * KZ;
-  const int jp = j == ny - 1 ? 0 : j + 1, jm = j == 0 ? ny - 1 : j - 1;
-  const size_t r0 = (size_t)k0 * plane4 + pi;
+  // 32-bit float4-unit offsets (fields of fewer than 2^32 cells)
+  const unsigned rn = (unsigned)(j == ny - 1 ? 0 : j + 1) * nx4 + x4;
+  const unsigned rs = (unsigned)(j == 0 ? ny - 1 : j - 1) * nx4 + x4;
+  const int xl = x4 == 0 ? nx - 1 : -1, xr = x4 == nx4 - 1 ? 4 - nx : 4;  // x-neighbour cells, wrapped
+  const unsigned u0 = (unsigned)k0 * plane4;
   const float idx2 = g.idx2, idy2 = g.idy2;
   cudaGridDependencySynchronize();
   const float4* P = reinterpret_cast<const float4*>(p);
+  const float4* Bq = reinterpret_cast<const float4*>(b);
   float4 c[KZ + 2];
 #pragma unroll
-  for (int q = 0; q < KZ; q++) c[q + 1] = __ldg(P + r0 + (size_t)q * plane4);
-  c[0] = k0 > 0 ? __ldg(P + r0 - plane4) : c[1];
-  c[KZ + 1] = k0 + KZ < g.nz ? __ldg(P + r0 + (size_t)KZ * plane4) : c[KZ];
+  for (int q = 0; q < KZ; q++) c[q + 1] = __ldg(P + (u0 + q * plane4 + pi));
+  c[0] = k0 > 0 ? __ldg(P + (u0 - plane4 + pi)) : c[1];
+  c[KZ + 1] = k0 + KZ < g.nz ? __ldg(P + (u0 + KZ * plane4 + pi)) : c[KZ];
 #pragma unroll
   for (int q = 0; q < KZ; q++) {
     const int k = k0 + q;
-    const size_t rc = r0 + (size_t)q * plane4;
-    const size_t lev = (size_t)k * plane4;
+    const unsigned lev = u0 + q * plane4;
     const float cup = __ldg(g.cup + k), cdn = __ldg(g.cdn + k), iS = __ldg(g.iS + k);
     const float4 cc = c[q + 1], zu = c[q + 2], zd = c[q];
     float left = __shfl_up_sync(0xffffffffu, cc.w, 1);
     float right = __shfl_down_sync(0xffffffffu, cc.x, 1);
-    const float* prow = p + (lev + (size_t)j * nx4) * 4;
-    if (lane == 0 || x4 == 0) left = __ldg(prow + (4 * x4 - 1 + nx) % nx);
-    if (lane == kBX - 1 || x4 == nx4 - 1) right = __ldg(prow + (4 * x4 + 4) % nx);
-    const float4 yn = __ldg(P + lev + (size_t)jp * nx4 + x4);
-    const float4 ys = __ldg(P + lev + (size_t)jm * nx4 + x4);
-    const float4 bq = __ldg(reinterpret_cast<const float4*>(b) + rc);
-    auto cell = [&](float pc, float xl, float xr, float nn, float ss, float uu, float dd, float bb) {
-      return srj_cell_f32(pc, xl, xr, nn, ss, uu, dd, bb, idx2, idy2, cup, cdn, iS, omega);
+    const float* pc = p + 4 * (lev + pi);  // first cell of this thread's unit
+    if (lane == 0 || x4 == 0) left = __ldg(pc + xl);
+    if (lane == kBX - 1 || x4 == nx4 - 1) right = __ldg(pc + xr);
+    const float4 yn = __ldg(P + (lev + rn));
+    const float4 ys = __ldg(P + (lev + rs));
+    const float4 bq = __ldg(Bq + (lev + pi));
+    auto cell = [&](float pcv, float xlv, float xrv, float nn, float ss, float uu, float dd, float bb) {
+      return srj_cell_f32(pcv, xlv, xrv, nn, ss, uu, dd, bb, idx2, idy2, cup, cdn, iS, omega);
     };
     float4 o;
     o.x = cell(cc.x, left, cc.y, yn.x, ys.x, zu.x, zd.x, bq.x);
     o.y = cell(cc.y, cc.x, cc.z, yn.y, ys.y, zu.y, zd.y, bq.y);
     o.z = cell(cc.z, cc.y, cc.w, yn.z, ys.z, zu.z, zd.z, bq.z);
     o.w = cell(cc.w, cc.z, right, yn.w, ys.w, zu.w, zd.w, bq.w);
-    if (active) reinterpret_cast<float4*>(out)[rc] = o;
+    if (active) reinterpret_cast<float4*>(out)[lev + pi] = o;
   }
 }
 
@@ -168,12 +175,24 @@ __device__ __forceinline__ void sweep_flat_tile(const Geom<float>& g, const floa
 //   1 .. 5   (KZ, BY) = (2,8), (4,8), (2,4), (4,4), (8,4): KZ levels per
 //            thread, 32 x BY threads
 //   6 .. 8   warps packed along the plane (sweep_flat_tile), KZ = 2, 4, 8
-constexpr int kSweepVariants = 9;
+//   9 .. 11  two sweeps per launch on a shared-memory tile of TY rows x
+//            TZ levels x all of x (k_sweep_f32_pair), (TY, TZ) = (8,4),
+//            (4,4), (4,8); used only for cycles of a multiple of 4 sweeps
+constexpr int kSweepVariants = 12;
 __host__ __device__ constexpr int sweep_kz(int v) {
-  return v == 0 ? 1 : v == 1 ? 2 : v == 2 ? 4 : v == 3 ? 2 : v == 4 ? 4 : v == 5 ? 8 : v == 6 ? 2 : v == 7 ? 4 : 8;
+  return v == 0 ? 1 : v == 1 ? 2 : v == 2 ? 4 : v == 3 ? 2 : v == 4 ? 4 : v == 5 ? 8 : v == 6 ? 2 : v == 7 ? 4
+         : v == 8 ? 8 : v == 9 ? 4 : v == 10 ? 4 : 8;
 }
-__host__ __device__ constexpr int sweep_by(int v) { return (v >= 3 && v <= 5) ? 4 : 8; }
-__host__ __device__ constexpr bool sweep_flat(int v) { return v >= 6; }
+__host__ __device__ constexpr int sweep_by(int v) { return (v >= 3 && v <= 5) || v == 10 || v == 11 ? 4 : 8; }
+__host__ __device__ constexpr bool sweep_flat(int v) { return v >= 6 && v <= 8; }
+__host__ __device__ constexpr bool sweep_pair(int v) { return v >= 9; }
+
+// shared memory of a pair-sweep tile: input p with two ghost rows and
+// levels on each side, b and the first sweep's result with one
+__host__ __device__ constexpr size_t pair_smem_bytes(int ty, int tz, int nx) {
+  return (size_t)((tz + 4) * (ty + 4) + 2 * (tz + 2) * (ty + 2)) * (nx / 4) * 16;
+}
+constexpr size_t kPairSmemMax = 227 * 1024;
 
 // Start of a solve: fold the previous solve into the totals, reset the state.
 __device__ __forceinline__ void begin_solve_state(SolveCtl* ctl) {
@@ -219,7 +238,7 @@ __device__ __forceinline__ bool cycle_decide(SolveCtl* ctl, const Red& red, doub
   if (!stop) {
     ctl->sweeps += ctl->M;
     ctl->cycles_inner += 1;
-    ctl->kernels += ctl->M;
+    ctl->kernels += ctl->kpc;
   }
   *red.counter = 0u;
   ctl->go = stop ? 0 : 1;

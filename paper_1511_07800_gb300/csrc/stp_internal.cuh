@@ -87,7 +87,7 @@ struct SolveCtl {
   int max_sweeps;    // cap on SRJ sweeps per solve
   int max_passes;    // cap on refinement passes per solve
   int M;             // SRJ cycle length
-  int pad0;
+  int kpc;           // kernels that run the M sweeps of a cycle
   // state of the current solve
   int sweeps, passes, cycles_inner, converged, bad, pad1;
   double prev, res, res_inner;
@@ -157,6 +157,11 @@ cudaError_t launch_sweep<double>(const Geom<double>&, const double*, const doubl
 void set_sweep_variant(int v);
 int sweep_variant_count();
 bool sweep_variant_ok(int v, int nx, int ny, int nz);
+// variants 9..11 run two sweeps per launch (launch_sweep_pair, cycles of a
+// multiple of 4 sweeps only); launch_sweep falls back to variant 0 for them
+bool sweep_variant_is_pair(int v);
+cudaError_t launch_sweep_pair(const Geom<float>& g, const float* p, const float* b, float om_a, float om_b,
+                              float* out, cudaStream_t s);
 
 // ||b - L p|| and the once-per-cycle decision (mode 0: FP64 solve, mode 1:
 // FP32 inner solve); sets the WHILE (h_loop) and IF (h_body) conditionals.

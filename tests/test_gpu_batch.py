@@ -81,6 +81,7 @@ def test_grouped_solves_match_own_solves(stp_lib, monkeypatch, env):
              case(nx=64, ny=32, nz=48, nu=1 / 800.0, cn_sweeps=3),
              case(nx=32, ny=32, nz=16, nu=1 / 300.0)]
     res = []
+    monkeypatch.setenv("STP_BATCH_GROUP_MAX_CHANNEL", "-1")
     for groups in ("0", "1"):
         monkeypatch.setenv("STP_BATCH_GROUPS", groups)
         for k, v in env.items():

@@ -254,21 +254,26 @@ def test_persistent_cycle_matches_per_sweep_kernels(stp_lib, monkeypatch):
 @pytest.mark.parametrize("shape", [(64, 24, 32), (32, 12, 16)])
 def test_sweep_variants_identical(stp_lib, monkeypatch, shape):
     """Every FP32 sweep tile shape the autotuner may pick computes the same
-    values (z levels per thread, rows per block and warps packed along the
-    plane only change the mapping).  The second grid has rows of 8 float4
-    units, so a packed warp holds four rows and wraps x inside the warp."""
+    values (z levels per thread, rows per block, warps packed along the
+    plane, and two sweeps per launch on a shared-memory tile only change the
+    mapping).  The second grid has rows of 8 float4 units, so a packed warp
+    holds four rows and wraps x inside the warp."""
     nx, ny, nz = shape
     cfg = case(nx=nx, ny=ny, nz=nz, stretch=2.0, les=0, nu=1 / 500.0, cn_sweeps=4)
     om = schedule(cfg, 32)
     ref = None
-    for v in range(9):
+    ran = set()
+    for v in range(12):
         monkeypatch.setenv("STP_SWEEP_VARIANT", str(v))
         with stp_lib.Channel(cfg, precision="fp32", omega=om) as ch:
             ch.set_fields(*turbulent_like(cfg, 13))
             ch.step(2)
             f = ch.get_fields()
+            ran.add(ch.sweep_tile()[0])
         if ref is None:
             ref = f
         else:
             for k in ("u", "v", "w", "p"):
                 assert np.array_equal(f[k], ref[k]), (v, k)
+    # the pair tiles (two sweeps per launch) that fit these grids did run
+    assert ({10, 11} | ({9} if ny % 8 == 0 else set())) <= ran, ran
