@@ -9,8 +9,8 @@ library: the C source `stp_oracle.c` is compiled on its own into
 
 Modules:
   this file   -- ctypes wrapper of the C oracle (step and its building blocks)
-  srj.py      -- SRJ relaxation schedule (Sec. 3.4) and the Jacobi eigenvalue
-                 bounds it is built from
+  srj.py      -- SRJ relaxation schedule (Sec. 3.4) and the eigenvalue bounds
+                 it is built from (point and z-line Jacobi)
   os_eig.py   -- Orr-Sommerfeld eigenvalue solver (Sec. 4.1)
 """
 import ctypes
@@ -45,7 +45,7 @@ class Params(ctypes.Structure):
         ("re_tau", ctypes.c_double), ("stretch", ctypes.c_double),
         ("cn_sweeps", ctypes.c_int), ("srj_m", ctypes.c_int),
         ("srj_omega", ctypes.POINTER(ctypes.c_double)),
-        ("ptol", ctypes.c_double), ("pmaxit", ctypes.c_int),
+        ("ptol", ctypes.c_double), ("pmaxit", ctypes.c_int), ("zline", ctypes.c_int),
     ]
 
 
@@ -76,6 +76,7 @@ def lib():
         L.orc_divergence.argtypes = [pp, dp, dp, dp, dp]
         L.orc_laplacian.argtypes = [pp, dp, dp]
         L.orc_srj_sweep.argtypes = [pp, dp, dp, ctypes.c_double, dp]
+        L.orc_line_sweep.argtypes = [pp, dp, dp, ctypes.c_double, dp]
         L.orc_poisson.argtypes = [pp, dp, dp, ctypes.c_double, ctypes.c_int, dp]
         L.orc_poisson.restype = ctypes.c_int
         L.orc_correct.argtypes = [pp, dp, dp, dp, dp]
@@ -97,7 +98,7 @@ class Oracle:
     (omega: the SRJ schedule as a float64 array)."""
 
     KEYS = ("nx", "ny", "nz", "Lx", "Ly", "Lz", "nu", "dt", "forcing", "fx", "ubulk", "les", "cs",
-            "vd_a", "re_tau", "stretch", "cn_sweeps", "ptol", "pmaxit")
+            "vd_a", "re_tau", "stretch", "cn_sweeps", "ptol", "pmaxit", "zline")
 
     def __init__(self, cfg):
         self.cfg = dict(cfg)
@@ -174,6 +175,12 @@ class Oracle:
     def srj_sweep(self, p, b, omega):
         out = self._c()
         lib().orc_srj_sweep(ctypes.byref(self.P), _ptr(p), _ptr(b), float(omega), _ptr(out))
+        return out
+
+    def line_sweep(self, p, b, omega):
+        """One z-line Jacobi-SOR sweep (each z column solved exactly)."""
+        out = self._c()
+        lib().orc_line_sweep(ctypes.byref(self.P), _ptr(p), _ptr(b), float(omega), _ptr(out))
         return out
 
     def poisson(self, b, p0=None, tol=1e-8, maxit=100000):

@@ -19,7 +19,8 @@ the schedule here is built from the mathematics of the method:
 mu_min and mu_max come from the separable structure of the discrete Poisson
 operator: Fourier modes in the periodic x and y directions, and for each
 (x, y) wavenumber a small generalized symmetric eigenproblem in z solved with
-scipy.
+scipy.  For z-line Jacobi (each z column solved exactly, Sec. 3.4's
+relaxation applied to whole lines) the operator splits the same way.
 """
 import numpy as np
 import scipy.linalg
@@ -74,6 +75,29 @@ def jacobi_bounds(nx, ny, nz, Lx, Ly, Lz, stretch=0.0):
     return float(mu_min), float(mu_max)
 
 
+def line_bounds(nx, ny, nz, Lx, Ly, Lz, stretch=0.0):
+    """(mu_min, mu_max) for z-line Jacobi: the smallest non-zero and the
+    largest eigenvalue of A^-1(-L), A = -L_z + (2/dx^2 + 2/dy^2) I the
+    operator of one z column with its x-y diagonal.  -L is the Kronecker sum
+    of -L_z (eigenvalues tau, from the symmetric generalized problem
+    W(-L_z) phi = tau W phi, W = diag(dz)) and the periodic x-y operator
+    (eigenvalues lam = 4/dx^2 sin^2(pi m/nx) + 4/dy^2 sin^2(pi n/ny)); A
+    shares the eigenvectors, so every eigenvalue is (tau + lam)/(tau + dxy).
+    All (tau, lam) pairs but the constant mode are enumerated."""
+    dx, dy = Lx / nx, Ly / ny
+    dz, cup, cdn, A0 = _z_operator(nz, Lz, stretch)
+    tau = scipy.linalg.eigh(A0, np.diag(dz), eigvals_only=True)
+    dxy = 2 / dx**2 + 2 / dy**2
+    lam = (4 / dx**2 * np.sin(np.pi * np.arange(nx) / nx) ** 2)[:, None] + \
+        (4 / dy**2 * np.sin(np.pi * np.arange(ny) / ny) ** 2)[None, :]
+    lam = lam.ravel()
+    mu = (tau[:, None] + lam[None, :]) / (tau[:, None] + dxy)
+    mu[0, 0] = np.inf          # the constant mode (tau_0 = 0, lam = 0) is the null space
+    mu_min = mu.min()
+    mu[0, 0] = -np.inf
+    return float(mu_min), float(mu.max())
+
+
 def stable_order(M):
     """Odd numbers 1..2M-1 in the recursive mirror-pair order (M = 2^p)."""
     assert M >= 1 and (M & (M - 1)) == 0, "cycle length must be a power of two"
@@ -104,8 +128,9 @@ def default_cycle_length(mu_min, mu_max, target=0.01, mmax=1024):
     return M
 
 
-def schedule_for(nx, ny, nz, Lx, Ly, Lz, stretch=0.0, M=0):
-    mn, mx = jacobi_bounds(nx, ny, nz, Lx, Ly, Lz, stretch)
+def schedule_for(nx, ny, nz, Lx, Ly, Lz, stretch=0.0, M=0, line=False):
+    """(omega, mu_min, mu_max) for point (default) or z-line Jacobi sweeps."""
+    mn, mx = (line_bounds if line else jacobi_bounds)(nx, ny, nz, Lx, Ly, Lz, stretch)
     if M <= 0:
         M = default_cycle_length(mn, mx)
     return chebyshev_schedule(mn, mx, M), mn, mx

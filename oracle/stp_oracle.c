@@ -58,6 +58,7 @@ typedef struct {
     const double *srj_omega; /* omega_1..omega_M, one per sweep of a cycle   */
     double ptol;      /* relative l2 residual tolerance of the pressure solve */
     int pmaxit;       /* cap on SRJ sweeps per solve                          */
+    int zline;        /* 0: point Jacobi-SOR sweeps; 1: z-line Jacobi-SOR      */
 } orc_params;
 
 /* ------------------------------------------------------------------------ */
@@ -571,6 +572,64 @@ static void srj_sweep(const grid *g, const double *p, const double *b, double om
     }
 }
 
+/* Tridiagonal solve (Thomas algorithm, no pivoting; the matrices here are
+   strictly diagonally dominant): lo[k] x[k-1] + di[k] x[k] + up[k] x[k+1]
+   = rhs[k], k = 0..n-1 (lo[0], up[n-1] unused).  cp, dp: scratch of n. */
+static void thomas(int n, const double *lo, const double *di, const double *up, const double *rhs, double *x,
+                   double *cp, double *dp)
+{
+    int k;
+    cp[0] = up[0] / di[0];
+    dp[0] = rhs[0] / di[0];
+    for (k = 1; k < n; k++) {
+        double m = di[k] - lo[k] * cp[k - 1];
+        cp[k] = (k < n - 1) ? up[k] / m : 0.0;
+        dp[k] = (rhs[k] - lo[k] * dp[k - 1]) / m;
+    }
+    x[n - 1] = dp[n - 1];
+    for (k = n - 2; k >= 0; k--) x[k] = dp[k] - cp[k] * x[k + 1];
+}
+
+/* z-line Jacobi-SOR sweep: the line value p^L solves the equations of
+   L p = b on a whole z column (i, j) at once, with the x and y neighbours
+   held at their old values; relaxed as p + omega (p^L - p).  The column
+   equations, multiplied by -1, are
+     (2/dx^2 + 2/dy^2 + cup_k + cdn_k) p^L_k - cup_k p^L_{k+1} - cdn_k p^L_{k-1}
+        = cxx (p_{i+1} + p_{i-1}) + cyy (p_{j+1} + p_{j-1}) - b_k,
+   a tridiagonal system per column (walls: cup = 0 at the top, cdn = 0 at
+   the bottom, as in the point sweep). */
+static void line_sweep(const grid *g, const double *p, const double *b, double omega, double *out)
+{
+    int j;
+#pragma omp parallel for schedule(static)
+    for (j = 0; j < g->ny; j++) {
+        int nz = g->nz, i, k;
+        double cxx = 1.0 / (g->dx * g->dx), cyy = 1.0 / (g->dy * g->dy);
+        double *lo = (double *)malloc(sizeof(double) * nz), *di = (double *)malloc(sizeof(double) * nz);
+        double *up = (double *)malloc(sizeof(double) * nz), *rhs = (double *)malloc(sizeof(double) * nz);
+        double *x = (double *)malloc(sizeof(double) * nz), *cp = (double *)malloc(sizeof(double) * nz);
+        double *dp = (double *)malloc(sizeof(double) * nz);
+        for (k = 0; k < nz; k++) {
+            double cup = (k < nz - 1) ? 1.0 / (g->hz[k + 1] * g->dz[k]) : 0.0;
+            double cdn = (k > 0) ? 1.0 / (g->hz[k] * g->dz[k]) : 0.0;
+            di[k] = 2.0 * cxx + 2.0 * cyy + cup + cdn;
+            up[k] = -cup;
+            lo[k] = -cdn;
+        }
+        for (i = 0; i < g->nx; i++) {
+            for (k = 0; k < nz; k++)
+                rhs[k] = cxx * (cen_g(g, p, i + 1, j, k) + cen_g(g, p, i - 1, j, k)) +
+                         cyy * (cen_g(g, p, i, j + 1, k) + cen_g(g, p, i, j - 1, k)) - b[IDX(g, i, j, k)];
+            thomas(nz, lo, di, up, rhs, x, cp, dp);
+            for (k = 0; k < nz; k++) {
+                double pc = p[IDX(g, i, j, k)];
+                out[IDX(g, i, j, k)] = pc + omega * (x[k] - pc);
+            }
+        }
+        free(lo); free(di); free(up); free(rhs); free(x); free(cp); free(dp);
+    }
+}
+
 static double norm2(const double *a, size_t n)
 {
     double s = 0.0;
@@ -588,11 +647,12 @@ static double residual_norm(const grid *g, const double *p, const double *b, dou
 }
 
 /* SRJ solve of L p = b from the guess in p.  Each cycle: test
-   ||b - L p||_2 <= tol ||b||_2, then M sweeps with omega_1..omega_M.
+   ||b - L p||_2 <= tol ||b||_2, then M sweeps with omega_1..omega_M (point
+   sweeps, or z-line sweeps when zline).
    Returns the number of sweeps; *rel gets the final relative residual
    (the absolute norm if ||b|| = 0).  Returns -1-sweeps if maxit was hit. */
 static int poisson_srj(const grid *g, double *p, const double *b, int M, const double *omega, double tol,
-                       int maxit, double *rel)
+                       int maxit, int zline, double *rel)
 {
     size_t n = (size_t)g->nx * g->ny * g->nz;
     double *tmp = (double *)malloc(sizeof(double) * n);
@@ -604,7 +664,10 @@ static int poisson_srj(const grid *g, double *p, const double *b, int M, const d
         if (r <= tol * nb) { status = it; break; }
         if (it >= maxit) { status = -1 - it; break; }
         for (m = 0; m < M; m++) {
-            srj_sweep(g, p, b, omega[m], q2);
+            if (zline)
+                line_sweep(g, p, b, omega[m], q2);
+            else
+                srj_sweep(g, p, b, omega[m], q2);
             memcpy(p, q2, sizeof(double) * n);
             it++;
         }
@@ -777,7 +840,7 @@ static int one_step(orc_state *s, double *stats)
     divergence(g, us, vs, ws, b);
     for (q = 0; q < nc; q++) b[q] = b[q] / P->dt;
     /* pressure, previous p as the guess */
-    it = poisson_srj(g, s->p, b, P->srj_m, P->srj_omega, P->ptol, P->pmaxit, &rel);
+    it = poisson_srj(g, s->p, b, P->srj_m, P->srj_omega, P->ptol, P->pmaxit, P->zline, &rel);
     if (it < 0) { status = 1; it = -1 - it; }
     /* projection */
     correct(P, g, s->p, us, vs, ws);
@@ -907,11 +970,16 @@ void orc_srj_sweep(const orc_params *P, const double *p, const double *b, double
     grid g; grid_make(P, &g); srj_sweep(&g, p, b, omega, out); grid_free(&g);
 }
 
+void orc_line_sweep(const orc_params *P, const double *p, const double *b, double omega, double *out)
+{
+    grid g; grid_make(P, &g); line_sweep(&g, p, b, omega, out); grid_free(&g);
+}
+
 int orc_poisson(const orc_params *P, double *p, const double *b, double tol, int maxit, double *rel)
 {
     grid g; int it;
     grid_make(P, &g);
-    it = poisson_srj(&g, p, b, P->srj_m, P->srj_omega, tol, maxit, rel);
+    it = poisson_srj(&g, p, b, P->srj_m, P->srj_omega, tol, maxit, P->zline, rel);
     grid_free(&g);
     return it;
 }
