@@ -88,6 +88,11 @@ typedef struct stp_config {
     int cfl_check;           /* 1: return STP_ECFL when U_max dt > 0.1 dx         */
     int device;              /* CUDA device ordinal                              */
     void *stream;            /* cudaStream_t to run on; NULL: the library's own  */
+    int zline;               /* pressure sweeps: 0 point Jacobi-SOR (Sec. 3.4);
+                                1 z-line Jacobi-SOR: each z column solved exactly
+                                (Thomas) with the x-y neighbours held, SRJ
+                                weights from the line-Jacobi spectrum (suits
+                                wall-stretched grids)                            */
 } stp_config;
 
 typedef struct stp_step_stats {

@@ -239,6 +239,41 @@ void jacobi_bounds(const stp_config& c, double* mn, double* mx) {
   *mx = tri_eig(z_problem(c, z, lx(c.nx / 2) + ly(c.ny / 2)), c.nz - 1);
 }
 
+// z-line Jacobi: A = -L_z + dxy I shares its eigenvectors with -L (the
+// Kronecker sum of -L_z and the periodic x-y operator), so the eigenvalues of
+// A^-1(-L) are (tau + lam)/(tau + dxy): tau of -L_z (W(-L_z) phi = tau W phi,
+// W = diag(dz), Sturm bisection), lam of the x-y operator.  The extremes over
+// all pairs but the constant mode are at tau in {0, tau_1, tau_max} and lam in
+// {0, lam_1, lam_max}.
+void line_bounds(const stp_config& c, double* mn, double* mx) {
+  const ZGrid z = make_z(c);
+  const int nz = c.nz;
+  std::vector<double> cup, cdn;
+  poisson_z(c, z, cup, cdn);
+  Tridiag t;
+  t.d.resize(nz);
+  t.e.assign(nz > 1 ? nz - 1 : 0, 0.0);
+  for (int k = 0; k < nz; k++) t.d[k] = cup[k] + cdn[k];
+  for (int k = 0; k + 1 < nz; k++) t.e[k] = (-1.0 / z.hz[k + 1]) / std::sqrt(z.dz[k] * z.dz[k + 1]);
+  const double dx = c.Lx / c.nx, dy = c.Ly / c.ny;
+  const double pi = 3.14159265358979323846;
+  const double dxy = 2.0 / (dx * dx) + 2.0 / (dy * dy);
+  const double lam1 = std::min(4.0 / (dx * dx) * std::pow(std::sin(pi / c.nx), 2),
+                               4.0 / (dy * dy) * std::pow(std::sin(pi / c.ny), 2));
+  const double lmax = 4.0 / (dx * dx) * std::pow(std::sin(pi * (c.nx / 2) / c.nx), 2) +
+                      4.0 / (dy * dy) * std::pow(std::sin(pi * (c.ny / 2) / c.ny), 2);
+  const double tau1 = nz > 1 ? tri_eig(t, 1) : 1e300, tmax = tri_eig(t, nz - 1);
+  *mn = std::min(lam1 / dxy, nz > 1 ? tau1 / (tau1 + dxy) : 1e300);
+  *mx = std::max(lmax / dxy, (tmax + lmax) / (tmax + dxy));
+}
+
+void solve_bounds(const stp_config& c, double* mn, double* mx) {
+  if (c.zline)
+    line_bounds(c, mn, mx);
+  else
+    jacobi_bounds(c, mn, mx);
+}
+
 double cycle_factor(double mn, double mx, int M) {
   const double x0 = (mx + mn) / (mx - mn);
   return 1.0 / std::cosh(M * std::acosh(x0));
@@ -306,6 +341,7 @@ int validate(const stp_config* c, std::string* why) {
   if (c->srj_m < 0 || c->srj_m > 4096) return *why = "srj_m out of range", STP_EINVAL;
   if (c->srj_omega && c->srj_m <= 0) return *why = "srj_omega given without srj_m", STP_EINVAL;
   if (c->srj_m % 2) return *why = "the SRJ cycle length must be even", STP_EINVAL;
+  if (c->zline != 0 && c->zline != 1) return *why = "zline must be 0 or 1", STP_EINVAL;
   if (!c->srj_omega && c->srj_m > 0 && !pow2(c->srj_m)) return *why = "library schedules need srj_m a power of two", STP_EINVAL;
   if (c->les && !(c->cs >= 0 && c->vd_a > 0 && c->re_tau > 0)) return *why = "bad LES constants", STP_EINVAL;
   return STP_OK;
@@ -337,6 +373,9 @@ Geom<T> geom_from(const stp_handle* h, T* pack) {
   g.S = pack + 8 * L;
   g.lm2 = pack + 9 * L;
   g.dzv = pack + 10 * L;
+  g.li = pack + 11 * L;
+  g.lu = pack + 12 * L;
+  g.ll = pack + 13 * L;
   return g;
 }
 
@@ -364,6 +403,20 @@ std::vector<double> metric_pack(const stp_config& c) {
     const double lm = c.cs * delta * phi;
     m[9 * L + k] = lm * lm;
     m[10 * L + k] = z.dz[k];
+  }
+  // z-line Thomas pivots of A = -L_z + dxy I: diagonal dxy + cup + cdn,
+  // off-diagonals -cup (k+1) and -cdn (k-1); m_k = D_k - cdn_k cup_{k-1}/m_{k-1}
+  {
+    const double dxy = 2.0 / (dx * dx) + 2.0 / (dy * dy);
+    double mprev = 1.0;
+    for (int k = 0; k < nz; k++) {
+      double mk = dxy + cup[k] + cdn[k];
+      if (k > 0) mk -= cdn[k] * cup[k - 1] / mprev;
+      m[11 * L + k] = 1.0 / mk;
+      m[12 * L + k] = cup[k] / mk;
+      m[13 * L + k] = cdn[k] / mk;
+      mprev = mk;
+    }
   }
   for (int k = 0; k <= nz; k++) {
     m[1 * L + k] = (k >= 1 && k < nz) ? 1.0 / z.hz[k] : 0.0;
@@ -436,7 +489,7 @@ int end_capture(stp_handle* h, cudaGraph_t g) {
 
 // FP32 cycles run as pair launches (two sweeps each) with the tuned variant
 bool uses_pairs(const stp_handle* h) {
-  return h->prec == STP_FP32_REFINE && h->cycle_blocks == 0 && sweep_variant_is_pair(h->sweep_variant) &&
+  return h->prec == STP_FP32_REFINE && h->cycle_blocks == 0 && !h->cfg.zline && sweep_variant_is_pair(h->sweep_variant) &&
          h->omega.size() % 4 == 0;
 }
 
@@ -459,6 +512,11 @@ int build_cycle(stp_handle* h, const Geom<T>& g, cudaGraph_t wb, cudaGraphCondit
     // the whole cycle in one persistent kernel
     CUDA_TRY(h, launch_cycle_f32(h->g32, (float*)A, (float*)B, (const float*)rhs, h->d_omega32, M, h->bar, h->ctl,
                                  h->cycle_blocks, h->cap));
+    return end_capture(h, ib);
+  }
+  if (h->cfg.zline) {
+    for (int m = 0; m < M; m++)
+      CUDA_TRY(h, launch_line_sweep<T>(g, (m % 2 == 0) ? A : B, rhs, (T)h->omega[m], (m % 2 == 0) ? B : A, h->cap));
     return end_capture(h, ib);
   }
   if (sizeof(T) == sizeof(float) && uses_pairs(h)) {
@@ -539,7 +597,7 @@ int pick_variant(const std::vector<std::pair<int, float>>& timed, float* us) {
 int tune_sweep(stp_handle* h) {
   if (h->sweep_variant >= 0) return STP_OK;
   h->sweep_variant = 0;
-  if (h->prec != STP_FP32_REFINE || h->nx % 4) return STP_OK;
+  if (h->prec != STP_FP32_REFINE || h->nx % 4 || h->cfg.zline) return STP_OK;
   if (const char* env = std::getenv("STP_SWEEP_VARIANT")) {
     const int v = std::atoi(env);
     if (sweep_variant_ok(v, h->nx, h->ny, h->nz)) h->sweep_variant = v;
@@ -706,6 +764,12 @@ int host_cycles(stp_handle* h, const Geom<T>& g, T* A, T* B, const T* rhs, int m
     if (sizeof(T) == sizeof(float) && h->cycle_blocks > 0) {
       CUDA_TRY(h, launch_cycle_f32(h->g32, (float*)A, (float*)B, (const float*)rhs, h->d_omega32, M, h->bar, h->ctl,
                                    h->cycle_blocks, h->st));
+      continue;
+    }
+    if (h->cfg.zline) {
+      for (int m = 0; m < M; m++)
+        CUDA_TRY(h, launch_line_sweep<T>(g, (m % 2 == 0) ? A : B, rhs, (T)h->omega[m], (m % 2 == 0) ? B : A,
+                                         h->st));
       continue;
     }
     if (sizeof(T) == sizeof(float) && uses_pairs(h)) {
@@ -978,7 +1042,7 @@ int stp_srj_schedule(const stp_config* cfg, int M, double* omega, int* M_out, do
   if (int rc = validate(cfg, &why)) return fail(nullptr, rc, why);
   if (M != 0 && (!pow2(M) || M > 1024)) return fail(nullptr, STP_EINVAL, "M must be 0 or a power of two <= 1024");
   double mn, mx;
-  jacobi_bounds(*cfg, &mn, &mx);
+  solve_bounds(*cfg, &mn, &mx);
   if (M == 0) M = auto_cycle(mn, mx);
   const std::vector<double> om = chebyshev(mn, mx, M);
   if (omega) std::copy(om.begin(), om.end(), omega);
@@ -1028,7 +1092,7 @@ int stp_init(const stp_config* cfg, stp_handle** out) {
     h->omega.assign(cfg->srj_omega, cfg->srj_omega + cfg->srj_m);
   } else {
     double mn, mx;
-    jacobi_bounds(*cfg, &mn, &mx);
+    solve_bounds(*cfg, &mn, &mx);
     const int M = cfg->srj_m > 0 ? cfg->srj_m : auto_cycle(mn, mx);
     h->omega = chebyshev(mn, mx, M);
   }
@@ -1091,7 +1155,8 @@ int stp_init(const stp_config* cfg, stp_handle** out) {
     // more than a graph-launched kernel boundary
     const char* env = std::getenv("STP_PERSISTENT");
     const bool allow = env && env[0] == '1';
-    if (allow && h->prec == STP_FP32_REFINE && h->nx % 4 == 0) h->cycle_blocks = cycle_grid_f32(h->dev);
+    if (allow && h->prec == STP_FP32_REFINE && h->nx % 4 == 0 && !cfg->zline)
+      h->cycle_blocks = cycle_grid_f32(h->dev);
   }
   if (cudaMallocHost((void**)&h->h_sc, sizeof(double) * SC_COUNT) != cudaSuccess ||
       cudaMallocHost((void**)&h->h_flag, sizeof(int) * FL_COUNT) != cudaSuccess ||
@@ -1499,7 +1564,7 @@ void plan_groups(stp_batch* b) {
   std::map<int, std::vector<int>> byM;
   for (size_t i = 0; i < b->hs.size(); i++) {
     stp_handle* h = b->hs[i];
-    if (h->prec != STP_FP32_REFINE || h->nx % 4 || h->net || h->cycle_blocks > 0) continue;
+    if (h->prec != STP_FP32_REFINE || h->nx % 4 || h->net || h->cycle_blocks > 0 || h->cfg.zline) continue;
     if (max_ch >= 0 && (long long)h->nc > max_ch) continue;
     byM[(int)h->omega.size()].push_back((int)i);
   }

@@ -327,6 +327,119 @@ __global__ void __launch_bounds__(1024, 1) k_cycle_f32(Geom<float> g, float* A, 
   }
 }
 
+// z-line Jacobi-SOR sweep (line relaxation of Sec. 3.4's SRJ): for every
+// column (i, j), r = b - L p (difference form, arithmetic in T), the column
+// system A delta = r with A = -L_z + (2/dx^2 + 2/dy^2) I by the Thomas
+// algorithm (pivots precomputed per level: li = 1/m_k, lu = cup_k/m_k), and
+// p' = p - omega delta; since A (p^L - p) = -(b - L p), this is
+// p + omega (p^L - p) for the line value p^L.  One thread per column,
+// consecutive threads along x (coalesced rows); the forward elimination
+// stores its values in out, the back substitution overwrites them with p'.
+template <typename T>
+__global__ void __launch_bounds__(128) k_line_sweep(Geom<T> g, const T* __restrict__ p, const T* __restrict__ b,
+                                                    T omega, T* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+  const int nx = g.nx, ny = g.ny, nz = g.nz;
+  cudaGridDependencySynchronize();
+  if (i >= nx) return;
+  const unsigned plane = (unsigned)nx * ny;
+  const unsigned c0 = (unsigned)j * nx + i;
+  const unsigned xp = (unsigned)j * nx + (i == nx - 1 ? 0 : i + 1), xm = (unsigned)j * nx + (i == 0 ? nx - 1 : i - 1);
+  const unsigned yp = (unsigned)(j == ny - 1 ? 0 : j + 1) * nx + i, ym = (unsigned)(j == 0 ? ny - 1 : j - 1) * nx + i;
+  const T idx2 = g.idx2, idy2 = g.idy2;
+  T pm = T(0), pc = __ldg(p + c0), dprev = T(0);
+#pragma unroll 4
+  for (int k = 0; k < nz; k++) {
+    const unsigned lev = (unsigned)k * plane;
+    const T pu = k < nz - 1 ? __ldg(p + lev + plane + c0) : pc;
+    T lap = idx2 * ((__ldg(p + lev + xp) - pc) + (__ldg(p + lev + xm) - pc)) +
+            idy2 * ((__ldg(p + lev + yp) - pc) + (__ldg(p + lev + ym) - pc));
+    if (k < nz - 1) lap += __ldg(g.cup + k) * (pu - pc);
+    if (k > 0) lap += __ldg(g.cdn + k) * (pm - pc);
+    const T r = __ldg(b + lev + c0) - lap;
+    const T d = (r + __ldg(g.cdn + k) * dprev) * __ldg(g.li + k);
+    out[lev + c0] = d;
+    dprev = d;
+    pm = pc;
+    pc = pu;
+  }
+  T dnext = T(0);
+#pragma unroll 4
+  for (int k = nz - 1; k >= 0; k--) {
+    const unsigned q = (unsigned)k * plane + c0;
+    const T delta = out[q] + __ldg(g.lu + k) * dnext;
+    out[q] = __ldg(p + q) - omega * delta;
+    dnext = delta;
+  }
+}
+
+// The same sweep with the column work staged in shared memory.  A block
+// owns C = 32 rb columns (32 consecutive x cells of rb rows) over all z
+// levels, and 512 threads.  Phase 1: every thread computes r = b - L p for
+// its column on one chunk of the levels (C columns x 512/C chunks, all
+// independent) into R[k][column].  Phase 2: C threads run the Thomas
+// elimination and back substitution of their columns in shared memory.
+// Phase 3: every thread writes p - omega delta for its column and chunk.
+// Same arithmetic per cell as k_line_sweep.
+template <typename T>
+__global__ void __launch_bounds__(512) k_line_sweep_smem(Geom<T> g, const T* __restrict__ p,
+                                                         const T* __restrict__ b, T omega, T* __restrict__ out,
+                                                         int rb) {
+  extern __shared__ __align__(16) unsigned char line_sm[];
+  T* R = reinterpret_cast<T*>(line_sm);  // [nz][C]
+  const int C = 32 * rb, nchunk = blockDim.x / C;
+  const int nx = g.nx, ny = g.ny, nz = g.nz;
+  const int nxb = (nx + 31) / 32;
+  const int i0 = (blockIdx.x % nxb) * 32, j0 = (blockIdx.x / nxb) * rb;
+  const int col = threadIdx.x % C, chunk = threadIdx.x / C;
+  const int i = i0 + (col & 31), j = j0 + (col >> 5);
+  const bool act = i < nx && j < ny;
+  const int ic = i < nx ? i : nx - 1, jc = j < ny ? j : ny - 1;  // in-bounds stand-ins for inactive columns
+  const unsigned plane = (unsigned)nx * ny;
+  const unsigned c0 = (unsigned)jc * nx + ic;
+  const unsigned xp = (unsigned)jc * nx + (ic == nx - 1 ? 0 : ic + 1), xm = (unsigned)jc * nx + (ic == 0 ? nx - 1 : ic - 1);
+  const unsigned yp = (unsigned)(jc == ny - 1 ? 0 : jc + 1) * nx + ic, ym = (unsigned)(jc == 0 ? ny - 1 : jc - 1) * nx + ic;
+  const int k0 = chunk * nz / nchunk, k1 = (chunk + 1) * nz / nchunk;
+  const T idx2 = g.idx2, idy2 = g.idy2;
+  cudaGridDependencySynchronize();
+#pragma unroll 4
+  for (int k = k0; k < k1; k++) {
+    const unsigned lev = (unsigned)k * plane;
+    const T pc = __ldg(p + lev + c0);
+    T lap = idx2 * ((__ldg(p + lev + xp) - pc) + (__ldg(p + lev + xm) - pc)) +
+            idy2 * ((__ldg(p + lev + yp) - pc) + (__ldg(p + lev + ym) - pc));
+    if (k < nz - 1) lap += __ldg(g.cup + k) * (__ldg(p + lev + plane + c0) - pc);
+    if (k > 0) lap += __ldg(g.cdn + k) * (__ldg(p + lev - plane + c0) - pc);
+    R[k * C + col] = (__ldg(b + lev + c0) - lap) * __ldg(g.li + k);  // r_k / m_k
+  }
+  __syncthreads();
+  if (chunk == 0) {
+    // forward elimination, one multiply-add a level: d_k = r_k/m_k + (cdn_k/m_k) d_{k-1}
+    T dprev = T(0);
+#pragma unroll 8
+    for (int k = 0; k < nz; k++) {
+      const T d = R[k * C + col] + __ldg(g.ll + k) * dprev;
+      R[k * C + col] = d;
+      dprev = d;
+    }
+    T dnext = T(0);
+#pragma unroll 8
+    for (int k = nz - 1; k >= 0; k--) {
+      const T delta = R[k * C + col] + __ldg(g.lu + k) * dnext;
+      R[k * C + col] = delta;
+      dnext = delta;
+    }
+  }
+  __syncthreads();
+  if (act) {
+#pragma unroll 4
+    for (int k = k0; k < k1; k++) {
+      const unsigned q = (unsigned)k * plane + c0;
+      out[q] = __ldg(p + q) - omega * R[k * C + col];
+    }
+  }
+}
+
 // arms the inner loop of a refinement pass and clears its correction
 __global__ void k_pass_begin(float* __restrict__ d, size_t n, int graph, cudaGraphConditionalHandle h_loop) {
   for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x)
@@ -585,6 +698,56 @@ cudaError_t launch_sweep<double>(const Geom<double>& g, const double* p, const d
   k_sweep_f64<<<l.grid, l.block, 0, s>>>(g, p, b, omega, out);
   return cudaGetLastError();
 }
+
+// rows per block of the shared-memory line sweep: 4, 2 or 1 (so that the
+// 32 rb columns divide the 512 threads), the most whose columns x nz values
+// fit in 96 KB (two blocks an SM); 0 when one row does not fit
+static int line_rows(int nz, size_t es) {
+  const size_t per_row = 32 * (size_t)nz * es;
+  for (int rb = 4; rb >= 1; rb /= 2)
+    if (rb * per_row <= 96 * 1024) return rb;
+  return 0;
+}
+
+template <typename T>
+cudaError_t launch_line_sweep(const Geom<T>& g, const T* p, const T* b, T omega, T* out, cudaStream_t s) {
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  const int rb = line_rows(g.nz, sizeof(T));
+  if (rb >= 1) {
+    const size_t smem = (size_t)32 * rb * g.nz * sizeof(T);
+    static bool attr_set = false;
+    if (!attr_set) {
+      cudaError_t e = cudaFuncSetAttribute(k_line_sweep_smem<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           96 * 1024);
+      if (e != cudaSuccess) return e;
+      attr_set = true;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(((g.nx + 31) / 32) * ((g.ny + rb - 1) / rb)));
+    cfg.blockDim = dim3(512);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k_line_sweep_smem<T>, g, p, b, omega, out, rb);
+    return e != cudaSuccess ? e : cudaGetLastError();
+  }
+  const dim3 grid((g.nx + 127) / 128, g.ny), block(128);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, k_line_sweep<T>, g, p, b, omega, out);
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
+template cudaError_t launch_line_sweep<float>(const Geom<float>&, const float*, const float*, float, float*,
+                                              cudaStream_t);
+template cudaError_t launch_line_sweep<double>(const Geom<double>&, const double*, const double*, double, double*,
+                                               cudaStream_t);
 
 int cycle_grid_f32(int device) {
   int per_sm = 0, sms = 0;

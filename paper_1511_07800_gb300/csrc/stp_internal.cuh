@@ -38,10 +38,13 @@ struct Geom {
   const T* S;      // [nz]    2/dx^2 + 2/dy^2 + cup + cdn
   const T* lm2;    // [nz]    (Cs Delta phi_w)^2 per level (LES)
   const T* dzv;    // [nz]    dz
+  const T* li;     // [nz]    z-line Thomas: 1/m_k, m_k the k-th pivot of A = -L_z + (2/dx^2 + 2/dy^2) I
+  const T* lu;     // [nz]    z-line Thomas: cup_k/m_k
+  const T* ll;     // [nz]    z-line Thomas: cdn_k/m_k
 };
 
 // Number of metric arrays packed into one device allocation per precision.
-constexpr int kMetricArrays = 13;
+constexpr int kMetricArrays = 14;
 
 // Reduction workspace (device).  Every reducing kernel writes one partial per
 // block, then the last block to finish sums the partials in block order, so
@@ -143,6 +146,11 @@ cudaError_t launch_explicit_only(const Geom<T>& g, bool les, const T* u, const T
 template <typename T>
 cudaError_t launch_diffusion_only(const Geom<T>& g, bool les, const T* u, const T* v, const T* w, const T* nu,
                                   T nu0, T* Du, T* Dv, T* Dw, cudaStream_t s);
+
+// One z-line Jacobi-SOR sweep: out = p - omega A^-1 (b - L p), A the z
+// column operator -L_z + (2/dx^2 + 2/dy^2) I (Thomas with the pivots li, lu).
+template <typename T>
+cudaError_t launch_line_sweep(const Geom<T>& g, const T* p, const T* b, T omega, T* out, cudaStream_t s);
 
 // One Jacobi-SOR sweep of L p = b with factor omega: out = p - omega (b - Lp)/S.
 template <typename T>

@@ -48,7 +48,7 @@ class Config(ctypes.Structure):
         ("cn_sweeps", ctypes.c_int), ("srj_m", ctypes.c_int),
         ("srj_omega", ctypes.POINTER(ctypes.c_double)),
         ("inner_tol", ctypes.c_double), ("cfl_check", ctypes.c_int),
-        ("device", ctypes.c_int), ("stream", ctypes.c_void_p),
+        ("device", ctypes.c_int), ("stream", ctypes.c_void_p), ("zline", ctypes.c_int),
     ]
 
 
@@ -152,7 +152,7 @@ def make_config(cfg, precision="fp64", device=0, stream=None, omega=None):
     c = Config()
     lib().stp_config_defaults(ctypes.byref(c))
     for k in ("nx", "ny", "nz", "Lx", "Ly", "Lz", "nu", "dt", "forcing", "fx", "ubulk", "les", "cs", "vd_a",
-              "re_tau", "stretch", "ptol", "pmaxit", "cn_sweeps", "srj_m", "inner_tol", "cfl_check"):
+              "re_tau", "stretch", "ptol", "pmaxit", "cn_sweeps", "srj_m", "inner_tol", "cfl_check", "zline"):
         if k in cfg and cfg[k] is not None:
             setattr(c, k, type(getattr(c, k))(cfg[k]))
     c.precision = STP_FP64 if precision in ("fp64", 0) else STP_FP32_REFINE

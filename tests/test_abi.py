@@ -61,3 +61,22 @@ def test_schedule_matches_oracle(stp_lib, orc, name, stretch):
     assert abs(mn - mn2) < 1e-9 * mn2 and abs(mx - mx2) < 1e-12
     assert len(om) == len(om2)
     assert np.allclose(om, om2, rtol=1e-8)
+
+
+@pytest.mark.parametrize("name,stretch", [("os_instability", 0.0), ("les_channel", 2.0)])
+def test_line_schedule_matches_oracle(stp_lib, orc, name, stretch):
+    """z-line SRJ: the library's bounds (closed-form extremes of
+    (tau + lam)/(tau + dxy), Sturm bisection for tau) equal the oracle's
+    enumeration of every eigenvalue pair, and the schedules agree."""
+    from oracle import srj
+    cfg = dict(inputs.preset(name), zline=1)
+    om, mn, mx = stp_lib.srj_schedule(cfg)
+    om2, mn2, mx2 = srj.schedule_for(cfg["nx"], cfg["ny"], cfg["nz"], cfg["Lx"], cfg["Ly"], cfg["Lz"], stretch,
+                                     line=True)
+    assert abs(mn - mn2) < 1e-9 * mn2 and abs(mx - mx2) < 1e-12
+    assert len(om) == len(om2)
+    assert np.allclose(om, om2, rtol=1e-8)
+    # on the wall-stretched grid the line spectrum is far better conditioned
+    if stretch > 0:
+        _, pmn, pmx = stp_lib.srj_schedule(inputs.preset(name))
+        assert (mx / mn) * 10 < pmx / pmn

@@ -1,0 +1,114 @@
+"""z-line relaxation of the pressure solve on the GPU: each z column solved
+exactly per sweep (Thomas), SRJ weights from the line-Jacobi spectrum.
+Parity with the oracle's line sweep (a plain Thomas solve per column)."""
+import numpy as np
+import pytest
+
+from paper_1511_07800_gb300 import inputs
+
+from .conftest import rel_err
+from .test_gpu_parity import case, turbulent_like
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+
+
+def line_schedule(cfg, M):
+    from oracle import srj
+    om, _, _ = srj.schedule_for(cfg["nx"], cfg["ny"], cfg["nz"], cfg["Lx"], cfg["Ly"], cfg["Lz"],
+                                cfg.get("stretch", 0.0), M, line=True)
+    return om
+
+
+def mean_free_rhs(cfg, seed):
+    rng = np.random.default_rng(seed)
+    b = rng.standard_normal((cfg["nz"], cfg["ny"], cfg["nx"]))
+    dz = np.diff(inputs.zfaces(cfg))[:, None, None]
+    return b - np.sum(b * dz) / np.sum(dz * np.ones_like(b)), rng
+
+
+@pytest.mark.parametrize("stretch,nx,ny,nz", [(0.0, 48, 20, 18), (2.0, 48, 20, 18), (2.0, 37, 21, 18),
+                                              (2.0, 8, 5, 400)])
+def test_line_fixed_sweeps_parity(stp_lib, orc, stretch, nx, ny, nz):
+    """The same line schedule applied for the same number of sweeps gives
+    the same pressure as the oracle's column-by-column Thomas solves (FP64;
+    ragged rows and row blocks; 400 levels take the kernel that keeps the
+    columns in global memory)."""
+    cfg = case(nx=nx, ny=ny, nz=nz, stretch=stretch, zline=1)
+    om = line_schedule(cfg, 32)
+    cfg["omega"] = om
+    b, rng = mean_free_rhs(cfg, 5)
+    p0 = rng.standard_normal(b.shape) * 0.1
+    o = orc.Oracle(cfg)
+    p_o, it_o, rel_o, conv_o = o.poisson(b, p0, tol=0.0, maxit=3 * 32)
+    with stp_lib.Channel(cfg, omega=om) as ch:
+        p_g = p0.copy()
+        st = ch.poisson_solve(b, p_g, tol=0.0, maxit=3 * 32)
+    assert st["sweeps"] == it_o == 96 and not st["converged"] and not conv_o
+    assert rel_err(p_g, p_o) < TOL64
+    # residuals near 1e-12 of ||b|| are FP64 rounding of L p: an absolute floor
+    assert abs(st["rel_res"] - rel_o) < 1e-9 * rel_o + 1e-11
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_line_solve_converges_to_tolerance(stp_lib, orc, precision):
+    """Tolerance-driven line solves stop at ||b - Lp|| <= 1e-8 ||b||,
+    checked with the oracle's operator, and take fewer sweeps than point
+    sweeps on the wall-stretched grid."""
+    cfg = case(nx=64, ny=24, nz=32, stretch=2.0)
+    b, _ = mean_free_rhs(cfg, 7)
+    o = orc.Oracle(cfg)
+    sweeps = {}
+    for zl in (1, 0):
+        with stp_lib.Channel(dict(cfg, zline=zl), precision=precision) as ch:
+            p = np.zeros_like(b)
+            st = ch.poisson_solve(b, p, tol=1e-8)
+        r = b - o.laplacian(p)
+        rel = np.sqrt(np.sum(r * r) / np.sum(b * b))
+        assert st["converged"] and rel <= 1e-8 * 1.0001, (zl, rel)
+        sweeps[zl] = st["sweeps"]
+    assert sweeps[1] < sweeps[0], sweeps
+
+
+@pytest.mark.parametrize("stretch,les,forcing", [(0.0, 0, 0), (2.0, 1, 1)])
+def test_line_step_parity_fp64(stp_lib, orc, stretch, les, forcing):
+    """Whole projection steps with line relaxation and the solves forced to
+    two cycles: every field agrees with the oracle to 1e-10."""
+    cfg = case(stretch=stretch, les=les, forcing=forcing, ptol=0.0, pmaxit=2 * 16, nu=1 / 500.0, zline=1)
+    om = line_schedule(cfg, 16)
+    o = orc.Oracle(dict(cfg, omega=om))
+    f0 = turbulent_like(cfg, 3)
+    o.set_fields(*f0)
+    so = o.step(5)
+    fo = o.get_fields()
+    with stp_lib.Channel(cfg, omega=om) as ch:
+        ch.set_fields(*f0)
+        sg = ch.step(5)
+        fg = ch.get_fields()
+    assert sg["sweeps"] == so["sweeps"] == 32
+    for k in ("u", "v", "w", "p", "nu"):
+        e = rel_err(fg[k], fo[k]) if k != "p" else rel_err(fg[k] - fg[k].mean(), fo[k] - fo[k].mean())
+        assert e < TOL64, (k, e)
+
+
+def test_line_step_fp32_vs_fp64_oracle(stp_lib, orc):
+    """FP32 line sweeps inside the FP64 refinement: per-field error against
+    the FP64 oracle (converged 1e-8 solves) within the bounds stated for the
+    FP32 point-sweep path."""
+    cfg = case(stretch=2.0, les=1, nu=1 / 500.0, cn_sweeps=6, zline=1)
+    om = line_schedule(cfg, 32)
+    o = orc.Oracle(dict(cfg, omega=om))
+    f0 = turbulent_like(cfg, 6)
+    o.set_fields(*f0)
+    o.step(5)
+    fo = o.get_fields()
+    with stp_lib.Channel(cfg, precision="fp32", omega=om) as ch:
+        ch.set_fields(*f0)
+        sg = ch.step(5)
+        fg = ch.get_fields()
+    assert sg["converged"] and sg["rel_res"] <= 1e-8
+    bounds = dict(u=2e-6, v=2e-6, w=2e-6, p=1e-3, nu=2e-6)
+    for k, bd in bounds.items():
+        e = rel_err(fg[k], fo[k]) if k != "p" else rel_err(fg[k] - fg[k].mean(), fo[k] - fo[k].mean())
+        assert e < bd, (k, e)
