@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--grid", default=None, help="override the cell counts, NXxNYxNZ (profiling runs)")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-guess comparison")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched uneven-channel measurement")
+    ap.add_argument("--no-les", action="store_true", help="skip the LES-grid point vs z-line solve measurement")
     return ap.parse_args()
 
 
@@ -265,6 +266,34 @@ def batched_channels(steps, warmup, peak):
     return out
 
 
+def les_line_vs_point(steps, warmup):
+    """Pressure-solve time on the wall-stretched LES grid (256 x 128 x 192,
+    tanh stretching 2, Smagorinsky, constant flux; FP32 with FP64
+    refinement), point SRJ sweeps against z-line sweeps, from the same
+    seeded initial fields.  GPU time of the solves by CUDA events inside the
+    library; steps timed after warm-up steps."""
+    from paper_1511_07800_gb300 import inputs, stp
+    cfg = inputs.preset("les_channel")
+    f0 = inputs.initial_fields("les_channel", cfg, seed=1)
+    cells = cfg["nx"] * cfg["ny"] * cfg["nz"]
+    out = {"workload": "les_channel 256x128x192, tanh 2, Cs 0.1, constant flux, FP32 + FP64 refinement, "
+                       "ptol 1e-8", "steps": steps, "warmup": warmup}
+    for name, zl in (("point", 0), ("zline", 1)):
+        c = dict(cfg, zline=zl)
+        with stp.Channel(c, precision="fp32") as ch:
+            ch.set_fields(*f0)
+            ch.step(warmup)
+            st = ch.step(steps)
+            sweeps = st["solve_sweeps"]
+            out[name] = {"M": len(stp.srj_schedule(c)[0]), "sweeps_per_step": sweeps / steps,
+                         "solve_ms_per_step": st["solve_ms"] / steps,
+                         "us_per_sweep": 1e3 * st["solve_ms"] / max(1, sweeps),
+                         "Mcell_steps_per_s_solve": cells * steps / (st["solve_ms"] / 1e3) / 1e6,
+                         "converged": st["converged"]}
+    out["solve_speedup_zline"] = out["point"]["solve_ms_per_step"] / out["zline"]["solve_ms_per_step"]
+    return out
+
+
 def run_reference(args):
     """The oracle (plain FP64 C, OpenMP over z) time-stepping the workload with
     its own tolerance-driven pressure solves, on rank 0's host cores."""
@@ -438,6 +467,11 @@ def run_ours(args):
             line["batched_channels"] = batched_channels(max(3, min(args.steps, 10)), args.warmup, peak)
         except Exception as ex:  # report, never fake
             line["batched_channels"] = {"error": str(ex)[:200]}
+    if rank == 0 and world == 1 and not args.no_les and args.grid is None:
+        try:
+            line["les_pressure_solve"] = les_line_vs_point(3, 3)
+        except Exception as ex:  # report, never fake
+            line["les_pressure_solve"] = {"error": str(ex)[:200]}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
             line["cpu_baseline"] = cpu_baseline_sample(cfg, fields, sweeps / args.steps)

@@ -440,6 +440,116 @@ __global__ void __launch_bounds__(512) k_line_sweep_smem(Geom<T> g, const T* __r
   }
 }
 
+// The shared-memory line sweep with phases 1 and 3 on vector units (float4
+// in FP32, double2 in FP64) of VW consecutive x cells: a thread handles one
+// unit of one row over a chunk of levels, with vector loads of the centre,
+// y and z neighbours and b, and scalar loads of the two x neighbours just
+// outside the unit.  For nx a multiple of 32 (whole 32-cell blocks of rows,
+// aligned vectors).  Phase 2 and the arithmetic per cell are those of
+// k_line_sweep_smem.
+template <typename T>
+struct VecOf;
+template <>
+struct VecOf<float> {
+  using V = float4;
+  static constexpr int W = 4;
+  __device__ static float get(const float4& v, int e) { return e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w; }
+  __device__ static void set(float4& v, int e, float x) {
+    if (e == 0) v.x = x; else if (e == 1) v.y = x; else if (e == 2) v.z = x; else v.w = x;
+  }
+};
+template <>
+struct VecOf<double> {
+  using V = double2;
+  static constexpr int W = 2;
+  __device__ static double get(const double2& v, int e) { return e == 0 ? v.x : v.y; }
+  __device__ static void set(double2& v, int e, double x) {
+    if (e == 0) v.x = x; else v.y = x;
+  }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(512) k_line_sweep_vec(Geom<T> g, const T* __restrict__ p, const T* __restrict__ b,
+                                                        T omega, T* __restrict__ out, int rb) {
+  using VT = VecOf<T>;
+  using V = typename VT::V;
+  constexpr int W = VT::W, UPR = 32 / W;  // vector units per 32-cell row segment
+  extern __shared__ __align__(16) unsigned char line_sm[];
+  T* R = reinterpret_cast<T*>(line_sm);  // [nz][C]
+  const int C = 32 * rb, U = UPR * rb, nchunk = blockDim.x / U;
+  const int nx = g.nx, ny = g.ny, nz = g.nz;
+  const int nxb = nx / 32;
+  const int i0 = (blockIdx.x % nxb) * 32, j0 = (blockIdx.x / nxb) * rb;
+  const int unit = threadIdx.x % U, chunk = threadIdx.x / U;
+  const int jr = unit / UPR, xu = unit % UPR;
+  const int i = i0 + W * xu, j = j0 + jr;
+  const bool act = j < ny;
+  const int jc = act ? j : ny - 1;
+  const unsigned plane = (unsigned)nx * ny;
+  const unsigned c0 = (unsigned)jc * nx + i;  // first cell of the unit
+  const unsigned yp = (unsigned)(jc == ny - 1 ? 0 : jc + 1) * nx + i, ym = (unsigned)(jc == 0 ? ny - 1 : jc - 1) * nx + i;
+  const unsigned xl = (unsigned)jc * nx + (i == 0 ? nx - 1 : i - 1), xr = (unsigned)jc * nx + (i + W == nx ? 0 : i + W);
+  const int k0 = chunk * nz / nchunk, k1 = (chunk + 1) * nz / nchunk;
+  const int col = jr * 32 + W * xu;
+  const T idx2 = g.idx2, idy2 = g.idy2;
+  cudaGridDependencySynchronize();
+#pragma unroll 2
+  for (int k = k0; k < k1; k++) {
+    const unsigned lev = (unsigned)k * plane;
+    const V c = __ldg(reinterpret_cast<const V*>(p + lev + c0));
+    const V yn = __ldg(reinterpret_cast<const V*>(p + lev + yp));
+    const V ys = __ldg(reinterpret_cast<const V*>(p + lev + ym));
+    const V zu = k < nz - 1 ? __ldg(reinterpret_cast<const V*>(p + lev + plane + c0)) : c;
+    const V zd = k > 0 ? __ldg(reinterpret_cast<const V*>(p + lev - plane + c0)) : c;
+    const V bq = __ldg(reinterpret_cast<const V*>(b + lev + c0));
+    const T left = __ldg(p + lev + xl), right = __ldg(p + lev + xr);
+    const T cup = __ldg(g.cup + k), cdn = __ldg(g.cdn + k), li = __ldg(g.li + k);
+    V o;
+#pragma unroll
+    for (int e = 0; e < W; e++) {
+      const T pc = VT::get(c, e);
+      const T xrv = e == W - 1 ? right : VT::get(c, e + 1);
+      const T xlv = e == 0 ? left : VT::get(c, e - 1);
+      T lap = idx2 * ((xrv - pc) + (xlv - pc)) + idy2 * ((VT::get(yn, e) - pc) + (VT::get(ys, e) - pc));
+      if (k < nz - 1) lap += cup * (VT::get(zu, e) - pc);
+      if (k > 0) lap += cdn * (VT::get(zd, e) - pc);
+      VT::set(o, e, (VT::get(bq, e) - lap) * li);
+    }
+    *reinterpret_cast<V*>(R + k * C + col) = o;
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < C) {
+    const int cl = threadIdx.x;
+    T dprev = T(0);
+#pragma unroll 8
+    for (int k = 0; k < nz; k++) {
+      const T d = R[k * C + cl] + __ldg(g.ll + k) * dprev;
+      R[k * C + cl] = d;
+      dprev = d;
+    }
+    T dnext = T(0);
+#pragma unroll 8
+    for (int k = nz - 1; k >= 0; k--) {
+      const T delta = R[k * C + cl] + __ldg(g.lu + k) * dnext;
+      R[k * C + cl] = delta;
+      dnext = delta;
+    }
+  }
+  __syncthreads();
+  if (act) {
+#pragma unroll 2
+    for (int k = k0; k < k1; k++) {
+      const unsigned q = (unsigned)k * plane + c0;
+      const V pv = __ldg(reinterpret_cast<const V*>(p + q));
+      const V dv = *reinterpret_cast<const V*>(R + k * C + col);
+      V o;
+#pragma unroll
+      for (int e = 0; e < W; e++) VT::set(o, e, VT::get(pv, e) - omega * VT::get(dv, e));
+      *reinterpret_cast<V*>(out + q) = o;
+    }
+  }
+}
+
 // arms the inner loop of a refinement pass and clears its correction
 __global__ void k_pass_begin(float* __restrict__ d, size_t n, int graph, cudaGraphConditionalHandle h_loop) {
   for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x)
@@ -721,6 +831,8 @@ cudaError_t launch_line_sweep(const Geom<T>& g, const T* p, const T* b, T omega,
     if (!attr_set) {
       cudaError_t e = cudaFuncSetAttribute(k_line_sweep_smem<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            96 * 1024);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_line_sweep_vec<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
       if (e != cudaSuccess) return e;
       attr_set = true;
     }
@@ -731,7 +843,8 @@ cudaError_t launch_line_sweep(const Geom<T>& g, const T* p, const T* b, T omega,
     cfg.stream = s;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cudaError_t e = cudaLaunchKernelEx(&cfg, k_line_sweep_smem<T>, g, p, b, omega, out, rb);
+    cudaError_t e = g.nx % 32 == 0 ? cudaLaunchKernelEx(&cfg, k_line_sweep_vec<T>, g, p, b, omega, out, rb)
+                                   : cudaLaunchKernelEx(&cfg, k_line_sweep_smem<T>, g, p, b, omega, out, rb);
     return e != cudaSuccess ? e : cudaGetLastError();
   }
   const dim3 grid((g.nx + 127) / 128, g.ny), block(128);

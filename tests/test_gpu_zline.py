@@ -29,12 +29,13 @@ def mean_free_rhs(cfg, seed):
 
 
 @pytest.mark.parametrize("stretch,nx,ny,nz", [(0.0, 48, 20, 18), (2.0, 48, 20, 18), (2.0, 37, 21, 18),
-                                              (2.0, 8, 5, 400)])
+                                              (2.0, 64, 21, 18), (0.0, 96, 8, 30), (2.0, 8, 5, 400)])
 def test_line_fixed_sweeps_parity(stp_lib, orc, stretch, nx, ny, nz):
     """The same line schedule applied for the same number of sweeps gives
     the same pressure as the oracle's column-by-column Thomas solves (FP64;
-    ragged rows and row blocks; 400 levels take the kernel that keeps the
-    columns in global memory)."""
+    ragged rows and row blocks; rows of a multiple of 32 cells take the
+    vector kernel; 400 levels take the kernel that keeps the columns in
+    global memory)."""
     cfg = case(nx=nx, ny=ny, nz=nz, stretch=stretch, zline=1)
     om = line_schedule(cfg, 32)
     cfg["omega"] = om
@@ -92,11 +93,12 @@ def test_line_step_parity_fp64(stp_lib, orc, stretch, les, forcing):
         assert e < TOL64, (k, e)
 
 
-def test_line_step_fp32_vs_fp64_oracle(stp_lib, orc):
+@pytest.mark.parametrize("nx", [40, 64])
+def test_line_step_fp32_vs_fp64_oracle(stp_lib, orc, nx):
     """FP32 line sweeps inside the FP64 refinement: per-field error against
     the FP64 oracle (converged 1e-8 solves) within the bounds stated for the
-    FP32 point-sweep path."""
-    cfg = case(stretch=2.0, les=1, nu=1 / 500.0, cn_sweeps=6, zline=1)
+    FP32 point-sweep path (64: the vector kernel)."""
+    cfg = case(nx=nx, stretch=2.0, les=1, nu=1 / 500.0, cn_sweeps=6, zline=1)
     om = line_schedule(cfg, 32)
     o = orc.Oracle(dict(cfg, omega=om))
     f0 = turbulent_like(cfg, 6)
