@@ -120,14 +120,27 @@ def measured_peaks():
         return {}
 
 
-def traffic_for(kernel_src, precision):
+def sweep_source_digest(precision):
+    """sha256 of the source that defines the SRJ sweep kernel: the FP32
+    tiles (poisson_common.cuh) or the FP64 kernel's definition."""
+    csrc = os.path.join(ROOT, "paper_1511_07800_gb300", "csrc")
+    if precision == "fp32":
+        text = open(os.path.join(csrc, "poisson_common.cuh"), "rb").read()
+    else:
+        src = open(os.path.join(csrc, "kernels_poisson.cu")).read()
+        a = src.index("k_sweep_f64_v2(Geom<double> g")
+        a = src.rindex("template <bool PDL>", 0, a)
+        text = src[a:src.index("\n}\n", a) + 3].encode()
+    return hashlib.sha256(text).hexdigest()
+
+
+def traffic_for(precision):
     """Per-launch DRAM bytes of the SRJ sweep from the committed ncu summary,
-    if the kernel source is unchanged since the capture; else None."""
+    if the sweep kernel's source is unchanged since the capture; else None."""
     path = os.path.join(ROOT, "profiles", "srj_sweep_traffic.json")
     try:
         rec = json.load(open(path))
-        src = open(kernel_src, "rb").read()
-        if rec.get("source_sha256") != hashlib.sha256(src).hexdigest():
+        if rec.get("source_sha256", {}).get(precision) != sweep_source_digest(precision):
             return None
         return rec["bytes_per_launch"].get(precision)
     except Exception:
@@ -429,13 +442,13 @@ def run_ours(args):
     achieved = bytes_per_sweep / t_sweep / 1e9 if sweeps else None
     peak = peaks.get("hbm_gbs", 6800.0)
     variant, _ = ch.sweep_tile()
-    names = {0: "k_sweep_f32_v4", 1: "k_sweep_f32_z<2,8>", 2: "k_sweep_f32_z<4,8>", 3: "k_sweep_f32_z<2,4>",
+    names = {0: "k_sweep_f32_z<1,8>", 1: "k_sweep_f32_z<2,8>", 2: "k_sweep_f32_z<4,8>", 3: "k_sweep_f32_z<2,4>",
              4: "k_sweep_f32_z<4,4>", 5: "k_sweep_f32_z<8,4>", 6: "k_sweep_f32_flat<2>", 7: "k_sweep_f32_flat<4>",
-             8: "k_sweep_f32_flat<8>"}
+             8: "k_sweep_f32_flat<8>", 9: "k_sweep_f32_pair<8,4>", 10: "k_sweep_f32_pair<4,4>",
+             11: "k_sweep_f32_pair<4,8>"}
     sweep_kernel = (names.get(variant, "k_sweep_f32") if args.precision == "fp32" else "k_sweep_f64_v2") + \
         " (SRJ sweep, autotuned tile variant %d)" % variant
-    kern = os.path.join(ROOT, "paper_1511_07800_gb300", "csrc", "kernels_poisson.cu")
-    traffic = traffic_for(kern, args.precision)
+    traffic = traffic_for(args.precision)
     line = {
         "metric": METRIC, "value": value, "unit": "Mcell*steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": ms_max / args.steps, "higher_is_better": True,
