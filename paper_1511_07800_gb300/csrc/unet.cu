@@ -1,7 +1,8 @@
 // 3-D U-Net for the learned pressure guess: forward, backward and Adam, all
 // in hand-written kernels.  BF16 weights and activations, FP32 accumulation
-// on the tensor cores (mma.sync m16n8k16), FP32 master weights, gradients
-// and optimiser state.
+// on the tensor cores (tcgen05 with TMEM accumulators for the 3x3x3
+// convolutions of the larger levels, mma.sync m16n8k16 for the rest), FP32
+// master weights, gradients and optimiser state.
 //
 // Network (channels-last [voxel][channel], voxel = ((n*D + z)*H + y)*W + x):
 //   encoder level l = 1..4 (16, 32, 64, 128 channels): two 3x3x3 conv+ReLU,
@@ -16,6 +17,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <string>
 #include <vector>
 
@@ -146,6 +148,280 @@ __global__ void __launch_bounds__(128) k_conv3(Dims dm, const bf16* __restrict__
         *reinterpret_cast<unsigned*>(y + v * ldy + co) = pack2(__float2bfloat16(v0), __float2bfloat16(v1));
       }
     }
+}
+
+// ---------------------------------------------------------------------------
+// The same convolution on the fifth-generation tensor cores (tcgen05, TMEM
+// accumulator), for layers whose level has w % 8 == 0 and h % 16 == 0 and
+// channel counts that are multiples of 16.
+//
+// A block computes 128 voxels, 8 (x) x 16 (y) at one z, for all cout
+// channels: M = 128, N = cout, K = 27 taps x cin.  The input is staged once
+// per group of up to 64 channels as a halo of 10 x 18 x 3 voxels (periodic
+// in x and y, zeros outside the walls) in the K-major core-matrix layout
+// without swizzle: 8-channel chunk j of halo voxel (hx, hy, hz) is 16 bytes
+// at j CHUNK + ((hz HY + hy) HX + hx) 16.  The A operand of tap (dz, dy, dx)
+// is then the descriptor whose start is the halo voxel (1+dx, 1+dy, 1+dz):
+// its 8-row core matrices are 8 consecutive x (16 bytes apart), the next 8
+// rows are the next y (SBO = 16 HX bytes), the next 8 channels the next
+// chunk (LBO = one chunk of the halo).  So the 27 taps need no data
+// movement.  The weights of a tap (cout x group channels, the same layout
+// with LBO = 128, SBO = 16 x group chunks) are either all resident (every
+// tap of a group loaded at once, then all the group's MMAs back to back,
+// one commit and one wait) or, when they do not fit, stream through a ring
+// of three stages, a stage refilled once the MMAs that read it have
+// completed (tcgen05.commit to that stage's mbarrier).  One thread issues
+// the MMAs and one thread polls each barrier while the others wait at the
+// block barrier.  Every wait is bounded; on a time-out the block sets *err,
+// skips the rest, and still frees its tensor memory.
+// ---------------------------------------------------------------------------
+constexpr int TC_TX = 8, TC_TY = 16, TC_HX = 10, TC_HY = 18, TC_HZ = 3;
+constexpr int TC_CHUNK = TC_HX * TC_HY * TC_HZ * 16;  // bytes of one 8-channel chunk of the halo
+constexpr int TC_CG = 64;                             // channels per halo group
+constexpr int TC_STAGES = 3;
+
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void cp16(uint32_t dst, const void* src, bool fill) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(fill ? 16 : 0)
+               : "memory");
+}
+
+// shared-memory matrix descriptor: no swizzle, K-major core matrices
+__device__ __forceinline__ uint64_t tc_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+
+// instruction descriptor of kind::f16: BF16 A and B, FP32 D, both K-major
+__host__ __device__ constexpr uint32_t tc_idesc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// bounded wait for phase `parity` of an mbarrier (about one second of
+// clock), polled with a short sleep between tries
+__device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t parity) {
+  const long long t0 = clock64();
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > 2000000000LL) return false;
+    __nanosleep(64);
+  }
+}
+
+__global__ void __launch_bounds__(128) k_conv3_tc(Dims dm, const bf16* __restrict__ x, int ldx, int cin,
+                                                  const bf16* __restrict__ wt, const float* __restrict__ bias,
+                                                  int cout, bf16* __restrict__ y, int ldy, int relu,
+                                                  const bf16* __restrict__ mask, int ldm, int resident, int* err) {
+  extern __shared__ __align__(1024) uint8_t tsm[];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int cgmax = cin < TC_CG ? cin : TC_CG;  // channels of the widest group
+  const int stage_bytes = cout * cgmax * 2;     // one tap's weights of one group
+  uint8_t* halo = tsm;
+  uint8_t* wst = tsm + (cgmax / 8) * TC_CHUNK;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(wst + (resident ? 27 : TC_STAGES) * stage_bytes);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + TC_STAGES);
+  volatile int* sfail = reinterpret_cast<volatile int*>(tslot + 1);
+  // block -> tile
+  const int nxt = dm.w / TC_TX, nyt = dm.h / TC_TY;
+  long long b = blockIdx.x;
+  const int xt = (int)(b % nxt);
+  b /= nxt;
+  const int yt = (int)(b % nyt);
+  b /= nyt;
+  const int z0 = (int)(b % dm.d);
+  const long long nn = b / dm.d;
+  const int x0 = xt * TC_TX, y0 = yt * TC_TY;
+  if (tid == 0) {
+    for (int s = 0; s < TC_STAGES; s++) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(mbar + s)));
+    *sfail = 0;
+  }
+  int ncols = 32;
+  while (ncols < cout) ncols <<= 1;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)), "r"(ncols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tslot;
+  const int ngroups = (cin + TC_CG - 1) / TC_CG;
+  const int Q = ngroups * 27;
+  const uint32_t idesc = tc_idesc(128, cout);
+  // streaming: one tap's weights of channel group g into a ring stage
+  auto load_w = [&](int q) {
+    const int g = q / 27, t = q % 27;
+    const int c0 = g * TC_CG, nch = min(TC_CG, cin - c0) / 8;
+    const uint32_t base = su32(wst + (q % TC_STAGES) * stage_bytes);
+    for (int o = tid; o < cout; o += 128) {
+      const bf16* src = wt + ((long long)t * cout + o) * cin + c0;
+      const uint32_t dst = base + (o / 8) * (nch * 128) + (o % 8) * 16;
+      for (int j = 0; j < nch; j++) cp16(dst + j * 128, src + 8 * j, true);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  // resident: every tap's weights of group g, (tap, row) pairs spread over the block
+  auto load_w_all = [&](int g) {
+    const int c0 = g * TC_CG, nch = min(TC_CG, cin - c0) / 8;
+    const uint32_t base = su32(wst);
+    for (int i = tid; i < 27 * cout; i += 128) {
+      const int t = i / cout, o = i - t * cout;
+      const bf16* src = wt + ((long long)t * cout + o) * cin + c0;
+      const uint32_t dst = base + t * stage_bytes + (o / 8) * (nch * 128) + (o % 8) * 16;
+      for (int j = 0; j < nch; j++) cp16(dst + j * 128, src + 8 * j, true);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  // halo of group g: one voxel per thread, its chunks inner
+  auto load_halo = [&](int g) {
+    const int c0 = g * TC_CG, nch = min(TC_CG, cin - c0) / 8;
+    const uint32_t base = su32(halo);
+    for (int i = tid; i < TC_HX * TC_HY * TC_HZ; i += 128) {
+      const int hx = i % TC_HX, hy = (i / TC_HX) % TC_HY, hz = i / (TC_HX * TC_HY);
+      int gx = x0 - 1 + hx, gy = y0 - 1 + hy;
+      const int gz = z0 - 1 + hz;
+      gx = gx < 0 ? gx + dm.w : (gx >= dm.w ? gx - dm.w : gx);
+      gy = gy < 0 ? gy + dm.h : (gy >= dm.h ? gy - dm.h : gy);
+      const bool in = gz >= 0 && gz < dm.d;
+      const long long v = ((nn * dm.d + (in ? gz : 0)) * dm.h + gy) * dm.w + gx;
+      const bf16* src = x + v * ldx + c0;
+      const uint32_t dst = base + i * 16;  // chunk 0 of voxel (hx, hy, hz); chunk j is TC_CHUNK further
+      for (int j = 0; j < nch; j++) cp16(dst + j * TC_CHUNK, src + 8 * j, in);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  // the MMAs of step q (group q / 27, tap q % 27) with that tap's weights at b0
+  auto issue_tap = [&](int q, uint32_t b0) {
+    const int g = q / 27, t = q % 27;
+    const int c0 = g * TC_CG, nch = min(TC_CG, cin - c0) / 8;
+    const int dz = t / 9, dy = (t / 3) % 3, dx = t % 3;  // halo offsets 0..2 (shift + 1)
+    const uint32_t a0 = su32(halo) + ((dz * TC_HY + dy) * TC_HX + dx) * 16;
+    for (int kk = 0; kk < nch / 2; kk++) {
+      const uint64_t ad = tc_desc(a0 + 2 * kk * TC_CHUNK, TC_CHUNK, TC_HX * 16);
+      const uint64_t bd = tc_desc(b0 + 2 * kk * 128, 128, nch * 128);
+      const uint32_t acc = (q > 0 || kk > 0) ? 1u : 0u;
+      asm volatile(
+          "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+          "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+          "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+    }
+  };
+  auto commit = [&](int stage) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     su32(mbar + stage))
+                 : "memory");
+  };
+  // one thread polls the barrier, the others wait at __syncthreads (no issue
+  // slots spent spinning); false on a time-out
+  auto block_wait = [&](int stage, uint32_t parity) {
+    if (tid == 0 && !tc_wait(su32(mbar + stage), parity)) *sfail = 1;
+    __syncthreads();
+    return *sfail == 0;
+  };
+  bool ok = true;
+  if (resident) {
+    for (int g = 0; g < ngroups && ok; g++) {
+      load_halo(g);
+      load_w_all(g);
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncthreads();
+      if (tid == 0) {
+        for (int t = 0; t < 27; t++) issue_tap(g * 27 + t, su32(wst + t * stage_bytes));
+        commit(0);
+      }
+      if (g + 1 < ngroups && !block_wait(0, g & 1)) ok = false;  // the next group overwrites halo and weights
+    }
+  } else {
+    load_halo(0);
+    load_w(0);
+    if (Q > 1) load_w(1);
+    for (int q = 0; q < Q; q++) {
+      const int g = q / 27, t = q % 27;
+      if (t == 0 && g > 0) {
+        // the previous group's MMAs read the halo: wait for the last of them
+        if (!block_wait((q - 1) % TC_STAGES, ((q - 1) / TC_STAGES) & 1)) {
+          ok = false;
+          break;
+        }
+        load_halo(g);
+      }
+      // this step's weights (and a new halo) have landed; the next step's may be in flight
+      if (t == 0 || q + 1 >= Q)
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+      else
+        asm volatile("cp.async.wait_group 1;" ::: "memory");
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncthreads();
+      if (tid == 0) {
+        issue_tap(q, su32(wst + (q % TC_STAGES) * stage_bytes));
+        commit(q % TC_STAGES);
+      }
+      // refill the stage that step q-1 used with step q+2's weights
+      if (q + 2 < Q) {
+        if (q >= 1 && !block_wait((q - 1) % TC_STAGES, ((q - 1) / TC_STAGES) & 1)) {
+          ok = false;
+          break;
+        }
+        load_w(q + 2);
+      }
+    }
+  }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  // all MMAs done: the last commit covers every earlier one
+  __syncthreads();
+  const bool done = ok && *sfail == 0 &&
+                    (resident ? block_wait(0, (ngroups - 1) & 1)
+                              : block_wait((Q - 1) % TC_STAGES, ((Q - 1) / TC_STAGES) & 1));
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (!done) {
+    if (tid == 0) atomicExch(err, 1);
+  } else {
+    const int r = warp * 32 + lane;  // TMEM lane = output row
+    const long long v = ((nn * dm.d + z0) * dm.h + y0 + r / 8) * dm.w + x0 + (r % 8);
+    for (int c = 0; c < cout; c += 16) {
+      uint32_t a[16];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+          : "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3]), "=r"(a[4]), "=r"(a[5]), "=r"(a[6]), "=r"(a[7]),
+            "=r"(a[8]), "=r"(a[9]), "=r"(a[10]), "=r"(a[11]), "=r"(a[12]), "=r"(a[13]), "=r"(a[14]), "=r"(a[15])
+          : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      uint32_t o[8];
+#pragma unroll
+      for (int h = 0; h < 8; h++) {
+        float v0 = __uint_as_float(a[2 * h]), v1 = __uint_as_float(a[2 * h + 1]);
+        const int co = c + 2 * h;
+        if (bias) {
+          v0 += bias[co];
+          v1 += bias[co + 1];
+        }
+        if (relu) {
+          v0 = fmaxf(v0, 0.f);
+          v1 = fmaxf(v1, 0.f);
+        }
+        if (mask) {
+          const bf16* mp = mask + v * ldm + co;
+          if (!(__bfloat162float(mp[0]) > 0.f)) v0 = 0.f;
+          if (!(__bfloat162float(mp[1]) > 0.f)) v1 = 0.f;
+        }
+        o[h] = pack2(__float2bfloat16(v0), __float2bfloat16(v1));
+      }
+      uint4* yp = reinterpret_cast<uint4*>(y + v * ldy + c);
+      yp[0] = make_uint4(o[0], o[1], o[2], o[3]);
+      yp[1] = make_uint4(o[4], o[5], o[6], o[7]);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));
 }
 
 // First layer: 1 input channel (FP32 input rounded to BF16) -> 16 channels, ReLU.
@@ -553,6 +829,8 @@ struct stp_unet {
   float *xin = nullptr, *tin = nullptr, *snorm = nullptr;  // normalised pairs, per-sample norms
   int guess_kernels = 0;                                   // kernels launched by one guess
   float out_scale = 1.f;                                   // the network predicts out_scale * dp / s
+  int* d_err = nullptr;                                    // set by a tensor-core kernel whose wait timed out
+  bool use_tc = true;                                      // tcgen05 convolutions where the shapes allow
   std::vector<void*> allocs;
   std::string err;
 };
@@ -570,6 +848,14 @@ int ufail(stp_unet* n, int code, const std::string& m) {
     if (e_ != cudaSuccess) return ufail(n, STP_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
   } while (0)
 
+// after a synchronisation: did a tensor-core convolution give up waiting?
+int check_tc_timeout(stp_unet* n) {
+  int e = 0;
+  UTRY(n, cudaMemcpy(&e, n->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (e) return ufail(n, STP_ETIMEOUT, "a tensor-core convolution timed out waiting for its MMAs");
+  return STP_OK;
+}
+
 template <typename T>
 int ualloc(stp_unet* n, T** p, size_t count) {
   cudaError_t e = cudaMalloc((void**)p, sizeof(T) * std::max<size_t>(count, 1));
@@ -581,10 +867,37 @@ int ualloc(stp_unet* n, T** p, size_t count) {
 // concat widths: decoder level l (0..2) input = kCh[l+1] + kCh[l]
 int cu_width(int l) { return kCh[l + 1] + kCh[l]; }
 
-// launch a 3x3x3 convolution (forward form)
+// shared memory of k_conv3_tc: the halo of the widest channel group, then
+// the weights (all 27 taps of a group when resident, else three stages)
+size_t conv3_tc_smem(int cin, int cout, bool resident) {
+  const int cg = std::min(cin, TC_CG);
+  return (size_t)(cg / 8) * TC_CHUNK + (size_t)(resident ? 27 : TC_STAGES) * cout * cg * 2 + 64;
+}
+constexpr size_t kTcSmemMax = 200 * 1024;
+
+bool conv3_tc_ok(const stp_unet* n, const Dims& dm, int ldx, int cin, int cout, int ldy) {
+  return n->use_tc && dm.w % TC_TX == 0 && dm.h % TC_TY == 0 && cin % 16 == 0 && cout % 16 == 0 && cout <= 256 &&
+         ldx % 8 == 0 && ldy % 8 == 0 && conv3_tc_smem(cin, cout, false) <= kTcSmemMax;
+}
+
+// launch a 3x3x3 convolution (forward form): tcgen05 where the shapes allow, else mma.sync
 int conv3(stp_unet* n, const Dims& dm, const bf16* x, int ldx, int cin, const bf16* wt, const float* bias, int cout,
           bf16* y, int ldy, int relu, const bf16* mask, int ldm) {
   const long long V = dm.vox();
+  if (conv3_tc_ok(n, dm, ldx, cin, cout, ldy)) {
+    static bool attr_set = false;
+    if (!attr_set) {
+      UTRY(n, cudaFuncSetAttribute(k_conv3_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmemMax));
+      attr_set = true;
+    }
+    const bool resident = conv3_tc_smem(cin, cout, true) <= kTcSmemMax;
+    const unsigned blocks = (unsigned)(V / (TC_TX * TC_TY));
+    k_conv3_tc<<<blocks, 128, conv3_tc_smem(cin, cout, resident), n->st>>>(dm, x, ldx, cin, wt, bias, cout, y, ldy,
+                                                                          relu, mask, ldm, resident ? 1 : 0,
+                                                                          n->d_err);
+    UTRY(n, cudaGetLastError());
+    return STP_OK;
+  }
   const unsigned gx = (unsigned)((V + 127) / 128);
   if (cout % 64 == 0) {
     k_conv3<8><<<dim3(gx, cout / 64), 128, 0, n->st>>>(dm, x, ldx, cin, wt, bias, cout, y, ldy, relu, mask, ldm);
@@ -875,11 +1188,14 @@ int stp_unet_create(int nmax, int nz, int ny, int nx, void* stream, stp_unet** o
   A(&n->snorm, (size_t)nmax);
   A(&n->gy, (size_t)V[0]);
   A(&n->loss, 1);
+  A(&n->d_err, 1);
+  if (const char* e = std::getenv("STP_UNET_TC")) n->use_tc = std::atoi(e) != 0;
   if (rc == STP_OK && cudaMallocHost((void**)&n->h_loss, sizeof(float)) != cudaSuccess) rc = STP_ENOMEM;
   if (rc == STP_OK) {
     cudaMemsetAsync(n->theta, 0, sizeof(float) * n->np, n->st);
     cudaMemsetAsync(n->m, 0, sizeof(float) * n->np, n->st);
     cudaMemsetAsync(n->v, 0, sizeof(float) * n->np, n->st);
+    cudaMemsetAsync(n->d_err, 0, sizeof(int), n->st);
     if (cudaStreamSynchronize(n->st) != cudaSuccess) rc = STP_ECUDA;
   }
   if (rc != STP_OK) {
@@ -929,7 +1245,7 @@ int stp_unet_forward(stp_unet* n, const float* x, float* y, int nb) {
   if (rc) return rc;
   UTRY(n, cudaMemcpyAsync(y, n->y, sizeof(float) * n->dm[0].vox() / n->nmax * nb, cudaMemcpyDeviceToDevice, n->st));
   UTRY(n, cudaStreamSynchronize(n->st));
-  return STP_OK;
+  return check_tc_timeout(n);
 }
 
 int stp_unet_gradient(stp_unet* n, const float* x, const float* target, int nb, float* grad, float* loss) {
@@ -946,7 +1262,7 @@ int stp_unet_gradient(stp_unet* n, const float* x, const float* target, int nb, 
   UTRY(n, cudaMemcpyAsync(n->h_loss, n->loss, sizeof(float), cudaMemcpyDeviceToHost, n->st));
   UTRY(n, cudaStreamSynchronize(n->st));
   if (loss) *loss = *n->h_loss;
-  return STP_OK;
+  return check_tc_timeout(n);
 }
 
 int stp_unet_train_step(stp_unet* n, const float* x, const float* target, int nb, float lr, float* loss) {
@@ -997,7 +1313,7 @@ int stp_unet_eval_pairs(stp_unet* n, const float* r, const float* dp, int nb, fl
   UTRY(n, cudaMemcpyAsync(n->h_loss, n->loss, sizeof(float), cudaMemcpyDeviceToHost, n->st));
   UTRY(n, cudaStreamSynchronize(n->st));
   if (loss) *loss = *n->h_loss;
-  return STP_OK;
+  return check_tc_timeout(n);
 }
 
 }  // extern "C"

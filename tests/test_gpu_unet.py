@@ -1,4 +1,5 @@
-"""The learned-guess U-Net on the GPU (BF16 tensor-core kernels) against
+"""The learned-guess U-Net on the GPU (BF16 tensor-core kernels: tcgen05
+with TMEM accumulators where the level's shape allows, mma.sync elsewhere) against
 the FP64 oracle, with the oracle's storage points rounded to bfloat16 where
 the CUDA path stores in bfloat16: forward pass, the gradient of the MSE
 loss, and one Adam step."""
@@ -22,9 +23,15 @@ def test_unet_param_count(stp_lib, orc):
     assert stp_lib.UNet.param_count() == unet.n_params()
 
 
-def test_unet_forward_parity(stp_lib, orc):
+# (2, 8, 8, 16): every level on the mma.sync kernels; (1, 8, 16, 16): the
+# full-resolution level on the tcgen05 kernel (w % 8 == 0, h % 16 == 0)
+SHAPES = [(2, 8, 8, 16), (1, 8, 16, 16)]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_unet_forward_parity(stp_lib, orc, shape):
     torch = pytest.importorskip("torch")
-    unet, theta, x, t = _setup(1)
+    unet, theta, x, t = _setup(1, shape)
     n, d, h, w = x.shape
     net = stp_lib.UNet(n, d, h, w)
     net.set_params(theta.astype(np.float32))
@@ -42,9 +49,10 @@ def test_unet_forward_parity(stp_lib, orc):
     net.close()
 
 
-def test_unet_gradient_parity(stp_lib, orc):
+@pytest.mark.parametrize("shape", SHAPES)
+def test_unet_gradient_parity(stp_lib, orc, shape):
     torch = pytest.importorskip("torch")
-    unet, theta, x, t = _setup(2)
+    unet, theta, x, t = _setup(2, shape)
     n, d, h, w = x.shape
     net = stp_lib.UNet(n, d, h, w)
     net.set_params(theta.astype(np.float32))
@@ -102,3 +110,33 @@ def test_unet_training_reduces_loss(stp_lib, orc):
         l1 = net.train_step(tx, tt, 1e-3)
     assert l1 < 0.5 * l0
     net.close()
+
+
+def test_tensor_core_conv_matches_mma_sync(stp_lib, orc, monkeypatch):
+    """The tcgen05 convolutions (TMEM accumulator, operands read from a
+    shared-memory halo) and the mma.sync ones compute the same network:
+    forward output and gradient agree to the rounding of the FP32
+    accumulation order (levels 1-3 of this shape run on tcgen05; level 1 has
+    all taps' weights resident, the 192- and 64-channel layers of level 3
+    stream them through the stage ring)."""
+    torch = pytest.importorskip("torch")
+    unet, theta, x, t = _setup(4, (1, 8, 64, 32))
+    n, d, h, w = x.shape
+    tx = torch.from_numpy(x.astype(np.float32)).cuda()
+    tt = torch.from_numpy(t.astype(np.float32)).cuda()
+    out = {}
+    for tc in ("0", "1"):
+        monkeypatch.setenv("STP_UNET_TC", tc)
+        net = stp_lib.UNet(n, d, h, w)
+        net.set_params(theta.astype(np.float32))
+        ty = torch.zeros_like(tx)
+        net.forward(tx, ty)
+        g = torch.zeros(stp_lib.UNet.param_count(), dtype=torch.float32, device="cuda")
+        loss = net.gradient(tx, tt, g)
+        out[tc] = (ty.cpu().numpy().astype(np.float64), g.cpu().numpy().astype(np.float64), loss)
+        net.close()
+    (y0, g0, l0), (y1, g1, l1) = out["0"], out["1"]
+    assert np.abs(y1 - y0).max() < 2e-2 * np.abs(y0).max()
+    assert abs(l1 - l0) < 1e-2 * l0
+    assert np.linalg.norm(g1 - g0) < 5e-2 * np.linalg.norm(g0)
+    assert g1 @ g0 / (np.linalg.norm(g1) * np.linalg.norm(g0)) > 0.998
