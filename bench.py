@@ -45,7 +45,8 @@ def parse():
     ap.add_argument("--grid", default=None, help="override the cell counts, NXxNYxNZ (profiling runs)")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-guess comparison")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched uneven-channel measurement")
-    ap.add_argument("--no-les", action="store_true", help="skip the LES-grid point vs z-line solve measurement")
+    ap.add_argument("--no-les", action="store_true",
+                    help="skip the LES measurements (point vs z-line solve; the paper's LES workload)")
     return ap.parse_args()
 
 
@@ -307,6 +308,38 @@ def les_line_vs_point(steps, warmup):
     return out
 
 
+def les_paper_steps(steps, warmup):
+    """The paper's LES workload (Sec. 5) at its own grid, 240 x 140 x 120,
+    Lx = 8, Ly = 4, Lz = 1, Re_* = 360, dt = 1e-4, Smagorinsky + van Driest,
+    FP32 with FP64 refinement, from its random Fourier-curl start; the
+    plane statistics are accumulated after every step, as a run gathering
+    the paper's averages would.  GPU time by CUDA events around the steps."""
+    import torch
+    from paper_1511_07800_gb300 import inputs, stp
+    cfg = inputs.preset("les_paper")
+    cells = cfg["nx"] * cfg["ny"] * cfg["nz"]
+    stream = torch.cuda.current_stream()
+    with stp.Channel(cfg, precision="fp32", stream=stream.cuda_stream) as ch:
+        ch.set_fields(*inputs.paper_les_initial(cfg, 1))
+        ch.step(max(3, warmup))
+        ch.stats_reset()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sweeps = 0
+        for _ in range(steps):
+            st = ch.step(1)
+            sweeps += st["sweeps"]
+            ch.stats_accumulate()
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+    return {"workload": "les_paper 240x140x120, Lx 8, Ly 4, Lz 1, Re_* 360, dt 1e-4, FP32 + FP64 refinement, "
+                        "statistics every step", "value": cells * steps / (ms / 1e3) / 1e6, "unit": "Mcell*steps/s",
+            "ms_per_step": ms / steps, "sweeps_per_step": sweeps / steps, "steps": steps,
+            "warmup": max(3, warmup), "converged": st["converged"]}
+
+
 def run_reference(args):
     """The oracle (plain FP64 C, OpenMP over z) time-stepping the workload with
     its own tolerance-driven pressure solves, on rank 0's host cores."""
@@ -485,6 +518,10 @@ def run_ours(args):
             line["les_pressure_solve"] = les_line_vs_point(3, 3)
         except Exception as ex:  # report, never fake
             line["les_pressure_solve"] = {"error": str(ex)[:200]}
+        try:
+            line["les_paper"] = les_paper_steps(10, 3)
+        except Exception as ex:  # report, never fake
+            line["les_paper"] = {"error": str(ex)[:200]}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
             line["cpu_baseline"] = cpu_baseline_sample(cfg, fields, sweeps / args.steps)

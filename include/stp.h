@@ -183,6 +183,22 @@ int stp_batch_create(stp_handle *const *handles, int n, void *stream, stp_batch 
 void stp_batch_destroy(stp_batch *b);
 const char *stp_batch_last_error(const stp_batch *b);
 
+/* LES statistics (Sec. 5).  The velocities are taken at the cell centres
+   (uc, vc, wc: the mean of the two faces of each component) and averaged
+   over x, y and the accumulated samples.
+   stp_stats_reset: clear the sums (the first call allocates two small
+   buffers); kc is the level of the two-point correlations, -1 for nz/2.
+   stp_stats_accumulate: add the current fields, asynchronously on the
+   handle's stream (call it between steps).
+   stp_stats_read (synchronises): moments [9][nz] = per level the means of
+   uc, vc, wc, uc^2, vc^2, wc^2, uc vc, uc wc, vc wc; corr [3][nx] = the
+   streamwise correlations R(d) = <q(x + d dx) q(x)> - <q>^2 of u, v (on their
+   faces) and wc at level kc; either may be NULL.  FP64 sums in a fixed
+   order. */
+int stp_stats_reset(stp_handle *h, int kc);
+int stp_stats_accumulate(stp_handle *h);
+int stp_stats_read(stp_handle *h, double *moments, double *corr, long long *nsamples, int *kc);
+
 /* The FP32 sweep tile variant the autotuner picked for this handle's grid
    (0..8, see above; -1 before the first solve, 0 in FP64) and, when it was
    timed, its time per sweep in microseconds (*us may be NULL). */

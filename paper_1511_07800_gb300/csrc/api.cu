@@ -82,6 +82,11 @@ struct stp_handle {
   int guess_kernels = 0;
   float *hr = nullptr, *hdp = nullptr;  // caller buffers for harvested pairs
   double* p_prev = nullptr;
+  // LES statistics (stp_stats_*)
+  double* st_mom = nullptr;   // [kStatMoments][nz] plane sums
+  double* st_corr = nullptr;  // [3][nx] two-point product sums
+  int st_kc = 0;
+  long long st_n = 0;
 };
 
 namespace {
@@ -1927,6 +1932,67 @@ void stp_batch_destroy(stp_batch* b) {
 }
 
 const char* stp_batch_last_error(const stp_batch* b) { return b ? b->err.c_str() : ""; }
+
+int stp_stats_reset(stp_handle* h, int kc) {
+  if (!h) return STP_EINVAL;
+  if (kc < -1 || kc >= h->nz) return fail(h, STP_EINVAL, "correlation level out of range");
+  CUDA_TRY(h, cudaSetDevice(h->dev));
+  if (!h->st_mom) {
+    cudaError_t e = cudaMalloc((void**)&h->st_mom, sizeof(double) * kStatMoments * h->nz);
+    if (e == cudaSuccess) {
+      h->allocs.push_back(h->st_mom);
+      e = cudaMalloc((void**)&h->st_corr, sizeof(double) * 3 * h->nx);
+    }
+    if (e != cudaSuccess) {
+      h->st_mom = h->st_corr = nullptr;
+      return fail(h, STP_ENOMEM, "statistics buffers");
+    }
+    h->allocs.push_back(h->st_corr);
+  }
+  h->st_kc = kc < 0 ? h->nz / 2 : kc;
+  h->st_n = 0;
+  CUDA_TRY(h, cudaMemsetAsync(h->st_mom, 0, sizeof(double) * kStatMoments * h->nz, h->st));
+  CUDA_TRY(h, cudaMemsetAsync(h->st_corr, 0, sizeof(double) * 3 * h->nx, h->st));
+  return STP_OK;
+}
+
+int stp_stats_accumulate(stp_handle* h) {
+  if (!h) return STP_EINVAL;
+  if (!h->st_mom) return fail(h, STP_EINVAL, "call stp_stats_reset first");
+  CUDA_TRY(h, cudaSetDevice(h->dev));
+  if (h->prec == STP_FP64)
+    CUDA_TRY(h, launch_les_stats<double>(h->nx, h->ny, h->nz, h->st_kc, (const double*)h->u, (const double*)h->v,
+                                         (const double*)h->w, h->st_mom, h->st_corr, h->st));
+  else
+    CUDA_TRY(h, launch_les_stats<float>(h->nx, h->ny, h->nz, h->st_kc, (const float*)h->u, (const float*)h->v,
+                                        (const float*)h->w, h->st_mom, h->st_corr, h->st));
+  h->st_n++;
+  return STP_OK;
+}
+
+int stp_stats_read(stp_handle* h, double* moments, double* corr, long long* nsamples, int* kc) {
+  if (!h) return STP_EINVAL;
+  if (!h->st_mom) return fail(h, STP_EINVAL, "call stp_stats_reset first");
+  if (nsamples) *nsamples = h->st_n;
+  if (kc) *kc = h->st_kc;
+  if (h->st_n == 0) return STP_OK;
+  CUDA_TRY(h, cudaSetDevice(h->dev));
+  std::vector<double> m((size_t)kStatMoments * h->nz), c((size_t)3 * h->nx);
+  CUDA_TRY(h, cudaMemcpyAsync(m.data(), h->st_mom, sizeof(double) * m.size(), cudaMemcpyDeviceToHost, h->st));
+  CUDA_TRY(h, cudaMemcpyAsync(c.data(), h->st_corr, sizeof(double) * c.size(), cudaMemcpyDeviceToHost, h->st));
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  const double inv = 1.0 / ((double)h->st_n * h->nx * h->ny);
+  for (double& x : m) x *= inv;
+  if (moments) std::copy(m.begin(), m.end(), moments);
+  if (corr) {
+    // R_cc(d) = <q_c(x + d) q_c(x)> - <q_c>^2 at the correlation level
+    for (int comp = 0; comp < 3; comp++) {
+      const double mean = m[(size_t)comp * h->nz + h->st_kc];
+      for (int d = 0; d < h->nx; d++) corr[comp * h->nx + d] = c[(size_t)comp * h->nx + d] * inv - mean * mean;
+    }
+  }
+  return STP_OK;
+}
 
 int stp_sweep_tile(const stp_handle* h, float* us) {
   if (!h) return STP_EINVAL;

@@ -250,6 +250,15 @@ cudaError_t launch_group_check(const Group& G, cudaGraphConditionalHandle h_loop
 cudaError_t launch_group_sweep(const Group& G, int m, cudaStream_t s);
 cudaError_t launch_group_addcorr(const Group& G, cudaStream_t s);
 
+// LES statistics (les_stats.cu): plane sums of the kStatMoments moments of
+// the cell-centred velocities per level (mom[m * nz + k]) and streamwise
+// two-point products of u, v, wc at level kc (corr[c * nx + d]), added to the
+// buffers.
+constexpr int kStatMoments = 9;
+template <typename T>
+cudaError_t launch_les_stats(int nx, int ny, int nz, int kc, const T* u, const T* v, const T* w, double* mom,
+                             double* corr, cudaStream_t s);
+
 // batched step: counter[0] = steps done, counter[1] = steps wanted
 cudaError_t launch_batch_begin(int* counter, cudaGraphConditionalHandle h_steps, cudaStream_t s);
 cudaError_t launch_batch_end(int* counter, cudaGraphConditionalHandle h_steps, cudaStream_t s);

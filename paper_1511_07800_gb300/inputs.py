@@ -21,6 +21,10 @@ Workloads (half-height units: Lz = 2, delta = 1):
                    bulk Re 5600 (nu = 1/2800), Smagorinsky Cs = 0.1, van Driest
                    A = 25, Re_tau = 180, constant flux U_b = 1, laminar
                    1.5 z (2 - z) + uniform noise of 10 % of U_cl, dt = 1e-3
+  les_paper        240 x 140 x 120, Lx = 8, Ly = 4, Lz = 1 (the paper's LES, its
+                   units), Re_* = 360, -dp/dx = 2, Smagorinsky, dt = 1e-4,
+                   u = U0/3 + a curl(f A) with random Fourier modes (5 per axis),
+                   a setting the curl term's rms to 10 % of max U0/3
 """
 import math
 
@@ -44,6 +48,12 @@ def preset(name, **over):
     elif name == "les_channel":
         base.update(nx=256, ny=128, nz=192, Lx=4 * PI, Ly=2 * PI, nu=1 / 2800.0, dt=1e-3,
                     forcing=1, ubulk=1.0, les=1, stretch=2.0)
+    elif name == "les_paper":
+        # the paper's LES in its own units: channel height 1, friction velocity
+        # 1, Re_* = 360 (nu = 1/360), -dp/dx = 2 so that the laminar profile is
+        # Re_* z (1 - z); van Driest d+ = z Re_* (re_tau is per half-height)
+        base.update(nx=240, ny=140, nz=120, Lx=8.0, Ly=4.0, Lz=1.0, nu=1 / 360.0, dt=1e-4, fx=2.0,
+                    les=1, re_tau=180.0)
     else:
         raise KeyError(name)
     base.update(over)
@@ -177,6 +187,68 @@ def batched_instances(count=64, seed=2, sizes=(32, 48, 64, 96, 128)):
     return out
 
 
+def _paper_f(z, Lz):
+    """Wall envelope of the perturbation, 1/2 + 1/2 sin(2 pi z/Lz - pi/2): zero
+    with zero slope at both walls."""
+    return 0.5 + 0.5 * np.sin(2 * PI * z / Lz - PI / 2)
+
+
+def paper_les_initial(cfg, seed, modes=5, scale=1.0 / 3.0, intensity=0.1):
+    """Turbulent-like start of the paper's LES: u = scale U0(z) + a curl(f(z) A(x)),
+    U0 the laminar profile of the forcing (fx/(2 nu)) z (Lz - z), f the wall
+    envelope above and A_i = sum over k_x, k_y, k_z = 1..modes of
+    S_i(k) sin(k.x) + C_i(k) cos(k.x), k = 2 pi (k_x/Lx, k_y/Ly, k_z/Lz), with
+    S and C uniform on [0, 1] (seeded).  The curl is taken discretely on the
+    MAC grid from psi = f A placed on the cell edges, so the field has zero
+    discrete divergence and w = 0 at the walls.  The paper gives no
+    amplitude for the curl term: taken with a = 1 its rms exceeds the base
+    flow and the advective CFL number at the paper's dt is about 2.  Here a
+    scales it to an rms (over the three components) of `intensity` times the
+    peak of scale U0 (a = 1 when intensity is None).  Returns (u, v, w)."""
+    rng = np.random.default_rng(seed)
+    nx, ny, nz = cfg["nx"], cfg["ny"], cfg["nz"]
+    Lx, Ly, Lz = cfg["Lx"], cfg["Ly"], cfg["Lz"]
+    dx, dy = Lx / nx, Ly / ny
+    zf, zc = zfaces(cfg), zcentres(cfg)
+    S = rng.uniform(0.0, 1.0, (3, modes, modes, modes))
+    C = rng.uniform(0.0, 1.0, (3, modes, modes, modes))
+    kk = np.arange(1, modes + 1)
+    kx, ky, kz = 2 * PI * kk / Lx, 2 * PI * kk / Ly, 2 * PI * kk / Lz
+
+    def A(comp, x, y, z):
+        """A_comp on the grid spanned by 1-D coordinate arrays x, y, z -> [z][y][x].
+        S sin(k.x) + C cos(k.x) = Re[(C - i S) e^{i k.x}], and e^{i k.x}
+        factors by axis, so the sum is taken one axis at a time."""
+        coef = C[comp] - 1j * S[comp]                                   # [a][b][c]
+        g = np.einsum("abc,cz->abz", coef, np.exp(1j * np.outer(kz, z)))
+        h = np.einsum("abz,by->azy", g, np.exp(1j * np.outer(ky, y)))
+        return np.einsum("azy,ax->zyx", h, np.exp(1j * np.outer(kx, x))).real
+
+    xi, xh = dx * np.arange(nx + 1), dx * (np.arange(nx + 1) + 0.5)
+    yj, yh = dy * np.arange(ny + 1), dy * (np.arange(ny + 1) + 0.5)
+    # psi on the edges: psi_x at (x_{i+1/2}, y_j, zf), psi_y at (x_i, y_{j+1/2}, zf),
+    # psi_z at (x_i, y_j, zc); one extra point along x and y for the differences
+    psx = _paper_f(zf, Lz)[:, None, None] * A(0, xh, yj, zf)
+    psy = _paper_f(zf, Lz)[:, None, None] * A(1, xi, yh, zf)
+    psz = _paper_f(zc, Lz)[:, None, None] * A(2, xi, yj, zc)
+    dzc = np.diff(zf)[:, None, None]
+    # u at (x_i, y_{j+1/2}, zc): d psi_z/dy - d psi_y/dz
+    u = (psz[:, 1:, :nx] - psz[:, :ny, :nx]) / dy - (psy[1:, :ny, :nx] - psy[:nz, :ny, :nx]) / dzc
+    # v at (x_{i+1/2}, y_j, zc): d psi_x/dz - d psi_z/dx
+    v = (psx[1:, :ny, :nx] - psx[:nz, :ny, :nx]) / dzc - (psz[:, :ny, 1:] - psz[:, :ny, :nx]) / dx
+    # w at (x_{i+1/2}, y_{j+1/2}, zf): d psi_y/dx - d psi_x/dy
+    w = (psy[:, :ny, 1:] - psy[:, :ny, :nx]) / dx - (psx[:, 1:, :nx] - psx[:, :ny, :nx]) / dy
+    w[0] = 0.0
+    w[-1] = 0.0
+    U0 = cfg["fx"] / (2.0 * cfg["nu"]) * zc * (Lz - zc)
+    if intensity is not None:
+        rms = np.sqrt((np.sum(u * u) + np.sum(v * v) + np.sum(w[1:-1] * w[1:-1])) /
+                      (u.size + v.size + w[1:-1].size))
+        a = intensity * scale * np.abs(U0).max() / rms
+        u, v, w = a * u, a * v, a * w
+    return u + scale * U0[:, None, None], v, w
+
+
 def initial_fields(name, cfg=None, seed=0):
     """Initial (u, v, w) of a named workload."""
     cfg = cfg or preset(name)
@@ -191,4 +263,6 @@ def initial_fields(name, cfg=None, seed=0):
     if name == "les_channel":
         u0, v0, w0 = poiseuille(cfg, 1.5)
         return noise(cfg, 0.15, seed, (u0, v0, w0))
+    if name == "les_paper":
+        return paper_les_initial(cfg, seed)
     raise KeyError(name)

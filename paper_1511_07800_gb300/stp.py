@@ -82,7 +82,8 @@ EXPORTS = ("stp_config_defaults", "stp_init", "stp_destroy", "stp_last_error", "
            "stp_unet_gradient", "stp_unet_train_step", "stp_unet_train_pairs", "stp_unet_eval_pairs",
            "stp_set_learned_guess", "stp_set_harvest", "stp_unet_set_output_scale", "stp_state_size",
            "stp_get_state", "stp_set_state", "stp_batch_create", "stp_batch_destroy", "stp_batch_last_error",
-           "stp_batch_step", "stp_batch_groups", "stp_sweep_tile")
+           "stp_batch_step", "stp_batch_groups", "stp_sweep_tile", "stp_stats_reset",
+           "stp_stats_accumulate", "stp_stats_read")
 
 _lib = None
 
@@ -137,6 +138,9 @@ def lib():
     L.stp_batch_step.argtypes = [vp, ctypes.c_int, ctypes.POINTER(BatchStats), ctypes.POINTER(StepStats)]
     L.stp_batch_groups.argtypes = [vp, ctypes.c_int, ctypes.POINTER(BatchGroup)]
     L.stp_sweep_tile.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
+    L.stp_stats_reset.argtypes = [vp, ctypes.c_int]
+    L.stp_stats_accumulate.argtypes = [vp]
+    L.stp_stats_read.argtypes = [vp, dp, dp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_int)]
     L.stp_state_size.argtypes = [vp]
     L.stp_state_size.restype = ctypes.c_longlong
     L.stp_get_state.argtypes = [vp, vp]
@@ -298,6 +302,27 @@ class Channel:
         a = ctypes.c_void_p(r_out.data_ptr()) if r_out is not None else None
         b = ctypes.c_void_p(dp_out.data_ptr()) if dp_out is not None else None
         self._check(lib().stp_set_harvest(self._h, a, b))
+
+    def stats_reset(self, kc=-1):
+        """Clear the LES statistics; kc: level of the two-point correlations (-1: nz/2)."""
+        self._check(lib().stp_stats_reset(self._h, int(kc)))
+
+    def stats_accumulate(self):
+        """Add the current fields to the statistics (asynchronous)."""
+        self._check(lib().stp_stats_accumulate(self._h))
+
+    def stats_read(self):
+        """(moments [9][nz], correlations [3][nx], samples, kc): means over x, y
+        and the samples of uc, vc, wc, uc^2, vc^2, wc^2, uc vc, uc wc, vc wc,
+        and R(d) of u, v, wc at level kc."""
+        mom = np.zeros((9, self.nz))
+        cor = np.zeros((3, self.nx))
+        n = ctypes.c_longlong(0)
+        kc = ctypes.c_int(0)
+        self._check(lib().stp_stats_read(self._h, mom.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                         cor.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(n),
+                                         ctypes.byref(kc)))
+        return mom, cor, n.value, kc.value
 
     def sweep_tile(self):
         """(variant, microseconds per sweep) picked by the FP32 sweep autotuner."""

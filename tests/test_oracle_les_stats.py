@@ -1,0 +1,72 @@
+"""Pins of the oracle's LES statistics (Sec. 5) against closed forms, and
+the library's bulk post-processing against the oracle's."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1511_07800_gb300 import inputs, les
+
+PI = math.pi
+
+
+def test_moments_and_correlation_of_cosine_modes():
+    """u = U(z) + a cos(2 pi m x/Lx): the centre value carries the mode with
+    amplitude a cos(pi m/nx); R_uu(d) = (a^2/2) cos(2 pi m d/nx) on the faces."""
+    from oracle import les_stats
+    nx, ny, nz, m, a = 24, 6, 5, 3, 0.7
+    x = np.arange(nx)
+    U = np.linspace(1.0, 2.0, nz)
+    u = U[:, None, None] + a * np.cos(2 * PI * m * x / nx)[None, None, :] * np.ones((nz, ny, nx))
+    v = np.zeros((nz, ny, nx))
+    w = np.zeros((nz + 1, ny, nx))
+    mom = les_stats.plane_moments(u, v, w)
+    ac = a * math.cos(PI * m / nx)
+    assert np.allclose(mom[0], U, atol=1e-13)
+    assert np.allclose(mom[3], U ** 2 + ac * ac / 2, atol=1e-12)
+    assert np.allclose(mom[[1, 2, 4, 5, 6, 7, 8]], 0.0, atol=1e-14)
+    c = les_stats.corr_x(u, v, w, 2)
+    R = c[0] - U[2] ** 2
+    assert np.allclose(R, a * a / 2 * np.cos(2 * PI * m * x / nx), atol=1e-12)
+
+
+def test_bulk_of_the_laminar_profile():
+    """The laminar profile of the paper's units, Re_* z (1 - z): bulk velocity
+    Re_*/6 and wall shear nu Re_* = 1 (u_tau = 1), to the grid's accuracy."""
+    from oracle import les_stats
+    cfg = inputs.preset("les_paper")
+    zc = inputs.zcentres(cfg)
+    re = 1.0 / cfg["nu"]
+    prof = re * zc * (1 - zc)
+    b = les_stats.bulk(prof, inputs.zfaces(cfg), cfg["nu"])
+    dz = 1.0 / cfg["nz"]
+    assert abs(b["U_mean"] - re / 6) < re * dz * dz
+    assert abs(b["u_tau"] - 1.0) < dz
+    assert abs(b["Cf"] - 2 / b["U_mean"] ** 2) < 4 * dz / b["U_mean"] ** 2
+    assert abs(b["pope_Umax_over_utau"] - (math.log(b["Re_tau"]) / 0.4 + 3.47)) < 1e-12
+
+
+def test_library_bulk_matches_oracle():
+    from oracle import les_stats
+    cfg = inputs.preset("les_paper", stretch=1.5)
+    rng = np.random.default_rng(2)
+    prof = 10 + rng.uniform(0, 5, cfg["nz"])
+    a, b = les.bulk(cfg, prof), les_stats.bulk(prof, inputs.zfaces(cfg), cfg["nu"])
+    for k in a:
+        assert abs(a[k] - b[k]) <= 1e-12 * max(1.0, abs(b[k])), k
+
+
+def test_paper_initial_condition_is_divergence_free(orc):
+    """The paper's turbulent-like start: zero discrete divergence (the curl of
+    an edge potential), w = 0 at the walls, plane mean of u exactly U0/3."""
+    cfg = inputs.preset("les_paper", nx=24, ny=14, nz=12)
+    u, v, w = inputs.paper_les_initial(cfg, 3)
+    o = orc.Oracle(dict(cfg, omega=[1.0]))
+    scale = np.abs(u).max() / (cfg["Lx"] / cfg["nx"])
+    assert np.abs(o.divergence(u, v, w)).max() < 1e-13 * scale
+    assert np.abs(w[0]).max() == 0.0 and np.abs(w[-1]).max() == 0.0
+    zc = inputs.zcentres(cfg)
+    U0 = cfg["fx"] / (2 * cfg["nu"]) * zc * (cfg["Lz"] - zc)
+    assert np.allclose(u.mean(axis=(1, 2)), U0 / 3, atol=1e-12 * U0.max())
+    assert np.abs(v.mean(axis=(1, 2))).max() < 1e-12 * np.abs(v).max()
+    assert (u - u.mean(axis=(1, 2), keepdims=True)).std() > 1.0
