@@ -381,6 +381,9 @@ Geom<T> geom_from(const stp_handle* h, T* pack) {
   g.li = pack + 11 * L;
   g.lu = pack + 12 * L;
   g.ll = pack + 13 * L;
+  g.tli = pack + 14 * L;
+  g.tlf = pack + 15 * L;
+  g.tlb = pack + 16 * L;
   return g;
 }
 
@@ -421,6 +424,37 @@ std::vector<double> metric_pack(const stp_config& c) {
       m[12 * L + k] = cup[k] / mk;
       m[13 * L + k] = cdn[k] / mk;
       mprev = mk;
+    }
+    // twisted: top-down pivots m_k for k < t, bottom-up pivots
+    // m'_k = D_k - cup_k cdn_{k+1}/m'_{k+1} for k > t, and at the twist
+    // gamma_t = D_t - cdn_t cup_{t-1}/m_{t-1} - cup_t cdn_{t+1}/m'_{t+1}
+    const int t = nz / 2;
+    std::vector<double> mt(nz), mb(nz);
+    for (int k = 0; k < nz; k++) {
+      mt[k] = dxy + cup[k] + cdn[k];
+      if (k > 0) mt[k] -= cdn[k] * cup[k - 1] / mt[k - 1];
+    }
+    for (int k = nz - 1; k >= 0; k--) {
+      mb[k] = dxy + cup[k] + cdn[k];
+      if (k < nz - 1) mb[k] -= cup[k] * cdn[k + 1] / mb[k + 1];
+    }
+    for (int k = 0; k < nz; k++) {
+      if (k < t) {
+        m[14 * L + k] = 1.0 / mt[k];
+        m[15 * L + k] = cdn[k] / mt[k];
+        m[16 * L + k] = cup[k] / mt[k];
+      } else if (k > t) {
+        m[14 * L + k] = 1.0 / mb[k];
+        m[15 * L + k] = cup[k] / mb[k];
+        m[16 * L + k] = cdn[k] / mb[k];
+      } else {
+        double gam = dxy + cup[k] + cdn[k];
+        if (k > 0) gam -= cdn[k] * cup[k - 1] / mt[k - 1];
+        if (k < nz - 1) gam -= cup[k] * cdn[k + 1] / mb[k + 1];
+        m[14 * L + k] = 1.0 / gam;
+        m[15 * L + k] = cdn[k] / gam;
+        m[16 * L + k] = cup[k] / gam;
+      }
     }
   }
   for (int k = 0; k <= nz; k++) {

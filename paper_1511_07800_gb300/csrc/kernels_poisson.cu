@@ -373,14 +373,96 @@ __global__ void __launch_bounds__(128) k_line_sweep(Geom<T> g, const T* __restri
   }
 }
 
+// One direction of the twisted elimination or substitution on a column in
+// shared memory: x_k = R_k + c_k x_(previous k) for the n levels
+// k = k0, k0 + s, k0 + 2s, ..., each x_k stored over R_k; x enters as the
+// value before k0.  The loads of R and c run one batch (8 levels in FP32, 4
+// in FP64, to keep two blocks an SM) ahead of the dependent multiply-adds;
+// they never touch a level being stored.
+template <typename T>
+__device__ __forceinline__ void line_chain(T* __restrict__ R, int C, const T* __restrict__ c, int k0, int s, int n,
+                                           T x) {
+  constexpr int B = sizeof(T) == 8 ? 4 : 8;
+  T r[B], cc[B];
+#pragma unroll
+  for (int e = 0; e < B; e++) {
+    r[e] = cc[e] = T(0);
+    if (e < n) {
+      r[e] = R[(k0 + e * s) * C];
+      cc[e] = __ldg(c + k0 + e * s);
+    }
+  }
+  for (int q = 0; q < n; q += B) {
+    T rn[B], cn[B];
+#pragma unroll
+    for (int e = 0; e < B; e++) {
+      rn[e] = cn[e] = T(0);
+      if (q + B + e < n) {
+        rn[e] = R[(k0 + (q + B + e) * s) * C];
+        cn[e] = __ldg(c + k0 + (q + B + e) * s);
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < B; e++) {
+      if (q + e < n) {
+        x = r[e] + cc[e] * x;
+        R[(k0 + (q + e) * s) * C] = x;
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < B; e++) {
+      r[e] = rn[e];
+      cc[e] = cn[e];
+    }
+  }
+}
+
+// Phase 2 of the shared-memory line sweeps: the column systems A delta = r
+// by the twisted factorisation (Thomas elimination from both walls, meeting
+// at level t = nz/2), with R_k holding r_k times the twisted 1/pivot on
+// entry and delta_k on exit.  Threads [0, C) take the upper part of their
+// column (levels below t), threads [C, 2C) the lower part (above t); both
+// chains are nz/2 levels, half of one-sided Thomas.  Called by every thread
+// of the block (it holds block barriers); needs 2C <= blockDim.x.
+template <typename T>
+__device__ __forceinline__ void line_solve_twisted(const Geom<T>& g, T* R, int C) {
+  const int nz = g.nz, t = nz >> 1;
+  const int th = threadIdx.x, cl = th % C;
+  const bool top = th < C, work = th < 2 * C;
+  if (work) {
+    if (top)
+      line_chain<T>(R + cl, C, g.tlf, 0, 1, t, T(0));  // d_k, k = 0 .. t-1
+    else
+      line_chain<T>(R + cl, C, g.tlf, nz - 1, -1, nz - 1 - t, T(0));  // e_k, k = nz-1 .. t+1
+  }
+  __syncthreads();
+  T xt = T(0);
+  if (work) {
+    xt = R[t * C + cl];
+    if (t > 0) xt += __ldg(g.tlf + t) * R[(t - 1) * C + cl];
+    if (t < nz - 1) xt += __ldg(g.tlb + t) * R[(t + 1) * C + cl];
+  }
+  __syncthreads();
+  if (work) {
+    if (top) {
+      R[t * C + cl] = xt;
+      line_chain<T>(R + cl, C, g.tlb, t - 1, -1, t, xt);  // delta_k, k = t-1 .. 0
+    } else {
+      line_chain<T>(R + cl, C, g.tlb, t + 1, 1, nz - 1 - t, xt);  // delta_k, k = t+1 .. nz-1
+    }
+  }
+  __syncthreads();
+}
+
 // The same sweep with the column work staged in shared memory.  A block
 // owns C = 32 rb columns (32 consecutive x cells of rb rows) over all z
 // levels, and 512 threads.  Phase 1: every thread computes r = b - L p for
 // its column on one chunk of the levels (C columns x 512/C chunks, all
-// independent) into R[k][column].  Phase 2: C threads run the Thomas
-// elimination and back substitution of their columns in shared memory.
+// independent) into R[k][column].  Phase 2: 2C threads solve the columns
+// in shared memory by the twisted factorisation (line_solve_twisted).
 // Phase 3: every thread writes p - omega delta for its column and chunk.
-// Same arithmetic per cell as k_line_sweep.
+// The residual of each cell is formed as in k_line_sweep; the column solve
+// eliminates from both walls instead of from the bottom one.
 template <typename T>
 __global__ void __launch_bounds__(512) k_line_sweep_smem(Geom<T> g, const T* __restrict__ p,
                                                          const T* __restrict__ b, T omega, T* __restrict__ out,
@@ -410,27 +492,10 @@ __global__ void __launch_bounds__(512) k_line_sweep_smem(Geom<T> g, const T* __r
             idy2 * ((__ldg(p + lev + yp) - pc) + (__ldg(p + lev + ym) - pc));
     if (k < nz - 1) lap += __ldg(g.cup + k) * (__ldg(p + lev + plane + c0) - pc);
     if (k > 0) lap += __ldg(g.cdn + k) * (__ldg(p + lev - plane + c0) - pc);
-    R[k * C + col] = (__ldg(b + lev + c0) - lap) * __ldg(g.li + k);  // r_k / m_k
+    R[k * C + col] = (__ldg(b + lev + c0) - lap) * __ldg(g.tli + k);  // r_k / pivot_k
   }
   __syncthreads();
-  if (chunk == 0) {
-    // forward elimination, one multiply-add a level: d_k = r_k/m_k + (cdn_k/m_k) d_{k-1}
-    T dprev = T(0);
-#pragma unroll 8
-    for (int k = 0; k < nz; k++) {
-      const T d = R[k * C + col] + __ldg(g.ll + k) * dprev;
-      R[k * C + col] = d;
-      dprev = d;
-    }
-    T dnext = T(0);
-#pragma unroll 8
-    for (int k = nz - 1; k >= 0; k--) {
-      const T delta = R[k * C + col] + __ldg(g.lu + k) * dnext;
-      R[k * C + col] = delta;
-      dnext = delta;
-    }
-  }
-  __syncthreads();
+  line_solve_twisted<T>(g, R, C);
   if (act) {
 #pragma unroll 4
     for (int k = k0; k < k1; k++) {
@@ -503,7 +568,7 @@ __global__ void __launch_bounds__(512) k_line_sweep_vec(Geom<T> g, const T* __re
     const V zd = k > 0 ? __ldg(reinterpret_cast<const V*>(p + lev - plane + c0)) : c;
     const V bq = __ldg(reinterpret_cast<const V*>(b + lev + c0));
     const T left = __ldg(p + lev + xl), right = __ldg(p + lev + xr);
-    const T cup = __ldg(g.cup + k), cdn = __ldg(g.cdn + k), li = __ldg(g.li + k);
+    const T cup = __ldg(g.cup + k), cdn = __ldg(g.cdn + k), li = __ldg(g.tli + k);
     V o;
 #pragma unroll
     for (int e = 0; e < W; e++) {
@@ -518,24 +583,7 @@ __global__ void __launch_bounds__(512) k_line_sweep_vec(Geom<T> g, const T* __re
     *reinterpret_cast<V*>(R + k * C + col) = o;
   }
   __syncthreads();
-  if ((int)threadIdx.x < C) {
-    const int cl = threadIdx.x;
-    T dprev = T(0);
-#pragma unroll 8
-    for (int k = 0; k < nz; k++) {
-      const T d = R[k * C + cl] + __ldg(g.ll + k) * dprev;
-      R[k * C + cl] = d;
-      dprev = d;
-    }
-    T dnext = T(0);
-#pragma unroll 8
-    for (int k = nz - 1; k >= 0; k--) {
-      const T delta = R[k * C + cl] + __ldg(g.lu + k) * dnext;
-      R[k * C + cl] = delta;
-      dnext = delta;
-    }
-  }
-  __syncthreads();
+  line_solve_twisted<T>(g, R, C);
   if (act) {
 #pragma unroll 2
     for (int k = k0; k < k1; k++) {
