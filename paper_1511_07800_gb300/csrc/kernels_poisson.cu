@@ -558,14 +558,19 @@ __global__ void __launch_bounds__(512) k_line_sweep_vec(Geom<T> g, const T* __re
   const int col = jr * 32 + W * xu;
   const T idx2 = g.idx2, idy2 = g.idy2;
   cudaGridDependencySynchronize();
+  // the unit's own values at levels k - 1 and k ride along in registers
+  // (zd, c): each level loads only level k + 1 of the unit
+  V c = {}, zd = {};
+  if (k0 < k1) {
+    c = __ldg(reinterpret_cast<const V*>(p + (unsigned)k0 * plane + c0));
+    zd = k0 > 0 ? __ldg(reinterpret_cast<const V*>(p + (unsigned)(k0 - 1) * plane + c0)) : c;
+  }
 #pragma unroll 2
   for (int k = k0; k < k1; k++) {
     const unsigned lev = (unsigned)k * plane;
-    const V c = __ldg(reinterpret_cast<const V*>(p + lev + c0));
     const V yn = __ldg(reinterpret_cast<const V*>(p + lev + yp));
     const V ys = __ldg(reinterpret_cast<const V*>(p + lev + ym));
     const V zu = k < nz - 1 ? __ldg(reinterpret_cast<const V*>(p + lev + plane + c0)) : c;
-    const V zd = k > 0 ? __ldg(reinterpret_cast<const V*>(p + lev - plane + c0)) : c;
     const V bq = __ldg(reinterpret_cast<const V*>(b + lev + c0));
     const T left = __ldg(p + lev + xl), right = __ldg(p + lev + xr);
     const T cup = __ldg(g.cup + k), cdn = __ldg(g.cdn + k), li = __ldg(g.tli + k);
@@ -581,6 +586,8 @@ __global__ void __launch_bounds__(512) k_line_sweep_vec(Geom<T> g, const T* __re
       VT::set(o, e, (VT::get(bq, e) - lap) * li);
     }
     *reinterpret_cast<V*>(R + k * C + col) = o;
+    zd = c;
+    c = zu;
   }
   __syncthreads();
   line_solve_twisted<T>(g, R, C);
