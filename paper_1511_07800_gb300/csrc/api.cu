@@ -380,10 +380,9 @@ Geom<T> geom_from(const stp_handle* h, T* pack) {
   g.dzv = pack + 10 * L;
   g.li = pack + 11 * L;
   g.lu = pack + 12 * L;
-  g.ll = pack + 13 * L;
-  g.tli = pack + 14 * L;
-  g.tlf = pack + 15 * L;
-  g.tlb = pack + 16 * L;
+  g.tli = pack + 13 * L;
+  g.tlf = pack + 14 * L;
+  g.tlb = pack + 15 * L;
   return g;
 }
 
@@ -412,27 +411,21 @@ std::vector<double> metric_pack(const stp_config& c) {
     m[9 * L + k] = lm * lm;
     m[10 * L + k] = z.dz[k];
   }
-  // z-line Thomas pivots of A = -L_z + dxy I: diagonal dxy + cup + cdn,
-  // off-diagonals -cup (k+1) and -cdn (k-1); m_k = D_k - cdn_k cup_{k-1}/m_{k-1}
+  // z-line Thomas pivots of A = -L_z + dxy I: diagonal D_k = dxy + cup + cdn,
+  // off-diagonals -cup (k+1) and -cdn (k-1).  One-sided (from the bottom
+  // wall): m_k = D_k - cdn_k cup_{k-1}/m_{k-1}.  Twisted: those top-down
+  // pivots for k < t, bottom-up pivots m'_k = D_k - cup_k cdn_{k+1}/m'_{k+1}
+  // for k > t, and gamma_t = D_t - cdn_t cup_{t-1}/m_{t-1} -
+  // cup_t cdn_{t+1}/m'_{t+1} at the twist level t = nz/2.
   {
     const double dxy = 2.0 / (dx * dx) + 2.0 / (dy * dy);
-    double mprev = 1.0;
-    for (int k = 0; k < nz; k++) {
-      double mk = dxy + cup[k] + cdn[k];
-      if (k > 0) mk -= cdn[k] * cup[k - 1] / mprev;
-      m[11 * L + k] = 1.0 / mk;
-      m[12 * L + k] = cup[k] / mk;
-      m[13 * L + k] = cdn[k] / mk;
-      mprev = mk;
-    }
-    // twisted: top-down pivots m_k for k < t, bottom-up pivots
-    // m'_k = D_k - cup_k cdn_{k+1}/m'_{k+1} for k > t, and at the twist
-    // gamma_t = D_t - cdn_t cup_{t-1}/m_{t-1} - cup_t cdn_{t+1}/m'_{t+1}
     const int t = nz / 2;
     std::vector<double> mt(nz), mb(nz);
     for (int k = 0; k < nz; k++) {
       mt[k] = dxy + cup[k] + cdn[k];
       if (k > 0) mt[k] -= cdn[k] * cup[k - 1] / mt[k - 1];
+      m[11 * L + k] = 1.0 / mt[k];
+      m[12 * L + k] = cup[k] / mt[k];
     }
     for (int k = nz - 1; k >= 0; k--) {
       mb[k] = dxy + cup[k] + cdn[k];
@@ -440,20 +433,20 @@ std::vector<double> metric_pack(const stp_config& c) {
     }
     for (int k = 0; k < nz; k++) {
       if (k < t) {
-        m[14 * L + k] = 1.0 / mt[k];
-        m[15 * L + k] = cdn[k] / mt[k];
-        m[16 * L + k] = cup[k] / mt[k];
+        m[13 * L + k] = 1.0 / mt[k];
+        m[14 * L + k] = cdn[k] / mt[k];
+        m[15 * L + k] = cup[k] / mt[k];
       } else if (k > t) {
-        m[14 * L + k] = 1.0 / mb[k];
-        m[15 * L + k] = cup[k] / mb[k];
-        m[16 * L + k] = cdn[k] / mb[k];
+        m[13 * L + k] = 1.0 / mb[k];
+        m[14 * L + k] = cup[k] / mb[k];
+        m[15 * L + k] = cdn[k] / mb[k];
       } else {
         double gam = dxy + cup[k] + cdn[k];
         if (k > 0) gam -= cdn[k] * cup[k - 1] / mt[k - 1];
         if (k < nz - 1) gam -= cup[k] * cdn[k + 1] / mb[k + 1];
-        m[14 * L + k] = 1.0 / gam;
-        m[15 * L + k] = cdn[k] / gam;
-        m[16 * L + k] = cup[k] / gam;
+        m[13 * L + k] = 1.0 / gam;
+        m[14 * L + k] = cdn[k] / gam;
+        m[15 * L + k] = cup[k] / gam;
       }
     }
   }

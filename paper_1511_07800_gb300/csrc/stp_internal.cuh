@@ -40,7 +40,6 @@ struct Geom {
   const T* dzv;    // [nz]    dz
   const T* li;     // [nz]    z-line Thomas: 1/m_k, m_k the k-th pivot of A = -L_z + (2/dx^2 + 2/dy^2) I
   const T* lu;     // [nz]    z-line Thomas: cup_k/m_k
-  const T* ll;     // [nz]    z-line Thomas: cdn_k/m_k
   // z-line twisted factorisation of the same A, eliminated from both walls
   // towards the twist level t = nz/2 (top-down pivots m_k above it,
   // bottom-up pivots m'_k below, gamma_t at it):
@@ -50,7 +49,7 @@ struct Geom {
 };
 
 // Number of metric arrays packed into one device allocation per precision.
-constexpr int kMetricArrays = 17;
+constexpr int kMetricArrays = 16;
 
 // Reduction workspace (device).  Every reducing kernel writes one partial per
 // block, then the last block to finish sums the partials in block order, so
