@@ -174,6 +174,36 @@ def cpu_baseline_sample(cfg, fields, sweeps_per_step):
                       % (cfg["nx"], cfg["ny"], cfg["nz"], cycles * M, cycles, M, dt)}
 
 
+def _oracle_threads():
+    import oracle
+    oracle.set_threads(len(os.sched_getaffinity(0)))
+    return oracle.get_threads()
+
+
+def oracle_us_per_sweep(cfg, zline, seed=5):
+    """The oracle's time per SRJ sweep (point or z-line) on the grid of cfg,
+    on the host cores.  The oracle tests its sweep cap once per cycle, so
+    this times one and two whole cycles of a fixed 32-weight schedule from
+    the same seeded start, after a warm-up cycle: the difference is 32
+    sweeps and one residual evaluation (the set-up cancels)."""
+    import numpy as np
+
+    import oracle
+    o = oracle.Oracle(dict(cfg, omega=[0.8, 1.0] * 16, zline=zline))
+    rng = np.random.default_rng(seed)
+    shape = (cfg["nz"], cfg["ny"], cfg["nx"])
+    b = rng.standard_normal(shape)
+    p0 = rng.standard_normal(shape) * 0.1
+    o.poisson(b, p0, tol=0.0, maxit=1)
+    t = {}
+    for n in (32, 64):
+        t0 = time.perf_counter()
+        _, it, _, _ = o.poisson(b, p0, tol=0.0, maxit=n)
+        t[n] = time.perf_counter() - t0
+        assert it == n
+    return 1e6 * (t[64] - t[32]) / 32
+
+
 def learned_comparison(cfg, steps):
     """Poisson time to 1e-8, learned guess vs plain, on the workload grid:
     train the U-Net on (residual, correction) pairs harvested from channels
@@ -220,7 +250,7 @@ def learned_comparison(cfg, steps):
             "note": "time per pressure solve to 1e-8 (GPU events), previous-step pressure as the plain guess"}
 
 
-def batched_channels(steps, warmup, peak):
+def batched_channels(steps, warmup, peak, oracle_sample=True):
     """Uneven-channel batch: 64 instances with sizes drawn from
     {32, 48, 64, 96, 128}^3 (seed 2), Re uniform in [5000, 10000],
     Orr-Sommerfeld amplitude log-uniform in [1e-5, 1e-3], FP32 with FP64
@@ -251,6 +281,7 @@ def batched_channels(steps, warmup, peak):
                  "ms_per_step": st["gpu_ms"] / steps, "gpu_launches": st["kernels"],
                  "sweeps_per_step": st["sweeps"] / steps, "converged": st["converged"]}
             if mode == "grouped":
+                last_sweeps = [c["sweeps"] for c in st["channels"]]
                 groups = b.groups()
                 r["groups"] = groups
                 g = max(groups, key=lambda x: x["cells"]) if groups else None
@@ -277,10 +308,31 @@ def batched_channels(steps, warmup, peak):
                          "note": "each channel stepped on its own, one after another (wall clock)"}
     for ch in chans:
         ch.close()
+    if oracle_sample:
+        import oracle
+        from oracle import srj
+        cores = _oracle_threads()
+        cells_o, t_o, held = 0, 0.0, []
+        for (cfg, f), s_gpu in list(zip(inst, last_sweeps))[:4]:
+            om, _, _ = srj.schedule_for(cfg["nx"], cfg["ny"], cfg["nz"], cfg["Lx"], cfg["Ly"], cfg["Lz"],
+                                        cfg.get("stretch", 0.0))
+            n = max(1, int(round(s_gpu / len(om)))) * len(om)
+            o = oracle.Oracle(dict(cfg, omega=om, ptol=0.0, pmaxit=n))
+            o.set_fields(*f)
+            t0 = time.perf_counter()
+            o.step(1)
+            t_o += time.perf_counter() - t0
+            cells_o += cfg["nx"] * cfg["ny"] * cfg["nz"]
+            held.append("%dx%dx%d:%d" % (cfg["nx"], cfg["ny"], cfg["nz"], n))
+        out["cpu_baseline"] = {
+            "kind": "oracle", "cores": cores, "value": cells_o / t_o / 1e6, "unit": "Mcell*steps/s",
+            "sample": "one FP64 oracle step of each of the first 4 instances from their start fields, each solve "
+                      "held to its channel's GPU sweep count of the last grouped step in whole cycles "
+                      "(grid:sweeps %s); %.2f s" % (", ".join(held), t_o)}
     return out
 
 
-def les_line_vs_point(steps, warmup):
+def les_line_vs_point(steps, warmup, oracle_sample=True):
     """Pressure-solve time on the wall-stretched LES grid (256 x 128 x 192,
     tanh stretching 2, Smagorinsky, constant flux; FP32 with FP64
     refinement), point SRJ sweeps against z-line sweeps, from the same
@@ -305,10 +357,18 @@ def les_line_vs_point(steps, warmup):
                          "Mcell_steps_per_s_solve": cells * steps / (st["solve_ms"] / 1e3) / 1e6,
                          "converged": st["converged"]}
     out["solve_speedup_zline"] = out["point"]["solve_ms_per_step"] / out["zline"]["solve_ms_per_step"]
+    if oracle_sample:
+        cores = _oracle_threads()
+        ous = {name: oracle_us_per_sweep(cfg, zl) for name, zl in (("point", 0), ("zline", 1))}
+        out["cpu_baseline"] = {
+            "kind": "oracle", "cores": cores, "unit": "us per sweep", "point": ous["point"], "zline": ous["zline"],
+            "gpu_over_oracle": {n: ous[n] / out[n]["us_per_sweep"] for n in ous},
+            "sample": "FP64 oracle sweeps on the same grid: two 32-sweep cycles less one, over 32 (a sweep plus "
+                      "1/32 of a residual evaluation)"}
     return out
 
 
-def les_paper_steps(steps, warmup):
+def les_paper_steps(steps, warmup, oracle_sample=True):
     """The paper's LES workload (Sec. 5) at its own grid, 240 x 140 x 120,
     Lx = 8, Ly = 4, Lz = 1, Re_* = 360, dt = 1e-4, Smagorinsky + van Driest,
     FP32 with FP64 refinement, from its random Fourier-curl start; the
@@ -334,10 +394,29 @@ def les_paper_steps(steps, warmup):
         e1.record(stream)
         e1.synchronize()
         ms = e0.elapsed_time(e1)
-    return {"workload": "les_paper 240x140x120, Lx 8, Ly 4, Lz 1, Re_* 360, dt 1e-4, FP32 + FP64 refinement, "
-                        "statistics every step", "value": cells * steps / (ms / 1e3) / 1e6, "unit": "Mcell*steps/s",
-            "ms_per_step": ms / steps, "sweeps_per_step": sweeps / steps, "steps": steps,
-            "warmup": max(3, warmup), "converged": st["converged"]}
+    out = {"workload": "les_paper 240x140x120, Lx 8, Ly 4, Lz 1, Re_* 360, dt 1e-4, FP32 + FP64 refinement, "
+                       "statistics every step", "value": cells * steps / (ms / 1e3) / 1e6, "unit": "Mcell*steps/s",
+           "ms_per_step": ms / steps, "sweeps_per_step": sweeps / steps, "steps": steps,
+           "warmup": max(3, warmup), "converged": st["converged"]}
+    if oracle_sample:
+        import oracle
+        cores = _oracle_threads()
+        us = oracle_us_per_sweep(cfg, 0)
+        o = oracle.Oracle(dict(cfg, omega=[0.8, 1.0] * 16, ptol=0.0, pmaxit=32))
+        o.set_fields(*inputs.paper_les_initial(cfg, 1))
+        t0 = time.perf_counter()
+        o.step(1)
+        t_step = time.perf_counter() - t0
+        s_gpu = sweeps / steps
+        t_proj = t_step + max(0.0, s_gpu - 32) * us * 1e-6
+        out["cpu_baseline"] = {
+            "kind": "oracle", "cores": cores, "value": cells / t_proj / 1e6, "unit": "Mcell*steps/s",
+            "oracle_step_s_at_32_sweeps": t_step, "oracle_us_per_sweep": us,
+            "sample": "one FP64 oracle step of the same workload from the same start with its solve held to 32 "
+                      "sweeps (%.2f s), plus the oracle's measured time per sweep for the other %.0f of the "
+                      "GPU's %.0f sweeps a step (projected; once-per-cycle residual checks not added)"
+                      % (t_step, max(0.0, s_gpu - 32), s_gpu)}
+    return out
 
 
 def run_reference(args):
@@ -511,16 +590,17 @@ def run_ours(args):
             line["poisson_learned_vs_plain"] = {"error": str(ex)[:200]}
     if rank == 0 and world == 1 and not args.no_batch and args.grid is None:
         try:
-            line["batched_channels"] = batched_channels(max(3, min(args.steps, 10)), args.warmup, peak)
+            line["batched_channels"] = batched_channels(max(3, min(args.steps, 10)), args.warmup, peak,
+                                                        not args.no_cpu_baseline)
         except Exception as ex:  # report, never fake
             line["batched_channels"] = {"error": str(ex)[:200]}
     if rank == 0 and world == 1 and not args.no_les and args.grid is None:
         try:
-            line["les_pressure_solve"] = les_line_vs_point(3, 3)
+            line["les_pressure_solve"] = les_line_vs_point(3, 3, not args.no_cpu_baseline)
         except Exception as ex:  # report, never fake
             line["les_pressure_solve"] = {"error": str(ex)[:200]}
         try:
-            line["les_paper"] = les_paper_steps(10, 3)
+            line["les_paper"] = les_paper_steps(10, 3, not args.no_cpu_baseline)
         except Exception as ex:  # report, never fake
             line["les_paper"] = {"error": str(ex)[:200]}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

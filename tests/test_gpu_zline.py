@@ -114,3 +114,24 @@ def test_line_step_fp32_vs_fp64_oracle(stp_lib, orc, nx):
     for k, bd in bounds.items():
         e = rel_err(fg[k], fo[k]) if k != "p" else rel_err(fg[k] - fg[k].mean(), fo[k] - fo[k].mean())
         assert e < bd, (k, e)
+
+
+@pytest.mark.parametrize("nz", [2, 3, 5])
+@pytest.mark.parametrize("nx", [37, 64])
+def test_line_short_columns_parity(stp_lib, orc, nx, nz):
+    """Columns of 2, 3 and 5 levels: the twist level t = nz/2 sits next to
+    a wall (nz = 2 leaves the upper chain empty), on the cell kernel (37)
+    and the vector kernel (64).  An explicit schedule, 8 sweeps, FP64,
+    against the oracle's plain Thomas solves to 1e-10."""
+    cfg = case(nx=nx, ny=6, nz=nz, stretch=2.0, zline=1)
+    om = [0.6, 0.9, 0.7, 1.0]  # all below 2/mu_max: a contracting iteration
+    cfg["omega"] = om
+    b, rng = mean_free_rhs(cfg, 11)
+    p0 = rng.standard_normal(b.shape) * 0.1
+    o = orc.Oracle(cfg)
+    p_o, it_o, _, _ = o.poisson(b, p0, tol=0.0, maxit=8)
+    with stp_lib.Channel(cfg, omega=om) as ch:
+        p_g = p0.copy()
+        st = ch.poisson_solve(b, p_g, tol=0.0, maxit=8)
+    assert st["sweeps"] == it_o == 8
+    assert rel_err(p_g, p_o) < TOL64
