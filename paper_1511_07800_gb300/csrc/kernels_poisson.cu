@@ -375,45 +375,58 @@ __global__ void __launch_bounds__(128) k_line_sweep(Geom<T> g, const T* __restri
 
 // One direction of the twisted elimination or substitution on a column in
 // shared memory: x_k = R_k + c_k x_(previous k) for the n levels
-// k = k0, k0 + s, k0 + 2s, ..., each x_k stored over R_k; x enters as the
-// value before k0.  The loads of R and c run one batch (8 levels in FP32, 4
-// in FP64, to keep two blocks an SM) ahead of the dependent multiply-adds;
-// they never touch a level being stored.
-template <typename T>
-__device__ __forceinline__ void line_chain(T* __restrict__ R, int C, const T* __restrict__ c, int k0, int s, int n,
-                                           T x) {
+// k = k0, k0 + S, k0 + 2S, ..., each x_k stored over R_k; x enters as the
+// value before k0.  R points at level k0 of the column (levels C apart), c
+// at coefficient k0.  S and C are compile-time, so every access is a
+// register plus an immediate offset.  Whole batches of B levels (8 in FP32,
+// 4 in FP64, to keep two blocks an SM) run without bounds tests, their
+// loads one batch ahead of the dependent multiply-adds (never touching a
+// level being stored); the last n mod B levels run one at a time.
+template <typename T, int S, int C>
+__device__ __forceinline__ void line_chain(T* R, const T* __restrict__ c, int n, T x) {
   constexpr int B = sizeof(T) == 8 ? 4 : 8;
-  T r[B], cc[B];
-#pragma unroll
-  for (int e = 0; e < B; e++) {
-    r[e] = cc[e] = T(0);
-    if (e < n) {
-      r[e] = R[(k0 + e * s) * C];
-      cc[e] = __ldg(c + k0 + e * s);
-    }
-  }
-  for (int q = 0; q < n; q += B) {
-    T rn[B], cn[B];
+  int q = 0;
+  if (n >= B) {
+    T r[B], cc[B];
 #pragma unroll
     for (int e = 0; e < B; e++) {
-      rn[e] = cn[e] = T(0);
-      if (q + B + e < n) {
-        rn[e] = R[(k0 + (q + B + e) * s) * C];
-        cn[e] = __ldg(c + k0 + (q + B + e) * s);
+      r[e] = R[e * S * C];
+      cc[e] = __ldg(c + e * S);
+    }
+    for (; q + 2 * B <= n; q += B) {
+      T rn[B], cn[B];
+#pragma unroll
+      for (int e = 0; e < B; e++) {
+        rn[e] = R[(B + e) * S * C];
+        cn[e] = __ldg(c + (B + e) * S);
       }
-    }
 #pragma unroll
-    for (int e = 0; e < B; e++) {
-      if (q + e < n) {
+      for (int e = 0; e < B; e++) {
         x = r[e] + cc[e] * x;
-        R[(k0 + (q + e) * s) * C] = x;
+        R[e * S * C] = x;
       }
+#pragma unroll
+      for (int e = 0; e < B; e++) {
+        r[e] = rn[e];
+        cc[e] = cn[e];
+      }
+      R += B * S * C;
+      c += B * S;
     }
 #pragma unroll
     for (int e = 0; e < B; e++) {
-      r[e] = rn[e];
-      cc[e] = cn[e];
+      x = r[e] + cc[e] * x;
+      R[e * S * C] = x;
     }
+    R += B * S * C;
+    c += B * S;
+    q += B;
+  }
+  for (; q < n; q++) {
+    x = *R + __ldg(c) * x;
+    *R = x;
+    R += S * C;
+    c += S;
   }
 }
 
@@ -424,16 +437,16 @@ __device__ __forceinline__ void line_chain(T* __restrict__ R, int C, const T* __
 // column (levels below t), threads [C, 2C) the lower part (above t); both
 // chains are nz/2 levels, half of one-sided Thomas.  Called by every thread
 // of the block (it holds block barriers); needs 2C <= blockDim.x.
-template <typename T>
-__device__ __forceinline__ void line_solve_twisted(const Geom<T>& g, T* R, int C) {
+template <typename T, int C>
+__device__ __forceinline__ void line_solve_twisted(const Geom<T>& g, T* R) {
   const int nz = g.nz, t = nz >> 1;
   const int th = threadIdx.x, cl = th % C;
   const bool top = th < C, work = th < 2 * C;
   if (work) {
     if (top)
-      line_chain<T>(R + cl, C, g.tlf, 0, 1, t, T(0));  // d_k, k = 0 .. t-1
+      line_chain<T, 1, C>(R + cl, g.tlf, t, T(0));  // d_k, k = 0 .. t-1
     else
-      line_chain<T>(R + cl, C, g.tlf, nz - 1, -1, nz - 1 - t, T(0));  // e_k, k = nz-1 .. t+1
+      line_chain<T, -1, C>(R + (nz - 1) * C + cl, g.tlf + nz - 1, nz - 1 - t, T(0));  // e_k, k = nz-1 .. t+1
   }
   __syncthreads();
   T xt = T(0);
@@ -446,9 +459,9 @@ __device__ __forceinline__ void line_solve_twisted(const Geom<T>& g, T* R, int C
   if (work) {
     if (top) {
       R[t * C + cl] = xt;
-      line_chain<T>(R + cl, C, g.tlb, t - 1, -1, t, xt);  // delta_k, k = t-1 .. 0
+      line_chain<T, -1, C>(R + (t - 1) * C + cl, g.tlb + t - 1, t, xt);  // delta_k, k = t-1 .. 0
     } else {
-      line_chain<T>(R + cl, C, g.tlb, t + 1, 1, nz - 1 - t, xt);  // delta_k, k = t+1 .. nz-1
+      line_chain<T, 1, C>(R + (t + 1) * C + cl, g.tlb + t + 1, nz - 1 - t, xt);  // delta_k, k = t+1 .. nz-1
     }
   }
   __syncthreads();
@@ -463,13 +476,12 @@ __device__ __forceinline__ void line_solve_twisted(const Geom<T>& g, T* R, int C
 // Phase 3: every thread writes p - omega delta for its column and chunk.
 // The residual of each cell is formed as in k_line_sweep; the column solve
 // eliminates from both walls instead of from the bottom one.
-template <typename T>
+template <typename T, int RB>
 __global__ void __launch_bounds__(512) k_line_sweep_smem(Geom<T> g, const T* __restrict__ p,
-                                                         const T* __restrict__ b, T omega, T* __restrict__ out,
-                                                         int rb) {
+                                                         const T* __restrict__ b, T omega, T* __restrict__ out) {
   extern __shared__ __align__(16) unsigned char line_sm[];
   T* R = reinterpret_cast<T*>(line_sm);  // [nz][C]
-  const int C = 32 * rb, nchunk = blockDim.x / C;
+  constexpr int rb = RB, C = 32 * RB, nchunk = 512 / C;
   const int nx = g.nx, ny = g.ny, nz = g.nz;
   const int nxb = (nx + 31) / 32;
   const int i0 = (blockIdx.x % nxb) * 32, j0 = (blockIdx.x / nxb) * rb;
@@ -495,7 +507,7 @@ __global__ void __launch_bounds__(512) k_line_sweep_smem(Geom<T> g, const T* __r
     R[k * C + col] = (__ldg(b + lev + c0) - lap) * __ldg(g.tli + k);  // r_k / pivot_k
   }
   __syncthreads();
-  line_solve_twisted<T>(g, R, C);
+  line_solve_twisted<T, C>(g, R);
   if (act) {
 #pragma unroll 4
     for (int k = k0; k < k1; k++) {
@@ -533,15 +545,15 @@ struct VecOf<double> {
   }
 };
 
-template <typename T>
+template <typename T, int RB>
 __global__ void __launch_bounds__(512) k_line_sweep_vec(Geom<T> g, const T* __restrict__ p, const T* __restrict__ b,
-                                                        T omega, T* __restrict__ out, int rb) {
+                                                        T omega, T* __restrict__ out) {
   using VT = VecOf<T>;
   using V = typename VT::V;
   constexpr int W = VT::W, UPR = 32 / W;  // vector units per 32-cell row segment
   extern __shared__ __align__(16) unsigned char line_sm[];
   T* R = reinterpret_cast<T*>(line_sm);  // [nz][C]
-  const int C = 32 * rb, U = UPR * rb, nchunk = blockDim.x / U;
+  constexpr int rb = RB, C = 32 * RB, U = UPR * RB, nchunk = 512 / U;
   const int nx = g.nx, ny = g.ny, nz = g.nz;
   const int nxb = nx / 32;
   const int i0 = (blockIdx.x % nxb) * 32, j0 = (blockIdx.x / nxb) * rb;
@@ -590,7 +602,7 @@ __global__ void __launch_bounds__(512) k_line_sweep_vec(Geom<T> g, const T* __re
     c = zu;
   }
   __syncthreads();
-  line_solve_twisted<T>(g, R, C);
+  line_solve_twisted<T, C>(g, R);
   if (act) {
 #pragma unroll 2
     for (int k = k0; k < k1; k++) {
@@ -874,33 +886,42 @@ static int line_rows(int nz, size_t es) {
   return 0;
 }
 
+// the shared-memory line sweeps at RB rows per block (the vector kernel for
+// rows of whole 32-cell segments); raises their shared-memory limit once
+template <typename T, int RB>
+static cudaError_t launch_line_rows(const Geom<T>& g, const T* p, const T* b, T omega, T* out, cudaStream_t s,
+                                    cudaLaunchAttribute* attr) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_line_sweep_smem<T, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         96 * 1024);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_line_sweep_vec<T, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(((g.nx + 31) / 32) * ((g.ny + RB - 1) / RB)));
+  cfg.blockDim = dim3(512);
+  cfg.dynamicSmemBytes = (size_t)32 * RB * g.nz * sizeof(T);
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e = g.nx % 32 == 0 ? cudaLaunchKernelEx(&cfg, k_line_sweep_vec<T, RB>, g, p, b, omega, out)
+                                 : cudaLaunchKernelEx(&cfg, k_line_sweep_smem<T, RB>, g, p, b, omega, out);
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_line_sweep(const Geom<T>& g, const T* p, const T* b, T omega, T* out, cudaStream_t s) {
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;
-  const int rb = line_rows(g.nz, sizeof(T));
-  if (rb >= 1) {
-    const size_t smem = (size_t)32 * rb * g.nz * sizeof(T);
-    static bool attr_set = false;
-    if (!attr_set) {
-      cudaError_t e = cudaFuncSetAttribute(k_line_sweep_smem<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           96 * 1024);
-      if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_line_sweep_vec<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-      if (e != cudaSuccess) return e;
-      attr_set = true;
-    }
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(((g.nx + 31) / 32) * ((g.ny + rb - 1) / rb)));
-    cfg.blockDim = dim3(512);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    cudaError_t e = g.nx % 32 == 0 ? cudaLaunchKernelEx(&cfg, k_line_sweep_vec<T>, g, p, b, omega, out, rb)
-                                   : cudaLaunchKernelEx(&cfg, k_line_sweep_smem<T>, g, p, b, omega, out, rb);
-    return e != cudaSuccess ? e : cudaGetLastError();
+  switch (line_rows(g.nz, sizeof(T))) {
+    case 4: return launch_line_rows<T, 4>(g, p, b, omega, out, s, attr);
+    case 2: return launch_line_rows<T, 2>(g, p, b, omega, out, s, attr);
+    case 1: return launch_line_rows<T, 1>(g, p, b, omega, out, s, attr);
+    default: break;
   }
   const dim3 grid((g.nx + 127) / 128, g.ny), block(128);
   cudaLaunchConfig_t cfg = {};
