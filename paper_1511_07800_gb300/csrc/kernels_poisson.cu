@@ -521,9 +521,10 @@ __global__ void __launch_bounds__(512) k_line_sweep_smem(Geom<T> g, const T* __r
 // in FP32, double2 in FP64) of VW consecutive x cells: a thread handles one
 // unit of one row over a chunk of levels, with vector loads of the centre,
 // y and z neighbours and b, and scalar loads of the two x neighbours just
-// outside the unit.  For nx a multiple of 32 (whole 32-cell blocks of rows,
-// aligned vectors).  Phase 2 and the arithmetic per cell are those of
-// k_line_sweep_smem.
+// outside the unit.  For nx a multiple of the vector width (aligned
+// vectors); the last 32-cell segment of a row may be partial, its units past
+// the row end reading the row's last unit (in bounds) and storing nothing.
+// Phase 2 and the arithmetic per cell are those of k_line_sweep_smem.
 template <typename T>
 struct VecOf;
 template <>
@@ -555,17 +556,17 @@ __global__ void __launch_bounds__(512) k_line_sweep_vec(Geom<T> g, const T* __re
   T* R = reinterpret_cast<T*>(line_sm);  // [nz][C]
   constexpr int rb = RB, C = 32 * RB, U = UPR * RB, nchunk = 512 / U;
   const int nx = g.nx, ny = g.ny, nz = g.nz;
-  const int nxb = nx / 32;
+  const int nxb = (nx + 31) / 32;
   const int i0 = (blockIdx.x % nxb) * 32, j0 = (blockIdx.x / nxb) * rb;
   const int unit = threadIdx.x % U, chunk = threadIdx.x / U;
   const int jr = unit / UPR, xu = unit % UPR;
   const int i = i0 + W * xu, j = j0 + jr;
-  const bool act = j < ny;
-  const int jc = act ? j : ny - 1;
+  const bool act = i < nx && j < ny;
+  const int ic = i < nx ? i : nx - W, jc = j < ny ? j : ny - 1;  // in-bounds stand-ins for inactive units
   const unsigned plane = (unsigned)nx * ny;
-  const unsigned c0 = (unsigned)jc * nx + i;  // first cell of the unit
-  const unsigned yp = (unsigned)(jc == ny - 1 ? 0 : jc + 1) * nx + i, ym = (unsigned)(jc == 0 ? ny - 1 : jc - 1) * nx + i;
-  const unsigned xl = (unsigned)jc * nx + (i == 0 ? nx - 1 : i - 1), xr = (unsigned)jc * nx + (i + W == nx ? 0 : i + W);
+  const unsigned c0 = (unsigned)jc * nx + ic;  // first cell of the unit
+  const unsigned yp = (unsigned)(jc == ny - 1 ? 0 : jc + 1) * nx + ic, ym = (unsigned)(jc == 0 ? ny - 1 : jc - 1) * nx + ic;
+  const unsigned xl = (unsigned)jc * nx + (ic == 0 ? nx - 1 : ic - 1), xr = (unsigned)jc * nx + (ic + W == nx ? 0 : ic + W);
   const int k0 = chunk * nz / nchunk, k1 = (chunk + 1) * nz / nchunk;
   const int col = jr * 32 + W * xu;
   const T idx2 = g.idx2, idy2 = g.idy2;
@@ -886,8 +887,8 @@ static int line_rows(int nz, size_t es) {
   return 0;
 }
 
-// the shared-memory line sweeps at RB rows per block (the vector kernel for
-// rows of whole 32-cell segments); raises their shared-memory limit once
+// the shared-memory line sweeps at RB rows per block (the vector kernel when
+// rows hold whole vectors); raises their shared-memory limit once
 template <typename T, int RB>
 static cudaError_t launch_line_rows(const Geom<T>& g, const T* p, const T* b, T omega, T* out, cudaStream_t s,
                                     cudaLaunchAttribute* attr) {
@@ -907,8 +908,8 @@ static cudaError_t launch_line_rows(const Geom<T>& g, const T* p, const T* b, T 
   cfg.stream = s;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cudaError_t e = g.nx % 32 == 0 ? cudaLaunchKernelEx(&cfg, k_line_sweep_vec<T, RB>, g, p, b, omega, out)
-                                 : cudaLaunchKernelEx(&cfg, k_line_sweep_smem<T, RB>, g, p, b, omega, out);
+  cudaError_t e = g.nx % VecOf<T>::W == 0 ? cudaLaunchKernelEx(&cfg, k_line_sweep_vec<T, RB>, g, p, b, omega, out)
+                                          : cudaLaunchKernelEx(&cfg, k_line_sweep_smem<T, RB>, g, p, b, omega, out);
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
