@@ -291,7 +291,11 @@ long long stp_unet_param_count(void);
 
 /* Network for up to nmax samples of nz x ny x nx (each a multiple of 8, at
    least 8) on the current device; stream NULL: its own stream.  Parameters
-   start at zero: set them with stp_unet_set_params. */
+   start at zero: set them with stp_unet_set_params.  Its 3x3x3 convolutions
+   run on tcgen05 where a level's shape allows (STP_UNET_TC=0 at create:
+   mma.sync everywhere), a block computing 1, 2 or 4 z planes chosen by the
+   layer's shape (STP_UNET_TC_PLANES=<1|2|4> forces a count where it is
+   valid; the forward output does not depend on it). */
 int stp_unet_create(int nmax, int nz, int ny, int nx, void *stream, stp_unet **out);
 void stp_unet_destroy(stp_unet *net);
 const char *stp_unet_last_error(const stp_unet *net);

@@ -155,13 +155,15 @@ __global__ void __launch_bounds__(128) k_conv3(Dims dm, const bf16* __restrict__
 // accumulator), for layers whose level has w % 8 == 0 and h % 16 == 0 and
 // channel counts that are multiples of 16.
 //
-// A block computes 128 voxels, 8 (x) x 16 (y) at one z, for all cout
-// channels: M = 128, N = cout, K = 27 taps x cin.  The input is staged once
-// per group of up to 64 channels as a halo of 10 x 18 x 3 voxels (periodic
-// in x and y, zeros outside the walls) in the K-major core-matrix layout
-// without swizzle: 8-channel chunk j of halo voxel (hx, hy, hz) is 16 bytes
-// at j CHUNK + ((hz HY + hy) HX + hx) 16.  The A operand of tap (dz, dy, dx)
-// is then the descriptor whose start is the halo voxel (1+dx, 1+dy, 1+dz):
+// A block computes zt planes of 128 voxels, 8 (x) x 16 (y) at zt
+// consecutive z, for all cout channels: per plane M = 128, N = cout,
+// K = 27 taps x cin, the zt accumulators side by side in tensor memory.  The
+// input is staged once per group of up to 64 channels as a halo of
+// 10 x 18 x (zt + 2) voxels (periodic in x and y, zeros outside the walls)
+// in the K-major core-matrix layout without swizzle: 8-channel chunk j of
+// halo voxel (hx, hy, hz) is 16 bytes at j CHUNK + ((hz HY + hy) HX + hx) 16,
+// CHUNK = 16 HX HY (zt + 2).  The A operand of tap (dz, dy, dx) for plane p
+// is then the descriptor whose start is the halo voxel (1+dx, 1+dy, p+dz):
 // its 8-row core matrices are 8 consecutive x (16 bytes apart), the next 8
 // rows are the next y (SBO = 16 HX bytes), the next 8 channels the next
 // chunk (LBO = one chunk of the halo).  So the 27 taps need no data
@@ -175,9 +177,9 @@ __global__ void __launch_bounds__(128) k_conv3(Dims dm, const bf16* __restrict__
 // block barrier.  Every wait is bounded; on a time-out the block sets *err,
 // skips the rest, and still frees its tensor memory.
 // ---------------------------------------------------------------------------
-constexpr int TC_TX = 8, TC_TY = 16, TC_HX = 10, TC_HY = 18, TC_HZ = 3;
-constexpr int TC_CHUNK = TC_HX * TC_HY * TC_HZ * 16;  // bytes of one 8-channel chunk of the halo
-constexpr int TC_CG = 64;                             // channels per halo group
+constexpr int TC_TX = 8, TC_TY = 16, TC_HX = 10, TC_HY = 18;
+constexpr int TC_PLANE = TC_HX * TC_HY * 16;  // bytes of one halo plane of one 8-channel chunk
+constexpr int TC_CG = 64;                     // channels per halo group
 constexpr int TC_STAGES = 3;
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -218,13 +220,16 @@ __device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t parity) {
 __global__ void __launch_bounds__(128) k_conv3_tc(Dims dm, const bf16* __restrict__ x, int ldx, int cin,
                                                   const bf16* __restrict__ wt, const float* __restrict__ bias,
                                                   int cout, bf16* __restrict__ y, int ldy, int relu,
-                                                  const bf16* __restrict__ mask, int ldm, int resident, int* err) {
+                                                  const bf16* __restrict__ mask, int ldm, int resident, int zt,
+                                                  int* err) {
   extern __shared__ __align__(1024) uint8_t tsm[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int cgmax = cin < TC_CG ? cin : TC_CG;  // channels of the widest group
   const int stage_bytes = cout * cgmax * 2;     // one tap's weights of one group
+  const int hz_n = zt + 2;                      // halo planes
+  const int chunk = TC_PLANE * hz_n;            // bytes of one 8-channel chunk of the halo
   uint8_t* halo = tsm;
-  uint8_t* wst = tsm + (cgmax / 8) * TC_CHUNK;
+  uint8_t* wst = tsm + (cgmax / 8) * chunk;
   uint64_t* mbar = reinterpret_cast<uint64_t*>(wst + (resident ? 27 : TC_STAGES) * stage_bytes);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + TC_STAGES);
   volatile int* sfail = reinterpret_cast<volatile int*>(tslot + 1);
@@ -235,15 +240,16 @@ __global__ void __launch_bounds__(128) k_conv3_tc(Dims dm, const bf16* __restric
   b /= nxt;
   const int yt = (int)(b % nyt);
   b /= nyt;
-  const int z0 = (int)(b % dm.d);
-  const long long nn = b / dm.d;
+  const int nzt = dm.d / zt;
+  const int z0 = (int)(b % nzt) * zt;
+  const long long nn = b / nzt;
   const int x0 = xt * TC_TX, y0 = yt * TC_TY;
   if (tid == 0) {
     for (int s = 0; s < TC_STAGES; s++) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(mbar + s)));
     *sfail = 0;
   }
   int ncols = 32;
-  while (ncols < cout) ncols <<= 1;
+  while (ncols < zt * cout) ncols <<= 1;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)), "r"(ncols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -283,7 +289,7 @@ __global__ void __launch_bounds__(128) k_conv3_tc(Dims dm, const bf16* __restric
   auto load_halo = [&](int g) {
     const int c0 = g * TC_CG, nch = min(TC_CG, cin - c0) / 8;
     const uint32_t base = su32(halo);
-    for (int i = tid; i < TC_HX * TC_HY * TC_HZ; i += 128) {
+    for (int i = tid; i < TC_HX * TC_HY * hz_n; i += 128) {
       const int hx = i % TC_HX, hy = (i / TC_HX) % TC_HY, hz = i / (TC_HX * TC_HY);
       int gx = x0 - 1 + hx, gy = y0 - 1 + hy;
       const int gz = z0 - 1 + hz;
@@ -292,25 +298,28 @@ __global__ void __launch_bounds__(128) k_conv3_tc(Dims dm, const bf16* __restric
       const bool in = gz >= 0 && gz < dm.d;
       const long long v = ((nn * dm.d + (in ? gz : 0)) * dm.h + gy) * dm.w + gx;
       const bf16* src = x + v * ldx + c0;
-      const uint32_t dst = base + i * 16;  // chunk 0 of voxel (hx, hy, hz); chunk j is TC_CHUNK further
-      for (int j = 0; j < nch; j++) cp16(dst + j * TC_CHUNK, src + 8 * j, in);
+      const uint32_t dst = base + i * 16;  // chunk 0 of voxel (hx, hy, hz); chunk j is `chunk` further
+      for (int j = 0; j < nch; j++) cp16(dst + j * chunk, src + 8 * j, in);
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
   };
-  // the MMAs of step q (group q / 27, tap q % 27) with that tap's weights at b0
+  // the MMAs of step q (group q / 27, tap q % 27) for every plane, with that
+  // tap's weights at b0; plane p accumulates in columns [p cout, (p+1) cout)
   auto issue_tap = [&](int q, uint32_t b0) {
     const int g = q / 27, t = q % 27;
     const int c0 = g * TC_CG, nch = min(TC_CG, cin - c0) / 8;
     const int dz = t / 9, dy = (t / 3) % 3, dx = t % 3;  // halo offsets 0..2 (shift + 1)
     const uint32_t a0 = su32(halo) + ((dz * TC_HY + dy) * TC_HX + dx) * 16;
-    for (int kk = 0; kk < nch / 2; kk++) {
-      const uint64_t ad = tc_desc(a0 + 2 * kk * TC_CHUNK, TC_CHUNK, TC_HX * 16);
-      const uint64_t bd = tc_desc(b0 + 2 * kk * 128, 128, nch * 128);
-      const uint32_t acc = (q > 0 || kk > 0) ? 1u : 0u;
-      asm volatile(
-          "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-          "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-          "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+    for (int pl = 0; pl < zt; pl++) {
+      for (int kk = 0; kk < nch / 2; kk++) {
+        const uint64_t ad = tc_desc(a0 + pl * TC_PLANE + 2 * kk * chunk, chunk, TC_HX * 16);
+        const uint64_t bd = tc_desc(b0 + 2 * kk * 128, 128, nch * 128);
+        const uint32_t acc = (q > 0 || kk > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem + (uint32_t)(pl * cout)),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+      }
     }
   };
   auto commit = [&](int stage) {
@@ -385,38 +394,40 @@ __global__ void __launch_bounds__(128) k_conv3_tc(Dims dm, const bf16* __restric
     if (tid == 0) atomicExch(err, 1);
   } else {
     const int r = warp * 32 + lane;  // TMEM lane = output row
-    const long long v = ((nn * dm.d + z0) * dm.h + y0 + r / 8) * dm.w + x0 + (r % 8);
-    for (int c = 0; c < cout; c += 16) {
-      uint32_t a[16];
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-          : "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3]), "=r"(a[4]), "=r"(a[5]), "=r"(a[6]), "=r"(a[7]),
-            "=r"(a[8]), "=r"(a[9]), "=r"(a[10]), "=r"(a[11]), "=r"(a[12]), "=r"(a[13]), "=r"(a[14]), "=r"(a[15])
-          : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c));
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      uint32_t o[8];
+    for (int pl = 0; pl < zt; pl++) {
+      const long long v = ((nn * dm.d + z0 + pl) * dm.h + y0 + r / 8) * dm.w + x0 + (r % 8);
+      for (int c = 0; c < cout; c += 16) {
+        uint32_t a[16];
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3]), "=r"(a[4]), "=r"(a[5]), "=r"(a[6]), "=r"(a[7]),
+              "=r"(a[8]), "=r"(a[9]), "=r"(a[10]), "=r"(a[11]), "=r"(a[12]), "=r"(a[13]), "=r"(a[14]), "=r"(a[15])
+            : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(pl * cout + c)));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        uint32_t o[8];
 #pragma unroll
-      for (int h = 0; h < 8; h++) {
-        float v0 = __uint_as_float(a[2 * h]), v1 = __uint_as_float(a[2 * h + 1]);
-        const int co = c + 2 * h;
-        if (bias) {
-          v0 += bias[co];
-          v1 += bias[co + 1];
+        for (int h = 0; h < 8; h++) {
+          float v0 = __uint_as_float(a[2 * h]), v1 = __uint_as_float(a[2 * h + 1]);
+          const int co = c + 2 * h;
+          if (bias) {
+            v0 += bias[co];
+            v1 += bias[co + 1];
+          }
+          if (relu) {
+            v0 = fmaxf(v0, 0.f);
+            v1 = fmaxf(v1, 0.f);
+          }
+          if (mask) {
+            const bf16* mp = mask + v * ldm + co;
+            if (!(__bfloat162float(mp[0]) > 0.f)) v0 = 0.f;
+            if (!(__bfloat162float(mp[1]) > 0.f)) v1 = 0.f;
+          }
+          o[h] = pack2(__float2bfloat16(v0), __float2bfloat16(v1));
         }
-        if (relu) {
-          v0 = fmaxf(v0, 0.f);
-          v1 = fmaxf(v1, 0.f);
-        }
-        if (mask) {
-          const bf16* mp = mask + v * ldm + co;
-          if (!(__bfloat162float(mp[0]) > 0.f)) v0 = 0.f;
-          if (!(__bfloat162float(mp[1]) > 0.f)) v1 = 0.f;
-        }
-        o[h] = pack2(__float2bfloat16(v0), __float2bfloat16(v1));
+        uint4* yp = reinterpret_cast<uint4*>(y + v * ldy + c);
+        yp[0] = make_uint4(o[0], o[1], o[2], o[3]);
+        yp[1] = make_uint4(o[4], o[5], o[6], o[7]);
       }
-      uint4* yp = reinterpret_cast<uint4*>(y + v * ldy + c);
-      yp[0] = make_uint4(o[0], o[1], o[2], o[3]);
-      yp[1] = make_uint4(o[4], o[5], o[6], o[7]);
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -831,6 +842,7 @@ struct stp_unet {
   float out_scale = 1.f;                                   // the network predicts out_scale * dp / s
   int* d_err = nullptr;                                    // set by a tensor-core kernel whose wait timed out
   bool use_tc = true;                                      // tcgen05 convolutions where the shapes allow
+  int tc_planes = 0;                                       // planes a tcgen05 block computes (0: by layer shape)
   std::vector<void*> allocs;
   std::string err;
 };
@@ -867,17 +879,41 @@ int ualloc(stp_unet* n, T** p, size_t count) {
 // concat widths: decoder level l (0..2) input = kCh[l+1] + kCh[l]
 int cu_width(int l) { return kCh[l + 1] + kCh[l]; }
 
-// shared memory of k_conv3_tc: the halo of the widest channel group, then
-// the weights (all 27 taps of a group when resident, else three stages)
-size_t conv3_tc_smem(int cin, int cout, bool resident) {
+// shared memory of k_conv3_tc with zt planes a block: the halo of the
+// widest channel group, then the weights (all 27 taps of a group when
+// resident, else three stages)
+size_t conv3_tc_smem(int cin, int cout, bool resident, int zt) {
   const int cg = std::min(cin, TC_CG);
-  return (size_t)(cg / 8) * TC_CHUNK + (size_t)(resident ? 27 : TC_STAGES) * cout * cg * 2 + 64;
+  return (size_t)(cg / 8) * TC_PLANE * (zt + 2) + (size_t)(resident ? 27 : TC_STAGES) * cout * cg * 2 + 64;
 }
 constexpr size_t kTcSmemMax = 200 * 1024;
 
 bool conv3_tc_ok(const stp_unet* n, const Dims& dm, int ldx, int cin, int cout, int ldy) {
   return n->use_tc && dm.w % TC_TX == 0 && dm.h % TC_TY == 0 && cin % 16 == 0 && cout % 16 == 0 && cout <= 256 &&
-         ldx % 8 == 0 && ldy % 8 == 0 && conv3_tc_smem(cin, cout, false) <= kTcSmemMax;
+         ldx % 8 == 0 && ldy % 8 == 0 && conv3_tc_smem(cin, cout, false, 1) <= kTcSmemMax;
+}
+
+// planes a block of k_conv3_tc computes (measured on GB300 over the
+// network's layer shapes): 4 when the block stays within 64 KB of shared
+// memory (four blocks an SM) and the layer still has 1024 blocks; else 2
+// when it fits and leaves 512 blocks; else 1.  Always a divisor of the depth,
+// accumulators within 128 tensor-memory columns, and resident weights.  A
+// forced count (STP_UNET_TC_PLANES: 1, 2 or 4) is halved until it is valid.
+int conv3_tc_planes(const stp_unet* n, const Dims& dm, int cin, int cout, bool resident) {
+  if (!resident) return 1;
+  const long long tiles = dm.vox() / (TC_TX * TC_TY);
+  auto fits = [&](int zt, size_t smem_max, long long min_blocks) {
+    return dm.d % zt == 0 && zt * cout <= 128 && conv3_tc_smem(cin, cout, true, zt) <= smem_max &&
+           tiles / zt >= min_blocks;
+  };
+  if (n->tc_planes == 1 || n->tc_planes == 2 || n->tc_planes == 4) {
+    for (int zt = n->tc_planes; zt > 1; zt /= 2)
+      if (fits(zt, kTcSmemMax, 1)) return zt;
+    return 1;
+  }
+  if (fits(4, 64 * 1024, 1024)) return 4;
+  if (fits(2, kTcSmemMax, 512)) return 2;
+  return 1;
 }
 
 // launch a 3x3x3 convolution (forward form): tcgen05 where the shapes allow, else mma.sync
@@ -890,11 +926,11 @@ int conv3(stp_unet* n, const Dims& dm, const bf16* x, int ldx, int cin, const bf
       UTRY(n, cudaFuncSetAttribute(k_conv3_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmemMax));
       attr_set = true;
     }
-    const bool resident = conv3_tc_smem(cin, cout, true) <= kTcSmemMax;
-    const unsigned blocks = (unsigned)(V / (TC_TX * TC_TY));
-    k_conv3_tc<<<blocks, 128, conv3_tc_smem(cin, cout, resident), n->st>>>(dm, x, ldx, cin, wt, bias, cout, y, ldy,
-                                                                          relu, mask, ldm, resident ? 1 : 0,
-                                                                          n->d_err);
+    const bool resident = conv3_tc_smem(cin, cout, true, 1) <= kTcSmemMax;
+    const int zt = conv3_tc_planes(n, dm, cin, cout, resident);
+    const unsigned blocks = (unsigned)(V / (TC_TX * TC_TY * zt));
+    k_conv3_tc<<<blocks, 128, conv3_tc_smem(cin, cout, resident, zt), n->st>>>(
+        dm, x, ldx, cin, wt, bias, cout, y, ldy, relu, mask, ldm, resident ? 1 : 0, zt, n->d_err);
     UTRY(n, cudaGetLastError());
     return STP_OK;
   }
@@ -1190,6 +1226,7 @@ int stp_unet_create(int nmax, int nz, int ny, int nx, void* stream, stp_unet** o
   A(&n->loss, 1);
   A(&n->d_err, 1);
   if (const char* e = std::getenv("STP_UNET_TC")) n->use_tc = std::atoi(e) != 0;
+  if (const char* e = std::getenv("STP_UNET_TC_PLANES")) n->tc_planes = std::atoi(e);
   if (rc == STP_OK && cudaMallocHost((void**)&n->h_loss, sizeof(float)) != cudaSuccess) rc = STP_ENOMEM;
   if (rc == STP_OK) {
     cudaMemsetAsync(n->theta, 0, sizeof(float) * n->np, n->st);

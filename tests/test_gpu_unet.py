@@ -140,3 +140,33 @@ def test_tensor_core_conv_matches_mma_sync(stp_lib, orc, monkeypatch):
     assert abs(l1 - l0) < 1e-2 * l0
     assert np.linalg.norm(g1 - g0) < 5e-2 * np.linalg.norm(g0)
     assert g1 @ g0 / (np.linalg.norm(g1) * np.linalg.norm(g0)) > 0.998
+
+
+@pytest.mark.parametrize("planes", ["2", "4"])
+def test_tensor_core_planes_per_block(stp_lib, orc, monkeypatch, planes):
+    """tcgen05 blocks computing 2 or 4 z planes (one halo of planes + 2, one
+    weight load, one accumulator per plane in tensor memory) give the same
+    network as one plane a block: each plane's accumulator sees the same
+    sequence of MMAs, so the forward output is bitwise equal; the gradient
+    (its weight part accumulated with atomics) agrees to rounding.  Level 3
+    of this shape is 2 deep, so a forced 4 falls back to 2 there."""
+    torch = pytest.importorskip("torch")
+    unet, theta, x, t = _setup(4, (1, 8, 64, 32))
+    n, d, h, w = x.shape
+    tx = torch.from_numpy(x.astype(np.float32)).cuda()
+    tt = torch.from_numpy(t.astype(np.float32)).cuda()
+    out = {}
+    monkeypatch.setenv("STP_UNET_TC", "1")
+    for pl in ("1", planes):
+        monkeypatch.setenv("STP_UNET_TC_PLANES", pl)
+        net = stp_lib.UNet(n, d, h, w)
+        net.set_params(theta.astype(np.float32))
+        ty = torch.zeros_like(tx)
+        net.forward(tx, ty)
+        g = torch.zeros(stp_lib.UNet.param_count(), dtype=torch.float32, device="cuda")
+        net.gradient(tx, tt, g)
+        out[pl] = (ty.cpu().numpy(), g.cpu().numpy().astype(np.float64))
+        net.close()
+    (y1, g1), (yp, gp) = out["1"], out[planes]
+    assert np.array_equal(y1, yp)
+    assert np.linalg.norm(gp - g1) < 1e-5 * np.linalg.norm(g1)
