@@ -295,7 +295,10 @@ long long stp_unet_param_count(void);
    run on tcgen05 where a level's shape allows (STP_UNET_TC=0 at create:
    mma.sync everywhere), a block computing 1, 2 or 4 z planes chosen by the
    layer's shape (STP_UNET_TC_PLANES=<1|2|4> forces a count where it is
-   valid; the forward output does not depend on it). */
+   valid; the forward output does not depend on it).  The mma.sync ones take
+   64, 32, 16 or 8 output channels a block by grid size (STP_UNET_MMA_NT=
+   <8|4|2|1> forces a width where the channels allow; results do not depend
+   on it either). */
 int stp_unet_create(int nmax, int nz, int ny, int nx, void *stream, stp_unet **out);
 void stp_unet_destroy(stp_unet *net);
 const char *stp_unet_last_error(const stp_unet *net);

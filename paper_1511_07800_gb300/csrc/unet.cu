@@ -49,20 +49,35 @@ __device__ __forceinline__ unsigned pack2(bf16 lo, bf16 hi) {
 }
 
 // source voxel of v shifted by tap t (periodic y, x; -1 outside the walls)
-__device__ __forceinline__ long long tap_src(const Dims& dm, long long v, int t) {
-  const int x = (int)(v % dm.w);
-  long long r = v / dm.w;
-  const int y = (int)(r % dm.h);
-  r /= dm.h;
-  const int z = (int)(r % dm.d);
-  const long long n = r / dm.d;
-  const int z2 = z + t / 9 - 1;
+// voxel index (below 2^31, checked at creation) as sample and coordinates,
+// in 32-bit arithmetic
+struct Coord {
+  int n, z, y, x;
+};
+__device__ __forceinline__ Coord coord_of(const Dims& dm, unsigned v) {
+  Coord c;
+  c.x = (int)(v % (unsigned)dm.w);
+  v /= (unsigned)dm.w;
+  c.y = (int)(v % (unsigned)dm.h);
+  v /= (unsigned)dm.h;
+  c.z = (int)(v % (unsigned)dm.d);
+  c.n = (int)(v / (unsigned)dm.d);
+  return c;
+}
+__device__ __forceinline__ long long voxel_at(const Dims& dm, int n, int z, int y, int x) {
+  return ((long long)(n * dm.d + z) * dm.h + y) * dm.w + x;
+}
+
+// source voxel of tap t = (kz*3 + ky)*3 + kx at c: periodic in x and y,
+// -1 outside the walls in z
+__device__ __forceinline__ long long tap_from(const Dims& dm, const Coord& c, int t) {
+  const int z2 = c.z + t / 9 - 1;
   if (z2 < 0 || z2 >= dm.d) return -1;
-  int y2 = y + (t / 3) % 3 - 1;
-  int x2 = x + t % 3 - 1;
+  int y2 = c.y + (t / 3) % 3 - 1;
+  int x2 = c.x + t % 3 - 1;
   y2 = y2 < 0 ? y2 + dm.h : (y2 >= dm.h ? y2 - dm.h : y2);
   x2 = x2 < 0 ? x2 + dm.w : (x2 >= dm.w ? x2 - dm.w : x2);
-  return ((n * dm.d + z2) * dm.h + y2) * dm.w + x2;
+  return voxel_at(dm, c.n, z2, y2, x2);
 }
 
 // ---------------------------------------------------------------------------
@@ -89,13 +104,17 @@ __global__ void __launch_bounds__(128) k_conv3(Dims dm, const bf16* __restrict__
 #pragma unroll
     for (int n = 0; n < NT; n++) acc[m][n][0] = acc[m][n][1] = acc[m][n][2] = acc[m][n][3] = 0.f;
   long long vrow[4];
+  Coord crow[4];
 #pragma unroll
-  for (int r = 0; r < 4; r++) vrow[r] = vb + (r >> 1) * 16 + g + (r & 1) * 8;
+  for (int r = 0; r < 4; r++) {
+    vrow[r] = vb + (r >> 1) * 16 + g + (r & 1) * 8;
+    crow[r] = coord_of(dm, (unsigned)(vrow[r] < V ? vrow[r] : 0));
+  }
   const int kc = cin >> 4;
   for (int t = 0; t < 27; t++) {
     long long src[4];
 #pragma unroll
-    for (int r = 0; r < 4; r++) src[r] = vrow[r] < V ? tap_src(dm, vrow[r], t) : -1;
+    for (int r = 0; r < 4; r++) src[r] = vrow[r] < V ? tap_from(dm, crow[r], t) : -1;
     for (int c = 0; c < kc; c++) {
       unsigned a[2][4];
 #pragma unroll
@@ -447,12 +466,18 @@ __global__ void k_conv_in(Dims dm, const float* __restrict__ x, const float* __r
     float acc[16];
 #pragma unroll
     for (int o = 0; o < 16; o++) acc[o] = ws[16 * 27 + o];
-    for (int t = 0; t < 27; t++) {
-      const long long s = tap_src(dm, v, t);
-      if (s < 0) continue;
-      const float xv = __bfloat162float(__float2bfloat16(x[s]));
+    // the taps in order, one z plane of 9 at a time: its 9 inputs are loaded
+    // together, then multiplied in; planes outside the walls add nothing
+    const Coord cv = coord_of(dm, (unsigned)v);
+    for (int kz = 0; kz < 3; kz++) {
+      if (tap_from(dm, cv, kz * 9) < 0) continue;
+      float xt[9];
 #pragma unroll
-      for (int o = 0; o < 16; o++) acc[o] = fmaf(ws[o * 27 + t], xv, acc[o]);
+      for (int u = 0; u < 9; u++) xt[u] = __bfloat162float(__float2bfloat16(x[tap_from(dm, cv, kz * 9 + u)]));
+#pragma unroll
+      for (int u = 0; u < 9; u++)
+#pragma unroll
+        for (int o = 0; o < 16; o++) acc[o] = fmaf(ws[o * 27 + kz * 9 + u], xt[u], acc[o]);
     }
 #pragma unroll
     for (int o = 0; o < 16; o += 2)
@@ -553,7 +578,7 @@ __global__ void __launch_bounds__(128) k_wgrad3(Dims dm, const bf16* __restrict_
 #pragma unroll
     for (int i = 0; i < 4; i++) {
       const bool ok = vk[i] < v1;
-      sk[i] = ok ? tap_src(dm, vk[i], t) : -1;
+      sk[i] = ok ? tap_from(dm, coord_of(dm, (unsigned)vk[i]), t) : -1;
       gzv[0][i] = ok ? gz[vk[i] * ldg + ob + g] : zero;
       gzv[1][i] = ok ? gz[vk[i] * ldg + ob + g + 8] : zero;
     }
@@ -612,7 +637,7 @@ __global__ void k_wgrad_in(Dims dm, const float* __restrict__ x, const bf16* __r
   for (int o = 0; o < 16; o++) acc[o] = 0.f;
   const long long V = dm.vox();
   for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x) {
-    const long long s = tap_src(dm, v, t);
+    const long long s = tap_from(dm, coord_of(dm, (unsigned)v), t);
     if (s < 0) continue;
     const float xv = __bfloat162float(__float2bfloat16(x[s]));
 #pragma unroll
@@ -631,68 +656,87 @@ __global__ void k_wgrad_in(Dims dm, const float* __restrict__ x, const bf16* __r
 // ---------------------------------------------------------------------------
 // pooling, upsampling and the gradient plumbing between levels
 // ---------------------------------------------------------------------------
-// out (coarse) = mean of the 2x2x2 fine block; fine dims dm
+// Pooling and upsampling move whole voxels: a thread owns one voxel and all
+// its channels (c a multiple of 8; leading dimensions multiples of 8, so
+// every 8-channel vector is 16 bytes, aligned), in 32-bit index arithmetic.
+__device__ __forceinline__ void unpack8(const uint4& u, float* f) {
+  const unsigned w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+  for (int i = 0; i < 4; i++) {
+    f[2 * i] = __bfloat162float(__ushort_as_bfloat16((unsigned short)(w[i] & 0xFFFFu)));
+    f[2 * i + 1] = __bfloat162float(__ushort_as_bfloat16((unsigned short)(w[i] >> 16)));
+  }
+}
+__device__ __forceinline__ uint4 pack8(const float* f) {
+  return make_uint4(pack2(__float2bfloat16(f[0]), __float2bfloat16(f[1])),
+                    pack2(__float2bfloat16(f[2]), __float2bfloat16(f[3])),
+                    pack2(__float2bfloat16(f[4]), __float2bfloat16(f[5])),
+                    pack2(__float2bfloat16(f[6]), __float2bfloat16(f[7])));
+}
+__device__ __forceinline__ uint4 ld16(const bf16* p) { return *reinterpret_cast<const uint4*>(p); }
+__device__ __forceinline__ void st16(bf16* p, const uint4& u) { *reinterpret_cast<uint4*>(p) = u; }
+
+// out (coarse) = mean of the 2x2x2 fine block (summed in block order); fine dims dm
 __global__ void k_pool(Dims dm, const bf16* __restrict__ x, int ldx, int c, bf16* __restrict__ y, int ldy) {
   const Dims cd{dm.n, dm.d / 2, dm.h / 2, dm.w / 2};
-  const long long total = cd.vox() * c;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
-    const int ch = (int)(e % c);
-    long long v = e / c;
-    const int xx = (int)(v % cd.w);
-    long long r = v / cd.w;
-    const int yy = (int)(r % cd.h);
-    r /= cd.h;
-    const int zz = (int)(r % cd.d);
-    const long long n = r / cd.d;
-    float s = 0.f;
+  const unsigned V = (unsigned)cd.vox();
+  for (unsigned v = blockIdx.x * blockDim.x + threadIdx.x; v < V; v += gridDim.x * blockDim.x) {
+    const Coord q = coord_of(cd, v);
+    long long f[8];
 #pragma unroll
-    for (int k = 0; k < 8; k++) {
-      const long long f = ((n * dm.d + 2 * zz + (k >> 2)) * dm.h + 2 * yy + ((k >> 1) & 1)) * dm.w + 2 * xx + (k & 1);
-      s += __bfloat162float(x[f * ldx + ch]);
+    for (int k = 0; k < 8; k++)
+      f[k] = voxel_at(dm, q.n, 2 * q.z + (k >> 2), 2 * q.y + ((k >> 1) & 1), 2 * q.x + (k & 1));
+    for (int ch = 0; ch < c; ch += 8) {
+      float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, e[8];
+#pragma unroll
+      for (int k = 0; k < 8; k++) {
+        unpack8(ld16(x + f[k] * ldx + ch), e);
+#pragma unroll
+        for (int i = 0; i < 8; i++) s[i] += e[i];
+      }
+#pragma unroll
+      for (int i = 0; i < 8; i++) s[i] *= 0.125f;
+      st16(y + (long long)v * ldy + ch, pack8(s));
     }
-    y[v * ldy + ch] = __float2bfloat16(s * 0.125f);
   }
 }
 
 // fine = coarse value (nearest); coarse dims cd
 __global__ void k_upsample(Dims cd, const bf16* __restrict__ x, int ldx, int c, bf16* __restrict__ y, int ldy) {
   const Dims fd{cd.n, cd.d * 2, cd.h * 2, cd.w * 2};
-  const long long total = fd.vox() * c;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
-    const int ch = (int)(e % c);
-    long long v = e / c;
-    const int xx = (int)(v % fd.w);
-    long long r = v / fd.w;
-    const int yy = (int)(r % fd.h);
-    r /= fd.h;
-    const int zz = (int)(r % fd.d);
-    const long long n = r / fd.d;
-    const long long cv = ((n * cd.d + zz / 2) * cd.h + yy / 2) * cd.w + xx / 2;
-    y[v * ldy + ch] = x[cv * ldx + ch];
+  const unsigned V = (unsigned)fd.vox();
+  for (unsigned v = blockIdx.x * blockDim.x + threadIdx.x; v < V; v += gridDim.x * blockDim.x) {
+    const Coord q = coord_of(fd, v);
+    const long long cv = voxel_at(cd, q.n, q.z / 2, q.y / 2, q.x / 2);
+    for (int ch = 0; ch < c; ch += 8) st16(y + (long long)v * ldy + ch, ld16(x + cv * ldx + ch));
   }
 }
 
-// coarse gradient of an upsample = sum over the fine block, times (act > 0)
+// coarse gradient of an upsample = sum over the fine block (in block
+// order), times (act > 0)
 __global__ void k_upsample_bwd_mask(Dims cd, const bf16* __restrict__ gf, int ldg, int c, const bf16* __restrict__ act,
                                     int lda, bf16* __restrict__ out, int ldo) {
   const Dims fd{cd.n, cd.d * 2, cd.h * 2, cd.w * 2};
-  const long long total = cd.vox() * c;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
-    const int ch = (int)(e % c);
-    long long v = e / c;
-    const int xx = (int)(v % cd.w);
-    long long r = v / cd.w;
-    const int yy = (int)(r % cd.h);
-    r /= cd.h;
-    const int zz = (int)(r % cd.d);
-    const long long n = r / cd.d;
-    float s = 0.f;
+  const unsigned V = (unsigned)cd.vox();
+  for (unsigned v = blockIdx.x * blockDim.x + threadIdx.x; v < V; v += gridDim.x * blockDim.x) {
+    const Coord q = coord_of(cd, v);
+    long long f[8];
 #pragma unroll
-    for (int k = 0; k < 8; k++) {
-      const long long f = ((n * fd.d + 2 * zz + (k >> 2)) * fd.h + 2 * yy + ((k >> 1) & 1)) * fd.w + 2 * xx + (k & 1);
-      s += __bfloat162float(gf[f * ldg + ch]);
+    for (int k = 0; k < 8; k++)
+      f[k] = voxel_at(fd, q.n, 2 * q.z + (k >> 2), 2 * q.y + ((k >> 1) & 1), 2 * q.x + (k & 1));
+    for (int ch = 0; ch < c; ch += 8) {
+      float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, e[8], a[8];
+#pragma unroll
+      for (int k = 0; k < 8; k++) {
+        unpack8(ld16(gf + f[k] * ldg + ch), e);
+#pragma unroll
+        for (int i = 0; i < 8; i++) s[i] += e[i];
+      }
+      unpack8(ld16(act + (long long)v * lda + ch), a);
+#pragma unroll
+      for (int i = 0; i < 8; i++) s[i] = a[i] > 0.f ? s[i] : 0.f;
+      st16(out + (long long)v * ldo + ch, pack8(s));
     }
-    out[v * ldo + ch] = __float2bfloat16(__bfloat162float(act[v * lda + ch]) > 0.f ? s : 0.f);
   }
 }
 
@@ -702,19 +746,22 @@ __global__ void k_pool_bwd_add_mask(Dims fd, const bf16* __restrict__ gc, int ld
                                     int lds, int c, const bf16* __restrict__ act, int lda, bf16* __restrict__ out,
                                     int ldo) {
   const Dims cd{fd.n, fd.d / 2, fd.h / 2, fd.w / 2};
-  const long long total = fd.vox() * c;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
-    const int ch = (int)(e % c);
-    long long v = e / c;
-    const int xx = (int)(v % fd.w);
-    long long r = v / fd.w;
-    const int yy = (int)(r % fd.h);
-    r /= fd.h;
-    const int zz = (int)(r % fd.d);
-    const long long n = r / fd.d;
-    const long long cv = ((n * cd.d + zz / 2) * cd.h + yy / 2) * cd.w + xx / 2;
-    const float s = 0.125f * __bfloat162float(gc[cv * ldc + ch]) + __bfloat162float(gskip[v * lds + ch]);
-    out[v * ldo + ch] = __float2bfloat16(__bfloat162float(act[v * lda + ch]) > 0.f ? s : 0.f);
+  const unsigned V = (unsigned)fd.vox();
+  for (unsigned v = blockIdx.x * blockDim.x + threadIdx.x; v < V; v += gridDim.x * blockDim.x) {
+    const Coord q = coord_of(fd, v);
+    const long long cv = voxel_at(cd, q.n, q.z / 2, q.y / 2, q.x / 2);
+    for (int ch = 0; ch < c; ch += 8) {
+      float g[8], k[8], a[8], s[8];
+      unpack8(ld16(gc + cv * ldc + ch), g);
+      unpack8(ld16(gskip + (long long)v * lds + ch), k);
+      unpack8(ld16(act + (long long)v * lda + ch), a);
+#pragma unroll
+      for (int i = 0; i < 8; i++) {
+        const float t = 0.125f * g[i] + k[i];
+        s[i] = a[i] > 0.f ? t : 0.f;
+      }
+      st16(out + (long long)v * ldo + ch, pack8(s));
+    }
   }
 }
 
@@ -843,6 +890,7 @@ struct stp_unet {
   int* d_err = nullptr;                                    // set by a tensor-core kernel whose wait timed out
   bool use_tc = true;                                      // tcgen05 convolutions where the shapes allow
   int tc_planes = 0;                                       // planes a tcgen05 block computes (0: by layer shape)
+  int mma_nt = 0;                                          // mma.sync 8-channel tiles a block (0: by grid size)
   std::vector<void*> allocs;
   std::string err;
 };
@@ -934,13 +982,37 @@ int conv3(stp_unet* n, const Dims& dm, const bf16* x, int ldx, int cin, const bf
     UTRY(n, cudaGetLastError());
     return STP_OK;
   }
+  // output channels a block: 64, 32, 16 or 8, the widest that still gives two
+  // blocks an SM (small levels have few 128-voxel rows); each output sees the
+  // same sequence of MMAs whichever width computes it (STP_UNET_MMA_NT =
+  // 8, 4, 2 or 1 forces a width where the channel count allows it)
   const unsigned gx = (unsigned)((V + 127) / 128);
-  if (cout % 64 == 0) {
-    k_conv3<8><<<dim3(gx, cout / 64), 128, 0, n->st>>>(dm, x, ldx, cin, wt, bias, cout, y, ldy, relu, mask, ldm);
-  } else if (cout == 32) {
-    k_conv3<4><<<dim3(gx, 1), 128, 0, n->st>>>(dm, x, ldx, cin, wt, bias, cout, y, ldy, relu, mask, ldm);
-  } else {
-    k_conv3<2><<<dim3(gx, (cout + 15) / 16), 128, 0, n->st>>>(dm, x, ldx, cin, wt, bias, cout, y, ldy, relu, mask,
+  const long long enough = 2LL * 152;
+  int nt = n->mma_nt;
+  if (nt != 8 && nt != 4 && nt != 2 && nt != 1) {
+    nt = 1;
+    for (int c = 8; c > 1; c /= 2)
+      if (cout % (8 * c) == 0 && (long long)gx * (cout / (8 * c)) >= enough) {
+        nt = c;
+        break;
+      }
+    if (nt == 1 && (long long)gx * ((cout + 15) / 16) >= enough) nt = 2;
+  }
+  if (nt == 8 && cout % 64) nt = 4;
+  if (nt == 4 && cout % 32) nt = 2;
+  switch (nt) {
+    case 8:
+      k_conv3<8><<<dim3(gx, cout / 64), 128, 0, n->st>>>(dm, x, ldx, cin, wt, bias, cout, y, ldy, relu, mask, ldm);
+      break;
+    case 4:
+      k_conv3<4><<<dim3(gx, cout / 32), 128, 0, n->st>>>(dm, x, ldx, cin, wt, bias, cout, y, ldy, relu, mask, ldm);
+      break;
+    case 2:
+      k_conv3<2><<<dim3(gx, (cout + 15) / 16), 128, 0, n->st>>>(dm, x, ldx, cin, wt, bias, cout, y, ldy, relu, mask,
+                                                                 ldm);
+      break;
+    default:
+      k_conv3<1><<<dim3(gx, (cout + 7) / 8), 128, 0, n->st>>>(dm, x, ldx, cin, wt, bias, cout, y, ldy, relu, mask,
                                                                ldm);
   }
   UTRY(n, cudaGetLastError());
@@ -999,7 +1071,7 @@ int forward(stp_unet* n, const float* x, int nb) {
     const int lde = l < 3 ? cu_width(l) : c;
     if ((rc = conv3(n, dm[l], n->ha[l], c, c, lb.wt, n->theta + lb.boff, c, e, lde, 1, nullptr, 0))) return rc;
     if (l < 3) {
-      k_pool<<<blocks_for(dm[l + 1].vox() * c), 256, 0, n->st>>>(dm[l], e, lde, c, n->q[l], c);
+      k_pool<<<blocks_for(dm[l + 1].vox()), 256, 0, n->st>>>(dm[l], e, lde, c, n->q[l], c);
       UTRY(n, cudaGetLastError());
       in = n->q[l];
       ldin = c;
@@ -1010,7 +1082,7 @@ int forward(stp_unet* n, const float* x, int nb) {
   int cdeep = kCh[3];
   for (int l = 2; l >= 0; l--) {
     const int c = kCh[l], cw = cu_width(l);
-    k_upsample<<<blocks_for(dm[l].vox() * cdeep), 256, 0, n->st>>>(dm[l + 1], deeper, cdeep, cdeep, n->u[l], cw);
+    k_upsample<<<blocks_for(dm[l].vox()), 256, 0, n->st>>>(dm[l + 1], deeper, cdeep, cdeep, n->u[l], cw);
     UTRY(n, cudaGetLastError());
     const Layer& la = P[8 + 2 * (2 - l)];
     const Layer& lb = P[9 + 2 * (2 - l)];
@@ -1053,7 +1125,7 @@ int backward(stp_unet* n, const float* x, int nb) {
     const int cd = kCh[l + 1];
     const bf16* act = l < 2 ? n->d[l + 1] : n->e4;
     bf16* out = l < 2 ? n->ga[l + 1] : n->ga[3];
-    k_upsample_bwd_mask<<<blocks_for(dm[l + 1].vox() * cd), 256, 0, n->st>>>(dm[l + 1], n->gu[l], cw, cd, act, cd, out,
+    k_upsample_bwd_mask<<<blocks_for(dm[l + 1].vox()), 256, 0, n->st>>>(dm[l + 1], n->gu[l], cw, cd, act, cd, out,
                                                                               cd);
     UTRY(n, cudaGetLastError());
   }
@@ -1071,7 +1143,7 @@ int backward(stp_unet* n, const float* x, int nb) {
     if (l < 3) {
       // gz = (pool backward of the gradient of q_l + skip gradient) * (e_l > 0)
       const bf16* e = n->u[l] + kCh[l + 1];
-      k_pool_bwd_add_mask<<<blocks_for(dm[l].vox() * c), 256, 0, n->st>>>(dm[l], gq_in, c, n->gu[l] + kCh[l + 1],
+      k_pool_bwd_add_mask<<<blocks_for(dm[l].vox()), 256, 0, n->st>>>(dm[l], gq_in, c, n->gu[l] + kCh[l + 1],
                                                                             cu_width(l), c, e, cu_width(l), gz, c);
       UTRY(n, cudaGetLastError());
     }
@@ -1153,6 +1225,7 @@ int stp_unet_create(int nmax, int nz, int ny, int nx, void* stream, stp_unet** o
   if (!out) return STP_EINVAL;
   *out = nullptr;
   if (nmax < 1 || nz < 8 || ny < 8 || nx < 8 || nz % 8 || ny % 8 || nx % 8) return STP_EINVAL;
+  if ((double)nmax * nz * ny * nx > 2147483647.0) return STP_EINVAL;  // voxel indices are 32-bit
   stp_unet* n = new stp_unet();
   n->nmax = nmax;
   for (int l = 0; l < 4; l++) n->dm[l] = Dims{nmax, nz >> l, ny >> l, nx >> l};
@@ -1227,6 +1300,7 @@ int stp_unet_create(int nmax, int nz, int ny, int nx, void* stream, stp_unet** o
   A(&n->d_err, 1);
   if (const char* e = std::getenv("STP_UNET_TC")) n->use_tc = std::atoi(e) != 0;
   if (const char* e = std::getenv("STP_UNET_TC_PLANES")) n->tc_planes = std::atoi(e);
+  if (const char* e = std::getenv("STP_UNET_MMA_NT")) n->mma_nt = std::atoi(e);
   if (rc == STP_OK && cudaMallocHost((void**)&n->h_loss, sizeof(float)) != cudaSuccess) rc = STP_ENOMEM;
   if (rc == STP_OK) {
     cudaMemsetAsync(n->theta, 0, sizeof(float) * n->np, n->st);

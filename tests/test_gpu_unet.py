@@ -170,3 +170,33 @@ def test_tensor_core_planes_per_block(stp_lib, orc, monkeypatch, planes):
     (y1, g1), (yp, gp) = out["1"], out[planes]
     assert np.array_equal(y1, yp)
     assert np.linalg.norm(gp - g1) < 1e-5 * np.linalg.norm(g1)
+
+
+def test_mma_sync_widths_bitwise(stp_lib, orc, monkeypatch):
+    """The mma.sync convolutions with 64, 32, 16 or 8 output channels a
+    block (forced; the library picks by grid size) compute every output
+    with the same sequence of MMAs: forward outputs are bitwise equal; the
+    loss and the gradient, which sum with atomics, agree to rounding."""
+    torch = pytest.importorskip("torch")
+    unet, theta, x, t = _setup(5, (1, 8, 64, 32))
+    n, d, h, w = x.shape
+    tx = torch.from_numpy(x.astype(np.float32)).cuda()
+    tt = torch.from_numpy(t.astype(np.float32)).cuda()
+    monkeypatch.setenv("STP_UNET_TC", "0")
+    out = {}
+    for nt in ("8", "4", "2", "1"):
+        monkeypatch.setenv("STP_UNET_MMA_NT", nt)
+        net = stp_lib.UNet(n, d, h, w)
+        net.set_params(theta.astype(np.float32))
+        ty = torch.zeros_like(tx)
+        net.forward(tx, ty)
+        g = torch.zeros(stp_lib.UNet.param_count(), dtype=torch.float32, device="cuda")
+        loss = net.gradient(tx, tt, g)
+        out[nt] = (ty.cpu().numpy(), g.cpu().numpy().astype(np.float64), loss)
+        net.close()
+    y8, g8, l8 = out["8"]
+    for nt in ("4", "2", "1"):
+        y, g, l = out[nt]
+        assert np.array_equal(y, y8), nt
+        assert abs(l - l8) <= 1e-6 * l8, nt
+        assert np.linalg.norm(g - g8) < 1e-5 * np.linalg.norm(g8), nt
