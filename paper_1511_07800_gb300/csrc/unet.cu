@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(128) k_conv3_tc(Dims dm, const bf16* __restric
                                                   const bf16* __restrict__ wt, const float* __restrict__ bias,
                                                   int cout, bf16* __restrict__ y, int ldy, int relu,
                                                   const bf16* __restrict__ mask, int ldm, int resident, int zt,
-                                                  int* err) {
+                                                  const bf16* __restrict__ wimg, int* err) {
   extern __shared__ __align__(1024) uint8_t tsm[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int cgmax = cin < TC_CG ? cin : TC_CG;  // channels of the widest group
@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(128) k_conv3_tc(Dims dm, const bf16* __restric
   uint8_t* halo = tsm;
   uint8_t* wst = tsm + (cgmax / 8) * chunk;
   uint64_t* mbar = reinterpret_cast<uint64_t*>(wst + (resident ? 27 : TC_STAGES) * stage_bytes);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + TC_STAGES);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + TC_STAGES + 1);  // mbar[TC_STAGES]: the bulk weight copy
   volatile int* sfail = reinterpret_cast<volatile int*>(tslot + 1);
   // block -> tile
   const int nxt = dm.w / TC_TX, nyt = dm.h / TC_TY;
@@ -264,7 +264,8 @@ __global__ void __launch_bounds__(128) k_conv3_tc(Dims dm, const bf16* __restric
   const long long nn = b / nzt;
   const int x0 = xt * TC_TX, y0 = yt * TC_TY;
   if (tid == 0) {
-    for (int s = 0; s < TC_STAGES; s++) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(mbar + s)));
+    for (int s = 0; s <= TC_STAGES; s++) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(mbar + s)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     *sfail = 0;
   }
   int ncols = 32;
@@ -356,11 +357,30 @@ __global__ void __launch_bounds__(128) k_conv3_tc(Dims dm, const bf16* __restric
   bool ok = true;
   if (resident) {
     for (int g = 0; g < ngroups && ok; g++) {
-      load_halo(g);
-      load_w_all(g);
+      if (wimg) {
+        // the group's 27 taps, pre-arranged in this layout, as one bulk copy
+        if (tid == 0) {
+          const uint32_t bytes = 27u * (uint32_t)stage_bytes;
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(mbar + TC_STAGES)),
+                       "r"(bytes)
+                       : "memory");
+          asm volatile(
+              "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(su32(wst)),
+              "l"(wimg + (size_t)g * 27 * (stage_bytes / 2)), "r"(bytes), "r"(su32(mbar + TC_STAGES))
+              : "memory");
+        }
+        load_halo(g);
+      } else {
+        load_halo(g);
+        load_w_all(g);
+      }
       asm volatile("cp.async.wait_group 0;" ::: "memory");
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncthreads();
+      if (wimg && !block_wait(TC_STAGES, g & 1)) {
+        ok = false;
+        break;
+      }
       if (tid == 0) {
         for (int t = 0; t < 27; t++) issue_tap(g * 27 + t, su32(wst + t * stage_bytes));
         commit(0);
@@ -780,6 +800,30 @@ __global__ void k_pack_weights(const float* __restrict__ w, int cout, int cin, b
   }
 }
 
+// wt [t][cout][cin] (BF16) -> the resident weights of k_conv3_tc exactly as
+// its shared memory holds them, so that a block loads a channel group's 27
+// taps with one bulk copy: for group g (64 channels), tap t, output o and
+// 8-channel chunk j, 16 bytes at g 27 S + t S + (o/8)(nch 128) + (o%8) 16 +
+// j 128, with S = 2 cout min(cin, 64) bytes a tap and nch the group's chunks
+__global__ void k_pack_image(const bf16* __restrict__ wt, int cin, int cout, bf16* __restrict__ img) {
+  const int cg = cin < TC_CG ? cin : TC_CG, ngroups = (cin + TC_CG - 1) / TC_CG;
+  const long long S = 2LL * cout * cg;
+  const long long total = (long long)ngroups * 27 * cout * (cg / 8);
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(e % (cg / 8));
+    long long r = e / (cg / 8);
+    const int o = (int)(r % cout);
+    r /= cout;
+    const int t = (int)(r % 27);
+    const int g = (int)(r / 27);
+    const int c0 = g * TC_CG, nch = min(TC_CG, cin - c0) / 8;
+    if (j >= nch) continue;
+    const long long off = g * 27 * S + t * S + (o / 8) * (nch * 128) + (o % 8) * 16 + j * 128;
+    *reinterpret_cast<uint4*>(reinterpret_cast<char*>(img) + off) =
+        *reinterpret_cast<const uint4*>(wt + ((long long)t * cout + o) * cin + c0 + 8 * j);
+  }
+}
+
 // mean((y - t)^2) (per-block partials, summed with atomics) and gy = 2(y - t)/n
 __global__ void k_mse(long long n, const float* __restrict__ y, const float* __restrict__ t, float* __restrict__ gy,
                       float* __restrict__ loss) {
@@ -861,6 +905,9 @@ struct Layer {
   int cin, cout, taps;
   long long woff, boff;  // offsets of W and b in the flat parameter vector
   bf16 *wt = nullptr, *wtt = nullptr;
+  // wt and wtt in the shared-memory order of k_conv3_tc's resident weights
+  // (null where that convolution does not run with resident weights)
+  bf16 *img = nullptr, *timg = nullptr;
 };
 
 int blocks_for(long long n, int threads = 256) {
@@ -965,8 +1012,8 @@ int conv3_tc_planes(const stp_unet* n, const Dims& dm, int cin, int cout, bool r
 }
 
 // launch a 3x3x3 convolution (forward form): tcgen05 where the shapes allow, else mma.sync
-int conv3(stp_unet* n, const Dims& dm, const bf16* x, int ldx, int cin, const bf16* wt, const float* bias, int cout,
-          bf16* y, int ldy, int relu, const bf16* mask, int ldm) {
+int conv3(stp_unet* n, const Dims& dm, const bf16* x, int ldx, int cin, const bf16* wt, const bf16* wimg,
+          const float* bias, int cout, bf16* y, int ldy, int relu, const bf16* mask, int ldm) {
   const long long V = dm.vox();
   if (conv3_tc_ok(n, dm, ldx, cin, cout, ldy)) {
     static bool attr_set = false;
@@ -978,7 +1025,8 @@ int conv3(stp_unet* n, const Dims& dm, const bf16* x, int ldx, int cin, const bf
     const int zt = conv3_tc_planes(n, dm, cin, cout, resident);
     const unsigned blocks = (unsigned)(V / (TC_TX * TC_TY * zt));
     k_conv3_tc<<<blocks, 128, conv3_tc_smem(cin, cout, resident, zt), n->st>>>(
-        dm, x, ldx, cin, wt, bias, cout, y, ldy, relu, mask, ldm, resident ? 1 : 0, zt, n->d_err);
+        dm, x, ldx, cin, wt, bias, cout, y, ldy, relu, mask, ldm, resident ? 1 : 0, zt, resident ? wimg : nullptr,
+        n->d_err);
     UTRY(n, cudaGetLastError());
     return STP_OK;
   }
@@ -1043,6 +1091,9 @@ int pack_all(stp_unet* n) {
     const long long tot = (long long)ly.cout * ly.cin * 27;
     k_pack_weights<<<blocks_for(tot), 256, 0, n->st>>>(n->theta + ly.woff, ly.cout, ly.cin, ly.wt, ly.wtt);
     UTRY(n, cudaGetLastError());
+    if (ly.img) k_pack_image<<<blocks_for(tot / 8), 256, 0, n->st>>>(ly.wt, ly.cin, ly.cout, ly.img);
+    if (ly.timg) k_pack_image<<<blocks_for(tot / 8), 256, 0, n->st>>>(ly.wtt, ly.cout, ly.cin, ly.timg);
+    UTRY(n, cudaGetLastError());
   }
   return STP_OK;
 }
@@ -1065,11 +1116,11 @@ int forward(stp_unet* n, const float* x, int nb) {
     const Layer& la = P[2 * l];
     const Layer& lb = P[2 * l + 1];
     if (l > 0) {
-      if ((rc = conv3(n, dm[l], in, ldin, la.cin, la.wt, n->theta + la.boff, c, n->ha[l], c, 1, nullptr, 0))) return rc;
+      if ((rc = conv3(n, dm[l], in, ldin, la.cin, la.wt, la.img, n->theta + la.boff, c, n->ha[l], c, 1, nullptr, 0))) return rc;
     }
     bf16* e = l < 3 ? n->u[l] + kCh[l + 1] : n->e4;
     const int lde = l < 3 ? cu_width(l) : c;
-    if ((rc = conv3(n, dm[l], n->ha[l], c, c, lb.wt, n->theta + lb.boff, c, e, lde, 1, nullptr, 0))) return rc;
+    if ((rc = conv3(n, dm[l], n->ha[l], c, c, lb.wt, lb.img, n->theta + lb.boff, c, e, lde, 1, nullptr, 0))) return rc;
     if (l < 3) {
       k_pool<<<blocks_for(dm[l + 1].vox()), 256, 0, n->st>>>(dm[l], e, lde, c, n->q[l], c);
       UTRY(n, cudaGetLastError());
@@ -1086,8 +1137,8 @@ int forward(stp_unet* n, const float* x, int nb) {
     UTRY(n, cudaGetLastError());
     const Layer& la = P[8 + 2 * (2 - l)];
     const Layer& lb = P[9 + 2 * (2 - l)];
-    if ((rc = conv3(n, dm[l], n->u[l], cw, cw, la.wt, n->theta + la.boff, c, n->hd[l], c, 1, nullptr, 0))) return rc;
-    if ((rc = conv3(n, dm[l], n->hd[l], c, c, lb.wt, n->theta + lb.boff, c, n->d[l], c, 1, nullptr, 0))) return rc;
+    if ((rc = conv3(n, dm[l], n->u[l], cw, cw, la.wt, la.img, n->theta + la.boff, c, n->hd[l], c, 1, nullptr, 0))) return rc;
+    if ((rc = conv3(n, dm[l], n->hd[l], c, c, lb.wt, lb.img, n->theta + lb.boff, c, n->d[l], c, 1, nullptr, 0))) return rc;
     deeper = n->d[l];
     cdeep = c;
   }
@@ -1117,10 +1168,10 @@ int backward(stp_unet* n, const float* x, int nb) {
     const Layer& lb = P[9 + 2 * (2 - l)];
     // conv b: input hd[l], gradient ga[l]
     if ((rc = wgrad3(n, dm[l], n->hd[l], c, c, n->ga[l], c, c, lb))) return rc;
-    if ((rc = conv3(n, dm[l], n->ga[l], c, c, lb.wtt, nullptr, c, n->gb[l], c, 0, n->hd[l], c))) return rc;
+    if ((rc = conv3(n, dm[l], n->ga[l], c, c, lb.wtt, lb.timg, nullptr, c, n->gb[l], c, 0, n->hd[l], c))) return rc;
     // conv a: input u[l], gradient gb[l]
     if ((rc = wgrad3(n, dm[l], n->u[l], cw, cw, n->gb[l], c, c, la))) return rc;
-    if ((rc = conv3(n, dm[l], n->gb[l], c, c, la.wtt, nullptr, cw, n->gu[l], cw, 0, nullptr, 0))) return rc;
+    if ((rc = conv3(n, dm[l], n->gb[l], c, c, la.wtt, la.timg, nullptr, cw, n->gu[l], cw, 0, nullptr, 0))) return rc;
     // upsample part -> gradient of the deeper level's output pre-activation
     const int cd = kCh[l + 1];
     const bf16* act = l < 2 ? n->d[l + 1] : n->e4;
@@ -1150,13 +1201,13 @@ int backward(stp_unet* n, const float* x, int nb) {
     // conv b: input ha[l]
     if ((rc = wgrad3(n, dm[l], n->ha[l], c, c, gz, c, c, lb))) return rc;
     bf16* gha = l == 3 ? n->gb[3] : n->ga[l];
-    if ((rc = conv3(n, dm[l], gz, c, c, lb.wtt, nullptr, c, gha, c, 0, n->ha[l], c))) return rc;
+    if ((rc = conv3(n, dm[l], gz, c, c, lb.wtt, lb.timg, nullptr, c, gha, c, 0, n->ha[l], c))) return rc;
     if (l > 0) {
       // conv a: input q[l-1]
       const int cp = kCh[l - 1];
       if ((rc = wgrad3(n, dm[l], n->q[l - 1], cp, cp, gha, c, c, la))) return rc;
       bf16* gq = l == 3 ? n->ga[3] : n->gb[l];
-      if ((rc = conv3(n, dm[l], gha, c, c, la.wtt, nullptr, cp, gq, cp, 0, nullptr, 0))) return rc;
+      if ((rc = conv3(n, dm[l], gha, c, c, la.wtt, la.timg, nullptr, cp, gq, cp, 0, nullptr, 0))) return rc;
       gq_in = gq;
     } else {
       // conv a of level 1: the network input (1 channel)
@@ -1271,10 +1322,18 @@ int stp_unet_create(int nmax, int nz, int ny, int nx, void* stream, stp_unet** o
   A(&n->grad, n->np);
   A(&n->m, n->np);
   A(&n->v, n->np);
+  // elements of the resident-weight image of a convolution cin -> cout, 0
+  // where k_conv3_tc would stream its weights (or not run at all)
+  auto image_elems = [](int ci, int co) -> size_t {
+    if (ci % 16 || co % 16 || co > 256 || conv3_tc_smem(ci, co, true, 1) > kTcSmemMax) return 0;
+    return (size_t)((ci + TC_CG - 1) / TC_CG) * 27 * co * std::min(ci, TC_CG);
+  };
   for (Layer& ly : n->L) {
     if (ly.taps == 27 && ly.cin > 1) {
       A(&ly.wt, (size_t)ly.cout * ly.cin * 27);
       A(&ly.wtt, (size_t)ly.cout * ly.cin * 27);
+      if (const size_t e = image_elems(ly.cin, ly.cout)) A(&ly.img, e);
+      if (const size_t e = image_elems(ly.cout, ly.cin)) A(&ly.timg, e);
     }
   }
   const long long V[4] = {n->dm[0].vox(), n->dm[1].vox(), n->dm[2].vox(), n->dm[3].vox()};
