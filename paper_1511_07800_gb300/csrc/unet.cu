@@ -676,9 +676,12 @@ __global__ void k_wgrad_in(Dims dm, const float* __restrict__ x, const bf16* __r
 // ---------------------------------------------------------------------------
 // pooling, upsampling and the gradient plumbing between levels
 // ---------------------------------------------------------------------------
-// Pooling and upsampling move whole voxels: a thread owns one voxel and all
-// its channels (c a multiple of 8; leading dimensions multiples of 8, so
-// every 8-channel vector is 16 bytes, aligned), in 32-bit index arithmetic.
+// Pooling and upsampling move 16-byte channel vectors (c a multiple of 8,
+// leading dimensions multiples of 8, so every vector is aligned), in 32-bit
+// index arithmetic.  The kernels that reduce 8 fine voxels into a coarse
+// one take one 8-channel vector a thread (blockIdx.y); those that write the
+// fine level take one voxel a thread, all its channels (whole rows of
+// stores).
 __device__ __forceinline__ void unpack8(const uint4& u, float* f) {
   const unsigned w[4] = {u.x, u.y, u.z, u.w};
 #pragma unroll
@@ -700,24 +703,24 @@ __device__ __forceinline__ void st16(bf16* p, const uint4& u) { *reinterpret_cas
 __global__ void k_pool(Dims dm, const bf16* __restrict__ x, int ldx, int c, bf16* __restrict__ y, int ldy) {
   const Dims cd{dm.n, dm.d / 2, dm.h / 2, dm.w / 2};
   const unsigned V = (unsigned)cd.vox();
+  if ((int)blockIdx.y * 8 >= c) return;
   for (unsigned v = blockIdx.x * blockDim.x + threadIdx.x; v < V; v += gridDim.x * blockDim.x) {
     const Coord q = coord_of(cd, v);
     long long f[8];
 #pragma unroll
     for (int k = 0; k < 8; k++)
       f[k] = voxel_at(dm, q.n, 2 * q.z + (k >> 2), 2 * q.y + ((k >> 1) & 1), 2 * q.x + (k & 1));
-    for (int ch = 0; ch < c; ch += 8) {
-      float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, e[8];
+    const int ch = blockIdx.y * 8;
+    float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, e[8];
 #pragma unroll
-      for (int k = 0; k < 8; k++) {
-        unpack8(ld16(x + f[k] * ldx + ch), e);
+    for (int k = 0; k < 8; k++) {
+      unpack8(ld16(x + f[k] * ldx + ch), e);
 #pragma unroll
-        for (int i = 0; i < 8; i++) s[i] += e[i];
-      }
-#pragma unroll
-      for (int i = 0; i < 8; i++) s[i] *= 0.125f;
-      st16(y + (long long)v * ldy + ch, pack8(s));
+      for (int i = 0; i < 8; i++) s[i] += e[i];
     }
+#pragma unroll
+    for (int i = 0; i < 8; i++) s[i] *= 0.125f;
+    st16(y + (long long)v * ldy + ch, pack8(s));
   }
 }
 
@@ -738,25 +741,25 @@ __global__ void k_upsample_bwd_mask(Dims cd, const bf16* __restrict__ gf, int ld
                                     int lda, bf16* __restrict__ out, int ldo) {
   const Dims fd{cd.n, cd.d * 2, cd.h * 2, cd.w * 2};
   const unsigned V = (unsigned)cd.vox();
+  if ((int)blockIdx.y * 8 >= c) return;
   for (unsigned v = blockIdx.x * blockDim.x + threadIdx.x; v < V; v += gridDim.x * blockDim.x) {
     const Coord q = coord_of(cd, v);
     long long f[8];
 #pragma unroll
     for (int k = 0; k < 8; k++)
       f[k] = voxel_at(fd, q.n, 2 * q.z + (k >> 2), 2 * q.y + ((k >> 1) & 1), 2 * q.x + (k & 1));
-    for (int ch = 0; ch < c; ch += 8) {
-      float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, e[8], a[8];
+    const int ch = blockIdx.y * 8;
+    float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, e[8], a[8];
 #pragma unroll
-      for (int k = 0; k < 8; k++) {
-        unpack8(ld16(gf + f[k] * ldg + ch), e);
+    for (int k = 0; k < 8; k++) {
+      unpack8(ld16(gf + f[k] * ldg + ch), e);
 #pragma unroll
-        for (int i = 0; i < 8; i++) s[i] += e[i];
-      }
-      unpack8(ld16(act + (long long)v * lda + ch), a);
-#pragma unroll
-      for (int i = 0; i < 8; i++) s[i] = a[i] > 0.f ? s[i] : 0.f;
-      st16(out + (long long)v * ldo + ch, pack8(s));
+      for (int i = 0; i < 8; i++) s[i] += e[i];
     }
+    unpack8(ld16(act + (long long)v * lda + ch), a);
+#pragma unroll
+    for (int i = 0; i < 8; i++) s[i] = a[i] > 0.f ? s[i] : 0.f;
+    st16(out + (long long)v * ldo + ch, pack8(s));
   }
 }
 
@@ -1122,7 +1125,7 @@ int forward(stp_unet* n, const float* x, int nb) {
     const int lde = l < 3 ? cu_width(l) : c;
     if ((rc = conv3(n, dm[l], n->ha[l], c, c, lb.wt, lb.img, n->theta + lb.boff, c, e, lde, 1, nullptr, 0))) return rc;
     if (l < 3) {
-      k_pool<<<blocks_for(dm[l + 1].vox()), 256, 0, n->st>>>(dm[l], e, lde, c, n->q[l], c);
+      k_pool<<<dim3(blocks_for(dm[l + 1].vox()), c / 8), 256, 0, n->st>>>(dm[l], e, lde, c, n->q[l], c);
       UTRY(n, cudaGetLastError());
       in = n->q[l];
       ldin = c;
@@ -1176,7 +1179,7 @@ int backward(stp_unet* n, const float* x, int nb) {
     const int cd = kCh[l + 1];
     const bf16* act = l < 2 ? n->d[l + 1] : n->e4;
     bf16* out = l < 2 ? n->ga[l + 1] : n->ga[3];
-    k_upsample_bwd_mask<<<blocks_for(dm[l + 1].vox()), 256, 0, n->st>>>(dm[l + 1], n->gu[l], cw, cd, act, cd, out,
+    k_upsample_bwd_mask<<<dim3(blocks_for(dm[l + 1].vox()), cd / 8), 256, 0, n->st>>>(dm[l + 1], n->gu[l], cw, cd, act, cd, out,
                                                                               cd);
     UTRY(n, cudaGetLastError());
   }
