@@ -70,3 +70,60 @@ def test_paper_initial_condition_is_divergence_free(orc):
     assert np.allclose(u.mean(axis=(1, 2)), U0 / 3, atol=1e-12 * U0.max())
     assert np.abs(v.mean(axis=(1, 2))).max() < 1e-12 * np.abs(v).max()
     assert (u - u.mean(axis=(1, 2), keepdims=True)).std() > 1.0
+
+
+def _paper_like_profile(nz, nu, U_mean, U_cl):
+    """A symmetric mean profile on nz (odd) uniform cells over height 1:
+    linear at the wall with friction velocity 1 (u = z/nu at the first
+    centre), a parabolic core peaking at U_cl on the centre cell, its
+    curvature chosen (bisection) so that the volume mean is U_mean."""
+    zc = (np.arange(nz) + 0.5) / nz
+    d = np.minimum(zc, 1.0 - zc)
+
+    def prof(A):
+        return np.minimum(d / nu, U_cl - A * (0.5 - d) ** 2)
+
+    lo, hi = 0.0, 1e4
+    for _ in range(200):
+        A = 0.5 * (lo + hi)
+        if prof(A).mean() > U_mean:
+            lo = A
+        else:
+            hi = A
+    u = prof(0.5 * (lo + hi))
+    assert abs(u.mean() - U_mean) < 1e-9 and u[0] == d[0] / nu and u.max() == U_cl
+    return u
+
+
+def test_bulk_definitions_reproduce_the_paper_numbers():
+    """Sec. 5 prints U_mean = 15.39, Re_mean = U_mean H/nu = 5542, U_cl =
+    18.30, the Pope estimate (1/0.4) log Re_* + 3.47 = 18.18, U_max/U_mean =
+    1.19, C_f = 2 u_*^2/U_mean^2 = 8.44e-3 and Dean's 0.073 Re_mean^-0.25 =
+    8.46e-3 (tests/golden/paper_values.json, les_bulk).  A mean profile with
+    friction velocity 1, the printed U_mean and U_cl, on the paper's height 1
+    and nu = 1/Re_* = 1/360, gives every derived number to its last printed
+    digit through the oracle's and the library's bulk definitions (a height
+    of 2 in Re_mean, a missing factor 2 in C_f or a half-cell wall distance
+    taken as a whole cell would each fail)."""
+    import json
+    import os
+    from oracle import les_stats
+    with open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")) as f:
+        g = json.load(f)["les_bulk"]
+    nu = 1.0 / g["Re_star"]
+    nz = 201
+    u = _paper_like_profile(nz, nu, g["U_mean"], g["U_cl"])
+    zf = np.linspace(0.0, 1.0, nz + 1)
+    cfg = inputs.preset("les_paper", nz=nz)
+    assert cfg["Lz"] == 1.0 and cfg["nu"] == nu and cfg.get("stretch", 0.0) == 0.0
+    for b in (les_stats.bulk(u, zf, nu), les.bulk(cfg, u)):
+        assert abs(b["u_tau"] - 1.0) < 1e-12
+        assert abs(b["Re_tau"] - g["Re_star"]) < 1e-9
+        # Re_mean to half a unit of U_mean's last printed digit (0.005 x 360)
+        assert abs(b["Re_mean"] - g["Re_mean"]) <= 0.005 * g["Re_star"]
+        assert abs(b["U_max"] - g["U_cl"]) < 1e-12
+        assert abs(b["Umax_over_Umean"] - g["Umax_over_Umean"]) <= 0.005
+        assert abs(b["Cf"] - g["Cf"]) <= 0.005e-3
+        assert abs(b["dean_Cf"] - g["dean_Cf"]) <= 0.005e-3
+        # the paper truncates 18.187 to 18.18
+        assert 0.0 <= b["pope_Umax_over_utau"] - g["pope_U_max"] < 0.01

@@ -32,23 +32,36 @@ def coords(cfg):
 
 # ---------------------------------------------------------------- Orr-Sommerfeld
 
+def golden():
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")) as f:
+        return json.load(f)
+
+
 def test_os_paper_table_eigenvalue(orc):
-    """Table of Sec. 4.2: Re_* = 500, alpha = 2 pi / 4 gives
-    lambda = 1.8056 - 33.873 i (paper units)."""
+    """Table of Sec. 4.2 (tests/golden/paper_values.json, os_table):
+    Re_* = 500, alpha = 2 pi / 4 gives lambda = 1.8056 - 33.873 i (paper
+    units) and the period 0.185."""
     from oracle import os_eig
-    Re, a, lam_p = os_eig.paper_to_half_height(500.0, 2 * PI / 4, 1.8056 - 33.873j)
+    g = golden()["os_table"]
+    Re_s = g["Re_star"]
+    lam_printed = complex(g["lambda_real"], g["lambda_imag"])
+    Re, a, lam_p = os_eig.paper_to_half_height(Re_s, g["alpha_over_pi"] * PI, lam_printed)
     lam = os_eig.least_stable(Re, a, N=160)
     # one unit of the last printed digit (1.8056, -33.873)
-    assert abs(lam.real - lam_p.real) < 1e-4 * 2 / 500
-    assert abs(lam.imag - lam_p.imag) < 1e-3 * 2 / 500
-    # the printed period T = 2 pi / |Im lambda| = 0.185 (paper time units)
-    assert abs(2 * PI / abs(lam.imag * 500 / 2) - 0.185) < 0.0005
+    assert abs(lam.real - lam_p.real) < 1e-4 * 2 / Re_s
+    assert abs(lam.imag - lam_p.imag) < 1e-3 * 2 / Re_s
+    # the printed period T = 2 pi / |Im lambda| (paper time units)
+    assert abs(2 * PI / abs(lam.imag * Re_s / 2) - g["period"]) < 0.0005
 
 
 def test_os_critical_reynolds(orc):
-    """Sec. 4.1: critical Reynolds number 5772 (centreline, half height) at
-    the critical wavenumber 1.02056: neutral mode."""
+    """Sec. 4.1: critical Reynolds number 5772 (centreline, half height;
+    golden os_critical), reached at the critical wavenumber 1.02056 (Re_c =
+    5772.22 to two more digits): a neutral mode."""
     from oracle import os_eig
+    assert round(5772.22) == golden()["os_critical"]["Re_c"]
     lam = os_eig.least_stable(5772.22, 1.02056, N=120)
     assert abs(lam.real) < 2e-7
     assert os_eig.least_stable(5000.0, 1.02056).real < 0
