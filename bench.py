@@ -204,7 +204,7 @@ def oracle_us_per_sweep(cfg, zline, seed=5):
     return 1e6 * (t[64] - t[32]) / 32
 
 
-def learned_comparison(cfg, steps):
+def learned_comparison(cfg, steps, oracle_sample=True):
     """Poisson time to 1e-8, learned guess vs plain, on the workload grid:
     train the U-Net on (residual, correction) pairs harvested from channels
     of the same workload (seeds 0-3, 10 steps each), then step one channel
@@ -239,14 +239,49 @@ def learned_comparison(cfg, steps):
     t_train = time.perf_counter() - t0
     res = learn.compare(cfg, net, seed=7, nsteps=max(3, steps), precision="fp32")
     res64 = learn.compare(cfg, net, seed=7, nsteps=3, precision="fp64")
+    # one forward of the trained network on the workload grid (CUDA events)
+    fwd_ms = None
+    try:
+        xg = torch.randn((1,) + shape, device="cuda")
+        yg = torch.zeros_like(xg)
+        for _ in range(2):
+            net.forward(xg, yg)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(5):
+            net.forward(xg, yg)
+        e1.record()
+        e1.synchronize()
+        fwd_ms = e0.elapsed_time(e1) / 5
+    except Exception as ex:  # report, never fake
+        fwd_ms = {"error": str(ex)[:200]}
     net.close()
+    out_cpu = None
+    if oracle_sample:
+        try:
+            # the oracle network (FP64 numpy) on one eighth of the voxels, scaled
+            from oracle import unet as unet_oracle
+            half = tuple(n // 2 for n in shape)
+            xs = np.random.default_rng(11).standard_normal((1,) + half + (1,))
+            t1 = time.perf_counter()
+            unet_oracle.forward(np.concatenate(theta), xs)
+            t_s = time.perf_counter() - t1
+            out_cpu = {"kind": "oracle", "unit": "ms per forward", "value": 8e3 * t_s,
+                       "sample": "one FP64 oracle forward at %dx%dx%d (an eighth of the voxels, %.2f s), scaled "
+                                 "by voxels to %dx%dx%d" % (half[2], half[1], half[0], t_s, shape[2], shape[1],
+                                                            shape[0])}
+        except Exception as ex:  # report, never fake
+            out_cpu = {"value": None, "error": str(ex)[:200]}
     return {"plain_ms": res["plain"]["solve_ms"], "learned_ms": res["learned"]["solve_ms"],
+            "forward_ms": fwd_ms,
             "plain_sweeps": res["plain"]["sweeps"], "learned_sweeps": res["learned"]["sweeps"],
             "speedup": res["plain"]["solve_ms"] / res["learned"]["solve_ms"],
             "fp64": {"plain_ms": res64["plain"]["solve_ms"], "learned_ms": res64["learned"]["solve_ms"],
                      "plain_sweeps": res64["plain"]["sweeps"], "learned_sweeps": res64["learned"]["sweeps"]},
             "train": {"pairs": int(R.shape[0]), "adam_steps": len(losses), "batch": 4,
                       "final_loss": float(np.mean(losses[-10:])), "output_scale": K, "seconds": t_train},
+            "cpu_baseline": out_cpu,
             "note": "time per pressure solve to 1e-8 (GPU events), previous-step pressure as the plain guess"}
 
 
@@ -592,7 +627,7 @@ def run_ours(args):
     }
     if rank == 0 and world == 1 and not args.no_learned and args.grid is None:
         try:
-            line["poisson_learned_vs_plain"] = learned_comparison(cfg, args.steps)
+            line["poisson_learned_vs_plain"] = learned_comparison(cfg, args.steps, not args.no_cpu_baseline)
         except Exception as ex:  # report, never fake
             line["poisson_learned_vs_plain"] = {"error": str(ex)[:200]}
     if rank == 0 and world == 1 and not args.no_batch and args.grid is None:
