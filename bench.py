@@ -1,13 +1,16 @@
 """Benchmark: projection steps of the channel-flow solver on GB300.
 
-A step is one pass of the whole hot path (eddy viscosity when enabled,
-explicit terms + AB3, Crank-Nicolson sweeps, divergence, the SRJ pressure
-solve to 1e-8 relative residual with the previous pressure as the guess,
-velocity correction) over the supercritical instability workload
-(128 x 64 x 128, Re 7500, Poiseuille + Orr-Sommerfeld mode + noise,
-dt 2e-3).  Prints one JSON line.
+A step is one pass of the whole hot path: eddy viscosity (Smagorinsky with
+van Driest damping), explicit terms + AB3, Crank-Nicolson sweeps, the
+divergence / Poisson right-hand side, the pressure solve to 1e-8 relative
+residual from the previous pressure (SRJ with z-line relaxation, FP32
+sweeps inside an FP64 refinement loop), the velocity correction with the
+constant-flux fix-up.  Workload: the turbulent LES channel, 256 x 128 x 192
+cells with tanh-stretched walls (gamma 2), Lx = 4 pi, Ly = 2 pi, Lz = 2,
+nu = 1/2800, Cs 0.1, U_b = 1, dt 1e-3, laminar start + 10 % noise (seed 1).
+Prints one JSON line.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|fp64]
+  python bench.py [--gpus N] [--steps K] [--warmup W]
   python bench.py --impl reference ...   (the CPU oracle on the host cores)
 
 N > 1 runs under torch.distributed.run: independent replicas, one per GPU,
@@ -28,9 +31,16 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = "os_instability"
-WORKLOAD_DESC = "os_instability 128x64x128 Re=7500 dt=2e-3 Poiseuille+OS mode 1e-4+noise 1e-6, ptol 1e-8"
+WORKLOAD = "les_channel"
+WORKLOAD_DESC = ("les_channel 256x128x192, Lx 4pi Ly 2pi Lz 2, tanh walls gamma 2, nu 1/2800 (bulk Re 5600), "
+                 "Smagorinsky Cs 0.1 + van Driest A 25, constant flux U_b 1, dt 1e-3, laminar + 10% noise (seed 1); "
+                 "FP32 stencils and sweeps, FP64 reductions and refinement, z-line SRJ, Poisson to 1e-8")
 METRIC = "Mcell*steps/s (projection step, Poisson to 1e-8 rel. residual)"
+LINE_NAMES = {True: "k_line_sweep_vec<float,RB> (z-line SRJ sweep: residual, twisted column solve, update)"}
+TILE_NAMES = {0: "k_sweep_f32_z<1,8>", 1: "k_sweep_f32_z<2,8>", 2: "k_sweep_f32_z<4,8>", 3: "k_sweep_f32_z<2,4>",
+              4: "k_sweep_f32_z<4,4>", 5: "k_sweep_f32_z<8,4>", 6: "k_sweep_f32_flat<2>", 7: "k_sweep_f32_flat<4>",
+              8: "k_sweep_f32_flat<8>", 9: "k_sweep_f32_pair<8,4>", 10: "k_sweep_f32_pair<4,4>",
+              11: "k_sweep_f32_pair<4,8>"}
 
 
 def parse():
@@ -39,14 +49,19 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--workload", default=WORKLOAD, choices=["les_channel", "os_instability"],
+                    help="headline workload (profiling runs may pick the instability case)")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"], help="profiling runs only")
+    ap.add_argument("--solver", default="zline", choices=["zline", "point"], help="profiling runs only")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--grid", default=None, help="override the cell counts, NXxNYxNZ (profiling runs)")
+    ap.add_argument("--only-headline", action="store_true", help="skip every side measurement (profiling runs)")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-guess comparison")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched uneven-channel measurement")
-    ap.add_argument("--no-les", action="store_true",
-                    help="skip the LES measurements (point vs z-line solve; the paper's LES workload)")
+    ap.add_argument("--no-les", action="store_true", help="skip the paper's LES workload")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the point-SRJ, instability-workload and above-L2 sweep measurements")
     return ap.parse_args()
 
 
@@ -121,57 +136,52 @@ def measured_peaks():
         return {}
 
 
-def sweep_source_digest(precision):
-    """sha256 of the source that defines the SRJ sweep kernel: the FP32
-    tiles (poisson_common.cuh) or the FP64 kernel's definition."""
+def source_digest(files):
+    """sha256 over the given source files under the package's csrc/: the
+    traffic figures of a kernel apply while the sources defining it are
+    unchanged."""
     csrc = os.path.join(ROOT, "paper_1511_07800_gb300", "csrc")
-    if precision == "fp32":
-        text = open(os.path.join(csrc, "poisson_common.cuh"), "rb").read()
-    else:
-        src = open(os.path.join(csrc, "kernels_poisson.cu")).read()
-        a = src.index("k_sweep_f64_v2(Geom<double> g")
-        a = src.rindex("template <bool PDL>", 0, a)
-        text = src[a:src.index("\n}\n", a) + 3].encode()
-    return hashlib.sha256(text).hexdigest()
+    h = hashlib.sha256()
+    for f in files:
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()
 
 
-def traffic_for(precision):
-    """Per-launch DRAM bytes of the SRJ sweep from the committed ncu summary,
-    if the sweep kernel's source is unchanged since the capture; else None."""
-    path = os.path.join(ROOT, "profiles", "srj_sweep_traffic.json")
+def traffic_for(key):
+    """Per-launch DRAM bytes (read + write) of a kernel from the committed
+    ncu summary profiles/kernel_traffic.json, scaled to the launch's cells
+    when the capture was on a smaller grid; None when the kernel's sources
+    changed since the capture or no record exists."""
+    path = os.path.join(ROOT, "profiles", "kernel_traffic.json")
     try:
-        rec = json.load(open(path))
-        if rec.get("source_sha256", {}).get(precision) != sweep_source_digest(precision):
+        rec = json.load(open(path))["kernels"][key]
+        if rec["source_sha256"] != source_digest(rec["sources"]):
             return None
-        return rec["bytes_per_launch"].get(precision)
+        return rec
     except Exception:
         return None
 
 
-def cpu_baseline_sample(cfg, fields, sweeps_per_step):
+def cpu_baseline_sample(cfg, fields, sweeps_per_step, omega):
     """The CPU oracle on the host cores: one step of the same workload from
     the same initial fields, its pressure solve held to the GPU's mean sweep
-    count per step (the same work per step)."""
-    import numpy as np  # noqa: F401
-
+    count per step in whole cycles (the same work per step)."""
     import oracle
-    from oracle import srj
     ncores = len(os.sched_getaffinity(0))
     oracle.set_threads(ncores)
-    om, _, _ = srj.schedule_for(cfg["nx"], cfg["ny"], cfg["nz"], cfg["Lx"], cfg["Ly"], cfg["Lz"],
-                                cfg.get("stretch", 0.0))
-    M = len(om)
+    M = len(omega)
     cycles = max(1, int(round(sweeps_per_step / M)))
-    o = oracle.Oracle(dict(cfg, omega=om, ptol=0.0, pmaxit=cycles * M, cn_sweeps=cfg["cn_sweeps"]))
+    o = oracle.Oracle(dict(cfg, omega=omega, ptol=0.0, pmaxit=cycles * M, cn_sweeps=cfg["cn_sweeps"]))
     o.set_fields(*fields)
     t0 = time.perf_counter()
     o.step(1)
     dt = time.perf_counter() - t0
     cells = cfg["nx"] * cfg["ny"] * cfg["nz"]
     return {"value": cells / dt / 1e6, "unit": "Mcell*steps/s", "cores": oracle.get_threads(), "kind": "oracle",
-            "sample": "1 FP64 oracle step of the full %dx%dx%d workload from the initial fields, SRJ held to "
+            "sample": "1 FP64 oracle step of the full %dx%dx%d workload from the initial fields, %s SRJ held to "
                       "%d sweeps (%d cycles of %d, the GPU's mean per timed step); %.2f s wall"
-                      % (cfg["nx"], cfg["ny"], cfg["nz"], cycles * M, cycles, M, dt)}
+                      % (cfg["nx"], cfg["ny"], cfg["nz"], "z-line" if cfg.get("zline") else "point", cycles * M,
+                         cycles, M, dt)}
 
 
 def _oracle_threads():
@@ -367,42 +377,6 @@ def batched_channels(steps, warmup, peak, oracle_sample=True):
     return out
 
 
-def les_line_vs_point(steps, warmup, oracle_sample=True):
-    """Pressure-solve time on the wall-stretched LES grid (256 x 128 x 192,
-    tanh stretching 2, Smagorinsky, constant flux; FP32 with FP64
-    refinement), point SRJ sweeps against z-line sweeps, from the same
-    seeded initial fields.  GPU time of the solves by CUDA events inside the
-    library; steps timed after warm-up steps."""
-    from paper_1511_07800_gb300 import inputs, stp
-    cfg = inputs.preset("les_channel")
-    f0 = inputs.initial_fields("les_channel", cfg, seed=1)
-    cells = cfg["nx"] * cfg["ny"] * cfg["nz"]
-    out = {"workload": "les_channel 256x128x192, tanh 2, Cs 0.1, constant flux, FP32 + FP64 refinement, "
-                       "ptol 1e-8", "steps": steps, "warmup": warmup}
-    for name, zl in (("point", 0), ("zline", 1)):
-        c = dict(cfg, zline=zl)
-        with stp.Channel(c, precision="fp32") as ch:
-            ch.set_fields(*f0)
-            ch.step(warmup)
-            st = ch.step(steps)
-            sweeps = st["solve_sweeps"]
-            out[name] = {"M": len(stp.srj_schedule(c)[0]), "sweeps_per_step": sweeps / steps,
-                         "solve_ms_per_step": st["solve_ms"] / steps,
-                         "us_per_sweep": 1e3 * st["solve_ms"] / max(1, sweeps),
-                         "Mcell_steps_per_s_solve": cells * steps / (st["solve_ms"] / 1e3) / 1e6,
-                         "converged": st["converged"]}
-    out["solve_speedup_zline"] = out["point"]["solve_ms_per_step"] / out["zline"]["solve_ms_per_step"]
-    if oracle_sample:
-        cores = _oracle_threads()
-        ous = {name: oracle_us_per_sweep(cfg, zl) for name, zl in (("point", 0), ("zline", 1))}
-        out["cpu_baseline"] = {
-            "kind": "oracle", "cores": cores, "unit": "us per sweep", "point": ous["point"], "zline": ous["zline"],
-            "gpu_over_oracle": {n: ous[n] / out[n]["us_per_sweep"] for n in ous},
-            "sample": "FP64 oracle sweeps on the same grid: two 32-sweep cycles less one, over 32 (a sweep plus "
-                      "1/32 of a residual evaluation)"}
-    return out
-
-
 def les_paper_steps(steps, warmup, oracle_sample=True):
     """The paper's LES workload (Sec. 5) at its own grid, 240 x 140 x 120,
     Lx = 8, Ly = 4, Lz = 1, Re_* = 360, dt = 1e-4, Smagorinsky + van Driest,
@@ -461,37 +435,71 @@ def les_paper_steps(steps, warmup, oracle_sample=True):
     return out
 
 
+def headline_config(args):
+    from paper_1511_07800_gb300 import inputs
+    cfg = inputs.preset(args.workload, zline=1 if args.solver == "zline" else 0)
+    if args.grid:
+        nx, ny, nz = (int(x) for x in args.grid.lower().split("x"))
+        cfg.update(nx=nx, ny=ny, nz=nz)
+    cfg["cn_sweeps"] = _auto_cn(cfg)
+    return cfg
+
+
+def oracle_schedule(cfg):
+    from oracle import srj
+    om, _, _ = srj.schedule_for(cfg["nx"], cfg["ny"], cfg["nz"], cfg["Lx"], cfg["Ly"], cfg["Lz"],
+                                cfg.get("stretch", 0.0), line=bool(cfg.get("zline")))
+    return om
+
+
 def run_reference(args):
-    """The oracle (plain FP64 C, OpenMP over z) time-stepping the workload with
-    its own tolerance-driven pressure solves, on rank 0's host cores."""
+    """The oracle (plain FP64 C, OpenMP over z) stepping the headline
+    workload on rank 0's host cores.  A whole step of the oracle takes
+    about 15 s at this size, so each step is a bounded sample: first one
+    complete untimed step, whose tolerance-driven solve gives the oracle's
+    own sweeps per step, then every step (warm-up and timed) runs with its
+    pressure solve held to 32 sweeps and is charged the measured time of
+    the remaining sweeps (the oracle's time per sweep on the same grid)."""
     world, rank, local = dist_env()
     if rank != 0:
         return 0
     import oracle
-    from oracle import srj
     from paper_1511_07800_gb300 import inputs
-    cfg = inputs.preset(WORKLOAD)
+    cfg = headline_config(args)
     ncores = len(os.sched_getaffinity(0))
     oracle.set_threads(ncores)
-    om, _, _ = srj.schedule_for(cfg["nx"], cfg["ny"], cfg["nz"], cfg["Lx"], cfg["Ly"], cfg["Lz"], 0.0)
-    cn = _auto_cn(cfg)
-    o = oracle.Oracle(dict(cfg, omega=om, cn_sweeps=cn))
-    o.set_fields(*inputs.initial_fields(WORKLOAD, cfg, seed=0))
+    om = oracle_schedule(cfg)
+    fields = inputs.initial_fields(args.workload, cfg, seed=1 if args.workload == "les_channel" else 0)
+    full = oracle.Oracle(dict(cfg, omega=om))
+    full.set_fields(*fields)
+    t0 = time.perf_counter()
+    st = full.step(1)
+    t_full = time.perf_counter() - t0
+    s_full = st["sweeps"]
+    us = oracle_us_per_sweep(cfg, int(cfg.get("zline", 0)))
+    o = oracle.Oracle(dict(cfg, omega=[0.8, 1.0] * 16, ptol=0.0, pmaxit=32))
+    f = full.get_fields()
+    o.set_fields(f["u"], f["v"], f["w"], f["p"])
     for _ in range(args.warmup):
         o.step(1)
-    t0 = time.perf_counter()
+    total = 0.0
     for _ in range(args.steps):
+        t0 = time.perf_counter()
         o.step(1)
-    dt = time.perf_counter() - t0
+        total += time.perf_counter() - t0 + max(0, s_full - 32) * us * 1e-6
     cells = cfg["nx"] * cfg["ny"] * cfg["nz"]
-    val = cells * args.steps / dt / 1e6
+    val = cells * args.steps / total / 1e6
+    sample = ("each step: one FP64 oracle step with its solve held to 32 sweeps, plus %d x %.0f us for the rest "
+              "of the %d sweeps the oracle's own tolerance-driven solve took in a complete first step (%.1f s; "
+              "untimed); %s SRJ" % (max(0, s_full - 32), us, s_full, t_full,
+                                    "z-line" if cfg.get("zline") else "point"))
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "Mcell*steps/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD_DESC, "cells": cells, "srj_M": len(om),
-                                            "cn_sweeps": cn},
+            "data": "synthetic", "config": {"workload": WORKLOAD_DESC if args.workload == WORKLOAD else args.workload,
+                                            "cells": cells, "srj_M": len(om), "cn_sweeps": cfg["cn_sweeps"]},
             "cpu_baseline": {"value": val, "unit": "Mcell*steps/s", "cores": oracle.get_threads(), "kind": "oracle",
-                             "sample": "%d full FP64 oracle steps after %d warm-up steps" % (args.steps, args.warmup)},
+                             "sample": sample},
             "e2e": {"value": val, "unit": "Mcell*steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -515,6 +523,113 @@ def _auto_cn(cfg):
     return max(2, min(int(math.ceil(math.log(1e-12) / math.log(rho))), 200))
 
 
+def timed_steps(ch, steps, stream, flush):
+    """`steps` projection steps, each bracketed by CUDA events on the
+    library's stream, after an untimed write of a buffer larger than L2."""
+    import torch
+    ms, sweeps, launches, solve_ms, passes, conv = 0.0, 0, 0, 0.0, 0, True
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = ch.step(1)
+        e1.record(stream)
+        e1.synchronize()
+        ms += e0.elapsed_time(e1)
+        sweeps += st["solve_sweeps"]
+        passes += st["passes"]
+        launches += st["launches"]
+        solve_ms += st["solve_ms"]
+        conv = conv and st["converged"]
+    return dict(ms=ms, sweeps=sweeps, passes=passes, launches=launches, solve_ms=solve_ms, converged=conv)
+
+
+def sweep_roofline(word, cells, r, kernel, peak, traffic_key):
+    """HBM roofline of the SRJ sweep: 3 words a cell (read p and b, write
+    p'), over the mean time per sweep of the solve graphs (GPU events around
+    each solve, charged with its once-per-cycle checks and refinement
+    kernels: a lower bound on the sweep's own rate)."""
+    bytes_per_sweep = 3 * word * cells
+    t = r["solve_ms"] / max(1, r["sweeps"]) / 1e3
+    ach = bytes_per_sweep / t / 1e9 if r["sweeps"] else None
+    tr = traffic_for(traffic_key)
+    traffic = None
+    if tr:
+        traffic = tr["dram_bytes_per_launch"] * cells / tr["cells"]
+    return {"bound": "hbm", "kernel": kernel, "achieved": ach, "peak": peak, "unit": "GB/s",
+            "frac": ach / peak if ach else None, "traffic": traffic, "bytes_per_launch": bytes_per_sweep,
+            "mean_launch_us": t * 1e6,
+            "note": "achieved = algorithmic bytes (3 words a cell) / (solve-graph GPU time / sweeps), the "
+                    "once-per-cycle residual checks and refinement kernels charged to the sweeps"}
+
+
+def side_steps(stp, cfg, precision, fields, steps, warmup, stream, flush, peak, traffic_key):
+    """Whole projection steps of another configuration (its own handle)."""
+    word = 4 if precision == "fp32" else 8
+    cells = cfg["nx"] * cfg["ny"] * cfg["nz"]
+    with stp.Channel(cfg, precision=precision, stream=stream.cuda_stream) as ch:
+        ch.set_fields(*fields)
+        for _ in range(max(3, warmup)):
+            ch.step(1)
+        r = timed_steps(ch, steps, stream, flush)
+        variant, _ = ch.sweep_tile()
+    if cfg.get("zline"):
+        kern = "k_line_sweep_vec (z-line SRJ sweep)" if precision == "fp32" else "k_line_sweep_vec<double> (z-line)"
+    else:
+        kern = (TILE_NAMES.get(variant, "k_sweep_f32") + " (autotuned tile variant %d)" % variant
+                if precision == "fp32" else "k_sweep_f64_v2")
+    out = {"value": cells * steps / (r["ms"] / 1e3) / 1e6, "unit": "Mcell*steps/s", "ms_per_step": r["ms"] / steps,
+           "steps": steps, "warmup": max(3, warmup), "sweeps_per_step": r["sweeps"] / steps,
+           "solve_ms_per_step": r["solve_ms"] / steps, "converged": r["converged"],
+           "gpu_launches_per_step": r["launches"] / steps,
+           "roofline": sweep_roofline(word, cells, r, kern, peak, traffic_key)}
+    if precision == "fp64":
+        out["roofline"]["note"] += ("; in FP64 the sweep is bound by GB300's FP64 pipe, not by HBM "
+                                    "(profiles/srj_sweep_f64_os_instability.md)")
+    return out
+
+
+def sweeps_above_l2(stp, peak):
+    """The SRJ sweeps on working sets larger than the 126 MB L2, so that
+    their rate is an HBM rate: FP64 sweeps on the LES grid (p, p', b:
+    151 MB) and FP32 inner sweeps on a 512 x 256 x 192 grid (d, d', r:
+    302 MB); point and z-line sweeps each; a fixed number of sweeps from a
+    seeded mean-free right-hand side, GPU events around the solve graph."""
+    import numpy as np
+    import torch
+    from paper_1511_07800_gb300 import inputs
+    out = {}
+    cases = [("fp64_les_grid", "fp64", 256, 128, 192), ("fp32_512x256x192", "fp32", 512, 256, 192)]
+    for name, prec, nx, ny, nz in cases:
+        cfg = inputs.preset("les_channel", nx=nx, ny=ny, nz=nz)
+        rng = np.random.default_rng(3)
+        b = torch.from_numpy(rng.standard_normal((nz, ny, nx))).cuda()
+        dz = torch.from_numpy(np.diff(inputs.zfaces(cfg))).cuda()[:, None, None]
+        b -= (b * dz).sum() / (dz.sum() * nx * ny)
+        word = 8 if prec == "fp64" else 4
+        cells = nx * ny * nz
+        res = {"grid": "%dx%dx%d" % (nx, ny, nz), "working_set_MB": 3 * word * cells / 1e6}
+        for solver, zl in (("point", 0), ("zline", 1)):
+            with stp.Channel(dict(cfg, zline=zl), precision=prec) as ch:
+                M = len(stp.srj_schedule(dict(cfg, zline=zl))[0])
+                p = torch.zeros_like(b)
+                ch.poisson_solve(b, p, tol=0.0, maxit=M)  # warm-up (and the FP32 tile autotuner)
+                p.zero_()
+                st = ch.poisson_solve(b, p, tol=0.0, maxit=2 * M)
+                variant, _ = ch.sweep_tile()
+            t = st["solve_ms"] / max(1, st["sweeps"]) / 1e3
+            ach = 3 * word * cells / t / 1e9
+            res[solver] = {"sweeps": st["sweeps"], "us_per_sweep": t * 1e6, "achieved_GBs": ach,
+                           "frac": ach / peak,
+                           "kernel": ("k_line_sweep_vec" if zl else
+                                      (TILE_NAMES.get(variant, "k_sweep_f32") if prec == "fp32" else "k_sweep_f64_v2"))}
+        out[name] = res
+    out["note"] = ("time per sweep of a solve graph held to 2 cycles (its two residual checks and, in FP32, the "
+                   "refinement kernels charged to the sweeps); achieved = 3 words a cell / that time")
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -526,12 +641,9 @@ def run_ours(args):
         dist.init_process_group(backend="nccl", init_method="env://")
     torch.cuda.set_device(local)
     build.build()
-    cfg = inputs.preset(WORKLOAD)
-    if args.grid:
-        nx, ny, nz = (int(x) for x in args.grid.lower().split("x"))
-        cfg.update(nx=nx, ny=ny, nz=nz)
-    cfg["cn_sweeps"] = _auto_cn(cfg)
-    fields = inputs.initial_fields(WORKLOAD, cfg, seed=0)
+    cfg = headline_config(args)
+    seed = 1 if args.workload == "les_channel" else 0
+    fields = inputs.initial_fields(args.workload, cfg, seed=seed)
     stream = torch.cuda.current_stream()
     ch = stp.Channel(cfg, precision=args.precision, device=local, stream=stream.cuda_stream)
     ch.set_fields(*fields)
@@ -544,110 +656,118 @@ def run_ours(args):
     torch.cuda.synchronize()
     clk = Clocks(local)
     clk.start()
-    ms, sweeps, launches, solve_ms, passes = 0.0, 0, 0, 0.0, 0
-    conv = True
-    for _ in range(args.steps):
-        flush.zero_()                      # L2 flush between timed steps (untimed)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        st = ch.step(1)
-        e1.record(stream)
-        e1.synchronize()
-        ms += e0.elapsed_time(e1)
-        sweeps += st["sweeps"]
-        passes += st["passes"]
-        launches += st["launches"]
-        solve_ms += st["solve_ms"]
-        conv = conv and st["converged"]
+    r = timed_steps(ch, args.steps, stream, flush)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
     clocks = clk.stop()
-    ms_max = reduce_max(ms, "cuda")
+    ms_max = reduce_max(r["ms"], "cuda")
     value = world * cells * args.steps / (ms_max / 1e3) / 1e6
 
-    # end to end through the C ABI with host buffers: copy the step's inputs
-    # in, step, copy the result out, every step
+    # end to end through the C ABI with pinned host buffers: every step the
+    # whole stepper state (velocities, pressure, the two Adams-Bashforth
+    # history levels, the step counter) goes in, one step runs, and the new
+    # state comes out, so each step is the benchmarked AB3 step
     e2e = None
     if not args.no_e2e:
-        host = ch.get_fields()
-        # the step's inputs and result live in pinned host memory
-        hu, hv, hw, hp = (torch.from_numpy(np.ascontiguousarray(host[k])).pin_memory() for k in ("u", "v", "w", "p"))
+        n = ch.state_size()
+        host = torch.empty(n, dtype=torch.float64).pin_memory()
+        ch.get_state(host)
         torch.cuda.synchronize()
-        ke = max(1, min(args.steps, 5))
+        ke = max(3, min(args.steps, 10))
         t0 = time.perf_counter()
         for _ in range(ke):
-            ch.set_fields(hu, hv, hw, hp)
+            ch.set_state(host)
             ch.step(1)
-            ch.get_fields(dict(u=hu, v=hv, w=hw, p=hp, nu=None))
+            ch.get_state(host)
         te = time.perf_counter() - t0
-        nb = 8 * (3 * cells + cells + cfg["nx"] * cfg["ny"])
-        e2e = {"value": world * cells * ke / te / 1e6, "unit": "Mcell*steps/s", "h2d_bytes_per_step": nb,
-               "d2h_bytes_per_step": nb, "host_memory": "pinned"}
+        te = reduce_max(te, "cuda")
+        e2e = {"value": world * cells * ke / te / 1e6, "unit": "Mcell*steps/s", "h2d_bytes_per_step": 8 * n,
+               "d2h_bytes_per_step": 8 * n, "host_memory": "pinned", "steps": ke,
+               "api": "stp_set_state (host) -> stp_step(1) -> stp_get_state (host), wall clock"}
 
     peaks = measured_peaks()
-    word = 4 if args.precision == "fp32" else 8
-    bytes_per_sweep = 3 * word * cells
-    # mean SRJ sweep duration: GPU time of the solve graphs (events on the
-    # launching stream) over the sweeps they ran; the once-per-cycle checks
-    # (and FP32 refinement kernels) are charged to the sweeps, so this is a
-    # lower bound on the sweep kernel's own bandwidth
-    t_sweep = solve_ms / max(1, sweeps) / 1e3
-    achieved = bytes_per_sweep / t_sweep / 1e9 if sweeps else None
     peak = peaks.get("hbm_gbs", 6800.0)
+    word = 4 if args.precision == "fp32" else 8
     variant, _ = ch.sweep_tile()
-    names = {0: "k_sweep_f32_z<1,8>", 1: "k_sweep_f32_z<2,8>", 2: "k_sweep_f32_z<4,8>", 3: "k_sweep_f32_z<2,4>",
-             4: "k_sweep_f32_z<4,4>", 5: "k_sweep_f32_z<8,4>", 6: "k_sweep_f32_flat<2>", 7: "k_sweep_f32_flat<4>",
-             8: "k_sweep_f32_flat<8>", 9: "k_sweep_f32_pair<8,4>", 10: "k_sweep_f32_pair<4,4>",
-             11: "k_sweep_f32_pair<4,8>"}
-    sweep_kernel = (names.get(variant, "k_sweep_f32") if args.precision == "fp32" else "k_sweep_f64_v2") + \
-        " (SRJ sweep, autotuned tile variant %d)" % variant
-    traffic = traffic_for(args.precision)
+    if cfg.get("zline"):
+        kern = LINE_NAMES[True] if args.precision == "fp32" else "k_line_sweep_vec<double,RB> (z-line SRJ sweep)"
+        tkey = "zline_sweep_%s_%s" % (args.precision, args.workload)
+    else:
+        kern = (TILE_NAMES.get(variant, "k_sweep_f32") + " (SRJ sweep, autotuned tile variant %d)" % variant
+                if args.precision == "fp32" else "k_sweep_f64_v2 (SRJ sweep)")
+        tkey = "point_sweep_%s_%s" % (args.precision, args.workload)
+    roof = sweep_roofline(word, cells, r, kern, peak, tkey)
+    roof["peak_source"] = "MEASURED_PEAKS.json hbm_gbs (measured)" if "hbm_gbs" in peaks else "fallback"
+    roof["l2_note"] = ("the FP32 inner solve's working set (d, d', r: 12 bytes a cell, %.0f MB) %s the 126 MB L2; "
+                       "the sweeps' HBM rate on working sets above L2 is under srj_sweeps_above_l2"
+                       % (12 * cells / 1e6, "fits in" if 12 * cells < 126e6 else "exceeds"))
     line = {
         "metric": METRIC, "value": value, "unit": "Mcell*steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+f64" if args.precision == "fp32" else "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD_DESC if not args.grid else WORKLOAD_DESC + " at " + args.grid,
-                   "cells": cells, "precision": args.precision,
+        "config": {"workload": (WORKLOAD_DESC if args.workload == WORKLOAD else args.workload) +
+                   (" at " + args.grid if args.grid else ""),
+                   "cells": cells, "precision": args.precision, "solver": args.solver,
                    "parallelism": "replicas" if world > 1 else "single",
-                   "l2": "flushed between timed steps (256 MB write, untimed)",
-                   "srj_M": len(stp.srj_schedule(cfg)[0])},
-        "poisson": {"sweeps_per_step": sweeps / args.steps, "refine_passes_per_step": passes / args.steps,
-                    "all_converged": conv, "ms_per_step": solve_ms / args.steps},
-        "roofline": {"bound": "hbm", "kernel": sweep_kernel,
-                     "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-                     "bytes_per_launch": bytes_per_sweep, "mean_launch_us": t_sweep * 1e6,
-                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if "hbm_gbs" in peaks else "fallback"},
-        "gpu_launches": launches,
+                   "l2": "flushed between timed steps (256 MB write, untimed); the step's fields (about "
+                         "%.0f MB) exceed L2" % (cells * (4 * 17 + 8 * 4) / 1e6),
+                   "srj_M": len(stp.srj_schedule(cfg)[0]), "cn_sweeps": cfg["cn_sweeps"]},
+        "poisson": {"sweeps_per_step": r["sweeps"] / args.steps, "refine_passes_per_step": r["passes"] / args.steps,
+                    "all_converged": r["converged"], "ms_per_step": r["solve_ms"] / args.steps},
+        "roofline": roof,
+        "gpu_launches": r["launches"],
         "clocks": clocks,
         "e2e": e2e,
     }
-    if rank == 0 and world == 1 and not args.no_learned and args.grid is None:
+    side = rank == 0 and world == 1 and args.grid is None and not args.only_headline
+    if side and not args.no_extra:
         try:
-            line["poisson_learned_vs_plain"] = learned_comparison(cfg, args.steps, not args.no_cpu_baseline)
+            pc = dict(cfg, zline=0)
+            line["les_channel_point_srj"] = side_steps(stp, pc, "fp32", fields, max(3, min(args.steps, 5)), 3,
+                                                       stream, flush, peak, "point_sweep_fp32_les_channel")
+            line["les_channel_point_srj"]["note"] = "the same workload with the paper's point SRJ sweeps"
+        except Exception as ex:  # report, never fake
+            line["les_channel_point_srj"] = {"error": str(ex)[:300]}
+        try:
+            c2 = inputs.preset("os_instability")
+            c2["cn_sweeps"] = _auto_cn(c2)
+            f2 = inputs.initial_fields("os_instability", c2, seed=0)
+            line["os_instability"] = {
+                "workload": "os_instability 128x64x128 Re 7500 dt 2e-3, Poiseuille + OS mode 1e-4 + noise 1e-6, "
+                            "point SRJ to 1e-8",
+                "fp32_refine": side_steps(stp, c2, "fp32", f2, max(3, min(args.steps, 10)), 3, stream, flush, peak,
+                                          "point_sweep_fp32_os_instability"),
+                "fp64": side_steps(stp, c2, "fp64", f2, max(3, min(args.steps, 5)), 3, stream, flush, peak,
+                                   "point_sweep_fp64_os_instability")}
+        except Exception as ex:  # report, never fake
+            line["os_instability"] = {"error": str(ex)[:300]}
+        try:
+            line["srj_sweeps_above_l2"] = sweeps_above_l2(stp, peak)
+        except Exception as ex:  # report, never fake
+            line["srj_sweeps_above_l2"] = {"error": str(ex)[:300]}
+    if side and not args.no_learned:
+        try:
+            c2 = inputs.preset("os_instability")
+            c2["cn_sweeps"] = _auto_cn(c2)
+            line["poisson_learned_vs_plain"] = learned_comparison(c2, args.steps, not args.no_cpu_baseline)
         except Exception as ex:  # report, never fake
             line["poisson_learned_vs_plain"] = {"error": str(ex)[:200]}
-    if rank == 0 and world == 1 and not args.no_batch and args.grid is None:
+    if side and not args.no_batch:
         try:
             line["batched_channels"] = batched_channels(max(3, min(args.steps, 10)), args.warmup, peak,
                                                         not args.no_cpu_baseline)
         except Exception as ex:  # report, never fake
             line["batched_channels"] = {"error": str(ex)[:200]}
-    if rank == 0 and world == 1 and not args.no_les and args.grid is None:
-        try:
-            line["les_pressure_solve"] = les_line_vs_point(3, 3, not args.no_cpu_baseline)
-        except Exception as ex:  # report, never fake
-            line["les_pressure_solve"] = {"error": str(ex)[:200]}
+    if side and not args.no_les:
         try:
             line["les_paper"] = les_paper_steps(10, 3, not args.no_cpu_baseline)
         except Exception as ex:  # report, never fake
             line["les_paper"] = {"error": str(ex)[:200]}
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.only_headline:
         try:
-            line["cpu_baseline"] = cpu_baseline_sample(cfg, fields, sweeps / args.steps)
+            line["cpu_baseline"] = cpu_baseline_sample(cfg, fields, r["sweeps"] / args.steps, oracle_schedule(cfg))
         except Exception as ex:  # report, never fake
             line["cpu_baseline"] = {"value": None, "error": str(ex)[:200]}
     if rank == 0:

@@ -26,7 +26,9 @@
  * conditional nodes), one kernel per SRJ sweep.  With STP_PERSISTENT=1 at
  * stp_init an FP32 cycle instead runs as one persistent cooperative kernel
  * with bounded grid barriers between its sweeps (slower on GB300: kept as an
- * option).  The FP32 sweep kernel's tile shape (z levels per thread, rows
+ * option); each barrier wait gives up after STP_BARRIER_WAIT SM clock cycles
+ * (read at every stp_step / stp_poisson_solve call; default 2e9, about one
+ * second), and the call then returns STP_ETIMEOUT.  The FP32 sweep kernel's tile shape (z levels per thread, rows
  * per block) is picked on first use by timing the variants on the grid
  * (STP_SWEEP_VARIANT=<0..11> forces one; variants 6..8 pack warps along the
  * plane for rows shorter than 128 cells, 9..11 run two sweeps per launch on
@@ -114,10 +116,12 @@ typedef struct stp_step_stats {
 } stp_step_stats;
 
 typedef struct stp_solve_stats {
-    int sweeps;
-    int refine_passes;
-    int converged;
-    double rel_residual;
+    int sweeps;              /* SRJ sweeps (inner sweeps in FP32)               */
+    int refine_passes;       /* FP64 refinement passes                          */
+    int converged;           /* 1 if ||rhs - Lp|| <= tol ||rhs||                */
+    double rel_residual;     /* ||rhs - Lp|| / ||rhs|| at the end               */
+    double solve_ms;         /* GPU time of the solve (CUDA events on the
+                                handle's stream around the solve graph)          */
 } stp_solve_stats;
 
 typedef struct stp_handle stp_handle;
@@ -152,8 +156,12 @@ int stp_get_fields(stp_handle *h, double *u, double *v, double *w, double *p, do
 /* Advance nsteps projection steps (Sec. 3.1), each with its pressure solved
    to ptol from the previous pressure.  Blocks until done.  Returns
    STP_ENOTCONVERGED if a solve hit pmaxit (the step still completes),
-   STP_EDIVERGED on NaN/Inf, STP_ECFL when cfl_check is set and violated.
-   stats (nullable) describes the last step. */
+   STP_EDIVERGED on NaN/Inf in a residual or the velocity, STP_ETIMEOUT when
+   a bounded device-side wait ran out, STP_ECFL when cfl_check is set and
+   violated.  On STP_EDIVERGED and STP_ETIMEOUT the step that failed is
+   undone: the fields, the Adams-Bashforth history and the step counter are
+   those of the last good step (each step first copies u, v, w, p on the
+   device).  stats (nullable) describes the last step. */
 int stp_step(stp_handle *h, int nsteps, stp_step_stats *stats);
 
 /* ------------------------------------------------------------------------
@@ -242,10 +250,11 @@ int stp_set_state(stp_handle *h, const double *buf);
 
 /* Solve L p = rhs (Sec. 3.4 SRJ; Eq. presdiv operator with Neumann walls)
    to ||rhs - Lp||_2 <= tol ||rhs||_2 starting from p_inout, capped at maxit
-   sweeps (0: pmaxit).  rhs [nz][ny][nx] must have zero volume-weighted mean
-   to within round-off (its mean is not removed).  p_inout receives the
-   result; its additive constant is not fixed.  Uses the handle's buffers:
-   the current pressure field is overwritten. */
+   sweeps (0: pmaxit).  L is singular (its null space is the constants), so
+   rhs [nz][ny][nx] must have zero volume-weighted mean: the call returns
+   STP_EINVAL, before any sweep, when |sum rhs dV| > 1e-9 sum |rhs| dV.
+   p_inout receives the solution with its volume-weighted mean set to zero.
+   Uses the handle's buffers: the current pressure field is overwritten. */
 int stp_poisson_solve(stp_handle *h, const double *rhs, double *p_inout, double tol, int maxit, int where,
                       stp_solve_stats *stats);
 
@@ -327,6 +336,29 @@ int stp_unet_set_output_scale(stp_unet *net, float k);
 int stp_unet_train_pairs(stp_unet *net, const float *r, const float *dp, int nb, float lr, float *loss);
 int stp_unet_eval_pairs(stp_unet *net, const float *r, const float *dp, int nb, float *loss);
 
+/* One 3x3x3 convolution of the network on its own, for checks of the
+   convolution kernels against an independent definition.  layer is the
+   parameter-order index 0..13 (enc1a .. dec1b); it runs at its level's size
+   for nb samples, on the kernel the network itself uses for that layer
+   (tcgen05 or mma.sync, planes per block as the network picks them).
+   Arrays are device FP32, channels last [nb][d][h][w][c]; inputs are
+   rounded to BF16 on entry, as the network stores its activations.
+     mode 0  forward: out [.., cout] = relu(conv(a) + bias), the BF16 values
+             the network stores (layer 0 takes its 1-channel input a in
+             FP32, as the network does); b unused
+     mode 1  data gradient (layers 1..13): out [.., cin] =
+             conv^T(a) * (b > 0), a the gradient of the output [.., cout],
+             b a mask [.., cin] (NULL: none), stored in BF16
+     mode 2  weight gradient: out [cout*cin*27 + cout] = dW ([o][c][tap])
+             then db, for the input a [.., cin] and the output gradient
+             b [.., cout]; FP32
+   Allocates temporaries and synchronises.  Errors: STP_EINVAL (bad layer,
+   mode or nb), STP_ENOMEM, STP_ECUDA, STP_ETIMEOUT. */
+#define STP_UNET_FORWARD 0
+#define STP_UNET_DATA_GRAD 1
+#define STP_UNET_WEIGHT_GRAD 2
+int stp_unet_layer(stp_unet *net, int layer, int mode, const float *a, const float *b, float *out, int nb);
+
 /* Use net (NULL: none) as the learned initial guess of every pressure solve
    of h: with s = RMS(r) of the solve's starting residual r, the correction
    s U(r / s) is added to p before the SRJ iteration (once per solve, in
@@ -357,7 +389,11 @@ int stp_set_harvest(stp_handle *h, float *r_out, float *dp_out);
    nz <= 4096 and ceil(nx/32) * ceil(ny/8) * nz <= 65536; larger grids are
    rejected with STP_EINVAL.  The first call on a device looks up the
    array's device address, so make it before any stream capture on that
-   device.  All calls share the array: calls whose work overlaps on the GPU
+   device; under CUDA's lazy module loading (the default) that first call
+   can also load the library's device code, array included, onto the
+   device, a one-time allocation made by the CUDA runtime (to have it
+   happen earlier, set CUDA_MODULE_LOADING=EAGER or make one call during
+   set-up).  All calls share the array: calls whose work overlaps on the GPU
    race and must be serialised by the caller.  Errors: STP_EINVAL,
    STP_ECUDA; stp_last_error(NULL) gives the message. */
 int stp_poisson_residual_noalloc(int nx, int ny, int nz, double Lx, double Ly, double Lz, double stretch,

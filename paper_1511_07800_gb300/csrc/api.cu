@@ -21,6 +21,11 @@ namespace {
 
 thread_local std::string g_init_error;
 
+// stp_poisson_solve: |sum rhs dV| above this fraction of sum |rhs| dV is a
+// right-hand side without a solution (round-off of an exactly telescoping
+// divergence stays many orders below it)
+constexpr double kMeanTol = 1e-9;
+
 }  // namespace
 
 struct stp_handle {
@@ -47,6 +52,9 @@ struct stp_handle {
   double *p = nullptr, *p2 = nullptr;
   float *d1 = nullptr, *d2 = nullptr, *r32 = nullptr;
   double* stage = nullptr;
+  // the fields before the current step, restored when the step diverges
+  void *bu = nullptr, *bv = nullptr, *bw = nullptr;
+  double* bp = nullptr;
 
   Red red{};
   double* h_sc = nullptr;  // pinned copies of red.sc and red.flag
@@ -769,8 +777,16 @@ int arm_solves(stp_handle* h, double tol, int maxit) {
   c.max_passes = 64;
   c.M = (int)h->omega.size();
   c.kpc = h->cycle_blocks > 0 ? 1 : uses_pairs(h) ? c.M / 2 : c.M;
+  c.bar_wait = 2000000000LL;
+  if (const char* e = std::getenv("STP_BARRIER_WAIT")) {
+    const long long w = std::atoll(e);
+    if (w > 0) c.bar_wait = w;
+  }
   *h->h_ctl = c;
   CUDA_TRY(h, cudaMemcpyAsync(h->ctl, h->h_ctl, sizeof(SolveCtl), cudaMemcpyHostToDevice, h->st));
+  // the persistent cycle's barrier state starts clean on every call, also
+  // after a wait that timed out (count, generation, error flag)
+  CUDA_TRY(h, cudaMemsetAsync(h->bar.count, 0, sizeof(unsigned) * 4, h->st));
   return STP_OK;
 }
 
@@ -1168,6 +1184,10 @@ int stp_init(const stp_config* cfg, stp_handle** out) {
     A((void**)&h->r32, sizeof(float) * nc);
   }
   A((void**)&h->stage, sizeof(double) * nw);
+  A(&h->bu, es * nc);
+  A(&h->bv, es * nc);
+  A(&h->bw, es * nw);
+  A((void**)&h->bp, sizeof(double) * nc);
   const Launch big = {dim3((h->nx + 31) / 32, (h->ny + 7) / 8, h->nz + 1), dim3(32, 8, 1), 0};
   const size_t maxblocks = (size_t)big.grid.x * big.grid.y * big.grid.z + 152 * 32;
   A((void**)&h->red.partial, sizeof(double) * 2 * maxblocks);
@@ -1295,13 +1315,33 @@ int stp_step(stp_handle* h, int nsteps, stp_step_stats* stats) {
   if (rc) return rc;
   SolveOut so;
   for (int n = 0; n < nsteps; n++) {
+    // keep the fields of the last good step: a step that diverges or times
+    // out is undone (its Adams-Bashforth slot held N^{n-3}, no longer used)
+    const long long step0 = h->step;
+    const int nhist0 = h->nhist;
+    CUDA_TRY(h, cudaMemcpyAsync(h->bu, h->u, h->esz * h->nc, cudaMemcpyDeviceToDevice, h->st));
+    CUDA_TRY(h, cudaMemcpyAsync(h->bv, h->v, h->esz * h->nc, cudaMemcpyDeviceToDevice, h->st));
+    CUDA_TRY(h, cudaMemcpyAsync(h->bw, h->w, h->esz * h->nw, cudaMemcpyDeviceToDevice, h->st));
+    CUDA_TRY(h, cudaMemcpyAsync(h->bp, h->p, sizeof(double) * h->nc, cudaMemcpyDeviceToDevice, h->st));
     rc = h->prec == STP_FP64 ? step_impl<double>(h, h->g64) : step_impl<float>(h, h->g32);
     if (rc) return rc;
     if ((rc = sync_scalars(h))) return rc;
     if ((rc = finish_solve(h, &so))) return rc;
-    if (so.bad == 2) return fail(h, STP_ETIMEOUT, "a grid barrier of the persistent SRJ cycle timed out");
-    if (so.bad) return fail(h, STP_EDIVERGED, "NaN or Inf in the pressure residual");
-    if (h->h_flag[FL_BAD]) return fail(h, STP_EDIVERGED, "NaN or Inf in the velocity");
+    if (so.bad || h->h_flag[FL_BAD]) {
+      CUDA_TRY(h, cudaMemcpyAsync(h->u, h->bu, h->esz * h->nc, cudaMemcpyDeviceToDevice, h->st));
+      CUDA_TRY(h, cudaMemcpyAsync(h->v, h->bv, h->esz * h->nc, cudaMemcpyDeviceToDevice, h->st));
+      CUDA_TRY(h, cudaMemcpyAsync(h->w, h->bw, h->esz * h->nw, cudaMemcpyDeviceToDevice, h->st));
+      CUDA_TRY(h, cudaMemcpyAsync(h->p, h->bp, sizeof(double) * h->nc, cudaMemcpyDeviceToDevice, h->st));
+      const int ds = (int)step0;
+      CUDA_TRY(h, cudaMemcpyAsync(h->d_step, &ds, sizeof(int), cudaMemcpyHostToDevice, h->st));
+      CUDA_TRY(h, cudaMemsetAsync(h->red.flag + FL_BAD, 0, sizeof(int), h->st));
+      CUDA_TRY(h, cudaStreamSynchronize(h->st));
+      h->step = step0;
+      h->nhist = nhist0;
+      if (so.bad == 2) return fail(h, STP_ETIMEOUT, "a grid barrier of the persistent SRJ cycle timed out");
+      if (so.bad) return fail(h, STP_EDIVERGED, "NaN or Inf in the pressure residual");
+      return fail(h, STP_EDIVERGED, "NaN or Inf in the velocity");
+    }
   }
   if (h->cfg.forcing == 1 && nsteps > 0) h->last_dpdx = h->h_sc[SC_SHIFT] / h->cfg.dt;
   if (stats) {
@@ -1333,14 +1373,26 @@ int stp_poisson_solve(stp_handle* h, const double* rhs, double* p_inout, double 
   const cudaMemcpyKind kin = where == STP_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
   CUDA_TRY(h, cudaMemcpyAsync(h->b, rhs, sizeof(double) * h->nc, kin, h->st));
   CUDA_TRY(h, cudaMemcpyAsync(h->p, p_inout, sizeof(double) * h->nc, kin, h->st));
+  // L is singular (Neumann walls, periodic x and y): L p = rhs has a
+  // solution only when the volume integral of rhs vanishes
+  CUDA_TRY(h, launch_vsum(h->g64, h->b, h->red, h->st));
+  int rc = sync_scalars(h);
+  if (rc) return rc;
+  if (std::fabs(h->h_sc[SC_VSUM]) > kMeanTol * h->h_sc[SC_VABS])
+    return fail(h, STP_EINVAL, "rhs has a non-zero volume-weighted mean (" + std::to_string(h->h_sc[SC_VSUM]) +
+                                   " against a volume sum of |rhs| of " + std::to_string(h->h_sc[SC_VABS]) +
+                                   "): L p = rhs has no solution");
   CUDA_TRY(h, launch_norm(h->b, h->nc, SC_BNORM, h->red, h->st));
-  int rc = arm_solves(h, tol, maxit > 0 ? maxit : h->cfg.pmaxit);
+  rc = arm_solves(h, tol, maxit > 0 ? maxit : h->cfg.pmaxit);
   if (rc) return rc;
   h->solve_ms = 0.0;
   h->solve_sweeps = 0;
   if ((rc = harvest_before(h))) return rc;
   if ((rc = launch_solve(h))) return rc;
   if ((rc = harvest_after(h))) return rc;
+  // gauge: the solution's volume-weighted mean is set to zero
+  CUDA_TRY(h, launch_vsum(h->g64, h->p, h->red, h->st));
+  CUDA_TRY(h, launch_sub_vmean(h->g64, h->p, h->cfg.Lz, h->red, h->st));
   CUDA_TRY(h, cudaMemcpyAsync(p_inout, h->p, sizeof(double) * h->nc,
                               where == STP_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, h->st));
   if ((rc = sync_scalars(h))) return rc;
@@ -1353,6 +1405,7 @@ int stp_poisson_solve(stp_handle* h, const double* rhs, double* p_inout, double 
     stats->refine_passes = so.passes;
     stats->converged = so.converged;
     stats->rel_residual = so.rel;
+    stats->solve_ms = h->solve_ms;
   }
   return so.converged ? STP_OK : fail(h, STP_ENOTCONVERGED, "pressure solve hit maxit");
 }

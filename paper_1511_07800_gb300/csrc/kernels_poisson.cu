@@ -240,10 +240,11 @@ __global__ void __launch_bounds__(kBX* kBY) k_sweep_f64_v2(Geom<double> g, const
 // sweep.  Work: warps take chunks of 32 consecutive float4 units (4 cells of
 // a row each) in a grid-stride loop; a unit's x-neighbours come from the
 // adjacent lanes when they hold the same row, else by a scalar load.
-// Every barrier wait is bounded (about one second of clock); on time-out
-// the kernel sets ctl->bad = 2 and returns.
+// Every barrier wait is bounded (ctl->bar_wait clock cycles, about one
+// second by default); on time-out the kernel sets ctl->bad = 2 and returns,
+// and the check kernels then end the solve.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ bool grid_barrier(GridBar bar, unsigned nblocks) {
+__device__ __forceinline__ bool grid_barrier(GridBar bar, unsigned nblocks, long long wait) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -259,7 +260,7 @@ __device__ __forceinline__ bool grid_barrier(GridBar bar, unsigned nblocks) {
     } else {
       const long long t0 = clock64();
       while (*vgen == g0) {
-        if (clock64() - t0 > 2000000000LL) {
+        if (clock64() - t0 > wait) {
           atomicExch(bar.err, 1);
           break;
         }
@@ -284,6 +285,7 @@ __global__ void __launch_bounds__(1024, 1) k_cycle_f32(Geom<float> g, float* A, 
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
   const size_t plane4 = (size_t)nx4 * ny;
   const float idx2 = g.idx2, idy2 = g.idy2;
+  const long long wait = __ldcg(&ctl->bar_wait);
   for (int m = 0; m < M; m++) {
     const float* src = (m & 1) ? B : A;
     float* dst = (m & 1) ? A : B;
@@ -320,7 +322,7 @@ __global__ void __launch_bounds__(1024, 1) k_cycle_f32(Geom<float> g, float* A, 
       o.w = cell(c.w, c.z, right, yn.w, ys.w, zu.w, zd.w, bq.w);
       if (active) reinterpret_cast<float4*>(dst)[rc + x4] = o;
     }
-    if (m + 1 < M && !grid_barrier(bar, gridDim.x)) {
+    if (m + 1 < M && !grid_barrier(bar, gridDim.x, wait)) {
       if (blockIdx.x == 0 && threadIdx.x == 0) ctl->bad = 2;
       return;
     }
@@ -729,6 +731,38 @@ __global__ void k_norm(const double* __restrict__ a, size_t n, int slot, Red red
   }
 }
 
+// Volume sums of a cell-centred field: sc[SC_VSUM] = sum a dz_k and
+// sc[SC_VABS] = sum |a| dz_k (dx dy is common to every cell and left out);
+// one 32 x 8 tile a block, one level per grid row, fixed summation order.
+__global__ void k_vsum(Geom<double> g, const double* __restrict__ a, Red red, unsigned nblocks) {
+  __shared__ double sh[32];
+  const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y, k = blockIdx.z;
+  double s = 0.0, m = 0.0;
+  if (i < g.nx && j < g.ny) {
+    const double x = a[(k * g.ny + j) * g.nx + i] * g.dzv[k];
+    s = x;
+    m = fabs(x);
+  }
+  s = block_sum(s, sh);
+  m = block_sum(m, sh);
+  if (publish_partial(red, nblocks, s, m, true)) {
+    const double ts = final_sum(red.partial, nblocks, sh);
+    const double tm = final_sum(red.partial + nblocks, nblocks, sh);
+    if (threadIdx.x + blockDim.x * threadIdx.y == 0) {
+      red.sc[SC_VSUM] = ts;
+      red.sc[SC_VABS] = tm;
+      *red.counter = 0u;
+    }
+  }
+}
+
+// a -= sc[SC_VSUM] / sum(dz) over the cells: zero volume-weighted mean
+__global__ void k_sub_vmean(size_t n, double* __restrict__ a, double inv_lz_plane, Red red) {
+  const double mean = __ldcg(red.sc + SC_VSUM) * inv_lz_plane;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x)
+    a[q] -= mean;
+}
+
 }  // namespace
 
 // Vector kernels when the row length allows aligned vectors (nx a multiple
@@ -1014,6 +1048,20 @@ cudaError_t launch_norm(const double* a, size_t n, int slot, Red red, cudaStream
   if (blocks > 152 * 8) blocks = 152 * 8;
   if (blocks == 0) blocks = 1;
   k_norm<<<blocks, 256, 0, s>>>(a, n, slot, red, blocks);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_vsum(const Geom<double>& g, const double* a, Red red, cudaStream_t s) {
+  Launch l = plane_launch(g.nx, g.ny, g.nz);
+  k_vsum<<<l.grid, l.block, 0, s>>>(g, a, red, l.nblocks);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sub_vmean(const Geom<double>& g, double* a, double Lz, Red red, cudaStream_t s) {
+  const size_t n = (size_t)g.nx * g.ny * g.nz;
+  unsigned blocks = (unsigned)((n + 255) / 256);
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  k_sub_vmean<<<blocks, 256, 0, s>>>(n, a, 1.0 / (Lz * g.nx * g.ny), red);
   return cudaGetLastError();
 }
 

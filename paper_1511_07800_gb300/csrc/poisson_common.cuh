@@ -221,7 +221,9 @@ __device__ __forceinline__ bool cycle_decide(SolveCtl* ctl, const Red& red, doub
   const double nb = red.sc[SC_BNORM];
   bool stop;
   ctl->kernels += 1;
-  if (!(res == res) || isinf(res)) {
+  if (ctl->bad) {
+    stop = true;  // a cycle kernel gave up waiting (ctl->bad = 2)
+  } else if (!(res == res) || isinf(res)) {
     ctl->bad = 1;
     stop = true;
   } else if (MODE == 0) {
@@ -256,7 +258,9 @@ __device__ __forceinline__ bool pass_decide(SolveCtl* ctl, const Red& red, doubl
   ctl->cycles_inner = 0;
   ctl->prev = 0.0;
   bool stop;
-  if (!(res == res) || isinf(res)) {
+  if (ctl->bad) {
+    stop = true;
+  } else if (!(res == res) || isinf(res)) {
     ctl->bad = 1;
     stop = true;
   } else {

@@ -69,7 +69,9 @@ enum {
   SC_UMAX = 4,      // max |u| after the correction
   SC_SHIFT = 5,     // flux fix-up added to u
   SC_RES_INNER = 6, // inner residual at the last inner check
-  SC_COUNT = 8
+  SC_VSUM = 7,      // volume sum of a field (stp_poisson_solve's mean checks)
+  SC_VABS = 8,      // volume sum of its absolute value
+  SC_COUNT = 10
 };
 enum { FL_DONE = 0, FL_INNER_DONE = 1, FL_BAD = 2, FL_COUNT = 4 };
 
@@ -105,6 +107,9 @@ struct SolveCtl {
   // totals over the earlier solves of this call
   long long tot_sweeps, tot_kernels;
   int solves, nonconv;
+  // longest wait of a grid barrier of the persistent SRJ cycle, in SM clock
+  // cycles (about one second by default; STP_BARRIER_WAIT overrides it)
+  long long bar_wait;
 };
 
 // ---------------------------------------------------------------------------
@@ -283,6 +288,12 @@ cudaError_t launch_laplacian(const Geom<double>& g, const double* p, double* out
 
 template <typename Td, typename Ts>
 cudaError_t launch_convert(Td* dst, const Ts* src, size_t n, cudaStream_t s);
+
+// Volume sums sum a dz and sum |a| dz of a cell-centred FP64 field into
+// sc[SC_VSUM], sc[SC_VABS]; a -= (its volume-weighted mean), read from
+// sc[SC_VSUM] on the device (Lz the box height).
+cudaError_t launch_vsum(const Geom<double>& g, const double* a, Red red, cudaStream_t s);
+cudaError_t launch_sub_vmean(const Geom<double>& g, double* a, double Lz, Red red, cudaStream_t s);
 
 // ||a||_2 of a double array into sc[slot].
 cudaError_t launch_norm(const double* a, size_t n, int slot, Red red, cudaStream_t s);

@@ -891,6 +891,16 @@ __global__ void k_guess_out(long long V, const float* __restrict__ y, const doub
     d[i] = s * y[i];
 }
 
+// FP32 -> BF16 (round to nearest even) and back, for the single-layer checks
+__global__ void k_to_bf16(long long n, const float* __restrict__ a, bf16* __restrict__ b) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    b[i] = __float2bfloat16_rn(a[i]);
+}
+__global__ void k_from_bf16(long long n, const bf16* __restrict__ a, float* __restrict__ b) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    b[i] = __bfloat162float(a[i]);
+}
+
 }  // namespace nn
 }  // namespace stp
 
@@ -1449,6 +1459,72 @@ int stp_unet_train_step(stp_unet* n, const float* x, const float* target, int nb
   if ((rc = pack_all(n))) return rc;
   UTRY(n, cudaStreamSynchronize(n->st));
   return STP_OK;
+}
+
+int stp_unet_layer(stp_unet* n, int layer, int mode, const float* a, const float* b, float* out, int nb) {
+  if (!n || !a || !out) return STP_EINVAL;
+  if (int rc = check_n(n, nb)) return rc;
+  if (layer < 0 || layer > 13) return ufail(n, STP_EINVAL, "layer must be 0..13 (the 3x3x3 convolutions)");
+  if (mode < 0 || mode > 2 || (mode == 1 && layer == 0)) return ufail(n, STP_EINVAL, "bad mode for this layer");
+  if (mode == 2 && !b) return ufail(n, STP_EINVAL, "the weight gradient needs gz");
+  const Layer& ly = n->L[layer];
+  const int lev = layer < 8 ? layer / 2 : 2 - (layer - 8) / 2;
+  const Dims dm{nb, n->dm[lev].d, n->dm[lev].h, n->dm[lev].w};
+  const long long V = dm.vox();
+  const int ci = ly.cin, co = ly.cout;
+  // temporaries: BF16 copies of the inputs and the BF16 output
+  bf16 *xa = nullptr, *xb = nullptr, *y = nullptr;
+  std::vector<void*> tmp;
+  auto talloc = [&](bf16** p, long long count) -> int {
+    if (cudaMalloc((void**)p, sizeof(bf16) * std::max<long long>(count, 1)) != cudaSuccess) return STP_ENOMEM;
+    tmp.push_back(*p);
+    return STP_OK;
+  };
+  auto done = [&](int rc) {
+    cudaStreamSynchronize(n->st);
+    for (void* p : tmp) cudaFree(p);
+    return rc;
+  };
+  int rc = STP_OK;
+  if (mode == 0) {
+    if (layer == 0) {
+      if ((rc = talloc(&y, V * co))) return done(ufail(n, rc, "cudaMalloc failed"));
+      k_conv_in<<<blocks_for(V), 256, 0, n->st>>>(dm, a, n->theta + ly.woff, n->theta + ly.boff, y, co);
+      if (cudaGetLastError() != cudaSuccess) return done(ufail(n, STP_ECUDA, "k_conv_in launch failed"));
+    } else {
+      if ((rc = talloc(&xa, V * ci)) || (rc = talloc(&y, V * co))) return done(ufail(n, rc, "cudaMalloc failed"));
+      k_to_bf16<<<blocks_for(V * ci), 256, 0, n->st>>>(V * ci, a, xa);
+      if ((rc = conv3(n, dm, xa, ci, ci, ly.wt, ly.img, n->theta + ly.boff, co, y, co, 1, nullptr, 0)))
+        return done(rc);
+    }
+    k_from_bf16<<<blocks_for(V * co), 256, 0, n->st>>>(V * co, y, out);
+  } else if (mode == 1) {
+    if ((rc = talloc(&xa, V * co)) || (rc = talloc(&y, V * ci)) || (b && (rc = talloc(&xb, V * ci))))
+      return done(ufail(n, rc, "cudaMalloc failed"));
+    k_to_bf16<<<blocks_for(V * co), 256, 0, n->st>>>(V * co, a, xa);
+    if (b) k_to_bf16<<<blocks_for(V * ci), 256, 0, n->st>>>(V * ci, b, xb);
+    if ((rc = conv3(n, dm, xa, co, co, ly.wtt, ly.timg, nullptr, ci, y, ci, 0, xb, xb ? ci : 0))) return done(rc);
+    k_from_bf16<<<blocks_for(V * ci), 256, 0, n->st>>>(V * ci, y, out);
+  } else {
+    UTRY(n, cudaMemsetAsync(n->grad + ly.woff, 0, sizeof(float) * ((long long)co * ci * 27 + co), n->st));
+    if ((rc = talloc(&xb, V * co))) return done(ufail(n, rc, "cudaMalloc failed"));
+    k_to_bf16<<<blocks_for(V * co), 256, 0, n->st>>>(V * co, b, xb);
+    if (layer == 0) {
+      k_wgrad_in<<<dim3((unsigned)std::min<long long>(152 * 2, (V + 255) / 256), 27), 256, 0, n->st>>>(
+          dm, a, xb, co, n->grad + ly.woff);
+      const int bx = (int)std::min<long long>(V, 1024);
+      k_bias_grad<<<dim3(bx, 1), 128, 0, n->st>>>(V, xb, co, co, n->grad + ly.boff);
+    } else {
+      if ((rc = talloc(&xa, V * ci))) return done(ufail(n, rc, "cudaMalloc failed"));
+      k_to_bf16<<<blocks_for(V * ci), 256, 0, n->st>>>(V * ci, a, xa);
+      if ((rc = wgrad3(n, dm, xa, ci, ci, xb, co, co, ly))) return done(rc);
+    }
+    UTRY(n, cudaMemcpyAsync(out, n->grad + ly.woff, sizeof(float) * ((long long)co * ci * 27 + co),
+                            cudaMemcpyDeviceToDevice, n->st));
+  }
+  if (cudaGetLastError() != cudaSuccess) return done(ufail(n, STP_ECUDA, "a layer-check kernel failed to launch"));
+  if (cudaStreamSynchronize(n->st) != cudaSuccess) return done(ufail(n, STP_ECUDA, "layer check failed"));
+  return done(check_tc_timeout(n));
 }
 
 int stp_unet_set_output_scale(stp_unet* n, float k) {

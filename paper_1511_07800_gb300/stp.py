@@ -72,7 +72,8 @@ class BatchGroup(ctypes.Structure):
 
 class SolveStats(ctypes.Structure):
     _fields_ = [("sweeps", ctypes.c_int), ("refine_passes", ctypes.c_int),
-                ("converged", ctypes.c_int), ("rel_residual", ctypes.c_double)]
+                ("converged", ctypes.c_int), ("rel_residual", ctypes.c_double),
+                ("solve_ms", ctypes.c_double)]
 
 
 EXPORTS = ("stp_config_defaults", "stp_init", "stp_destroy", "stp_last_error", "stp_set_fields",
@@ -83,7 +84,7 @@ EXPORTS = ("stp_config_defaults", "stp_init", "stp_destroy", "stp_last_error", "
            "stp_set_learned_guess", "stp_set_harvest", "stp_unet_set_output_scale", "stp_state_size",
            "stp_get_state", "stp_set_state", "stp_batch_create", "stp_batch_destroy", "stp_batch_last_error",
            "stp_batch_step", "stp_batch_groups", "stp_sweep_tile", "stp_stats_reset",
-           "stp_stats_accumulate", "stp_stats_read")
+           "stp_stats_accumulate", "stp_stats_read", "stp_unet_layer")
 
 _lib = None
 
@@ -147,6 +148,7 @@ def lib():
     L.stp_set_state.argtypes = [vp, vp]
     L.stp_unet_set_output_scale.argtypes = [vp, ctypes.c_float]
     L.stp_set_harvest.argtypes = [vp, vp, vp]
+    L.stp_unet_layer.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp, vp, ctypes.c_int]
     _lib = L
     return L
 
@@ -264,7 +266,7 @@ class Channel:
         rc = self._check(lib().stp_poisson_solve(self._h, _addr(rhs)[0], _addr(p0)[0], float(tol), int(maxit), where,
                                                  ctypes.byref(st)), allow=(STP_ENOTCONVERGED,))
         return dict(sweeps=st.sweeps, passes=st.refine_passes, converged=bool(st.converged),
-                    rel_res=st.rel_residual, status=rc)
+                    rel_res=st.rel_residual, solve_ms=st.solve_ms, status=rc)
 
     def eval(self, term, out=None):
         """A term of the step on the current fields (see stp_eval)."""
@@ -280,13 +282,22 @@ class Channel:
         self._check(lib().stp_eval(self._h, t, ptr[0], ptr[1], ptr[2], where))
         return out if len(out) > 1 else out[0]
 
-    def get_state(self):
-        """The whole time-stepper state as a float64 numpy array (checkpoint)."""
-        buf = np.zeros(int(lib().stp_state_size(self._h)))
-        self._check(lib().stp_get_state(self._h, ctypes.c_void_p(buf.ctypes.data)))
-        return buf
+    def state_size(self):
+        return int(lib().stp_state_size(self._h))
+
+    def get_state(self, out=None):
+        """The whole time-stepper state as a float64 host array (checkpoint);
+        `out` may be a host float64 tensor (e.g. pinned) of state_size()."""
+        if out is None:
+            out = np.zeros(self.state_size())
+        ptr = out.data_ptr() if hasattr(out, "data_ptr") else out.ctypes.data
+        self._check(lib().stp_get_state(self._h, ctypes.c_void_p(ptr)))
+        return out
 
     def set_state(self, buf):
+        if hasattr(buf, "data_ptr"):
+            self._check(lib().stp_set_state(self._h, ctypes.c_void_p(buf.data_ptr())))
+            return
         buf = np.ascontiguousarray(buf, dtype=np.float64)
         self._check(lib().stp_set_state(self._h, ctypes.c_void_p(buf.ctypes.data)))
 
@@ -411,6 +422,15 @@ class UNet:
         self._check(lib().stp_unet_eval_pairs(self._h, ctypes.c_void_p(r.data_ptr()), ctypes.c_void_p(dp.data_ptr()),
                                               int(r.shape[0]), ctypes.byref(loss)))
         return loss.value
+
+    def layer(self, index, mode, a, b, out):
+        """One convolution on its own (stp_unet_layer): mode "forward",
+        "data_grad" or "weight_grad"; a, b, out torch CUDA float32 tensors
+        (b may be None), channels last."""
+        m = {"forward": 0, "data_grad": 1, "weight_grad": 2}[mode]
+        bp = ctypes.c_void_p(b.data_ptr()) if b is not None else None
+        self._check(lib().stp_unet_layer(self._h, int(index), m, ctypes.c_void_p(a.data_ptr()), bp,
+                                         ctypes.c_void_p(out.data_ptr()), int(a.shape[0])))
 
     def close(self):
         if getattr(self, "_h", None) is not None and _lib is not None:

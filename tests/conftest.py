@@ -33,3 +33,12 @@ def rel_err(a, b):
     a, b = np.asarray(a), np.asarray(b)
     den = max(float(np.abs(b).max()), 1e-300)
     return float(np.abs(a - b).max()) / den
+
+
+def gauge(p, cfg):
+    """p with its volume-weighted mean removed (the gauge stp_poisson_solve
+    returns: L p = b fixes p only up to a constant)."""
+    import numpy as np
+    from paper_1511_07800_gb300 import inputs
+    dz = np.diff(inputs.zfaces(cfg))[:, None, None]
+    return p - np.sum(p * dz) / (np.sum(dz) * p.shape[1] * p.shape[2])
