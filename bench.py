@@ -378,7 +378,7 @@ def batched_channels(steps, warmup, peak, oracle_sample=True):
 
 
 def les_paper_steps(steps, warmup, oracle_sample=True):
-    """The paper's LES workload (Sec. 5) at its own grid, 240 x 140 x 120,
+    """The paper's LES workload (Sec. 6) at its own grid, 240 x 140 x 120,
     Lx = 8, Ly = 4, Lz = 1, Re_* = 360, dt = 1e-4, Smagorinsky + van Driest,
     FP32 with FP64 refinement, from its random Fourier-curl start; the
     plane statistics are accumulated after every step, as a run gathering

@@ -191,7 +191,7 @@ int stp_batch_create(stp_handle *const *handles, int n, void *stream, stp_batch 
 void stp_batch_destroy(stp_batch *b);
 const char *stp_batch_last_error(const stp_batch *b);
 
-/* LES statistics (Sec. 5).  The velocities are taken at the cell centres
+/* LES statistics (Sec. 6).  The velocities are taken at the cell centres
    (uc, vc, wc: the mean of the two faces of each component) and averaged
    over x, y and the accumulated samples.
    stp_stats_reset: clear the sums (the first call allocates two small

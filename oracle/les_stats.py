@@ -1,4 +1,4 @@
-"""LES statistics (Sec. 5) -- TEST INFRASTRUCTURE ONLY (part of the oracle).
+"""LES statistics (Sec. 6) -- TEST INFRASTRUCTURE ONLY (part of the oracle).
 
 Plain numpy definitions of what the library's statistics kernels and its
 bulk post-processing compute, written from the paper's definitions:

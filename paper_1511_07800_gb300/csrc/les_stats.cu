@@ -1,4 +1,4 @@
-// Statistics of the LES (Sec. 5): plane averages of the velocity moments per
+// Statistics of the LES (Sec. 6): plane averages of the velocity moments per
 // level and streamwise two-point correlations, accumulated on the device
 // between steps.  Velocities are taken at the cell centres (the mean of the
 // two faces of each component), so that products are of co-located values.

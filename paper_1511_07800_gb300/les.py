@@ -1,4 +1,4 @@
-"""Bulk quantities of the LES (Sec. 5) from the mean profile the library's
+"""Bulk quantities of the LES (Sec. 6) from the mean profile the library's
 statistics kernels accumulate (Channel.stats_read): host post-processing of
 a few numbers, not part of the time step.
 

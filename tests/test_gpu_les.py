@@ -1,4 +1,4 @@
-"""The paper's LES workload (Sec. 5) on the GPU: its turbulent-like start,
+"""The paper's LES workload (Sec. 6) on the GPU: its turbulent-like start,
 whole steps against the oracle, and the statistics kernels (plane moments,
 two-point correlations) against the oracle's plain definitions."""
 import numpy as np

@@ -1,4 +1,4 @@
-"""Pins of the oracle's LES statistics (Sec. 5) against closed forms, and
+"""Pins of the oracle's LES statistics (Sec. 6) against closed forms, and
 the library's bulk post-processing against the same closed forms."""
 import math
 
@@ -97,7 +97,7 @@ def _paper_like_profile(nz, nu, U_mean, U_cl):
 
 
 def test_bulk_definitions_reproduce_the_paper_numbers():
-    """Sec. 5 prints U_mean = 15.39, Re_mean = U_mean H/nu = 5542, U_cl =
+    """Sec. 6 prints U_mean = 15.39, Re_mean = U_mean H/nu = 5542, U_cl =
     18.30, the Pope estimate (1/0.4) log Re_* + 3.47 = 18.18, U_max/U_mean =
     1.19, C_f = 2 u_*^2/U_mean^2 = 8.44e-3 and Dean's 0.073 Re_mean^-0.25 =
     8.46e-3 (tests/golden/paper_values.json, les_bulk).  A mean profile with
