@@ -437,7 +437,7 @@ def les_paper_steps(steps, warmup, oracle_sample=True):
 
 def headline_config(args):
     from paper_1511_07800_gb300 import inputs
-    cfg = inputs.preset(args.workload, zline=1 if args.solver == "zline" else 0)
+    cfg = inputs.preset(args.workload, zline=1 if args.solver == "zline" else 0, cn_zline=1)
     if args.grid:
         nx, ny, nz = (int(x) for x in args.grid.lower().split("x"))
         cfg.update(nx=nx, ny=ny, nz=nz)
@@ -507,20 +507,27 @@ def run_reference(args):
 
 def _auto_cn(cfg):
     """Crank-Nicolson Jacobi sweeps for the workload, by the library's rule
-    (contraction hS/(1+hS) per sweep, down to 1e-12); both arms get the
-    count explicitly so they run the same sweeps."""
+    (contraction hS/(1+hS) per sweep, down to 1e-12; S the largest diagonal
+    weight for point sweeps, the x-y coupling weights alone for z-line
+    sweeps); both arms get the count explicitly so they run the same
+    sweeps."""
     from paper_1511_07800_gb300 import inputs
     zf = inputs.zfaces(cfg)
     dz = [zf[k + 1] - zf[k] for k in range(cfg["nz"])]
     zc = [0.5 * (zf[k] + zf[k + 1]) for k in range(cfg["nz"])]
     dzf = [dz[0]] + [zc[k] - zc[k - 1] for k in range(1, cfg["nz"])] + [dz[-1]]
     dx, dy = cfg["Lx"] / cfg["nx"], cfg["Ly"] / cfg["ny"]
-    smax = max(4 / dx**2 + 4 / dy**2 + 2 / (dzf[k] * dz[k]) + 2 / (dzf[k + 1] * dz[k]) for k in range(cfg["nz"]))
+    if cfg.get("cn_zline"):
+        smax = 2 / dx**2 + 2 / dy**2
+    else:
+        smax = max(4 / dx**2 + 4 / dy**2 + 2 / (dzf[k] * dz[k]) + 2 / (dzf[k + 1] * dz[k])
+                   for k in range(cfg["nz"]))
     hs = 0.5 * cfg["dt"] * cfg["nu"] * (4.0 if cfg.get("les") else 1.0) * smax
     rho = hs / (1 + hs)
     if rho <= 0:
         return 1
-    return max(2, min(int(math.ceil(math.log(1e-12) / math.log(rho))), 200))
+    lo = 1 if cfg.get("cn_zline") else 2
+    return max(lo, min(int(math.ceil(math.log(1e-12) / math.log(rho))), 200))
 
 
 def timed_steps(ch, steps, stream, flush):

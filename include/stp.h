@@ -95,6 +95,13 @@ typedef struct stp_config {
                                 (Thomas) with the x-y neighbours held, SRJ
                                 weights from the line-Jacobi spectrum (suits
                                 wall-stretched grids)                            */
+    int cn_zline;            /* Crank-Nicolson system: 0 point Jacobi sweeps;
+                                1 z-line Jacobi: each z column solved exactly
+                                (Thomas) with the x-y neighbours of the previous
+                                iterate (Sec. 3.1 names no solver; the wall-
+                                normal couplings of a stretched grid then cost
+                                no sweeps: automatic count from the x-y
+                                couplings alone)                                  */
 } stp_config;
 
 typedef struct stp_step_stats {

@@ -46,6 +46,7 @@ class Params(ctypes.Structure):
         ("cn_sweeps", ctypes.c_int), ("srj_m", ctypes.c_int),
         ("srj_omega", ctypes.POINTER(ctypes.c_double)),
         ("ptol", ctypes.c_double), ("pmaxit", ctypes.c_int), ("zline", ctypes.c_int),
+        ("cn_zline", ctypes.c_int),
     ]
 
 
@@ -98,7 +99,7 @@ class Oracle:
     (omega: the SRJ schedule as a float64 array)."""
 
     KEYS = ("nx", "ny", "nz", "Lx", "Ly", "Lz", "nu", "dt", "forcing", "fx", "ubulk", "les", "cs",
-            "vd_a", "re_tau", "stretch", "cn_sweeps", "ptol", "pmaxit", "zline")
+            "vd_a", "re_tau", "stretch", "cn_sweeps", "ptol", "pmaxit", "zline", "cn_zline")
 
     def __init__(self, cfg):
         self.cfg = dict(cfg)

@@ -59,6 +59,7 @@ typedef struct {
     double ptol;      /* relative l2 residual tolerance of the pressure solve */
     int pmaxit;       /* cap on SRJ sweeps per solve                          */
     int zline;        /* 0: point Jacobi-SOR sweeps; 1: z-line Jacobi-SOR      */
+    int cn_zline;     /* Crank-Nicolson by 0: point Jacobi; 1: z-line Jacobi  */
 } orc_params;
 
 /* ------------------------------------------------------------------------ */
@@ -447,8 +448,89 @@ static void diffusion(const grid *g, const double *u, const double *v, const dou
     }
 }
 
-/* Crank-Nicolson system (I - dt/2 D) a* = rhs by point Jacobi, rhs as the
-   first iterate.  One sweep: a_new = (rhs + dt/2 (D a + S_D a)) / (1 + dt/2 S_D). */
+static void thomas(int n, const double *lo, const double *di, const double *up, const double *rhs, double *x,
+                   double *cp, double *dp);
+
+/* One z-line Jacobi sweep of (I - h D) a = rhs: for every column the
+   z-couplings of D are kept implicit and the x-y neighbours are taken from
+   the previous iterate a, i.e. per column
+     (1 + h S_D) x_k - h cz+_k x_{k+1} - h cz-_k x_{k-1}
+         = rhs_k + h sum_{x-y nb} c_nb a_nb,
+   solved exactly (Thomas).  S_D is the diagonal weight of D (wall ghosts
+   folded in), cz+/- the coefficients of D on the levels above and below,
+   c_nb those of the x-y neighbours. */
+static void cn_line_sweep(const grid *g, const double *nu, double h, const double *ru, const double *rv,
+                          const double *rw, const double *au, const double *av, const double *aw, double *us,
+                          double *vs, double *ws)
+{
+    int j, nz = g->nz;
+    double dx2 = g->dx * g->dx, dy2 = g->dy * g->dy;
+#pragma omp parallel for schedule(static)
+    for (j = 0; j < g->ny; j++) {
+        double *lo = (double *)malloc(sizeof(double) * 6 * (nz + 1)), *di = lo + (nz + 1), *up = di + (nz + 1);
+        double *rh = up + (nz + 1), *cp = rh + (nz + 1), *dp = cp + (nz + 1);
+        double *x = (double *)malloc(sizeof(double) * (nz + 1));
+        int i, k;
+        for (i = 0; i < g->nx; i++) {
+            /* u: levels 0..nz-1 */
+            for (k = 0; k < nz; k++) {
+                double czp = (k < nz - 1) ? nu_xz(g, nu, i, j, k + 1) / (g->dzf[k + 1] * g->dz[k]) : 0.0;
+                double czm = (k > 0) ? nu_xz(g, nu, i, j, k) / (g->dzf[k] * g->dz[k]) : 0.0;
+                double xy = (cen_g(g, nu, i, j, k) * vel_g(g, au, i + 1, j, k) +
+                             cen_g(g, nu, i - 1, j, k) * vel_g(g, au, i - 1, j, k)) / dx2 +
+                            (nu_xy(g, nu, i, j + 1, k) * vel_g(g, au, i, j + 1, k) +
+                             nu_xy(g, nu, i, j, k) * vel_g(g, au, i, j - 1, k)) / dy2;
+                di[k] = 1.0 + h * diag_u(g, nu, i, j, k);
+                up[k] = -h * czp;
+                lo[k] = -h * czm;
+                rh[k] = ru[IDX(g, i, j, k)] + h * xy;
+            }
+            thomas(nz, lo, di, up, rh, x, cp, dp);
+            for (k = 0; k < nz; k++) us[IDX(g, i, j, k)] = x[k];
+            /* v: levels 0..nz-1 */
+            for (k = 0; k < nz; k++) {
+                double czp = (k < nz - 1) ? nu_yz(g, nu, i, j, k + 1) / (g->dzf[k + 1] * g->dz[k]) : 0.0;
+                double czm = (k > 0) ? nu_yz(g, nu, i, j, k) / (g->dzf[k] * g->dz[k]) : 0.0;
+                double xy = (nu_xy(g, nu, i + 1, j, k) * vel_g(g, av, i + 1, j, k) +
+                             nu_xy(g, nu, i, j, k) * vel_g(g, av, i - 1, j, k)) / dx2 +
+                            (cen_g(g, nu, i, j, k) * vel_g(g, av, i, j + 1, k) +
+                             cen_g(g, nu, i, j - 1, k) * vel_g(g, av, i, j - 1, k)) / dy2;
+                di[k] = 1.0 + h * diag_v(g, nu, i, j, k);
+                up[k] = -h * czp;
+                lo[k] = -h * czm;
+                rh[k] = rv[IDX(g, i, j, k)] + h * xy;
+            }
+            thomas(nz, lo, di, up, rh, x, cp, dp);
+            for (k = 0; k < nz; k++) vs[IDX(g, i, j, k)] = x[k];
+            /* w: interior faces 1..nz-1 (row k - 1 of the system); the wall
+               faces are zero and couple to nothing */
+            ws[IDX(g, i, j, 0)] = 0.0;
+            ws[IDX(g, i, j, nz)] = 0.0;
+            if (nz >= 2) {
+                for (k = 1; k < nz; k++) {
+                    double czp = (k < nz - 1) ? cen_g(g, nu, i, j, k) / (g->dz[k] * g->hz[k]) : 0.0;
+                    double czm = (k > 1) ? cen_g(g, nu, i, j, k - 1) / (g->dz[k - 1] * g->hz[k]) : 0.0;
+                    double xy = (nu_xz(g, nu, i + 1, j, k) * wv(g, aw, i + 1, j, k) +
+                                 nu_xz(g, nu, i, j, k) * wv(g, aw, i - 1, j, k)) / dx2 +
+                                (nu_yz(g, nu, i, j + 1, k) * wv(g, aw, i, j + 1, k) +
+                                 nu_yz(g, nu, i, j, k) * wv(g, aw, i, j - 1, k)) / dy2;
+                    di[k - 1] = 1.0 + h * diag_w(g, nu, i, j, k);
+                    up[k - 1] = -h * czp;
+                    lo[k - 1] = -h * czm;
+                    rh[k - 1] = rw[IDX(g, i, j, k)] + h * xy;
+                }
+                thomas(nz - 1, lo, di, up, rh, x, cp, dp);
+                for (k = 1; k < nz; k++) ws[IDX(g, i, j, k)] = x[k - 1];
+            }
+        }
+        free(lo);
+        free(x);
+    }
+}
+
+/* Crank-Nicolson system (I - dt/2 D) a* = rhs by point Jacobi (or, with
+   cn_zline, z-line Jacobi), rhs as the first iterate.  One point sweep:
+   a_new = (rhs + dt/2 (D a + S_D a)) / (1 + dt/2 S_D). */
 static void cn_solve(const orc_params *P, const grid *g, const double *nu, double *ru, double *rv, double *rw,
                      double *us, double *vs, double *ws)
 {
@@ -463,6 +545,13 @@ static void cn_solve(const orc_params *P, const grid *g, const double *nu, doubl
     memcpy(av, rv, sizeof(double) * nc);
     memcpy(aw, rw, sizeof(double) * nw);
     for (s = 0; s < P->cn_sweeps; s++) {
+        if (P->cn_zline) {
+            cn_line_sweep(g, nu, h, ru, rv, rw, au, av, aw, us, vs, ws);
+            memcpy(au, us, sizeof(double) * nc);
+            memcpy(av, vs, sizeof(double) * nc);
+            memcpy(aw, ws, sizeof(double) * nw);
+            continue;
+        }
         diffusion(g, au, av, aw, nu, Du, Dv, Dw);
 #pragma omp parallel for schedule(static)
         for (k = 0; k < nz; k++) {

@@ -55,6 +55,7 @@ struct stp_handle {
   // the fields before the current step, restored when the step diverges
   void *bu = nullptr, *bv = nullptr, *bw = nullptr;
   double* bp = nullptr;
+  void* cn_scr = nullptr;  // z-line Crank-Nicolson: (c', d') pairs of the forward elimination
 
   Red red{};
   double* h_sc = nullptr;  // pinned copies of red.sc and red.flag
@@ -326,19 +327,25 @@ int auto_cycle(double mn, double mx) {
 // Jacobi sweeps for the CN system: the iteration contracts by at most
 // hS/(1+hS), S the largest diagonal weight (nu_T bounded by 4 nu with LES);
 // enough sweeps to reach 1e-12.
+// Crank-Nicolson sweeps to a 1e-12 contraction.  Point Jacobi contracts by
+// hS/(1+hS) a sweep with S the largest diagonal weight; z-line Jacobi by the
+// same bound with S the x-y coupling weights alone (the column matrix is an
+// M-matrix whose row sums are at least 1 + h S_xy).  nu_T is bounded by 4 nu
+// with LES.
 int auto_cn_sweeps(const stp_config& c, const ZGrid& z) {
   const double dx = c.Lx / c.nx, dy = c.Ly / c.ny;
   double smax = 0.0;
   for (int k = 0; k < c.nz; k++) {
     const double sz = 2.0 / (z.dzf[k] * z.dz[k]) + 2.0 / (z.dzf[k + 1] * z.dz[k]);
-    smax = std::max(smax, 4.0 / (dx * dx) + 4.0 / (dy * dy) + sz);
+    smax = std::max(smax, 4.0 / (dx * dx) + 4.0 / (dy * dy) + (c.cn_zline ? 0.0 : sz));
   }
+  if (c.cn_zline) smax = 2.0 / (dx * dx) + 2.0 / (dy * dy);
   const double nu = c.nu * (c.les ? 4.0 : 1.0);
   const double hs = 0.5 * c.dt * nu * smax;
   const double rho = hs / (1.0 + hs);
   if (rho <= 0) return 1;
   int k = (int)std::ceil(std::log(1e-12) / std::log(rho));
-  return std::max(2, std::min(k, 200));
+  return std::max(c.cn_zline ? 1 : 2, std::min(k, 200));
 }
 
 int validate(const stp_config* c, std::string* why) {
@@ -355,6 +362,7 @@ int validate(const stp_config* c, std::string* why) {
   if (c->srj_omega && c->srj_m <= 0) return *why = "srj_omega given without srj_m", STP_EINVAL;
   if (c->srj_m % 2) return *why = "the SRJ cycle length must be even", STP_EINVAL;
   if (c->zline != 0 && c->zline != 1) return *why = "zline must be 0 or 1", STP_EINVAL;
+  if (c->cn_zline != 0 && c->cn_zline != 1) return *why = "cn_zline must be 0 or 1", STP_EINVAL;
   if (!c->srj_omega && c->srj_m > 0 && !pow2(c->srj_m)) return *why = "library schedules need srj_m a power of two", STP_EINVAL;
   if (c->les && !(c->cs >= 0 && c->vd_a > 0 && c->re_tau > 0)) return *why = "bad LES constants", STP_EINVAL;
   return STP_OK;
@@ -948,9 +956,14 @@ int step_pre(stp_handle* h, const Geom<T>& g, cudaStream_t s) {
   const int n = h->cn_sweeps;
   for (int k = 0; k < n; k++) {
     void** out = ((n - 1 - k) % 2 == 0) ? U : Tb;
-    CUDA_TRY(h, launch_cn_sweep<T>(g, c.les != 0, nu, nu0, (T)(0.5 * c.dt), (const T*)h->ru, (const T*)h->rv,
-                                   (const T*)h->rw, (const T*)cur[0], (const T*)cur[1], (const T*)cur[2],
-                                   (T*)out[0], (T*)out[1], (T*)out[2], s));
+    if (c.cn_zline)
+      CUDA_TRY(h, launch_cn_line<T>(g, c.les != 0, nu, nu0, (T)(0.5 * c.dt), (const T*)h->ru, (const T*)h->rv,
+                                    (const T*)h->rw, (const T*)cur[0], (const T*)cur[1], (const T*)cur[2],
+                                    (T*)out[0], (T*)out[1], (T*)out[2], h->cn_scr, s));
+    else
+      CUDA_TRY(h, launch_cn_sweep<T>(g, c.les != 0, nu, nu0, (T)(0.5 * c.dt), (const T*)h->ru, (const T*)h->rv,
+                                     (const T*)h->rw, (const T*)cur[0], (const T*)cur[1], (const T*)cur[2],
+                                     (T*)out[0], (T*)out[1], (T*)out[2], s));
     cur = out;
   }
   if (n == 0) {
@@ -1188,6 +1201,7 @@ int stp_init(const stp_config* cfg, stp_handle** out) {
   A(&h->bv, es * nc);
   A(&h->bw, es * nw);
   A((void**)&h->bp, sizeof(double) * nc);
+  if (cfg->cn_zline) A(&h->cn_scr, 2 * es * 3 * nw);
   const Launch big = {dim3((h->nx + 31) / 32, (h->ny + 7) / 8, h->nz + 1), dim3(32, 8, 1), 0};
   const size_t maxblocks = (size_t)big.grid.x * big.grid.y * big.grid.z + 152 * 32;
   A((void**)&h->red.partial, sizeof(double) * 2 * maxblocks);

@@ -265,15 +265,18 @@ __global__ void __launch_bounds__(kBX* kBY) k_momentum(Geom<T> g, const T* __res
   Pt<T> P(g, i, j, k);
   const int q = at(g.nx, g.ny, i, j, k);
   const T hdt = T(0.5) * dt;
+  // a history level whose coefficient is zero is not read: after the fields
+  // are set its slot may hold anything, even the Inf of a run that diverged
+  auto hist = [&](const T* __restrict__ f, int level) { return n >= level ? __ldg(f + q) : T(0); };
   if (k < g.nz) {
     const ViscU<T, LES> a = visc_u<T, LES>(P, N, u, v, w, true);
     const T n0 = -adv_u(P, u, v, w) + a.cross + fx;
     Nu0[q] = n0;
-    ru[q] = __ldg(u + q) + dt * (b0 * n0 + b1 * __ldg(Nu1 + q) + b2 * __ldg(Nu2 + q)) + hdt * a.diff;
+    ru[q] = __ldg(u + q) + dt * (b0 * n0 + b1 * hist(Nu1, 1) + b2 * hist(Nu2, 2)) + hdt * a.diff;
     const ViscU<T, LES> bb = visc_v<T, LES>(P, N, u, v, w, true);
     const T m0 = -adv_v(P, u, v, w) + bb.cross;
     Nv0[q] = m0;
-    rv[q] = __ldg(v + q) + dt * (b0 * m0 + b1 * __ldg(Nv1 + q) + b2 * __ldg(Nv2 + q)) + hdt * bb.diff;
+    rv[q] = __ldg(v + q) + dt * (b0 * m0 + b1 * hist(Nv1, 1) + b2 * hist(Nv2, 2)) + hdt * bb.diff;
   }
   if (k == 0 || k == g.nz) {
     Nw0[q] = T(0);
@@ -282,7 +285,7 @@ __global__ void __launch_bounds__(kBX* kBY) k_momentum(Geom<T> g, const T* __res
     const ViscU<T, LES> c = visc_w<T, LES>(P, N, u, v, w, true);
     const T l0 = -adv_w(P, u, v, w) + c.cross;
     Nw0[q] = l0;
-    rw[q] = __ldg(w + q) + dt * (b0 * l0 + b1 * __ldg(Nw1 + q) + b2 * __ldg(Nw2 + q)) + hdt * c.diff;
+    rw[q] = __ldg(w + q) + dt * (b0 * l0 + b1 * hist(Nw1, 1) + b2 * hist(Nw2, 2)) + hdt * c.diff;
   }
 }
 
@@ -340,6 +343,114 @@ __global__ void __launch_bounds__(kBX* kBY) k_cn_sweep(Geom<T> g, Visc<T, LES> N
   } else {
     const ViscU<T, LES> c = visc_w<T, LES>(P, N, au, av, aw, false);
     ow[q] = (__ldg(rw + q) + hdt * (c.diff + c.diag * __ldg(aw + q))) / (T(1) + hdt * c.diag);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// One z-line Jacobi sweep of (I - dt/2 D) a = rhs for the three components:
+// per column the z couplings of D stay implicit and the x-y neighbours come
+// from the previous iterate a,
+//   (1 + h S_D) x_k - h cz+_k x_{k+1} - h cz-_k x_{k-1}
+//       = rhs_k + h sum_{x-y nb} c_nb a_nb,
+// solved by the Thomas algorithm.  One thread per column and component
+// (blockIdx.z: u, v, w), consecutive threads along x; the forward
+// elimination keeps (c'_k, d'_k) in the scratch array, the back
+// substitution reads them.  S_D, the couplings and the wall ghosts are those
+// of the point sweep (visc_u / visc_v / visc_w).
+// ---------------------------------------------------------------------------
+template <typename T>
+struct Pair;
+template <>
+struct Pair<float> {
+  using V = float2;
+};
+template <>
+struct Pair<double> {
+  using V = double2;
+};
+
+template <typename T, bool LES>
+__global__ void __launch_bounds__(128) k_cn_line(Geom<T> g, Visc<T, LES> N, T h, const T* __restrict__ ru,
+                                                  const T* __restrict__ rv, const T* __restrict__ rw,
+                                                  const T* __restrict__ au, const T* __restrict__ av,
+                                                  const T* __restrict__ aw, T* __restrict__ ou, T* __restrict__ ov,
+                                                  T* __restrict__ ow, typename Pair<T>::V* __restrict__ scr) {
+  using V2 = typename Pair<T>::V;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, comp = blockIdx.z;
+  const int nx = g.nx, ny = g.ny, nz = g.nz;
+  if (i >= nx) return;
+  const int im = i == 0 ? nx - 1 : i - 1, ip = i == nx - 1 ? 0 : i + 1;
+  const int jm = j == 0 ? ny - 1 : j - 1, jp = j == ny - 1 ? 0 : j + 1;
+  const int plane = nx * ny, c0 = j * nx + i;
+  V2* __restrict__ S = scr + (size_t)comp * (nz + 1) * plane;
+  const T idx2 = g.idx2, idy2 = g.idy2;
+  T cprev = T(0), dprev = T(0);
+  if (comp < 2) {
+    const T* __restrict__ a = comp == 0 ? au : av;
+    const T* __restrict__ r = comp == 0 ? ru : rv;
+    T* __restrict__ o = comp == 0 ? ou : ov;
+    for (int k = 0; k < nz; k++) {
+      const int lev = k * plane;
+      T nxp, nxm, nyp, nym, nzp, nzm;
+      if (comp == 0) {
+        nxp = N.c(i, j, k);
+        nxm = N.c(im, j, k);
+        nyp = N.e4(im, i, j, jp, k);
+        nym = N.e4(im, i, jm, j, k);
+        nzp = N.ez_x(im, i, j, k + 1);
+        nzm = N.ez_x(im, i, j, k);
+      } else {
+        nxp = N.e4(i, ip, jm, j, k);
+        nxm = N.e4(im, i, jm, j, k);
+        nyp = N.c(i, j, k);
+        nym = N.c(i, jm, k);
+        nzp = N.ez_y(i, jm, j, k + 1);
+        nzm = N.ez_y(i, jm, j, k);
+      }
+      const T idz = __ldg(g.idz + k), izp = __ldg(g.idzf + k + 1), izm = __ldg(g.idzf + k);
+      const T gu = (k == nz - 1) ? T(2) : T(1), gd = (k == 0) ? T(2) : T(1);
+      const T sd = (nxp + nxm) * idx2 + (nyp + nym) * idy2 + (gu * nzp * izp + gd * nzm * izm) * idz;
+      const T xy = (nxp * __ldg(a + lev + j * nx + ip) + nxm * __ldg(a + lev + j * nx + im)) * idx2 +
+                   (nyp * __ldg(a + lev + jp * nx + i) + nym * __ldg(a + lev + jm * nx + i)) * idy2;
+      const T lo = k > 0 ? -h * nzm * izm * idz : T(0);
+      const T up = k < nz - 1 ? -h * nzp * izp * idz : T(0);
+      const T inv = T(1) / ((T(1) + h * sd) - lo * cprev);
+      cprev = up * inv;
+      dprev = (__ldg(r + lev + c0) + h * xy - lo * dprev) * inv;
+      S[lev + c0] = V2{cprev, dprev};
+    }
+    T x = T(0);
+    for (int k = nz - 1; k >= 0; k--) {
+      const V2 cd = S[k * plane + c0];
+      x = cd.y - cd.x * x;
+      o[k * plane + c0] = x;
+    }
+  } else {
+    // w on the interior faces 1..nz-1; the wall faces are zero
+    ow[c0] = T(0);
+    ow[nz * plane + c0] = T(0);
+    for (int c = 1; c < nz; c++) {
+      const int lev = c * plane;
+      const T nxp = N.ez_x(i, ip, j, c), nxm = N.ez_x(im, i, j, c);
+      const T nyp = N.ez_y(i, j, jp, c), nym = N.ez_y(i, jm, j, c);
+      const T nzp = N.c(i, j, c), nzm = N.c(i, j, c - 1);
+      const T ih = __ldg(g.ihz + c), izp = __ldg(g.idz + c), izm = __ldg(g.idz + c - 1);
+      const T sd = (nxp + nxm) * idx2 + (nyp + nym) * idy2 + (nzp * izp + nzm * izm) * ih;
+      const T xy = (nxp * __ldg(aw + lev + j * nx + ip) + nxm * __ldg(aw + lev + j * nx + im)) * idx2 +
+                   (nyp * __ldg(aw + lev + jp * nx + i) + nym * __ldg(aw + lev + jm * nx + i)) * idy2;
+      const T lo = c > 1 ? -h * nzm * izm * ih : T(0);
+      const T up = c < nz - 1 ? -h * nzp * izp * ih : T(0);
+      const T inv = T(1) / ((T(1) + h * sd) - lo * cprev);
+      cprev = up * inv;
+      dprev = (__ldg(rw + lev + c0) + h * xy - lo * dprev) * inv;
+      S[lev + c0] = V2{cprev, dprev};
+    }
+    T x = T(0);
+    for (int c = nz - 1; c >= 1; c--) {
+      const V2 cd = S[c * plane + c0];
+      x = cd.y - cd.x * x;
+      ow[c * plane + c0] = x;
+    }
   }
 }
 
@@ -509,6 +620,22 @@ cudaError_t launch_cn_sweep(const Geom<T>& g, bool les, const T* nu, T nu0, T hd
 }
 
 template <typename T>
+cudaError_t launch_cn_line(const Geom<T>& g, bool les, const T* nu, T nu0, T hdt, const T* ru, const T* rv,
+                           const T* rw, const T* au, const T* av, const T* aw, T* ou, T* ov, T* ow, void* scratch,
+                           cudaStream_t s) {
+  const dim3 block(128), grid((g.nx + 127) / 128, g.ny, 3);
+  using V2 = typename Pair<T>::V;
+  if (les) {
+    Visc<T, true> N{nu, nu0, g.nx, g.ny, g.nz};
+    k_cn_line<T, true><<<grid, block, 0, s>>>(g, N, hdt, ru, rv, rw, au, av, aw, ou, ov, ow, (V2*)scratch);
+  } else {
+    Visc<T, false> N{nu, nu0, g.nx, g.ny, g.nz};
+    k_cn_line<T, false><<<grid, block, 0, s>>>(g, N, hdt, ru, rv, rw, au, av, aw, ou, ov, ow, (V2*)scratch);
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_explicit_only(const Geom<T>& g, bool les, const T* u, const T* v, const T* w, const T* nu,
                                  T nu0, T fx, T* Nu, T* Nv, T* Nw, cudaStream_t s) {
   Launch l = plane_launch(g.nx, g.ny, g.nz + 1);
@@ -578,6 +705,8 @@ cudaError_t launch_convert(Td* dst, const Ts* src, size_t n, cudaStream_t s) {
                                           Hist<T>, T, T*, T*, T*, cudaStream_t);                                    \
   template cudaError_t launch_cn_sweep<T>(const Geom<T>&, bool, const T*, T, T, const T*, const T*, const T*,      \
                                           const T*, const T*, const T*, T*, T*, T*, cudaStream_t);                  \
+  template cudaError_t launch_cn_line<T>(const Geom<T>&, bool, const T*, T, T, const T*, const T*, const T*,       \
+                                         const T*, const T*, const T*, T*, T*, T*, void*, cudaStream_t);            \
   template cudaError_t launch_explicit_only<T>(const Geom<T>&, bool, const T*, const T*, const T*, const T*, T, T, \
                                                T*, T*, T*, cudaStream_t);                                           \
   template cudaError_t launch_diffusion_only<T>(const Geom<T>&, bool, const T*, const T*, const T*, const T*, T,   \

@@ -144,6 +144,13 @@ cudaError_t launch_cn_sweep(const Geom<T>& g, bool les, const T* nu, T nu0, T hd
                             const T* rw, const T* au, const T* av, const T* aw, T* ou, T* ov, T* ow,
                             cudaStream_t s);
 
+// One z-line Jacobi sweep of the same system (columns solved by Thomas,
+// x-y neighbours from a); scratch holds 3 (nz + 1) nx ny pairs of T.
+template <typename T>
+cudaError_t launch_cn_line(const Geom<T>& g, bool les, const T* nu, T nu0, T hdt, const T* ru, const T* rv,
+                           const T* rw, const T* au, const T* av, const T* aw, T* ou, T* ov, T* ow, void* scratch,
+                           cudaStream_t s);
+
 // b = D u / dt, ||b||^2 reduced into sc[SC_BNORM] (as the norm), flags reset.
 template <typename T>
 cudaError_t launch_divergence_rhs(const Geom<T>& g, const T* u, const T* v, const T* w, double idt, double* b,

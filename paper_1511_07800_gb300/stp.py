@@ -49,6 +49,7 @@ class Config(ctypes.Structure):
         ("srj_omega", ctypes.POINTER(ctypes.c_double)),
         ("inner_tol", ctypes.c_double), ("cfl_check", ctypes.c_int),
         ("device", ctypes.c_int), ("stream", ctypes.c_void_p), ("zline", ctypes.c_int),
+        ("cn_zline", ctypes.c_int),
     ]
 
 
@@ -158,7 +159,8 @@ def make_config(cfg, precision="fp64", device=0, stream=None, omega=None):
     c = Config()
     lib().stp_config_defaults(ctypes.byref(c))
     for k in ("nx", "ny", "nz", "Lx", "Ly", "Lz", "nu", "dt", "forcing", "fx", "ubulk", "les", "cs", "vd_a",
-              "re_tau", "stretch", "ptol", "pmaxit", "cn_sweeps", "srj_m", "inner_tol", "cfl_check", "zline"):
+              "re_tau", "stretch", "ptol", "pmaxit", "cn_sweeps", "srj_m", "inner_tol", "cfl_check", "zline",
+              "cn_zline"):
         if k in cfg and cfg[k] is not None:
             setattr(c, k, type(getattr(c, k))(cfg[k]))
     c.precision = STP_FP64 if precision in ("fp64", 0) else STP_FP32_REFINE

@@ -134,6 +134,49 @@ def test_step_parity_fp64(stp_lib, orc, stretch, les, forcing):
         assert abs(sg["ubulk"] - 1.0) < 1e-12
 
 
+@pytest.mark.parametrize("stretch,les,forcing,sweeps", [(2.0, 1, 1, 2), (0.0, 0, 0, 3), (2.0, 0, 0, 1),
+                                                         (1.0, 1, 0, 4)])
+def test_step_parity_cn_zline_fp64(stp_lib, orc, stretch, les, forcing, sweeps):
+    """Whole steps with the Crank-Nicolson system solved by z-line Jacobi
+    sweeps (Thomas on every column, x-y neighbours from the previous
+    iterate), held to a few sweeps so that every sweep's exact arithmetic
+    matters: every field agrees with the oracle's line sweeps to 1e-10."""
+    cfg = case(stretch=stretch, les=les, forcing=forcing, ptol=0.0, pmaxit=2 * 16, nu=1 / 300.0, dt=4e-3,
+               cn_zline=1, cn_sweeps=sweeps)
+    om = schedule(cfg, 16)
+    fo, so, fg, sg = run_both(stp_lib, orc, cfg, turbulent_like(cfg, 3), 4, om)
+    for k in ("u", "v", "w", "p", "nu"):
+        e = rel_err(fg[k], fo[k]) if k != "p" else rel_err(fg[k] - fg[k].mean(), fo[k] - fo[k].mean())
+        assert e < TOL64, (k, e)
+
+
+@pytest.mark.parametrize("shape", [(40, 19, 14), (33, 7, 9), (64, 24, 32)])
+def test_step_cn_zline_fp32_and_converged(stp_lib, orc, shape):
+    """FP32 steps with z-line Crank-Nicolson sweeps and converged pressure
+    solves stay within the FP32 bounds of the FP64 oracle; with the automatic
+    sweep count (contraction below 1e-12) the z-line and point solves of the
+    Crank-Nicolson system give the same step to 1e-10 in FP64."""
+    nx, ny, nz = shape
+    base = case(nx=nx, ny=ny, nz=nz, stretch=2.0, les=1, nu=1 / 500.0, cn_zline=1, cn_sweeps=5)
+    om = schedule(base, 16)
+    fo, so, fg, sg = run_both(stp_lib, orc, base, turbulent_like(base, 6), 3, om, precision="fp32")
+    assert sg["converged"]
+    scale = max(np.abs(fo[k]).max() for k in ("u", "v", "w"))
+    for k in ("u", "v", "w"):
+        assert np.abs(fg[k] - fo[k]).max() / scale < 2e-6, k
+    out = {}
+    for zl in (0, 1):
+        # fixed pressure sweeps, so that the solves stay linear in b and the
+        # two runs differ only by the Crank-Nicolson solutions (1e-12)
+        with stp_lib.Channel(dict(base, cn_zline=zl, cn_sweeps=0, ptol=0.0, pmaxit=32), precision="fp64",
+                             omega=om) as ch:
+            ch.set_fields(*turbulent_like(base, 6))
+            ch.step(3)
+            out[zl] = ch.get_fields()
+    for k in ("u", "v", "w"):
+        assert rel_err(out[1][k], out[0][k]) < 1e-10, k
+
+
 def test_step_parity_converged_solves(stp_lib, orc):
     """Steps with tolerance-driven solves take the same sweep counts and
     agree to 1e-10 (instability workload shape on a 2-D slice)."""

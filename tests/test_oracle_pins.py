@@ -503,3 +503,67 @@ def test_projection_divergence_invariant(orc):
     # the noise gives |div u^n| ~ 1e-3/h ~ 0.1; the projection removes it to the
     # solver tolerance
     assert np.sqrt(np.sum(d * d)) < 2e-9 * np.sqrt(np.sum(o.divergence(u, v, w) ** 2)) + 1e-12
+
+
+# ------------------------------------------------- Crank-Nicolson on z lines
+
+def _cn_dense(o, cfg, nu, ru, rv, rw):
+    """The Crank-Nicolson system (I - dt/2 D) a = rhs solved directly: D is
+    assembled column by column from the oracle's diffusion operator applied
+    to unit vectors (it is linear and acts on each component alone), and
+    each component's system is solved with numpy's dense solver."""
+    h = 0.5 * cfg["dt"]
+    sc, sw = ru.shape, rw.shape
+    out = []
+    for comp, (rhs, shape) in enumerate(((ru, sc), (rv, sc), (rw, sw))):
+        n = int(np.prod(shape))
+        idx = [q for q in range(n) if comp < 2 or 0 < q // (shape[1] * shape[2]) < shape[0] - 1]
+        A = np.zeros((len(idx), len(idx)))
+        for col, q in enumerate(idx):
+            e = [np.zeros(sc), np.zeros(sc), np.zeros(sw)]
+            e[comp].flat[q] = 1.0
+            D = o.diffusion(*e, nu)[comp]
+            A[:, col] = -h * D.ravel()[idx]
+            A[col, col] += 1.0
+        a = np.zeros(shape)
+        a.flat[idx] = np.linalg.solve(A, rhs.ravel()[idx])
+        out.append(a)
+    return out
+
+
+def test_cn_line_jacobi_reaches_the_direct_solution(orc):
+    """The z-line reading of the Crank-Nicolson solve (each z column solved
+    exactly with the x-y neighbours of the previous iterate) converges to
+    the solution of (I - dt/2 D) a = rhs found by a dense direct solve, on a
+    wall-stretched grid with a spatially varying eddy viscosity; so does
+    point Jacobi, to the same solution."""
+    cfg = small_cfg(nx=4, ny=3, nz=5, stretch=2.0, dt=0.05)
+    u, v, w, p, nu = inputs.random_state(cfg, 13)
+    o = orc.Oracle(cfg)
+    exact = _cn_dense(o, cfg, nu, u, v, w)
+    for zl, sweeps in ((1, 40), (0, 400)):
+        a = orc.Oracle(dict(cfg, cn_zline=zl, cn_sweeps=sweeps)).cn_solve(nu, u, v, w)
+        for got, want in zip(a, exact):
+            assert np.abs(got - want).max() < 1e-12 * max(1.0, np.abs(want).max()), zl
+
+
+def test_cn_line_jacobi_contraction_bound(orc):
+    """Each z-line sweep contracts the error in the max norm at least by
+    rho = h S / (1 + h S), S the largest sum of the x-y coupling weights
+    (2 nu_max / dx^2 + 2 nu_max / dy^2), since the column matrix is an
+    M-matrix with row sums >= 1 + h S_xy; here rho is far below the
+    point-Jacobi contraction, whose bound includes the stiff z couplings."""
+    cfg = small_cfg(nx=6, ny=5, nz=7, stretch=2.0, dt=0.05)
+    u, v, w, p, nu = inputs.random_state(cfg, 14)
+    o = orc.Oracle(cfg)
+    exact = _cn_dense(o, cfg, nu, u, v, w)
+    dx, dy = cfg["Lx"] / cfg["nx"], cfg["Ly"] / cfg["ny"]
+    hs = 0.5 * cfg["dt"] * nu.max() * (2 / dx**2 + 2 / dy**2)
+    rho = hs / (1 + hs)
+    prev = max(np.abs(a - b).max() for a, b in zip((u, v, w), exact))
+    for n in (1, 2, 3):
+        a = orc.Oracle(dict(cfg, cn_zline=1, cn_sweeps=n)).cn_solve(nu, u, v, w)
+        err = max(np.abs(x - y).max() for x, y in zip(a, exact))
+        assert err <= rho * prev * (1 + 1e-9) + 1e-14, (n, err, rho * prev)
+        prev = err
+    assert rho < 0.5
