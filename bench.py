@@ -215,10 +215,12 @@ def oracle_us_per_sweep(cfg, zline, seed=5):
 
 
 def learned_comparison(cfg, steps, oracle_sample=True):
-    """Poisson time to 1e-8, learned guess vs plain, on the workload grid:
+    """Poisson time to 1e-8, learned against plain, on the workload grid:
     train the U-Net on (residual, correction) pairs harvested from channels
     of the same workload (seeds 0-3, 10 steps each), then step one channel
-    (seed 7) with and without the guess and compare the solves."""
+    (seed 7) plainly, with the network as the initial guess of every solve
+    and with it as a preconditioner at every refinement pass (FP32) or SRJ
+    cycle (FP64), and compare the solves."""
     import numpy as np
     import torch
     from paper_1511_07800_gb300 import learn, stp
@@ -227,28 +229,13 @@ def learned_comparison(cfg, steps, oracle_sample=True):
     R, DP = learn.harvest(cfg, seeds=range(4), steps_per_seed=10)
     K = learn.output_scale(R, DP, 4, shape)
     net = stp.UNet(4, *shape)
-    rng = np.random.default_rng(3)
-    theta = []
-    # He-normal initialisation (std sqrt(2/fan_in)), zero bias, small output layer
-    cin = 1
-    specs = []
-    for c in (16, 32, 64, 128):
-        specs += [(cin, c, 27), (c, c, 27)]
-        cin = c
-    for l in (2, 1, 0):
-        c = (16, 32, 64, 128)[l]
-        specs += [((16, 32, 64, 128)[l + 1] + c, c, 27), (c, c, 27)]
-    specs.append((16, 1, 1))
-    for i, (ci, co, taps) in enumerate(specs):
-        std = math.sqrt(2.0 / (ci * taps)) if i < len(specs) - 1 else 0.1 / math.sqrt(ci)
-        theta.append(rng.standard_normal(co * ci * taps) * std)
-        theta.append(np.zeros(co))
-    net.set_params(np.concatenate(theta).astype(np.float32))
+    theta = learn.he_init(3)
+    net.set_params(theta)
     net.set_output_scale(K)
     losses = learn.train(net, R, DP, 150, 4, 1e-3) + learn.train(net, R, DP, 100, 4, 3e-4)
     t_train = time.perf_counter() - t0
-    res = learn.compare(cfg, net, seed=7, nsteps=max(3, steps), precision="fp32")
-    res64 = learn.compare(cfg, net, seed=7, nsteps=3, precision="fp64")
+    res = learn.compare_modes(cfg, net, seed=7, nsteps=max(3, steps), precision="fp32")
+    res64 = learn.compare_modes(cfg, net, seed=7, nsteps=3, precision="fp64")
     # one forward of the trained network on the workload grid (CUDA events)
     fwd_ms = None
     try:
@@ -275,7 +262,7 @@ def learned_comparison(cfg, steps, oracle_sample=True):
             half = tuple(n // 2 for n in shape)
             xs = np.random.default_rng(11).standard_normal((1,) + half + (1,))
             t1 = time.perf_counter()
-            unet_oracle.forward(np.concatenate(theta), xs)
+            unet_oracle.forward(theta.astype(np.float64), xs)
             t_s = time.perf_counter() - t1
             out_cpu = {"kind": "oracle", "unit": "ms per forward", "value": 8e3 * t_s,
                        "sample": "one FP64 oracle forward at %dx%dx%d (an eighth of the voxels, %.2f s), scaled "
@@ -283,16 +270,14 @@ def learned_comparison(cfg, steps, oracle_sample=True):
                                                             shape[0])}
         except Exception as ex:  # report, never fake
             out_cpu = {"value": None, "error": str(ex)[:200]}
-    return {"plain_ms": res["plain"]["solve_ms"], "learned_ms": res["learned"]["solve_ms"],
-            "forward_ms": fwd_ms,
-            "plain_sweeps": res["plain"]["sweeps"], "learned_sweeps": res["learned"]["sweeps"],
-            "speedup": res["plain"]["solve_ms"] / res["learned"]["solve_ms"],
-            "fp64": {"plain_ms": res64["plain"]["solve_ms"], "learned_ms": res64["learned"]["solve_ms"],
-                     "plain_sweeps": res64["plain"]["sweeps"], "learned_sweeps": res64["learned"]["sweeps"]},
+    return {"plain_ms": res["plain"]["solve_ms"], "learned_ms": res["guess"]["solve_ms"],
+            "speedup": res["guess"]["speedup"], "preconditioner_speedup": res["precond"]["speedup"],
+            "forward_ms": fwd_ms, "fp32": res, "fp64": res64,
             "train": {"pairs": int(R.shape[0]), "adam_steps": len(losses), "batch": 4,
                       "final_loss": float(np.mean(losses[-10:])), "output_scale": K, "seconds": t_train},
             "cpu_baseline": out_cpu,
-            "note": "time per pressure solve to 1e-8 (GPU events), previous-step pressure as the plain guess"}
+            "note": "time per pressure solve to 1e-8 (GPU events), previous-step pressure as the plain guess; "
+                    "guess: the network once per solve; precond: at every refinement pass"}
 
 
 def batched_channels(steps, warmup, peak, oracle_sample=True):

@@ -374,6 +374,17 @@ int stp_unet_layer(stp_unet *net, int layer, int mode, const float *a, const flo
    pointer, which must stay valid while set. */
 int stp_set_learned_guess(stp_handle *h, stp_unet *net);
 
+/* How the network of stp_set_learned_guess enters the solve:
+     0  (default) initial guess, once per solve, as above;
+     1  preconditioner: applied to the current residual throughout the
+        solve.  In FP32 with refinement every refinement pass starts its
+        inner SRJ solve of L d = r from d = s U(r / s) (s = RMS(r)) instead
+        of zero; in FP64, before the sweeps of every SRJ cycle,
+        p += s U(r / s) with r = b - L p.  The SRJ iteration still decides
+        convergence and finishes to ptol.
+   Rebuilds the solve graph. */
+int stp_set_learned_mode(stp_handle *h, int mode);
+
 /* Record training pairs of every pressure solve of h into caller device
    arrays (FP32 [nz][ny][nx], NULL: stop): r_out = b - L p_prev at the start
    of the solve, dp_out = p - p_prev after it. */

@@ -88,6 +88,7 @@ struct stp_handle {
   GridBar bar{};
   // learned guess and training-pair harvest
   stp_unet* net = nullptr;
+  int learned_mode = 0;        // 0: guess once per solve; 1: at every refinement pass / SRJ cycle
   int guess_kernels = 0;
   float *hr = nullptr, *hdp = nullptr;  // caller buffers for harvested pairs
   double* p_prev = nullptr;
@@ -556,6 +557,14 @@ int build_cycle(stp_handle* h, const Geom<T>& g, cudaGraph_t wb, cudaGraphCondit
   if ((rc = add_conditional(h, wb, leaf_node(wb), h_body, cudaGraphCondTypeIf, &ib, &ifn))) return rc;
   if ((rc = begin_capture(h, ib, nullptr))) return rc;
   const int M = (int)h->omega.size();
+  if (sizeof(T) == sizeof(double) && h->net && h->learned_mode == 1) {
+    // learned preconditioner in an FP64 solve: before every cycle's sweeps,
+    // r = b - L p and p += s U(r / s)
+    CUDA_TRY(h, launch_outer(h->g64, h->p, h->b, h->r32, h->ctl, h->red, 0, 0, 0, h->cap));
+    if ((rc = unet_guess(h->net, h->r32, h->red.sc + SC_INNER_REF, h->d1, h->cap, &h->guess_kernels)))
+      return fail(h, rc, "learned preconditioner: " + std::string(stp_unet_last_error(h->net)));
+    CUDA_TRY(h, launch_addcorr(h->p, h->d1, h->nc, h->cap));
+  }
   if (sizeof(T) == sizeof(float) && h->cycle_blocks > 0) {
     // the whole cycle in one persistent kernel
     CUDA_TRY(h, launch_cycle_f32(h->g32, (float*)A, (float*)B, (const float*)rhs, h->d_omega32, M, h->bar, h->ctl,
@@ -719,7 +728,7 @@ int append_solve(stp_handle* h, cudaGraph_t G, cudaGraphNode_t dep, cudaGraphNod
     CUDA_TRY(h, cudaGraphConditionalHandleCreate(&h_loop, G, 1, cudaGraphCondAssignDefault));
     if ((rc = begin_capture(h, G, dep))) return rc;
     CUDA_TRY(h, launch_begin(h->ctl, 1, h_loop, h->cap));
-    if (h->net) {
+    if (h->net && h->learned_mode == 0) {
       // learned guess: r = b - L p (FP32), p += s U(r / s)
       CUDA_TRY(h, launch_outer(h->g64, h->p, h->b, h->r32, h->ctl, h->red, 0, 0, 0, h->cap));
       if ((rc = unet_guess(h->net, h->r32, h->red.sc + SC_INNER_REF, h->d1, h->cap, &h->guess_kernels)))
@@ -736,7 +745,7 @@ int append_solve(stp_handle* h, cudaGraph_t G, cudaGraphNode_t dep, cudaGraphNod
     if ((rc = begin_capture(h, G, dep))) return rc;
     CUDA_TRY(h, launch_begin(h->ctl, 0, 0, h->cap));
     CUDA_TRY(h, launch_outer(h->g64, h->p, h->b, h->r32, h->ctl, h->red, 0, 1, h_pass, h->cap));
-    if (h->net) {
+    if (h->net && h->learned_mode == 0) {
       // learned guess at the start of the solve: p += s U(r / s), then the
       // residual of the new p decides the first pass
       if ((rc = unet_guess(h->net, h->r32, h->red.sc + SC_INNER_REF, h->d1, h->cap, &h->guess_kernels)))
@@ -752,6 +761,12 @@ int append_solve(stp_handle* h, cudaGraph_t G, cudaGraphNode_t dep, cudaGraphNod
     CUDA_TRY(h, cudaGraphConditionalHandleCreate(&h_loop, pb, 1, 0));
     if ((rc = begin_capture(h, pb, nullptr))) return rc;
     CUDA_TRY(h, launch_pass_begin(h->d1, h->nc, 1, h_loop, h->cap));
+    if (h->net && h->learned_mode == 1) {
+      // learned preconditioner: every pass starts its inner solve of
+      // L d = r from d = s U(r / s) instead of zero
+      if ((rc = unet_guess(h->net, h->r32, h->red.sc + SC_INNER_REF, h->d1, h->cap, &h->guess_kernels)))
+        return fail(h, rc, "learned preconditioner: " + std::string(stp_unet_last_error(h->net)));
+    }
     if ((rc = end_capture(h, pb))) return rc;
     if ((rc = add_conditional(h, pb, leaf_node(pb), h_loop, cudaGraphCondTypeWhile, &wb, &wn))) return rc;
     if ((rc = build_cycle<float>(h, h->g32, wb, h_loop, h->d1, h->d2, h->r32, 1))) return rc;
@@ -817,6 +832,12 @@ int host_cycles(stp_handle* h, const Geom<T>& g, T* A, T* B, const T* rhs, int m
     int go = 0, rc = read_go(h, &go);
     if (rc) return rc;
     if (!go) return STP_OK;
+    if (sizeof(T) == sizeof(double) && h->net && h->learned_mode == 1) {
+      CUDA_TRY(h, launch_outer(h->g64, h->p, h->b, h->r32, h->ctl, h->red, 0, 0, 0, h->st));
+      rc = unet_guess(h->net, h->r32, h->red.sc + SC_INNER_REF, h->d1, h->st, &h->guess_kernels);
+      if (rc) return fail(h, rc, "learned preconditioner failed");
+      CUDA_TRY(h, launch_addcorr(h->p, h->d1, h->nc, h->st));
+    }
     if (sizeof(T) == sizeof(float) && h->cycle_blocks > 0) {
       CUDA_TRY(h, launch_cycle_f32(h->g32, (float*)A, (float*)B, (const float*)rhs, h->d_omega32, M, h->bar, h->ctl,
                                    h->cycle_blocks, h->st));
@@ -845,7 +866,7 @@ int host_solve(stp_handle* h) {
   set_sweep_variant(h->sweep_variant);
   CUDA_TRY(h, launch_begin(h->ctl, 0, 0, h->st));
   if (h->prec == STP_FP64) {
-    if (h->net) {
+    if (h->net && h->learned_mode == 0) {
       CUDA_TRY(h, launch_outer(h->g64, h->p, h->b, h->r32, h->ctl, h->red, 0, 0, 0, h->st));
       int rc = unet_guess(h->net, h->r32, h->red.sc + SC_INNER_REF, h->d1, h->st, &h->guess_kernels);
       if (rc) return fail(h, rc, "learned guess failed");
@@ -854,7 +875,7 @@ int host_solve(stp_handle* h) {
     return host_cycles<double>(h, h->g64, h->p, h->p2, h->b, 0);
   }
   CUDA_TRY(h, launch_outer(h->g64, h->p, h->b, h->r32, h->ctl, h->red, 0, 0, 0, h->st));
-  if (h->net) {
+  if (h->net && h->learned_mode == 0) {
     int rc = unet_guess(h->net, h->r32, h->red.sc + SC_INNER_REF, h->d1, h->st, &h->guess_kernels);
     if (rc) return fail(h, rc, "learned guess failed");
     CUDA_TRY(h, launch_addcorr(h->p, h->d1, h->nc, h->st));
@@ -865,6 +886,10 @@ int host_solve(stp_handle* h) {
     if (rc) return rc;
     if (!go) return STP_OK;
     CUDA_TRY(h, launch_pass_begin(h->d1, h->nc, 0, 0, h->st));
+    if (h->net && h->learned_mode == 1) {
+      rc = unet_guess(h->net, h->r32, h->red.sc + SC_INNER_REF, h->d1, h->st, &h->guess_kernels);
+      if (rc) return fail(h, rc, "learned preconditioner failed");
+    }
     if ((rc = host_cycles<float>(h, h->g32, h->d1, h->d2, h->r32, 1))) return rc;
     CUDA_TRY(h, launch_addcorr(h->p, h->d1, h->nc, h->st));
     CUDA_TRY(h, launch_outer(h->g64, h->p, h->b, h->r32, h->ctl, h->red, 1, 0, 0, h->st));
@@ -914,7 +939,12 @@ int finish_solve(stp_handle* h, SolveOut* o) {
   o->kernels = c.tot_kernels + c.kernels;
   // the learned guess runs once per solve: its kernels, the outer residual
   // before it, the correction and (FP32) the residual after it
-  if (h->net) o->kernels += (long long)c.solves * (h->guess_kernels + 3);
+  if (h->net && h->learned_mode == 0) o->kernels += (long long)c.solves * (h->guess_kernels + 3);
+  // preconditioner: the network once per pass (FP32), or residual, network
+  // and correction once per cycle (FP64); the last solve's counts
+  if (h->net && h->learned_mode == 1)
+    o->kernels += h->prec == STP_FP64 ? (long long)(c.sweeps / std::max(1, c.M)) * (h->guess_kernels + 2)
+                                      : (long long)c.passes * h->guess_kernels;
   o->tot_sweeps = c.tot_sweeps + c.sweeps;
   o->nonconv = c.nonconv + (c.converged ? 0 : 1);
   const double nb = h->h_sc[SC_BNORM];
@@ -972,7 +1002,7 @@ int step_pre(stp_handle* h, const Geom<T>& g, cudaStream_t s) {
     CUDA_TRY(h, cudaMemcpyAsync(h->w, h->rw, h->esz * h->nw, cudaMemcpyDeviceToDevice, s));
   }
   // b = D u* / dt
-  CUDA_TRY(h, launch_divergence_rhs<T>(g, u, v, w, 1.0 / c.dt, h->b, h->red, s));
+  CUDA_TRY(h, launch_divergence_rhs<T>(g, u, v, w, 1.0 / c.dt, h->b, h->red, c.Lz, s));
   return STP_OK;
 }
 
@@ -1397,6 +1427,7 @@ int stp_poisson_solve(stp_handle* h, const double* rhs, double* p_inout, double 
                                    " against a volume sum of |rhs| of " + std::to_string(h->h_sc[SC_VABS]) +
                                    "): L p = rhs has no solution");
   CUDA_TRY(h, launch_norm(h->b, h->nc, SC_BNORM, h->red, h->st));
+  CUDA_TRY(h, cudaMemsetAsync(h->red.sc + SC_BMEAN, 0, sizeof(double), h->st));
   rc = arm_solves(h, tol, maxit > 0 ? maxit : h->cfg.pmaxit);
   if (rc) return rc;
   h->solve_ms = 0.0;
@@ -1516,6 +1547,19 @@ int stp_set_learned_guess(stp_handle* h, stp_unet* net) {
   return STP_OK;
 }
 
+int stp_set_learned_mode(stp_handle* h, int mode) {
+  if (!h) return STP_EINVAL;
+  if (mode != 0 && mode != 1) return fail(h, STP_EINVAL, "learned mode must be 0 or 1");
+  CUDA_TRY(h, cudaSetDevice(h->dev));
+  CUDA_TRY(h, cudaStreamSynchronize(h->st));
+  if (h->solve_exec) cudaGraphExecDestroy(h->solve_exec);
+  if (h->solve_graph) cudaGraphDestroy(h->solve_graph);
+  h->solve_exec = nullptr;
+  h->solve_graph = nullptr;
+  h->learned_mode = mode;
+  return STP_OK;
+}
+
 int stp_set_harvest(stp_handle* h, float* r_out, float* dp_out) {
   if (!h) return STP_EINVAL;
   if ((r_out == nullptr) != (dp_out == nullptr)) return fail(h, STP_EINVAL, "give both r_out and dp_out, or neither");
@@ -1582,10 +1626,10 @@ int stp_eval(stp_handle* h, int term, double* a, double* b, double* c, int where
     case STP_TERM_DIVERGENCE:
       if (h->prec == STP_FP64)
         CUDA_TRY(h, launch_divergence_rhs<double>(h->g64, (double*)h->u, (double*)h->v, (double*)h->w, 1.0, h->stage,
-                                                  h->red, h->st));
+                                                  h->red, cf.Lz, h->st));
       else
         CUDA_TRY(h, launch_divergence_rhs<float>(h->g32, (float*)h->u, (float*)h->v, (float*)h->w, 1.0, h->stage,
-                                                 h->red, h->st));
+                                                 h->red, cf.Lz, h->st));
       CUDA_TRY(h, cudaMemcpyAsync(a, h->stage, sizeof(double) * h->nc,
                                   where == STP_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, h->st));
       break;

@@ -61,6 +61,51 @@ __device__ __forceinline__ double block_max(double v, double* sh) {
   return v;
 }
 
+__device__ __forceinline__ float warp_sum_f32(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_max_f32(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Sum over the block of FP32 values: each warp sums its 32 values in FP32
+// (relative error about 2e-6), the warp sums are added in FP64 in a fixed
+// order.  Valid in thread 0.  On GB300 a per-thread FP64 warp reduction
+// costs as much as a whole FP32 stencil, so the kernels whose per-cell
+// values are FP32 reduce this way.
+__device__ __forceinline__ double block_sum_f32(float v, double* sh) {
+  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  const int nthr = blockDim.x * blockDim.y * blockDim.z;
+  v = warp_sum_f32(v);
+  __syncthreads();
+  if ((tid & 31) == 0) sh[tid >> 5] = (double)v;
+  __syncthreads();
+  double d = 0.0;
+  if (tid < 32) {
+    d = (tid < (nthr >> 5)) ? sh[tid] : 0.0;
+    d = warp_sum(d);
+  }
+  return d;
+}
+__device__ __forceinline__ double block_max_f32(float v, double* sh) {
+  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  const int nthr = blockDim.x * blockDim.y * blockDim.z;
+  v = warp_max_f32(v);
+  __syncthreads();
+  if ((tid & 31) == 0) sh[tid >> 5] = (double)v;
+  __syncthreads();
+  double d = 0.0;
+  if (tid < 32) {
+    d = (tid < (nthr >> 5)) ? sh[tid] : 0.0;
+    d = warp_max(d);
+  }
+  return d;
+}
+
 __device__ __forceinline__ unsigned block_linear() {
   return blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
 }

@@ -97,7 +97,7 @@ __global__ void kg_begin(Group G) {
   }
 }
 
-// refinement residual r = b - L p (FP64, stored FP32) and the pass decision
+// refinement residual r = b - mean(b) - L p (FP64, stored FP32; as k_outer) and the pass decision
 __global__ void __launch_bounds__(kBX* kBY) kg_outer(Group G, int after_pass, cudaGraphConditionalHandle h_pass) {
   __shared__ double sh[32];
   const int c = group_chan(G.soff, G.n, blockIdx.x);
@@ -108,14 +108,15 @@ __global__ void __launch_bounds__(kBX* kBY) kg_outer(Group G, int after_pass, cu
   const int t = blockIdx.x - __ldg(G.soff + c);
   int i, j, k;
   scalar_cell(t, nx, ny, &i, &j, &k);
-  double s = 0.0;
+  const double bmean = __ldcg(C.red.sc + SC_BMEAN);
+  float r2 = 0.f;
   if (i < nx && j < ny) {
     double pc;
-    const double r = point_residual(g, C.p, C.b, i, j, k, &pc);
-    C.r32[(k * ny + j) * nx + i] = (float)r;
-    s = r * r;
+    const float r = (float)(point_residual(g, C.p, C.b, i, j, k, &pc) - bmean);
+    C.r32[(k * ny + j) * nx + i] = r;
+    r2 = r * r;
   }
-  s = block_sum(s, sh);
+  double s = block_sum_f32(r2, sh);
   const unsigned nb = (unsigned)(__ldg(G.soff + c + 1) - __ldg(G.soff + c));
   if (publish_local(C.red, nb, (unsigned)t, s)) {
     const double tot = final_sum(C.red.partial, nb, sh);
@@ -160,13 +161,13 @@ __global__ void __launch_bounds__(kBX* kBY) kg_check(Group G, cudaGraphCondition
   const int t = blockIdx.x - __ldg(G.soff + c);
   int i, j, k;
   scalar_cell(t, nx, ny, &i, &j, &k);
-  double s = 0.0;
+  float r2 = 0.f;
   if (i < nx && j < ny) {
     float pc;
-    const double r = (double)point_residual(g, C.d1, C.r32, i, j, k, &pc);
-    s = r * r;
+    const float r = point_residual(g, C.d1, C.r32, i, j, k, &pc);
+    r2 = r * r;
   }
-  s = block_sum(s, sh);
+  double s = block_sum_f32(r2, sh);
   const unsigned nb = (unsigned)(__ldg(G.soff + c + 1) - __ldg(G.soff + c));
   if (publish_local(C.red, nb, (unsigned)t, s)) {
     const double tot = final_sum(C.red.partial, nb, sh);

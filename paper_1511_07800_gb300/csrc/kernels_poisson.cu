@@ -638,12 +638,23 @@ __global__ void __launch_bounds__(kBX* kBY) k_check(Geom<T> g, const T* __restri
   __shared__ double sh[32];
   const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y, k = blockIdx.z;
   double s = 0.0;
-  if (i < g.nx && j < g.ny) {
-    T pc;
-    const double r = (double)point_residual(g, p, b, i, j, k, &pc);
-    s = r * r;
+  if (sizeof(T) == sizeof(float)) {
+    // FP32 inner solve: squares and warp sums in FP32, warp sums added in FP64
+    float r2 = 0.f;
+    if (i < g.nx && j < g.ny) {
+      T pc;
+      const float r = (float)point_residual(g, p, b, i, j, k, &pc);
+      r2 = r * r;
+    }
+    s = block_sum_f32(r2, sh);
+  } else {
+    if (i < g.nx && j < g.ny) {
+      T pc;
+      const double r = (double)point_residual(g, p, b, i, j, k, &pc);
+      s = r * r;
+    }
+    s = block_sum(s, sh);
   }
-  s = block_sum(s, sh);
   if (publish_partial(red, nblocks, s, 0.0, false)) {
     const double tot = final_sum(red.partial, nblocks, sh);
     if (threadIdx.x == 0 && threadIdx.y == 0) {
@@ -656,22 +667,25 @@ __global__ void __launch_bounds__(kBX* kBY) k_check(Geom<T> g, const T* __restri
   }
 }
 
-// Refinement residual: r = b - L p in FP64 (difference form), stored in FP32
-// for the inner solve; decides whether another refinement pass runs.
+// Refinement residual: r = b - mean(b) - L p in FP64 (difference form; the
+// volume mean of b that FP32 differences leave, zero otherwise), stored in
+// FP32 for the inner solve, its norm summed from the stored values; decides
+// whether another refinement pass runs.
 __global__ void __launch_bounds__(kBX* kBY) k_outer(Geom<double> g, const double* __restrict__ p,
                                                      const double* __restrict__ b, float* __restrict__ r32,
                                                      SolveCtl* ctl, Red red, unsigned nblocks, int after_pass,
                                                      int graph, cudaGraphConditionalHandle h_loop) {
   __shared__ double sh[32];
   const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y, k = blockIdx.z;
-  double s = 0.0;
+  const double bmean = __ldcg(red.sc + SC_BMEAN);
+  float r2 = 0.f;
   if (i < g.nx && j < g.ny) {
     double pc;
-    const double r = point_residual(g, p, b, i, j, k, &pc);
-    r32[(k * g.ny + j) * g.nx + i] = (float)r;
-    s = r * r;
+    const float r = (float)(point_residual(g, p, b, i, j, k, &pc) - bmean);
+    r32[(k * g.ny + j) * g.nx + i] = r;
+    r2 = r * r;
   }
-  s = block_sum(s, sh);
+  double s = block_sum_f32(r2, sh);
   if (publish_partial(red, nblocks, s, 0.0, false)) {
     const double tot = final_sum(red.partial, nblocks, sh);
     if (threadIdx.x == 0 && threadIdx.y == 0) {

@@ -384,29 +384,41 @@ __global__ void __launch_bounds__(128) k_cn_line(Geom<T> g, Visc<T, LES> N, T h,
   const int plane = nx * ny, c0 = j * nx + i;
   V2* __restrict__ S = scr + (size_t)comp * (nz + 1) * plane;
   const T idx2 = g.idx2, idy2 = g.idy2;
+  // cell viscosity at (a, b) of level k, even reflection at the walls
+  auto nuc = [&](int a, int b, int k) -> T {
+    if (!LES) return N.nu0;
+    k = k < 0 ? 0 : (k >= nz ? nz - 1 : k);
+    return __ldg(N.nu + k * plane + b * nx + a);
+  };
   T cprev = T(0), dprev = T(0);
   if (comp < 2) {
+    // u: cells (im, i) of rows j (levels k-1, k, k+1), jp and jm (level k);
+    // v: cells (i) of rows j, jm (levels k-1, k, k+1), ip and im of rows jm, j (level k).
+    // The two cells carried along z are A (im, j | i, jm) and B (i, j).
+    const int aA = comp == 0 ? im : i, bA = comp == 0 ? j : jm;
     const T* __restrict__ a = comp == 0 ? au : av;
     const T* __restrict__ r = comp == 0 ? ru : rv;
     T* __restrict__ o = comp == 0 ? ou : ov;
+    T Am = nuc(aA, bA, -1), Bm = nuc(i, j, -1), A0 = nuc(aA, bA, 0), B0 = nuc(i, j, 0);
+#pragma unroll 2
     for (int k = 0; k < nz; k++) {
       const int lev = k * plane;
-      T nxp, nxm, nyp, nym, nzp, nzm;
+      const T Ap = nuc(aA, bA, k + 1), Bp = nuc(i, j, k + 1);
+      T nxp, nxm, nyp, nym;
       if (comp == 0) {
-        nxp = N.c(i, j, k);
-        nxm = N.c(im, j, k);
-        nyp = N.e4(im, i, j, jp, k);
-        nym = N.e4(im, i, jm, j, k);
-        nzp = N.ez_x(im, i, j, k + 1);
-        nzm = N.ez_x(im, i, j, k);
+        const T c1 = nuc(im, jp, k), c2 = nuc(i, jp, k), c3 = nuc(im, jm, k), c4 = nuc(i, jm, k);
+        nxp = B0;
+        nxm = A0;
+        nyp = T(0.25) * (A0 + B0 + c1 + c2);
+        nym = T(0.25) * (c3 + c4 + A0 + B0);
       } else {
-        nxp = N.e4(i, ip, jm, j, k);
-        nxm = N.e4(im, i, jm, j, k);
-        nyp = N.c(i, j, k);
-        nym = N.c(i, jm, k);
-        nzp = N.ez_y(i, jm, j, k + 1);
-        nzm = N.ez_y(i, jm, j, k);
+        const T c1 = nuc(ip, jm, k), c2 = nuc(ip, j, k), c3 = nuc(im, jm, k), c4 = nuc(im, j, k);
+        nxp = T(0.25) * (A0 + c1 + B0 + c2);
+        nxm = T(0.25) * (c3 + A0 + c4 + B0);
+        nyp = B0;
+        nym = A0;
       }
+      const T nzp = T(0.25) * (A0 + B0 + Ap + Bp), nzm = T(0.25) * (Am + Bm + A0 + B0);
       const T idz = __ldg(g.idz + k), izp = __ldg(g.idzf + k + 1), izm = __ldg(g.idzf + k);
       const T gu = (k == nz - 1) ? T(2) : T(1), gd = (k == 0) ? T(2) : T(1);
       const T sd = (nxp + nxm) * idx2 + (nyp + nym) * idy2 + (gu * nzp * izp + gd * nzm * izm) * idz;
@@ -418,22 +430,31 @@ __global__ void __launch_bounds__(128) k_cn_line(Geom<T> g, Visc<T, LES> N, T h,
       cprev = up * inv;
       dprev = (__ldg(r + lev + c0) + h * xy - lo * dprev) * inv;
       S[lev + c0] = V2{cprev, dprev};
+      Am = A0;
+      Bm = B0;
+      A0 = Ap;
+      B0 = Bp;
     }
     T x = T(0);
+#pragma unroll 4
     for (int k = nz - 1; k >= 0; k--) {
       const V2 cd = S[k * plane + c0];
       x = cd.y - cd.x * x;
       o[k * plane + c0] = x;
     }
   } else {
-    // w on the interior faces 1..nz-1; the wall faces are zero
+    // w on the interior faces 1..nz-1 (the wall faces are zero): cells
+    // (i, j), (ip, j), (im, j), (i, jp), (i, jm) of levels c-1 and c
     ow[c0] = T(0);
     ow[nz * plane + c0] = T(0);
+    T q0 = nuc(i, j, 0), q1 = nuc(ip, j, 0), q2 = nuc(im, j, 0), q3 = nuc(i, jp, 0), q4 = nuc(i, jm, 0);
+#pragma unroll 2
     for (int c = 1; c < nz; c++) {
       const int lev = c * plane;
-      const T nxp = N.ez_x(i, ip, j, c), nxm = N.ez_x(im, i, j, c);
-      const T nyp = N.ez_y(i, j, jp, c), nym = N.ez_y(i, jm, j, c);
-      const T nzp = N.c(i, j, c), nzm = N.c(i, j, c - 1);
+      const T p0 = nuc(i, j, c), p1 = nuc(ip, j, c), p2 = nuc(im, j, c), p3 = nuc(i, jp, c), p4 = nuc(i, jm, c);
+      const T nxp = T(0.25) * (q0 + q1 + p0 + p1), nxm = T(0.25) * (q2 + q0 + p2 + p0);
+      const T nyp = T(0.25) * (q0 + q3 + p0 + p3), nym = T(0.25) * (q4 + q0 + p4 + p0);
+      const T nzp = p0, nzm = q0;
       const T ih = __ldg(g.ihz + c), izp = __ldg(g.idz + c), izm = __ldg(g.idz + c - 1);
       const T sd = (nxp + nxm) * idx2 + (nyp + nym) * idy2 + (nzp * izp + nzm * izm) * ih;
       const T xy = (nxp * __ldg(aw + lev + j * nx + ip) + nxm * __ldg(aw + lev + j * nx + im)) * idx2 +
@@ -444,8 +465,14 @@ __global__ void __launch_bounds__(128) k_cn_line(Geom<T> g, Visc<T, LES> N, T h,
       cprev = up * inv;
       dprev = (__ldg(rw + lev + c0) + h * xy - lo * dprev) * inv;
       S[lev + c0] = V2{cprev, dprev};
+      q0 = p0;
+      q1 = p1;
+      q2 = p2;
+      q3 = p3;
+      q4 = p4;
     }
     T x = T(0);
+#pragma unroll 4
     for (int c = nz - 1; c >= 1; c--) {
       const V2 cd = S[c * plane + c0];
       x = cd.y - cd.x * x;
@@ -457,33 +484,57 @@ __global__ void __launch_bounds__(128) k_cn_line(Geom<T> g, Visc<T, LES> N, T h,
 // ---------------------------------------------------------------------------
 // Eq. presdiv right-hand side b = D u* / dt, with ||b||_2 reduced in FP64.
 // Also clears the convergence flags of the coming solve.
+//   FP64 fields: FP64 arithmetic; the sum of b over the box telescopes to
+//     zero to FP64 rounding, so b has no mean the Poisson iteration could
+//     not remove (sc[SC_BMEAN] = 0).
+//   FP32 fields: FP32 arithmetic (the fields carry FP32 rounding already);
+//     b is stored in FP64, and its volume mean, which FP32 differences leave
+//     at about 1e-8 of ||b||, goes to sc[SC_BMEAN], from where the
+//     refinement residual removes it.  Sums of squares and of b dz in FP32
+//     per warp, FP64 across warps.
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(kBX* kBY) k_divergence(Geom<T> g, const T* __restrict__ u, const T* __restrict__ v,
                                                           const T* __restrict__ w, double idt, double* __restrict__ b,
-                                                          Red red, unsigned nblocks) {
+                                                          Red red, unsigned nblocks, double inv_vol) {
   __shared__ double sh[32];
   const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y, k = blockIdx.z;
-  double s = 0.0;
-  if (i < g.nx && j < g.ny) {
-    const int ip = i == g.nx - 1 ? 0 : i + 1, jp = j == g.ny - 1 ? 0 : j + 1;
-    const int q = at(g.nx, g.ny, i, j, k);
-    // differences taken in FP64 (exact for FP32 inputs), so that the sum of b
-    // over the box telescopes to zero to FP64 rounding: the constant mode of
-    // b, which no Poisson iteration can remove, stays at that level
-    const double d = ((double)__ldg(u + at(g.nx, g.ny, ip, j, k)) - (double)__ldg(u + q)) * (double)g.idx +
-                     ((double)__ldg(v + at(g.nx, g.ny, i, jp, k)) - (double)__ldg(v + q)) * (double)g.idy +
-                     ((double)__ldg(w + q + g.nx * g.ny) - (double)__ldg(w + q)) * (double)__ldg(g.idz + k);
-    const double bt = d * idt;
-    b[q] = bt;
-    s = bt * bt;
+  double s = 0.0, sm = 0.0;
+  if constexpr (sizeof(T) == sizeof(float)) {
+    float s2 = 0.f, sb = 0.f;
+    if (i < g.nx && j < g.ny) {
+      const int ip = i == g.nx - 1 ? 0 : i + 1, jp = j == g.ny - 1 ? 0 : j + 1;
+      const int q = at(g.nx, g.ny, i, j, k);
+      const float d = (__ldg(u + at(g.nx, g.ny, ip, j, k)) - __ldg(u + q)) * g.idx +
+                      (__ldg(v + at(g.nx, g.ny, i, jp, k)) - __ldg(v + q)) * g.idy +
+                      (__ldg(w + q + g.nx * g.ny) - __ldg(w + q)) * __ldg(g.idz + k);
+      const float bt = d * (float)idt;
+      b[q] = (double)bt;
+      s2 = bt * bt;
+      sb = bt * __ldg(g.dzv + k);
+    }
+    s = block_sum_f32(s2, sh);
+    sm = block_sum_f32(sb, sh);
+  } else {
+    if (i < g.nx && j < g.ny) {
+      const int ip = i == g.nx - 1 ? 0 : i + 1, jp = j == g.ny - 1 ? 0 : j + 1;
+      const int q = at(g.nx, g.ny, i, j, k);
+      const double d = (__ldg(u + at(g.nx, g.ny, ip, j, k)) - __ldg(u + q)) * g.idx +
+                       (__ldg(v + at(g.nx, g.ny, i, jp, k)) - __ldg(v + q)) * g.idy +
+                       (__ldg(w + q + g.nx * g.ny) - __ldg(w + q)) * __ldg(g.idz + k);
+      const double bt = d * idt;
+      b[q] = bt;
+      s = bt * bt;
+    }
+    s = block_sum(s, sh);
   }
-  s = block_sum(s, sh);
-  if (publish_partial(red, nblocks, s, 0.0, false)) {
+  if (publish_partial(red, nblocks, s, sm, true)) {
     const double tot = final_sum(red.partial, nblocks, sh);
+    const double mean = sizeof(T) == sizeof(float) ? final_sum(red.partial + nblocks, nblocks, sh) * inv_vol : 0.0;
     const int tid = threadIdx.x + blockDim.x * threadIdx.y;
     if (tid == 0) {
       red.sc[SC_BNORM] = sqrt(tot);
+      red.sc[SC_BMEAN] = mean;
       red.flag[FL_DONE] = 0;
       red.flag[FL_INNER_DONE] = 0;
       *red.counter = 0u;
@@ -494,6 +545,10 @@ __global__ void __launch_bounds__(kBX* kBY) k_divergence(Geom<T> g, const T* __r
 // ---------------------------------------------------------------------------
 // Eq. project u_p_1: u = u* - dt G p with w = 0 on the walls; reduces the
 // volume-weighted mean of u and max |u| (FP64).  Grid z covers 0..nz.
+//   FP64 fields: FP64 arithmetic.
+//   FP32 fields: the pressure differences in FP64 (p is FP64 and may carry
+//     a large constant), everything else in FP32; the sums in FP32 per warp,
+//     FP64 across warps.
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(kBX* kBY) k_correct(Geom<T> g, const double* __restrict__ p, double dt,
@@ -502,29 +557,57 @@ __global__ void __launch_bounds__(kBX* kBY) k_correct(Geom<T> g, const double* _
                                                        double inv_vol, Red red, unsigned nblocks) {
   __shared__ double sh[32];
   const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y, k = blockIdx.z;
-  double s = 0.0, m = 0.0;
-  if (i < g.nx && j < g.ny) {
-    const int im = i == 0 ? g.nx - 1 : i - 1, jm = j == 0 ? g.ny - 1 : j - 1;
-    const int q = at(g.nx, g.ny, i, j, k);
-    if (k < g.nz) {
-      const double pc = __ldg(p + q);
-      const double un = (double)u[q] - dt * (pc - __ldg(p + at(g.nx, g.ny, im, j, k))) * (double)g.idx;
-      const double vn = (double)v[q] - dt * (pc - __ldg(p + at(g.nx, g.ny, i, jm, k))) * (double)g.idy;
-      const T ut = (T)un;
-      u[q] = ut;
-      v[q] = (T)vn;
-      s = (double)ut * __ldg(dz64 + k);
-      m = fabs((double)ut);
+  double bs, bm;
+  if constexpr (sizeof(T) == sizeof(float)) {
+    float s = 0.f, m = 0.f;
+    if (i < g.nx && j < g.ny) {
+      const int im = i == 0 ? g.nx - 1 : i - 1, jm = j == 0 ? g.ny - 1 : j - 1;
+      const int q = at(g.nx, g.ny, i, j, k);
+      const float cx = (float)dt * g.idx, cy = (float)dt * g.idy;
+      if (k < g.nz) {
+        const double pc = __ldg(p + q);
+        const float dpx = (float)(pc - __ldg(p + at(g.nx, g.ny, im, j, k)));
+        const float dpy = (float)(pc - __ldg(p + at(g.nx, g.ny, i, jm, k)));
+        const float ut = u[q] - cx * dpx;
+        u[q] = ut;
+        v[q] = v[q] - cy * dpy;
+        s = ut * __ldg(g.dzv + k);
+        m = fabsf(ut);
+      }
+      if (k == 0 || k == g.nz) {
+        w[q] = 0.f;
+      } else {
+        const float dpz = (float)(__ldg(p + q) - __ldg(p + q - g.nx * g.ny));
+        w[q] = w[q] - (float)dt * __ldg(g.ihz + k) * dpz;
+      }
     }
-    if (k == 0 || k == g.nz) {
-      w[q] = T(0);
-    } else {
-      const double wn = (double)w[q] - dt * (__ldg(p + q) - __ldg(p + q - g.nx * g.ny)) * __ldg(ihz64 + k);
-      w[q] = (T)wn;
+    bs = block_sum_f32(s, sh);
+    bm = block_max_f32(m, sh);
+  } else {
+    double s = 0.0, m = 0.0;
+    if (i < g.nx && j < g.ny) {
+      const int im = i == 0 ? g.nx - 1 : i - 1, jm = j == 0 ? g.ny - 1 : j - 1;
+      const int q = at(g.nx, g.ny, i, j, k);
+      if (k < g.nz) {
+        const double pc = __ldg(p + q);
+        const double un = (double)u[q] - dt * (pc - __ldg(p + at(g.nx, g.ny, im, j, k))) * (double)g.idx;
+        const double vn = (double)v[q] - dt * (pc - __ldg(p + at(g.nx, g.ny, i, jm, k))) * (double)g.idy;
+        const T ut = (T)un;
+        u[q] = ut;
+        v[q] = (T)vn;
+        s = (double)ut * __ldg(dz64 + k);
+        m = fabs((double)ut);
+      }
+      if (k == 0 || k == g.nz) {
+        w[q] = T(0);
+      } else {
+        const double wn = (double)w[q] - dt * (__ldg(p + q) - __ldg(p + q - g.nx * g.ny)) * __ldg(ihz64 + k);
+        w[q] = (T)wn;
+      }
     }
+    bs = block_sum(s, sh);
+    bm = block_max(m, sh);
   }
-  const double bs = block_sum(s, sh);
-  const double bm = block_max(m, sh);
   if (publish_partial(red, nblocks, bs, bm, true)) {
     const double tot = final_sum(red.partial, nblocks, sh);
     const double mx = final_max(red.partial + nblocks, nblocks, sh);
@@ -541,8 +624,13 @@ __global__ void __launch_bounds__(kBX* kBY) k_correct(Geom<T> g, const double* _
 template <typename T>
 __global__ void k_flux_shift(int n, T* __restrict__ u, double target, Red red) {
   const double shift = target - __ldcg(red.sc + SC_BULK);
-  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x)
-    u[q] = (T)((double)u[q] + shift);
+  if constexpr (sizeof(T) == sizeof(float)) {
+    // FP32 fields: the shift rounded once, the additions in FP32
+    const float sh = (float)shift;
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) u[q] += sh;
+  } else {
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) u[q] += shift;
+  }
   if (blockIdx.x == 0 && threadIdx.x == 0) red.sc[SC_SHIFT] = shift;
 }
 
@@ -665,9 +753,9 @@ cudaError_t launch_diffusion_only(const Geom<T>& g, bool les, const T* u, const 
 
 template <typename T>
 cudaError_t launch_divergence_rhs(const Geom<T>& g, const T* u, const T* v, const T* w, double idt, double* b,
-                                  Red red, cudaStream_t s) {
+                                  Red red, double Lz, cudaStream_t s) {
   Launch l = plane_launch(g.nx, g.ny, g.nz);
-  k_divergence<T><<<l.grid, l.block, 0, s>>>(g, u, v, w, idt, b, red, l.nblocks);
+  k_divergence<T><<<l.grid, l.block, 0, s>>>(g, u, v, w, idt, b, red, l.nblocks, 1.0 / ((double)g.nx * g.ny * Lz));
   return cudaGetLastError();
 }
 
@@ -712,7 +800,7 @@ cudaError_t launch_convert(Td* dst, const Ts* src, size_t n, cudaStream_t s) {
   template cudaError_t launch_diffusion_only<T>(const Geom<T>&, bool, const T*, const T*, const T*, const T*, T,   \
                                                 T*, T*, T*, cudaStream_t);                                          \
   template cudaError_t launch_divergence_rhs<T>(const Geom<T>&, const T*, const T*, const T*, double, double*, Red,\
-                                                cudaStream_t);                                                      \
+                                                double, cudaStream_t);                                              \
   template cudaError_t launch_correct_impl<T>(const Geom<T>&, const double*, double, T*, T*, T*, const double*,    \
                                               const double*, double, Red, cudaStream_t);                            \
   template cudaError_t launch_flux_shift<T>(const Geom<T>&, T*, double, Red, cudaStream_t);

@@ -71,6 +71,7 @@ enum {
   SC_RES_INNER = 6, // inner residual at the last inner check
   SC_VSUM = 7,      // volume sum of a field (stp_poisson_solve's mean checks)
   SC_VABS = 8,      // volume sum of its absolute value
+  SC_BMEAN = 9,     // volume mean of b left by FP32 differences (removed in the refinement residual)
   SC_COUNT = 10
 };
 enum { FL_DONE = 0, FL_INNER_DONE = 1, FL_BAD = 2, FL_COUNT = 4 };
@@ -152,9 +153,11 @@ cudaError_t launch_cn_line(const Geom<T>& g, bool les, const T* nu, T nu0, T hdt
                            cudaStream_t s);
 
 // b = D u / dt, ||b||^2 reduced into sc[SC_BNORM] (as the norm), flags reset.
+// FP32 fields: FP32 arithmetic, and the volume mean of b (which FP32
+// differences no longer cancel exactly) into sc[SC_BMEAN]; FP64: 0 there.
 template <typename T>
 cudaError_t launch_divergence_rhs(const Geom<T>& g, const T* u, const T* v, const T* w, double idt, double* b,
-                                  Red red, cudaStream_t s);
+                                  Red red, double Lz, cudaStream_t s);
 
 // Terms for checks (stp_eval).
 template <typename T>

@@ -85,7 +85,7 @@ EXPORTS = ("stp_config_defaults", "stp_init", "stp_destroy", "stp_last_error", "
            "stp_set_learned_guess", "stp_set_harvest", "stp_unet_set_output_scale", "stp_state_size",
            "stp_get_state", "stp_set_state", "stp_batch_create", "stp_batch_destroy", "stp_batch_last_error",
            "stp_batch_step", "stp_batch_groups", "stp_sweep_tile", "stp_stats_reset",
-           "stp_stats_accumulate", "stp_stats_read", "stp_unet_layer")
+           "stp_stats_accumulate", "stp_stats_read", "stp_unet_layer", "stp_set_learned_mode")
 
 _lib = None
 
@@ -150,6 +150,7 @@ def lib():
     L.stp_unet_set_output_scale.argtypes = [vp, ctypes.c_float]
     L.stp_set_harvest.argtypes = [vp, vp, vp]
     L.stp_unet_layer.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp, vp, ctypes.c_int]
+    L.stp_set_learned_mode.argtypes = [vp, ctypes.c_int]
     _lib = L
     return L
 
@@ -307,6 +308,11 @@ class Channel:
         """Start every pressure solve from the network's guess (None: off)."""
         self._net = net
         self._check(lib().stp_set_learned_guess(self._h, net._h if net is not None else None))
+
+    def set_learned_mode(self, mode):
+        """0: the network's guess once per solve; 1: as a preconditioner at
+        every refinement pass (FP32) or SRJ cycle (FP64)."""
+        self._check(lib().stp_set_learned_mode(self._h, int(mode)))
 
     def set_harvest(self, r_out, dp_out):
         """Record (residual, correction) pairs of each solve into two CUDA

@@ -58,6 +58,47 @@ def test_learned_guess_solves_to_tolerance(stp_lib, orc, precision):
     net.close()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_learned_preconditioner_solves_to_tolerance(stp_lib, orc, precision):
+    """The network as a preconditioner (stp_set_learned_mode 1: applied to
+    the residual at every refinement pass in FP32, before every SRJ cycle in
+    FP64), untrained: every solve still converges to ptol, the step agrees
+    with the plain step to that level, and the host-driven solve takes the
+    same path as the graph."""
+    torch = pytest.importorskip("torch")
+    from oracle import unet
+    from paper_1511_07800_gb300 import learn
+    cfg = _cfg()
+    net = stp_lib.UNet(1, *GRID)
+    net.set_params(unet.init_params(12).astype(np.float32))
+    fields, sweeps = {}, {}
+    for mode in ("plain", "precond", "precond_host"):
+        import os
+        if mode == "precond_host":
+            os.environ["STP_HOST_SOLVE"] = "1"
+        try:
+            with stp_lib.Channel(cfg, precision=precision) as ch:
+                ch.set_fields(*learn.varied_fields(cfg, 4))
+                ch.step(2)
+                if mode != "plain":
+                    ch.set_learned_guess(net)
+                    ch.set_learned_mode(1)
+                sw = 0
+                for _ in range(3):
+                    st = ch.step(1)
+                    assert st["converged"] and st["rel_res"] <= cfg["ptol"], mode
+                    sw += st["sweeps"]
+                fields[mode], sweeps[mode] = ch.get_fields(), sw
+        finally:
+            os.environ.pop("STP_HOST_SOLVE", None)
+    for k in ("u", "v", "w"):
+        a, b = fields["plain"][k], fields["precond"][k]
+        assert np.abs(a - b).max() <= 1e-6 * np.abs(b).max(), k
+        assert np.array_equal(fields["precond"][k], fields["precond_host"][k]), k
+    assert sweeps["precond"] == sweeps["precond_host"]
+    net.close()
+
+
 def test_trained_guess_reduces_srj_work(stp_lib, orc):
     """Train on pairs harvested from six channels, evaluate on a seventh:
     the validation loss falls well below that of the zero guess, and the
