@@ -28,7 +28,13 @@
  * with bounded grid barriers between its sweeps (slower on GB300: kept as an
  * option); each barrier wait gives up after STP_BARRIER_WAIT SM clock cycles
  * (read at every stp_step / stp_poisson_solve call; default 2e9, about one
- * second), and the call then returns STP_ETIMEOUT.  The FP32 sweep kernel's tile shape (z levels per thread, rows
+ * second), and the call then returns STP_ETIMEOUT.  With
+ * STP_LINE_PERSISTENT=1 at stp_init an FP32 z-line cycle runs as one
+ * cooperative launch in which every 32 x 4-column tile waits only for its
+ * four x-y neighbour tiles to finish the previous sweep (bitwise the same
+ * results; the same bounded waits; STP_WAIT_SKEW=<n> makes every tile wait
+ * for a sweep count no neighbour reaches, so that tests can make those
+ * waits run out).  The FP32 sweep kernel's tile shape (z levels per thread, rows
  * per block) is picked on first use by timing the variants on the grid
  * (STP_SWEEP_VARIANT=<0..11> forces one; variants 6..8 pack warps along the
  * plane for rows shorter than 128 cells, 9..11 run two sweeps per launch on

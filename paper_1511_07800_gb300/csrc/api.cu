@@ -82,6 +82,8 @@ struct stp_handle {
   cudaGraphExec_t solve_exec = nullptr;
   bool host_solve = false;     // STP_HOST_SOLVE=1: drive the solve from the host
   int cycle_blocks = 0;        // >0: FP32 cycles run as one persistent cooperative kernel
+  int line_rb = 0;             // >0: FP32 z-line cycles run as one persistent kernel (tile rows)
+  int* line_flags = nullptr;   // its per-tile sweep counters
   int sweep_variant = -1;      // FP32 sweep kernel variant chosen by the autotuner (-1: not yet)
   float sweep_us = 0.f;        // its measured time per sweep
   float* d_omega32 = nullptr;  // the schedule on the device (FP32)
@@ -572,6 +574,11 @@ int build_cycle(stp_handle* h, const Geom<T>& g, cudaGraph_t wb, cudaGraphCondit
     return end_capture(h, ib);
   }
   if (h->cfg.zline) {
+    if (sizeof(T) == sizeof(float) && h->line_rb > 0) {
+      CUDA_TRY(h, launch_line_cycle_f32(h->g32, h->line_rb, (float*)A, (float*)B, (const float*)rhs, h->d_omega32, M,
+                                        h->line_flags, h->ctl, h->cap));
+      return end_capture(h, ib);
+    }
     for (int m = 0; m < M; m++)
       CUDA_TRY(h, launch_line_sweep<T>(g, (m % 2 == 0) ? A : B, rhs, (T)h->omega[m], (m % 2 == 0) ? B : A, h->cap));
     return end_capture(h, ib);
@@ -799,17 +806,20 @@ int arm_solves(stp_handle* h, double tol, int maxit) {
   c.max_sweeps = maxit;
   c.max_passes = 64;
   c.M = (int)h->omega.size();
-  c.kpc = h->cycle_blocks > 0 ? 1 : uses_pairs(h) ? c.M / 2 : c.M;
+  c.kpc = (h->cycle_blocks > 0 || h->line_rb > 0) ? 1 : uses_pairs(h) ? c.M / 2 : c.M;
   c.bar_wait = 2000000000LL;
   if (const char* e = std::getenv("STP_BARRIER_WAIT")) {
     const long long w = std::atoll(e);
     if (w > 0) c.bar_wait = w;
   }
+  if (const char* e = std::getenv("STP_WAIT_SKEW")) c.wait_skew = std::max(0, std::atoi(e));
   *h->h_ctl = c;
   CUDA_TRY(h, cudaMemcpyAsync(h->ctl, h->h_ctl, sizeof(SolveCtl), cudaMemcpyHostToDevice, h->st));
   // the persistent cycle's barrier state starts clean on every call, also
   // after a wait that timed out (count, generation, error flag)
   CUDA_TRY(h, cudaMemsetAsync(h->bar.count, 0, sizeof(unsigned) * 4, h->st));
+  if (h->line_rb > 0)
+    CUDA_TRY(h, cudaMemsetAsync(h->line_flags, 0, sizeof(int) * line_cycle_tiles(h->g32, h->line_rb), h->st));
   return STP_OK;
 }
 
@@ -844,6 +854,11 @@ int host_cycles(stp_handle* h, const Geom<T>& g, T* A, T* B, const T* rhs, int m
       continue;
     }
     if (h->cfg.zline) {
+      if (sizeof(T) == sizeof(float) && h->line_rb > 0) {
+        CUDA_TRY(h, launch_line_cycle_f32(h->g32, h->line_rb, (float*)A, (float*)B, (const float*)rhs, h->d_omega32,
+                                          M, h->line_flags, h->ctl, h->st));
+        continue;
+      }
       for (int m = 0; m < M; m++)
         CUDA_TRY(h, launch_line_sweep<T>(g, (m % 2 == 0) ? A : B, rhs, (T)h->omega[m], (m % 2 == 0) ? B : A,
                                          h->st));
@@ -1253,6 +1268,20 @@ int stp_init(const stp_config* cfg, stp_handle** out) {
     const bool allow = env && env[0] == '1';
     if (allow && h->prec == STP_FP32_REFINE && h->nx % 4 == 0 && !cfg->zline)
       h->cycle_blocks = cycle_grid_f32(h->dev);
+  }
+  {
+    // persistent z-line cycles (STP_LINE_PERSISTENT=1): one cooperative
+    // launch per SRJ cycle, tiles synchronised with their neighbours
+    const char* env = std::getenv("STP_LINE_PERSISTENT");
+    if (env && env[0] == '1' && h->prec == STP_FP32_REFINE && cfg->zline) {
+      Geom<float> gtmp{};
+      gtmp.nx = h->nx;
+      gtmp.ny = h->ny;
+      gtmp.nz = h->nz;
+      const int rb = line_cycle_rows(gtmp, h->dev);
+      if (rb > 0 && dalloc(h, (void**)&h->line_flags, sizeof(int) * line_cycle_tiles(gtmp, rb)) == STP_OK)
+        h->line_rb = rb;
+    }
   }
   if (cudaMallocHost((void**)&h->h_sc, sizeof(double) * SC_COUNT) != cudaSuccess ||
       cudaMallocHost((void**)&h->h_flag, sizeof(int) * FL_COUNT) != cudaSuccess ||

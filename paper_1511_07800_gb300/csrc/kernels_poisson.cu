@@ -548,18 +548,29 @@ struct VecOf<double> {
   }
 };
 
-template <typename T, int RB>
-__global__ void __launch_bounds__(512) k_line_sweep_vec(Geom<T> g, const T* __restrict__ p, const T* __restrict__ b,
-                                                        T omega, T* __restrict__ out) {
+// loads of p in the line sweeps: through the read-only path, or (COH) from
+// L2, for data that other blocks of the same kernel write (the persistent
+// cycle below)
+template <bool COH, typename V>
+__device__ __forceinline__ V ldp(const V* a) {
+  if constexpr (COH) return __ldcg(a);
+  else return __ldg(a);
+}
+
+// One tile of the vector line sweep: 32 RB columns (32 x cells of RB rows),
+// tile number `tile` (x tiles fastest), all three phases.  R is the block's
+// shared column array.  PDL: wait for the previous kernel after the index
+// set-up.
+template <typename T, int RB, bool COH, bool PDL>
+__device__ __forceinline__ void line_vec_tile(const Geom<T>& g, const T* __restrict__ p, const T* __restrict__ b,
+                                              T omega, T* __restrict__ out, int tile, T* R) {
   using VT = VecOf<T>;
   using V = typename VT::V;
   constexpr int W = VT::W, UPR = 32 / W;  // vector units per 32-cell row segment
-  extern __shared__ __align__(16) unsigned char line_sm[];
-  T* R = reinterpret_cast<T*>(line_sm);  // [nz][C]
   constexpr int rb = RB, C = 32 * RB, U = UPR * RB, nchunk = 512 / U;
   const int nx = g.nx, ny = g.ny, nz = g.nz;
   const int nxb = (nx + 31) / 32;
-  const int i0 = (blockIdx.x % nxb) * 32, j0 = (blockIdx.x / nxb) * rb;
+  const int i0 = (tile % nxb) * 32, j0 = (tile / nxb) * rb;
   const int unit = threadIdx.x % U, chunk = threadIdx.x / U;
   const int jr = unit / UPR, xu = unit % UPR;
   const int i = i0 + W * xu, j = j0 + jr;
@@ -572,22 +583,22 @@ __global__ void __launch_bounds__(512) k_line_sweep_vec(Geom<T> g, const T* __re
   const int k0 = chunk * nz / nchunk, k1 = (chunk + 1) * nz / nchunk;
   const int col = jr * 32 + W * xu;
   const T idx2 = g.idx2, idy2 = g.idy2;
-  cudaGridDependencySynchronize();
+  if (PDL) cudaGridDependencySynchronize();
   // the unit's own values at levels k - 1 and k ride along in registers
   // (zd, c): each level loads only level k + 1 of the unit
   V c = {}, zd = {};
   if (k0 < k1) {
-    c = __ldg(reinterpret_cast<const V*>(p + (unsigned)k0 * plane + c0));
-    zd = k0 > 0 ? __ldg(reinterpret_cast<const V*>(p + (unsigned)(k0 - 1) * plane + c0)) : c;
+    c = ldp<COH>(reinterpret_cast<const V*>(p + (unsigned)k0 * plane + c0));
+    zd = k0 > 0 ? ldp<COH>(reinterpret_cast<const V*>(p + (unsigned)(k0 - 1) * plane + c0)) : c;
   }
 #pragma unroll 2
   for (int k = k0; k < k1; k++) {
     const unsigned lev = (unsigned)k * plane;
-    const V yn = __ldg(reinterpret_cast<const V*>(p + lev + yp));
-    const V ys = __ldg(reinterpret_cast<const V*>(p + lev + ym));
-    const V zu = k < nz - 1 ? __ldg(reinterpret_cast<const V*>(p + lev + plane + c0)) : c;
+    const V yn = ldp<COH>(reinterpret_cast<const V*>(p + lev + yp));
+    const V ys = ldp<COH>(reinterpret_cast<const V*>(p + lev + ym));
+    const V zu = k < nz - 1 ? ldp<COH>(reinterpret_cast<const V*>(p + lev + plane + c0)) : c;
     const V bq = __ldg(reinterpret_cast<const V*>(b + lev + c0));
-    const T left = __ldg(p + lev + xl), right = __ldg(p + lev + xr);
+    const T left = ldp<COH>(p + lev + xl), right = ldp<COH>(p + lev + xr);
     const T cup = __ldg(g.cup + k), cdn = __ldg(g.cdn + k), li = __ldg(g.tli + k);
     V o;
 #pragma unroll
@@ -610,12 +621,81 @@ __global__ void __launch_bounds__(512) k_line_sweep_vec(Geom<T> g, const T* __re
 #pragma unroll 2
     for (int k = k0; k < k1; k++) {
       const unsigned q = (unsigned)k * plane + c0;
-      const V pv = __ldg(reinterpret_cast<const V*>(p + q));
+      const V pv = ldp<COH>(reinterpret_cast<const V*>(p + q));
       const V dv = *reinterpret_cast<const V*>(R + k * C + col);
       V o;
 #pragma unroll
       for (int e = 0; e < W; e++) VT::set(o, e, VT::get(pv, e) - omega * VT::get(dv, e));
       *reinterpret_cast<V*>(out + q) = o;
+    }
+  }
+}
+
+template <typename T, int RB>
+__global__ void __launch_bounds__(512) k_line_sweep_vec(Geom<T> g, const T* __restrict__ p, const T* __restrict__ b,
+                                                        T omega, T* __restrict__ out) {
+  extern __shared__ __align__(16) unsigned char line_sm[];
+  line_vec_tile<T, RB, false, true>(g, p, b, omega, out, blockIdx.x, reinterpret_cast<T*>(line_sm));
+}
+
+__device__ __forceinline__ int ld_acquire(const int* a) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(a) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(int* a, int v) {
+  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(a), "r"(v) : "memory");
+}
+
+// A whole SRJ cycle of M FP32 z-line sweeps (A -> B -> A ...) in one
+// cooperative launch, one block per tile of the vector line sweep.
+// Instead of a grid barrier between sweeps, a tile waits only for the four
+// tiles whose cells its stencil reads (x and y neighbours, periodic) to
+// have finished the previous sweep: flags[t] counts the sweeps tile t has
+// completed (all tiles hold the same count between launches, so a launch
+// reads its starting count from its own flag).  That also keeps a tile from
+// overwriting cells a neighbour still reads: a neighbour reads this tile's
+// cells of the buffer being overwritten during its previous sweep, which has
+// ended.  p is read from L2 (other blocks write it within the launch).  Every
+// wait is bounded by ctl->bar_wait clock cycles; on time-out the block sets
+// ctl->bad = 2 and returns, and the blocks waiting on it time out in turn.
+template <int RB>
+__global__ void __launch_bounds__(512) k_line_cycle_f32(Geom<float> g, float* A, float* B, const float* __restrict__ b,
+                                                        const float* __restrict__ omega, int M, int* flags,
+                                                        SolveCtl* ctl) {
+  extern __shared__ __align__(16) unsigned char line_sm[];
+  float* R = reinterpret_cast<float*>(line_sm);
+  __shared__ int s_ok;
+  const int ntx = (g.nx + 31) / 32, nty = (g.ny + RB - 1) / RB;
+  const int tile = blockIdx.x, tx = tile % ntx, ty = tile / ntx;
+  const int nb0 = ty * ntx + (tx == 0 ? ntx - 1 : tx - 1), nb1 = ty * ntx + (tx == ntx - 1 ? 0 : tx + 1);
+  const int nb2 = (ty == 0 ? nty - 1 : ty - 1) * ntx + tx, nb3 = (ty == nty - 1 ? 0 : ty + 1) * ntx + tx;
+  const int base = ld_acquire(flags + tile) + __ldcg(&ctl->wait_skew);
+  const long long wait = __ldcg(&ctl->bar_wait);
+  for (int m = 0; m < M; m++) {
+    if (m > 0) {
+      if (threadIdx.x == 0) {
+        int ok = 1;
+        const long long t0 = clock64();
+        const int need = base + m;
+        while (ok && (ld_acquire(flags + nb0) < need || ld_acquire(flags + nb1) < need ||
+                      ld_acquire(flags + nb2) < need || ld_acquire(flags + nb3) < need)) {
+          if (clock64() - t0 > wait) ok = 0;
+          else __nanosleep(32);
+        }
+        s_ok = ok;
+      }
+      __syncthreads();
+      if (!s_ok) {
+        if (threadIdx.x == 0) ctl->bad = 2;
+        return;
+      }
+    }
+    line_vec_tile<float, RB, true, false>(g, (m & 1) ? B : A, b, __ldg(omega + m), (m & 1) ? A : B, tile, R);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      st_release(flags + tile, base - __ldcg(&ctl->wait_skew) + m + 1);
     }
   }
 }
@@ -986,6 +1066,59 @@ template cudaError_t launch_line_sweep<float>(const Geom<float>&, const float*, 
                                               cudaStream_t);
 template cudaError_t launch_line_sweep<double>(const Geom<double>&, const double*, const double*, double, double*,
                                                cudaStream_t);
+
+// Persistent z-line cycles (FP32, vector kernel): the rows per tile of the
+// line sweep, and 0 when the grid does not take them (rows not a multiple
+// of 4 cells, columns too tall for shared memory, or more tiles than can be
+// resident at once)
+int line_cycle_rows(const Geom<float>& g, int device) {
+  if (g.nx % 4) return 0;
+  const int rb = line_rows(g.nz, sizeof(float));
+  if (rb == 0) return 0;
+  const int tiles = ((g.nx + 31) / 32) * ((g.ny + rb - 1) / rb);
+  const size_t smem = (size_t)32 * rb * g.nz * sizeof(float);
+  int per_sm = 0, sms = 0;
+  cudaError_t e;
+  switch (rb) {
+    case 4:
+      e = cudaFuncSetAttribute(k_line_cycle_f32<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_line_cycle_f32<4>, 512, smem);
+      break;
+    case 2:
+      e = cudaFuncSetAttribute(k_line_cycle_f32<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_line_cycle_f32<2>, 512, smem);
+      break;
+    default:
+      e = cudaFuncSetAttribute(k_line_cycle_f32<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_line_cycle_f32<1>, 512, smem);
+  }
+  if (e != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return 0;
+  return tiles <= per_sm * sms ? rb : 0;
+}
+
+int line_cycle_tiles(const Geom<float>& g, int rb) { return ((g.nx + 31) / 32) * ((g.ny + rb - 1) / rb); }
+
+cudaError_t launch_line_cycle_f32(const Geom<float>& g, int rb, float* A, float* B, const float* b,
+                                  const float* omega, int M, int* flags, SolveCtl* ctl, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)line_cycle_tiles(g, rb));
+  cfg.blockDim = dim3(512);
+  cfg.dynamicSmemBytes = (size_t)32 * rb * g.nz * sizeof(float);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e;
+  switch (rb) {
+    case 4: e = cudaLaunchKernelEx(&cfg, k_line_cycle_f32<4>, g, A, B, b, omega, M, flags, ctl); break;
+    case 2: e = cudaLaunchKernelEx(&cfg, k_line_cycle_f32<2>, g, A, B, b, omega, M, flags, ctl); break;
+    default: e = cudaLaunchKernelEx(&cfg, k_line_cycle_f32<1>, g, A, B, b, omega, M, flags, ctl);
+  }
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
 
 int cycle_grid_f32(int device) {
   int per_sm = 0, sms = 0;

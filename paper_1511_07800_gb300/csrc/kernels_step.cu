@@ -483,58 +483,43 @@ __global__ void __launch_bounds__(128) k_cn_line(Geom<T> g, Visc<T, LES> N, T h,
 
 // ---------------------------------------------------------------------------
 // Eq. presdiv right-hand side b = D u* / dt, with ||b||_2 reduced in FP64.
-// Also clears the convergence flags of the coming solve.
-//   FP64 fields: FP64 arithmetic; the sum of b over the box telescopes to
-//     zero to FP64 rounding, so b has no mean the Poisson iteration could
-//     not remove (sc[SC_BMEAN] = 0).
-//   FP32 fields: FP32 arithmetic (the fields carry FP32 rounding already);
-//     b is stored in FP64, and its volume mean, which FP32 differences leave
-//     at about 1e-8 of ||b||, goes to sc[SC_BMEAN], from where the
-//     refinement residual removes it.  Sums of squares and of b dz in FP32
-//     per warp, FP64 across warps.
+// Also clears the convergence flags of the coming solve.  The differences
+// are taken in FP64 (exact for FP32 inputs) and scaled in FP64: the three
+// terms of b nearly cancel (u* is divergence-free up to O(dt)), so FP32
+// arithmetic here would put rounding of the size of the terms into b; and
+// the sum of b over the box telescopes to zero to FP64 rounding, so b has
+// no mean the Poisson iteration could not remove (sc[SC_BMEAN] = 0).  FP32
+// fields sum the squares in FP32 per warp and FP64 across warps.
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(kBX* kBY) k_divergence(Geom<T> g, const T* __restrict__ u, const T* __restrict__ v,
                                                           const T* __restrict__ w, double idt, double* __restrict__ b,
-                                                          Red red, unsigned nblocks, double inv_vol) {
+                                                          Red red, unsigned nblocks) {
   __shared__ double sh[32];
   const int i = blockIdx.x * kBX + threadIdx.x, j = blockIdx.y * kBY + threadIdx.y, k = blockIdx.z;
-  double s = 0.0, sm = 0.0;
-  if constexpr (sizeof(T) == sizeof(float)) {
-    float s2 = 0.f, sb = 0.f;
-    if (i < g.nx && j < g.ny) {
-      const int ip = i == g.nx - 1 ? 0 : i + 1, jp = j == g.ny - 1 ? 0 : j + 1;
-      const int q = at(g.nx, g.ny, i, j, k);
-      const float d = (__ldg(u + at(g.nx, g.ny, ip, j, k)) - __ldg(u + q)) * g.idx +
-                      (__ldg(v + at(g.nx, g.ny, i, jp, k)) - __ldg(v + q)) * g.idy +
-                      (__ldg(w + q + g.nx * g.ny) - __ldg(w + q)) * __ldg(g.idz + k);
-      const float bt = d * (float)idt;
-      b[q] = (double)bt;
-      s2 = bt * bt;
-      sb = bt * __ldg(g.dzv + k);
-    }
-    s = block_sum_f32(s2, sh);
-    sm = block_sum_f32(sb, sh);
-  } else {
-    if (i < g.nx && j < g.ny) {
-      const int ip = i == g.nx - 1 ? 0 : i + 1, jp = j == g.ny - 1 ? 0 : j + 1;
-      const int q = at(g.nx, g.ny, i, j, k);
-      const double d = (__ldg(u + at(g.nx, g.ny, ip, j, k)) - __ldg(u + q)) * g.idx +
-                       (__ldg(v + at(g.nx, g.ny, i, jp, k)) - __ldg(v + q)) * g.idy +
-                       (__ldg(w + q + g.nx * g.ny) - __ldg(w + q)) * __ldg(g.idz + k);
-      const double bt = d * idt;
-      b[q] = bt;
-      s = bt * bt;
-    }
-    s = block_sum(s, sh);
+  double bt = 0.0;
+  if (i < g.nx && j < g.ny) {
+    const int ip = i == g.nx - 1 ? 0 : i + 1, jp = j == g.ny - 1 ? 0 : j + 1;
+    const int q = at(g.nx, g.ny, i, j, k);
+    const double d = ((double)__ldg(u + at(g.nx, g.ny, ip, j, k)) - (double)__ldg(u + q)) * (double)g.idx +
+                     ((double)__ldg(v + at(g.nx, g.ny, i, jp, k)) - (double)__ldg(v + q)) * (double)g.idy +
+                     ((double)__ldg(w + q + g.nx * g.ny) - (double)__ldg(w + q)) * (double)__ldg(g.idz + k);
+    bt = d * idt;
+    b[q] = bt;
   }
-  if (publish_partial(red, nblocks, s, sm, true)) {
+  double s;
+  if constexpr (sizeof(T) == sizeof(float)) {
+    const float bf = (float)bt;
+    s = block_sum_f32(bf * bf, sh);
+  } else {
+    s = block_sum(bt * bt, sh);
+  }
+  if (publish_partial(red, nblocks, s, 0.0, false)) {
     const double tot = final_sum(red.partial, nblocks, sh);
-    const double mean = sizeof(T) == sizeof(float) ? final_sum(red.partial + nblocks, nblocks, sh) * inv_vol : 0.0;
     const int tid = threadIdx.x + blockDim.x * threadIdx.y;
     if (tid == 0) {
       red.sc[SC_BNORM] = sqrt(tot);
-      red.sc[SC_BMEAN] = mean;
+      red.sc[SC_BMEAN] = 0.0;
       red.flag[FL_DONE] = 0;
       red.flag[FL_INNER_DONE] = 0;
       *red.counter = 0u;
@@ -755,7 +740,8 @@ template <typename T>
 cudaError_t launch_divergence_rhs(const Geom<T>& g, const T* u, const T* v, const T* w, double idt, double* b,
                                   Red red, double Lz, cudaStream_t s) {
   Launch l = plane_launch(g.nx, g.ny, g.nz);
-  k_divergence<T><<<l.grid, l.block, 0, s>>>(g, u, v, w, idt, b, red, l.nblocks, 1.0 / ((double)g.nx * g.ny * Lz));
+  (void)Lz;
+  k_divergence<T><<<l.grid, l.block, 0, s>>>(g, u, v, w, idt, b, red, l.nblocks);
   return cudaGetLastError();
 }
 

@@ -71,7 +71,7 @@ enum {
   SC_RES_INNER = 6, // inner residual at the last inner check
   SC_VSUM = 7,      // volume sum of a field (stp_poisson_solve's mean checks)
   SC_VABS = 8,      // volume sum of its absolute value
-  SC_BMEAN = 9,     // volume mean of b left by FP32 differences (removed in the refinement residual)
+  SC_BMEAN = 9,     // a volume mean of b to remove in the refinement residual (0: b from the step telescopes)
   SC_COUNT = 10
 };
 enum { FL_DONE = 0, FL_INNER_DONE = 1, FL_BAD = 2, FL_COUNT = 4 };
@@ -111,6 +111,11 @@ struct SolveCtl {
   // longest wait of a grid barrier of the persistent SRJ cycle, in SM clock
   // cycles (about one second by default; STP_BARRIER_WAIT overrides it)
   long long bar_wait;
+  // added to the sweep count a persistent z-line tile waits for (0; a
+  // positive value, from STP_WAIT_SKEW, asks for a count nothing reaches,
+  // so that a test can make the bounded waits run out)
+  int wait_skew;
+  int pad3;
 };
 
 // ---------------------------------------------------------------------------
@@ -152,9 +157,8 @@ cudaError_t launch_cn_line(const Geom<T>& g, bool les, const T* nu, T nu0, T hdt
                            const T* rw, const T* au, const T* av, const T* aw, T* ou, T* ov, T* ow, void* scratch,
                            cudaStream_t s);
 
-// b = D u / dt, ||b||^2 reduced into sc[SC_BNORM] (as the norm), flags reset.
-// FP32 fields: FP32 arithmetic, and the volume mean of b (which FP32
-// differences no longer cancel exactly) into sc[SC_BMEAN]; FP64: 0 there.
+// b = D u / dt (FP64 arithmetic in both precisions), ||b||^2 reduced into
+// sc[SC_BNORM] (as the norm), flags reset; sc[SC_BMEAN] = 0 (b telescopes).
 template <typename T>
 cudaError_t launch_divergence_rhs(const Geom<T>& g, const T* u, const T* v, const T* w, double idt, double* b,
                                   Red red, double Lz, cudaStream_t s);
@@ -206,6 +210,14 @@ cudaError_t launch_outer(const Geom<double>& g, const double* p, const double* b
 int cycle_grid_f32(int device);
 cudaError_t launch_cycle_f32(const Geom<float>& g, float* A, float* B, const float* b, const float* omega, int M,
                              GridBar bar, SolveCtl* ctl, int nblocks, cudaStream_t s);
+// One SRJ cycle of M FP32 z-line sweeps in one cooperative launch, tiles
+// synchronised with their x-y neighbours through flags (ints, one a tile,
+// zero at the start of a call).  line_cycle_rows: the tile's rows, 0 when
+// the grid cannot run it (then the per-sweep kernels run).
+int line_cycle_rows(const Geom<float>& g, int device);
+int line_cycle_tiles(const Geom<float>& g, int rb);
+cudaError_t launch_line_cycle_f32(const Geom<float>& g, int rb, float* A, float* B, const float* b,
+                                  const float* omega, int M, int* flags, SolveCtl* ctl, cudaStream_t s);
 // start of a refinement pass: d = 0 and the inner loop armed
 cudaError_t launch_pass_begin(float* d, size_t n, int graph, cudaGraphConditionalHandle h_loop, cudaStream_t s);
 // p += d

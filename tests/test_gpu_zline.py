@@ -172,3 +172,62 @@ def test_line_rows_per_block_fp32(stp_lib, orc, nx, nz):
     r = b - o.laplacian(p)
     rel = np.sqrt(np.sum(r * r) / np.sum(b * b))
     assert st["converged"] and rel <= 1e-8 * 1.0001, rel
+
+
+@pytest.mark.parametrize("shape", [(256, 24, 40), (96, 13, 64), (64, 8, 200)])
+def test_persistent_line_cycle_bitwise(stp_lib, monkeypatch, shape):
+    """FP32 z-line cycles as one cooperative launch (STP_LINE_PERSISTENT=1;
+    each tile waits for its x-y neighbour tiles' previous sweep instead of
+    a kernel boundary) give bitwise the fields of the one-launch-per-sweep
+    path: same arithmetic per cell, the same values read.  Grids with rows
+    per tile of 4, 4 (a partial last tile row) and 2 (tall columns)."""
+    nx, ny, nz = shape
+    cfg = case(nx=nx, ny=ny, nz=nz, stretch=2.0, les=1, nu=1 / 500.0, cn_sweeps=4, zline=1)
+    om = line_schedule(cfg, 32)
+    out = []
+    for mode in ("0", "1"):
+        monkeypatch.setenv("STP_LINE_PERSISTENT", mode)
+        with stp_lib.Channel(cfg, precision="fp32", omega=om) as ch:
+            ch.set_fields(*turbulent_like(cfg, 14))
+            st = ch.step(3)
+            assert st["converged"]
+            out.append((ch.get_fields(), st))
+    (fa, sa), (fb, sb) = out
+    assert sa["sweeps"] == sb["sweeps"] and sa["passes"] == sb["passes"]
+    assert sb["launches"] < sa["launches"]
+    for k in ("u", "v", "w", "p"):
+        assert np.array_equal(fa[k], fb[k]), k
+
+
+def test_persistent_line_cycle_timeout_recovers(stp_lib, monkeypatch):
+    """Tiles of the persistent line cycle that wait for a sweep count no
+    neighbour reaches (STP_WAIT_SKEW=1, set on the host) give up after
+    STP_BARRIER_WAIT clock cycles (here 1e6, about half a millisecond):
+    STP_ETIMEOUT, the fields of the last good step kept, and the next call
+    (flags cleared, no skew) steps as a fresh handle does."""
+    cfg = case(nx=128, ny=16, nz=32, stretch=2.0, les=1, nu=1 / 500.0, cn_sweeps=4, zline=1)
+    om = line_schedule(cfg, 32)
+    monkeypatch.setenv("STP_LINE_PERSISTENT", "1")
+    f0 = turbulent_like(cfg, 15)
+    with stp_lib.Channel(cfg, precision="fp32", omega=om) as ref:
+        ref.set_fields(*f0)
+        ref.step(2)
+        want = ref.get_fields()
+    with stp_lib.Channel(cfg, precision="fp32", omega=om) as ch:
+        ch.set_fields(*f0)
+        before = ch.get_fields()
+        monkeypatch.setenv("STP_BARRIER_WAIT", "1000000")
+        monkeypatch.setenv("STP_WAIT_SKEW", "1")
+        with pytest.raises(stp_lib.StpError) as e:
+            ch.step(1)
+        assert e.value.code == stp_lib.STP_ETIMEOUT
+        after = ch.get_fields()
+        for k in ("u", "v", "w", "p"):
+            assert np.array_equal(after[k], before[k]), k
+        monkeypatch.delenv("STP_BARRIER_WAIT")
+        monkeypatch.delenv("STP_WAIT_SKEW")
+        st = ch.step(2)
+        assert st["converged"]
+        got = ch.get_fields()
+    for k in ("u", "v", "w", "p"):
+        assert np.array_equal(got[k], want[k]), k
