@@ -100,26 +100,34 @@ def test_learned_preconditioner_solves_to_tolerance(stp_lib, orc, precision):
 
 
 def test_trained_guess_reduces_srj_work(stp_lib, orc):
-    """Train on pairs harvested from six channels, evaluate on a seventh:
-    the validation loss falls well below that of the zero guess, and the
-    FP64 solves started from the learned guess need no more SRJ sweeps
-    than the plain solves from the previous pressure (the gain is printed)."""
+    """Train on pairs harvested from twenty channels, evaluate on an unseen
+    one: the validation loss falls well below that of the zero guess, and
+    the FP64 solves started from the learned guess take at least 10 % fewer
+    SRJ sweeps than the plain solves from the previous pressure (in FP64 a
+    guess that removes most of the error saves whole cycles).  At this grid
+    a solve is launch-bound and the forward's fixed cost hides the gain in
+    time; the time to 1e-8 at scale is the 20k-pair experiment of
+    learn.config4 (1.25x in FP64 at 128 x 64 x 128).  The gains are printed."""
     torch = pytest.importorskip("torch")
-    from oracle import unet
     from paper_1511_07800_gb300 import learn
     cfg = _cfg()
-    R, DP = learn.harvest(cfg, seeds=range(6), steps_per_seed=30)
+    R, DP = learn.harvest(cfg, seeds=range(20), steps_per_seed=30)
     Rv, DPv = learn.harvest(cfg, seeds=[50], steps_per_seed=8)
     K = learn.output_scale(R, DP, 8, GRID)
     net = stp_lib.UNet(8, *GRID)
-    net.set_params(unet.init_params(0).astype(np.float32))
+    net.set_params(learn.he_init(0))
     net.set_output_scale(K)
     # loss of the zero guess in these units is 1 (K normalises dp/s)
-    learn.train(net, R, DP, 300, 8, 1e-3)
-    learn.train(net, R, DP, 200, 8, 3e-4)
+    learn.train(net, R, DP, 1500, 8, 1e-3)
+    learn.train(net, R, DP, 500, 8, 3e-4)
     val = net.eval_pairs(Rv.contiguous(), DPv.contiguous())
+    print("validation loss", val)
     assert val < 0.5, val
-    res = learn.compare(cfg, net, seed=50, nsteps=8, precision="fp64")
+    one = stp_lib.UNet(1, *GRID)
+    one.set_params(net.get_params())
+    one.set_output_scale(K)
+    res = learn.compare_modes(cfg, one, seed=50, nsteps=8, precision="fp64")
     print("learned vs plain (FP64):", res)
-    assert res["learned"]["sweeps"] <= res["plain"]["sweeps"]
+    assert res["guess"]["sweeps"] <= 0.9 * res["plain"]["sweeps"], res
+    one.close()
     net.close()
