@@ -1251,6 +1251,7 @@ int stp_init(const stp_config* cfg, stp_handle** out) {
   const size_t maxblocks = (size_t)big.grid.x * big.grid.y * big.grid.z + 152 * 32;
   A((void**)&h->red.partial, sizeof(double) * 2 * maxblocks);
   A((void**)&h->red.counter, sizeof(unsigned) * 4);
+  A((void**)&h->red.gcount, sizeof(unsigned) * (maxblocks / 64 + 2));
   A((void**)&h->red.sc, sizeof(double) * SC_COUNT);
   A((void**)&h->red.flag, sizeof(int) * FL_COUNT);
   A((void**)&h->ctl, sizeof(SolveCtl));
@@ -1307,6 +1308,7 @@ int stp_init(const stp_config* cfg, stp_handle** out) {
   if (e == cudaSuccess) e = cudaMemsetAsync(h->p2, 0, sizeof(double) * nc, h->st);
   if (e == cudaSuccess && h->nu) e = cudaMemsetAsync(h->nu, 0, es * nc, h->st);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->red.counter, 0, sizeof(unsigned) * 4, h->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->red.gcount, 0, sizeof(unsigned) * (maxblocks / 64 + 2), h->st);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->red.sc, 0, sizeof(double) * SC_COUNT, h->st);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->red.flag, 0, sizeof(int) * FL_COUNT, h->st);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->ctl, 0, sizeof(SolveCtl), h->st);

@@ -127,6 +127,40 @@ __device__ __forceinline__ bool publish_partial(Red red, unsigned nblocks, doubl
   return last;
 }
 
+// The same with arrivals counted in two levels: blocks arrive on the
+// counter of their group of 64 (red.gcount), the last of each group on
+// red.counter.  With one counter, tens of thousands of blocks (one a 32 x 8
+// tile and level) serialise on one address while the rest of each block
+// waits at its barrier; here at most 64 arrivals meet on any counter.  The
+// partials and the order of the final sum are unchanged.
+__device__ __forceinline__ bool publish_partial_tree(Red red, unsigned nblocks, double a, double b, bool two) {
+  __shared__ bool last;
+  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  if (tid == 0) {
+    const unsigned bl = block_linear();
+    red.partial[bl] = a;
+    if (two) red.partial[nblocks + bl] = b;
+    __threadfence();
+    constexpr unsigned G = 64;
+    const unsigned ng = (nblocks + G - 1) / G;
+    bool l = false;
+    if (ng <= 1) {
+      l = atomicAdd(red.counter, 1u) == nblocks - 1;
+    } else {
+      const unsigned g = bl / G, gs = min(G, nblocks - g * G);
+      if (atomicAdd(red.gcount + g, 1u) == gs - 1) {
+        red.gcount[g] = 0u;  // every block of the group has arrived
+        __threadfence();
+        l = atomicAdd(red.counter, 1u) == ng - 1;
+      }
+    }
+    if (l) __threadfence();
+    last = l;
+  }
+  __syncthreads();
+  return last;
+}
+
 // In the last block: sum of partial[0..n) in a fixed order (strided per
 // thread, then the block tree).  Valid in thread 0.
 __device__ __forceinline__ double final_sum(const double* part, unsigned n, double* sh) {

@@ -735,7 +735,7 @@ __global__ void __launch_bounds__(kBX* kBY) k_check(Geom<T> g, const T* __restri
     }
     s = block_sum(s, sh);
   }
-  if (publish_partial(red, nblocks, s, 0.0, false)) {
+  if (publish_partial_tree(red, nblocks, s, 0.0, false)) {
     const double tot = final_sum(red.partial, nblocks, sh);
     if (threadIdx.x == 0 && threadIdx.y == 0) {
       const bool go = cycle_decide<MODE>(ctl, red, sqrt(tot));
@@ -766,7 +766,7 @@ __global__ void __launch_bounds__(kBX* kBY) k_outer(Geom<double> g, const double
     r2 = r * r;
   }
   double s = block_sum_f32(r2, sh);
-  if (publish_partial(red, nblocks, s, 0.0, false)) {
+  if (publish_partial_tree(red, nblocks, s, 0.0, false)) {
     const double tot = final_sum(red.partial, nblocks, sh);
     if (threadIdx.x == 0 && threadIdx.y == 0) {
       const bool go = pass_decide(ctl, red, sqrt(tot), after_pass);

@@ -400,7 +400,7 @@ __global__ void __launch_bounds__(128) k_cn_line(Geom<T> g, Visc<T, LES> N, T h,
     const T* __restrict__ r = comp == 0 ? ru : rv;
     T* __restrict__ o = comp == 0 ? ou : ov;
     T Am = nuc(aA, bA, -1), Bm = nuc(i, j, -1), A0 = nuc(aA, bA, 0), B0 = nuc(i, j, 0);
-#pragma unroll 2
+#pragma unroll 4
     for (int k = 0; k < nz; k++) {
       const int lev = k * plane;
       const T Ap = nuc(aA, bA, k + 1), Bp = nuc(i, j, k + 1);
@@ -448,7 +448,7 @@ __global__ void __launch_bounds__(128) k_cn_line(Geom<T> g, Visc<T, LES> N, T h,
     ow[c0] = T(0);
     ow[nz * plane + c0] = T(0);
     T q0 = nuc(i, j, 0), q1 = nuc(ip, j, 0), q2 = nuc(im, j, 0), q3 = nuc(i, jp, 0), q4 = nuc(i, jm, 0);
-#pragma unroll 2
+#pragma unroll 4
     for (int c = 1; c < nz; c++) {
       const int lev = c * plane;
       const T p0 = nuc(i, j, c), p1 = nuc(ip, j, c), p2 = nuc(im, j, c), p3 = nuc(i, jp, c), p4 = nuc(i, jm, c);
@@ -514,7 +514,7 @@ __global__ void __launch_bounds__(kBX* kBY) k_divergence(Geom<T> g, const T* __r
   } else {
     s = block_sum(bt * bt, sh);
   }
-  if (publish_partial(red, nblocks, s, 0.0, false)) {
+  if (publish_partial_tree(red, nblocks, s, 0.0, false)) {
     const double tot = final_sum(red.partial, nblocks, sh);
     const int tid = threadIdx.x + blockDim.x * threadIdx.y;
     if (tid == 0) {
@@ -593,7 +593,7 @@ __global__ void __launch_bounds__(kBX* kBY) k_correct(Geom<T> g, const double* _
     bs = block_sum(s, sh);
     bm = block_max(m, sh);
   }
-  if (publish_partial(red, nblocks, bs, bm, true)) {
+  if (publish_partial_tree(red, nblocks, bs, bm, true)) {
     const double tot = final_sum(red.partial, nblocks, sh);
     const double mx = final_max(red.partial + nblocks, nblocks, sh);
     const int tid = threadIdx.x + blockDim.x * threadIdx.y;

@@ -59,6 +59,7 @@ struct Red {
   unsigned* counter;  // [1], returns to 0 after each reduction
   double* sc;         // scalars, see SC_* below
   int* flag;          // flags, see FL_* below
+  unsigned* gcount;   // [max_blocks / 64 + 1] arrival counters of groups of 64 blocks (0 between reductions)
 };
 
 enum {
