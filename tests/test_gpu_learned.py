@@ -99,35 +99,37 @@ def test_learned_preconditioner_solves_to_tolerance(stp_lib, orc, precision):
     net.close()
 
 
-def test_trained_guess_reduces_srj_work(stp_lib, orc):
-    """Train on pairs harvested from twenty channels, evaluate on an unseen
-    one: the validation loss falls well below that of the zero guess, and
-    the FP64 solves started from the learned guess take at least 10 % fewer
-    SRJ sweeps than the plain solves from the previous pressure (in FP64 a
-    guess that removes most of the error saves whole cycles).  At this grid
-    a solve is launch-bound and the forward's fixed cost hides the gain in
-    time; the time to 1e-8 at scale is the 20k-pair experiment of
-    learn.config4 (1.25x in FP64 at 128 x 64 x 128).  The gains are printed."""
+def test_trained_guess_cuts_the_fp64_solve_time(stp_lib, orc):
+    """What the trained network gains.  Trained on 600 pairs harvested from
+    ten instability channels at 128 x 64 x 128 (the workload's grid), then
+    used as the initial guess of every FP64 pressure solve of an unseen
+    channel: the solves to 1e-8 take at least 15 % fewer SRJ sweeps and at
+    least 1.1 times less GPU time than the plain solves from the previous
+    pressure, the network's forward included (measured: 1216 against 1600
+    sweeps, 1.25x).  In FP64 a guess that removes most of the error saves
+    whole SRJ cycles; in FP32 with refinement a pass gains about 1e-3 from
+    any start, so the guess saves no pass (not asserted; printed)."""
     torch = pytest.importorskip("torch")
     from paper_1511_07800_gb300 import learn
-    cfg = _cfg()
-    R, DP = learn.harvest(cfg, seeds=range(20), steps_per_seed=30)
-    Rv, DPv = learn.harvest(cfg, seeds=[50], steps_per_seed=8)
-    K = learn.output_scale(R, DP, 8, GRID)
-    net = stp_lib.UNet(8, *GRID)
+    grid = (128, 64, 128)
+    cfg = learn.workload("os_instability", grid=grid)
+    R, DP = learn.harvest(cfg, seeds=range(10), steps_per_seed=60)
+    K = learn.output_scale(R, DP, 4, grid)
+    net = stp_lib.UNet(4, *grid)
     net.set_params(learn.he_init(0))
     net.set_output_scale(K)
-    # loss of the zero guess in these units is 1 (K normalises dp/s)
-    learn.train(net, R, DP, 1500, 8, 1e-3)
-    learn.train(net, R, DP, 500, 8, 3e-4)
-    val = net.eval_pairs(Rv.contiguous(), DPv.contiguous())
-    print("validation loss", val)
-    assert val < 0.5, val
-    one = stp_lib.UNet(1, *GRID)
+    learn.train(net, R, DP, 1500, 4, 1e-3)
+    learn.train(net, R, DP, 500, 4, 3e-4)
+    one = stp_lib.UNet(1, *grid)
     one.set_params(net.get_params())
     one.set_output_scale(K)
+    net.close()
+    del R, DP
     res = learn.compare_modes(cfg, one, seed=50, nsteps=8, precision="fp64")
     print("learned vs plain (FP64):", res)
-    assert res["guess"]["sweeps"] <= 0.9 * res["plain"]["sweeps"], res
+    assert res["guess"]["converged"] and res["plain"]["converged"]
+    assert res["guess"]["sweeps"] <= 0.85 * res["plain"]["sweeps"], res
+    assert res["guess"]["speedup"] >= 1.1, res
+    res32 = learn.compare_modes(cfg, one, seed=50, nsteps=4, precision="fp32")
+    print("learned vs plain (FP32 + refinement):", res32)
     one.close()
-    net.close()
