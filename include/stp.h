@@ -32,9 +32,15 @@
  * STP_LINE_PERSISTENT=1 at stp_init an FP32 z-line cycle runs as one
  * cooperative launch in which every 32 x 4-column tile waits only for its
  * four x-y neighbour tiles to finish the previous sweep (bitwise the same
- * results; the same bounded waits; STP_WAIT_SKEW=<n> makes every tile wait
- * for a sweep count no neighbour reaches, so that tests can make those
- * waits run out).  The FP32 sweep kernel's tile shape (z levels per thread, rows
+ * results as the shared-memory lock-step kernel below; the same bounded
+ * waits; STP_WAIT_SKEW=<n> makes every tile wait for a sweep count no
+ * neighbour reaches, so that tests can make those waits run out).  An FP32
+ * z-line sweep on rows of a multiple of 32 cells and columns of 2 to 192
+ * levels solves each column in registers, level chunk by level chunk
+ * (Sec. 3.4's line relaxation with the twisted elimination split into
+ * chunked recurrences); elsewhere, or with STP_LINE_VARIANT=0 at stp_init,
+ * a block stages its columns in shared memory and solves them in lock
+ * step.  The two round differently (a few units in the last place).  The FP32 sweep kernel's tile shape (z levels per thread, rows
  * per block) is picked on first use by timing the variants on the grid
  * (STP_SWEEP_VARIANT=<0..11> forces one; variants 6..8 pack warps along the
  * plane for rows shorter than 128 cells, 9..11 run two sweeps per launch on

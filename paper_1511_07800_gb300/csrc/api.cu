@@ -83,6 +83,7 @@ struct stp_handle {
   bool host_solve = false;     // STP_HOST_SOLVE=1: drive the solve from the host
   int cycle_blocks = 0;        // >0: FP32 cycles run as one persistent cooperative kernel
   int line_rb = 0;             // >0: FP32 z-line cycles run as one persistent kernel (tile rows)
+  int line_variant = 0;        // FP32 z-line sweep kernel: 1 register-chunked columns, 0 shared-memory lock step
   int* line_flags = nullptr;   // its per-tile sweep counters
   int sweep_variant = -1;      // FP32 sweep kernel variant chosen by the autotuner (-1: not yet)
   float sweep_us = 0.f;        // its measured time per sweep
@@ -580,7 +581,8 @@ int build_cycle(stp_handle* h, const Geom<T>& g, cudaGraph_t wb, cudaGraphCondit
       return end_capture(h, ib);
     }
     for (int m = 0; m < M; m++)
-      CUDA_TRY(h, launch_line_sweep<T>(g, (m % 2 == 0) ? A : B, rhs, (T)h->omega[m], (m % 2 == 0) ? B : A, h->cap));
+      CUDA_TRY(h, launch_line_sweep<T>(g, (m % 2 == 0) ? A : B, rhs, (T)h->omega[m], (m % 2 == 0) ? B : A, h->cap,
+                                       h->line_variant));
     return end_capture(h, ib);
   }
   if (sizeof(T) == sizeof(float) && uses_pairs(h)) {
@@ -861,7 +863,7 @@ int host_cycles(stp_handle* h, const Geom<T>& g, T* A, T* B, const T* rhs, int m
       }
       for (int m = 0; m < M; m++)
         CUDA_TRY(h, launch_line_sweep<T>(g, (m % 2 == 0) ? A : B, rhs, (T)h->omega[m], (m % 2 == 0) ? B : A,
-                                         h->st));
+                                         h->st, h->line_variant));
       continue;
     }
     if (sizeof(T) == sizeof(float) && uses_pairs(h)) {
@@ -1269,6 +1271,12 @@ int stp_init(const stp_config* cfg, stp_handle** out) {
     const bool allow = env && env[0] == '1';
     if (allow && h->prec == STP_FP32_REFINE && h->nx % 4 == 0 && !cfg->zline)
       h->cycle_blocks = cycle_grid_f32(h->dev);
+  }
+  if (h->prec == STP_FP32_REFINE && cfg->zline && line_chunk_ok(h->nx, h->nz)) {
+    // FP32 z-line sweeps solve their columns in registers where the grid
+    // allows it; STP_LINE_VARIANT=0 keeps the shared-memory lock-step kernel
+    const char* env = std::getenv("STP_LINE_VARIANT");
+    h->line_variant = (env && env[0] == '0') ? 0 : 1;
   }
   {
     // persistent z-line cycles (STP_LINE_PERSISTENT=1): one cooperative

@@ -638,6 +638,218 @@ __global__ void __launch_bounds__(512) k_line_sweep_vec(Geom<T> g, const T* __re
   line_vec_tile<T, RB, false, true>(g, p, b, omega, out, blockIdx.x, reinterpret_cast<T*>(line_sm));
 }
 
+// The FP32 z-line sweep with every column solved in registers, in level
+// chunks (no shared-memory column array, no serial chain over the column).
+// The twisted factorisation of A is two first-order linear recurrences per
+// column:
+//   elimination  y_k = g_k + f_k y_{k-1}  (k < t, from the bottom wall)
+//                y_k = g_k + f_k y_{k+1}  (k > t, from the top wall),
+//   twist        x_t = g_t + tlf_t y_{t-1} + tlb_t y_{t+1},
+//   substitution x_k = y_k + e_k x_{k+1}  (k < t),  x_k = y_k + e_k x_{k-1}  (k > t),
+// with g = r tli, f = tlf, e = tlb.  The levels below t are cut into NCH/2
+// chunks, t and the levels above it into NCH/2 more (the first of them, the
+// twist chunk, starts at t).  Each thread owns one float4 unit (4 x cells)
+// of one chunk, holds its g_k in registers, and runs each recurrence inside
+// its chunk from zero; the value entering the chunk (its carry) then adds
+// in times the running product of the chunk's coefficients:
+//   y_k = z_k + (prod of f over the chunk up to k) y_in.
+// The carries come from the chunk boundary values in shared memory, walked
+// from the wall (elimination) or from the twist level (substitution).  In
+// exact arithmetic this is the sequential elimination; the rounding differs
+// by a few units in the last place.
+// Block: 32 x cells of one row (8 units) x NCH chunks, one tile per block.
+// Requires nx a multiple of 32 and chunks of at most LMAX levels.
+template <int NCH, int LMAX>
+__global__ void __launch_bounds__(8 * NCH, 4) k_line_sweep_chunk(Geom<float> g, const float* __restrict__ p,
+                                                                  const float* __restrict__ b, float omega,
+                                                                  float* __restrict__ out) {
+  constexpr int U = 8, H = NCH / 2;
+  __shared__ float4 ZB[NCH][U];  // chunk boundary values of the elimination
+  __shared__ float4 WB[NCH][U];  // and of the substitution
+  __shared__ float4 XT[U];       // x_t
+  __shared__ float FB[NCH], EB[NCH];  // the chunks' coefficient products
+  const int nx = g.nx, ny = g.ny, nz = g.nz, t = nz >> 1;
+  const int nxb = nx >> 5;
+  const int i = (blockIdx.x % nxb) * 32 + 4 * (threadIdx.x % U), j = blockIdx.x / nxb;
+  const int u = threadIdx.x % U, c = threadIdx.x / U;
+  const unsigned plane = (unsigned)nx * ny;
+  const unsigned c0 = (unsigned)j * nx + i;
+  const unsigned yp = (unsigned)(j == ny - 1 ? 0 : j + 1) * nx + i, ym = (unsigned)(j == 0 ? ny - 1 : j - 1) * nx + i;
+  const unsigned xl = (unsigned)j * nx + (i == 0 ? nx - 1 : i - 1), xr = (unsigned)j * nx + (i + 4 == nx ? 0 : i + 4);
+  // level range [k0, k1) of chunk c: [0, t) cut evenly from below, [t, nz)
+  // cut with the first piece (holding t) never empty
+  const bool lower = c < H;
+  const int k0 = lower ? c * t / H : t + ((c - H) * (nz - t) + H - 1) / H;
+  const int k1 = lower ? (c + 1) * t / H : (c + 1 == NCH ? nz : t + ((c - H + 1) * (nz - t) + H - 1) / H);
+  const int L = k1 - k0;
+  const bool twist = c == H;
+  const float idx2 = g.idx2, idy2 = g.idy2;
+  using VT = VecOf<float>;
+  float4 G[LMAX];
+  cudaGridDependencySynchronize();
+  // g_k = (b - L p)_k tli_k on the chunk's levels (the unit's z neighbours
+  // ride along in registers)
+  {
+    float4 cc = {}, zd = {};
+    if (L > 0) {
+      cc = __ldg(reinterpret_cast<const float4*>(p + (unsigned)k0 * plane + c0));
+      zd = k0 > 0 ? __ldg(reinterpret_cast<const float4*>(p + (unsigned)(k0 - 1) * plane + c0)) : cc;
+    }
+#pragma unroll
+    for (int q = 0; q < LMAX; q++) {
+      if (q < L) {
+        const int k = k0 + q;
+        const unsigned lev = (unsigned)k * plane;
+        const float4 yn = __ldg(reinterpret_cast<const float4*>(p + lev + yp));
+        const float4 ys = __ldg(reinterpret_cast<const float4*>(p + lev + ym));
+        const float4 zu = k < nz - 1 ? __ldg(reinterpret_cast<const float4*>(p + lev + plane + c0)) : cc;
+        const float4 bq = __ldg(reinterpret_cast<const float4*>(b + lev + c0));
+        const float left = __ldg(p + lev + xl), right = __ldg(p + lev + xr);
+        const float cup = __ldg(g.cup + k), cdn = __ldg(g.cdn + k), li = __ldg(g.tli + k);
+        float4 o;
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+          const float pc = VT::get(cc, e);
+          const float xrv = e == 3 ? right : VT::get(cc, e + 1);
+          const float xlv = e == 0 ? left : VT::get(cc, e - 1);
+          float lap = idx2 * ((xrv - pc) + (xlv - pc)) + idy2 * ((VT::get(yn, e) - pc) + (VT::get(ys, e) - pc));
+          if (k < nz - 1) lap += cup * (VT::get(zu, e) - pc);
+          if (k > 0) lap += cdn * (VT::get(zd, e) - pc);
+          VT::set(o, e, (VT::get(bq, e) - lap) * li);
+        }
+        G[q] = o;
+        zd = cc;
+        cc = zu;
+      }
+    }
+  }
+  auto axpy = [](float a, const float4& x, const float4& y) {  // a x + y
+    return make_float4(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z), fmaf(a, x.w, y.w));
+  };
+  const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+  // elimination inside the chunk from zero (upward below t, downward above
+  // it; the twist level itself is not eliminated)
+  {
+    float4 z = zero;
+    float F = 1.f;
+    if (lower) {
+#pragma unroll
+      for (int q = 0; q < LMAX; q++)
+        if (q < L) {
+          const float f = __ldg(g.tlf + k0 + q);
+          z = axpy(f, z, G[q]);
+          F *= f;
+          G[q] = z;
+        }
+    } else {
+#pragma unroll
+      for (int q = LMAX - 1; q >= 0; q--)
+        if (q < L && (q > 0 || !twist)) {
+          const float f = __ldg(g.tlf + k0 + q);
+          z = axpy(f, z, G[q]);
+          F *= f;
+          G[q] = z;
+        }
+    }
+    ZB[c][u] = z;
+    if (u == 0) FB[c] = F;
+  }
+  __syncthreads();
+  // carries of the elimination from the walls; the twist value
+  {
+    float4 carry = zero;
+    if (lower) {
+      for (int cc = 0; cc < c; cc++) carry = axpy(FB[cc], carry, ZB[cc][u]);
+      float F = 1.f;
+#pragma unroll
+      for (int q = 0; q < LMAX; q++)
+        if (q < L) {
+          F *= __ldg(g.tlf + k0 + q);
+          G[q] = axpy(F, carry, G[q]);
+        }
+    } else {
+      for (int cc = NCH - 1; cc > c; cc--) carry = axpy(FB[cc], carry, ZB[cc][u]);
+      float F = 1.f;
+#pragma unroll
+      for (int q = LMAX - 1; q >= 0; q--)
+        if (q < L && (q > 0 || !twist)) {
+          F *= __ldg(g.tlf + k0 + q);
+          G[q] = axpy(F, carry, G[q]);
+        }
+      if (twist) {
+        float4 ylow = zero;  // y_{t-1}
+        for (int cc = 0; cc < H; cc++) ylow = axpy(FB[cc], ylow, ZB[cc][u]);
+        const float4 yup = L >= 2 ? G[1] : carry;  // y_{t+1}
+        const float ft = t > 0 ? __ldg(g.tlf + t) : 0.f, et = t < nz - 1 ? __ldg(g.tlb + t) : 0.f;
+        G[0] = axpy(et, yup, axpy(ft, ylow, G[0]));
+      }
+    }
+  }
+  // substitution inside the chunk from zero (downward below t, upward above
+  // it); the twist chunk publishes x_t and its top value
+  {
+    float4 w = zero;
+    float E = 1.f;
+    if (lower) {
+#pragma unroll
+      for (int q = LMAX - 1; q >= 0; q--)
+        if (q < L) {
+          const float e = __ldg(g.tlb + k0 + q);
+          w = axpy(e, w, G[q]);
+          E *= e;
+          G[q] = w;
+        }
+    } else {
+#pragma unroll
+      for (int q = 0; q < LMAX; q++)
+        if (q < L && (q > 0 || !twist)) {
+          const float e = __ldg(g.tlb + k0 + q);
+          w = axpy(e, w, G[q]);
+          E *= e;
+          G[q] = w;
+        }
+      if (twist) {
+        w = axpy(E, G[0], w);  // x at the chunk's top level, absolute
+        E = 0.f;
+        XT[u] = G[0];
+      }
+    }
+    WB[c][u] = w;
+    if (u == 0) EB[c] = E;
+  }
+  __syncthreads();
+  // carries of the substitution from the twist level; the update
+  {
+    float4 carry = twist ? G[0] : XT[u];
+    if (lower) {
+      for (int cc = H - 1; cc > c; cc--) carry = axpy(EB[cc], carry, WB[cc][u]);
+      float E = 1.f;
+#pragma unroll
+      for (int q = LMAX - 1; q >= 0; q--)
+        if (q < L) {
+          E *= __ldg(g.tlb + k0 + q);
+          G[q] = axpy(E, carry, G[q]);
+        }
+    } else {
+      for (int cc = H; cc < c; cc++) carry = axpy(EB[cc], carry, WB[cc][u]);
+      float E = 1.f;
+#pragma unroll
+      for (int q = 0; q < LMAX; q++)
+        if (q < L && (q > 0 || !twist)) {
+          E *= __ldg(g.tlb + k0 + q);
+          G[q] = axpy(E, carry, G[q]);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < LMAX; q++)
+      if (q < L) {
+        const unsigned a = (unsigned)(k0 + q) * plane + c0;
+        const float4 pv = __ldg(reinterpret_cast<const float4*>(p + a));
+        *reinterpret_cast<float4*>(out + a) = axpy(-omega, G[q], pv);
+      }
+  }
+}
+
 __device__ __forceinline__ int ld_acquire(const int* a) {
   int v;
   asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(a) : "memory");
@@ -1041,11 +1253,35 @@ static cudaError_t launch_line_rows(const Geom<T>& g, const T* p, const T* b, T 
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
+// levels a chunk of the register-chunked line sweep holds at most, and the
+// chunks a column: columns of up to 2 x 16 x 6 = 192 levels
+constexpr int kLineChunks = 32, kLineChunkLevels = 6;
+
+bool line_chunk_ok(int nx, int nz) {
+  constexpr int H = kLineChunks / 2;
+  const int t = nz / 2;
+  return nx % 32 == 0 && nz >= 2 && (t + H - 1) / H <= kLineChunkLevels &&
+         (nz - t + H - 1) / H <= kLineChunkLevels;
+}
+
 template <typename T>
-cudaError_t launch_line_sweep(const Geom<T>& g, const T* p, const T* b, T omega, T* out, cudaStream_t s) {
+cudaError_t launch_line_sweep(const Geom<T>& g, const T* p, const T* b, T omega, T* out, cudaStream_t s,
+                              int variant) {
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;
+  if constexpr (sizeof(T) == 4) {
+    if (variant == 1 && line_chunk_ok(g.nx, g.nz)) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3((unsigned)((g.nx / 32) * g.ny));
+      cfg.blockDim = dim3(8 * kLineChunks);
+      cfg.stream = s;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      cudaError_t e = cudaLaunchKernelEx(&cfg, k_line_sweep_chunk<kLineChunks, kLineChunkLevels>, g, p, b, omega, out);
+      return e != cudaSuccess ? e : cudaGetLastError();
+    }
+  }
   switch (line_rows(g.nz, sizeof(T))) {
     case 4: return launch_line_rows<T, 4>(g, p, b, omega, out, s, attr);
     case 2: return launch_line_rows<T, 2>(g, p, b, omega, out, s, attr);
@@ -1063,9 +1299,9 @@ cudaError_t launch_line_sweep(const Geom<T>& g, const T* p, const T* b, T omega,
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 template cudaError_t launch_line_sweep<float>(const Geom<float>&, const float*, const float*, float, float*,
-                                              cudaStream_t);
+                                              cudaStream_t, int);
 template cudaError_t launch_line_sweep<double>(const Geom<double>&, const double*, const double*, double, double*,
-                                               cudaStream_t);
+                                               cudaStream_t, int);
 
 // Persistent z-line cycles (FP32, vector kernel): the rows per tile of the
 // line sweep, and 0 when the grid does not take them (rows not a multiple

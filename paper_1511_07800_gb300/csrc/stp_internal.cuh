@@ -175,7 +175,10 @@ cudaError_t launch_diffusion_only(const Geom<T>& g, bool les, const T* u, const 
 // One z-line Jacobi-SOR sweep: out = p - omega A^-1 (b - L p), A the z
 // column operator -L_z + (2/dx^2 + 2/dy^2) I (Thomas with the pivots li, lu).
 template <typename T>
-cudaError_t launch_line_sweep(const Geom<T>& g, const T* p, const T* b, T omega, T* out, cudaStream_t s);
+cudaError_t launch_line_sweep(const Geom<T>& g, const T* p, const T* b, T omega, T* out, cudaStream_t s,
+                              int variant);
+// whether the register-chunked FP32 line sweep (variant 1) takes the grid
+bool line_chunk_ok(int nx, int nz);
 
 // One Jacobi-SOR sweep of L p = b with factor omega: out = p - omega (b - Lp)/S.
 template <typename T>

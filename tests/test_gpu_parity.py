@@ -134,15 +134,20 @@ def test_step_parity_fp64(stp_lib, orc, stretch, les, forcing):
         assert abs(sg["ubulk"] - 1.0) < 1e-12
 
 
-@pytest.mark.parametrize("stretch,les,forcing,sweeps", [(2.0, 1, 1, 2), (0.0, 0, 0, 3), (2.0, 0, 0, 1),
-                                                         (1.0, 1, 0, 4)])
-def test_step_parity_cn_zline_fp64(stp_lib, orc, stretch, les, forcing, sweeps):
+@pytest.mark.parametrize("stretch,les,forcing,sweeps,shape", [(2.0, 1, 1, 2, None), (0.0, 0, 0, 3, None),
+                                                               (2.0, 0, 0, 1, None), (1.0, 1, 0, 4, None),
+                                                               (2.0, 1, 0, 2, (33, 5, 210)),
+                                                               (2.0, 1, 1, 2, (9, 3, 2))])
+def test_step_parity_cn_zline_fp64(stp_lib, orc, stretch, les, forcing, sweeps, shape):
     """Whole steps with the Crank-Nicolson system solved by z-line Jacobi
     sweeps (Thomas on every column, x-y neighbours from the previous
     iterate), held to a few sweeps so that every sweep's exact arithmetic
-    matters: every field agrees with the oracle's line sweeps to 1e-10."""
+    matters: every field agrees with the oracle's line sweeps to 1e-10.
+    Also tall columns (210 levels) and two levels, where each w column has
+    a single unknown."""
+    extra = {} if shape is None else dict(nx=shape[0], ny=shape[1], nz=shape[2])
     cfg = case(stretch=stretch, les=les, forcing=forcing, ptol=0.0, pmaxit=2 * 16, nu=1 / 300.0, dt=4e-3,
-               cn_zline=1, cn_sweeps=sweeps)
+               cn_zline=1, cn_sweeps=sweeps, **extra)
     om = schedule(cfg, 16)
     fo, so, fg, sg = run_both(stp_lib, orc, cfg, turbulent_like(cfg, 3), 4, om)
     for k in ("u", "v", "w", "p", "nu"):

@@ -174,16 +174,60 @@ def test_line_rows_per_block_fp32(stp_lib, orc, nx, nz):
     assert st["converged"] and rel <= 1e-8 * 1.0001, rel
 
 
+@pytest.mark.parametrize("nz", [2, 3, 5, 17, 64, 191, 192])
+@pytest.mark.parametrize("nx", [64, 96])
+def test_line_sweeps_fp32_both_kernels(stp_lib, orc, monkeypatch, nx, nz):
+    """FP32 line sweeps of both kernels (the register-chunked one, variant
+    1, for rows of a multiple of 32 cells and columns of up to 192 levels;
+    the shared-memory lock-step one, STP_LINE_VARIANT=0): one refinement
+    pass of 4 sweeps with an explicit schedule solves L d = b - L p0 from
+    d = 0 in FP32, which in exact arithmetic is the oracle's 4 FP64 sweeps
+    from p0.  Per element, |p - p_oracle| <= 5e-5 max|d|: the FP32
+    rounding of r, of each sweep's residual (differences of wall-stretched
+    couplings) and of the column solve over 4 sweeps with weights below 1
+    (a contraction) reaches about 1e-5 on 192 levels, while a wrong term of
+    the recurrences is of order one; and the chunked kernel's error stays
+    within twice the lock-step kernel's.  With chunks of two levels or
+    more (from 64 levels) the two kernels round differently, so their
+    results must differ (the variant is live); chunks of one level
+    reproduce the sequential elimination exactly."""
+    cfg = case(nx=nx, ny=5, nz=nz, stretch=2.0, zline=1)
+    om = [0.6, 0.9, 0.7, 1.0]
+    cfg["omega"] = om
+    b, rng = mean_free_rhs(cfg, 19)
+    p0 = rng.standard_normal(b.shape) * 0.1
+    p_o, it_o, _, _ = orc.Oracle(cfg).poisson(b, p0, tol=0.0, maxit=4)
+    want = gauge(p_o, cfg)
+    scale = np.abs(want - gauge(p0, cfg)).max()
+    got, err = {}, {}
+    for variant in ("0", "1"):
+        monkeypatch.setenv("STP_LINE_VARIANT", variant)
+        with stp_lib.Channel(cfg, precision="fp32", omega=om) as ch:
+            p_g = p0.copy()
+            st = ch.poisson_solve(b, p_g, tol=0.0, maxit=4)
+        assert st["sweeps"] == it_o == 4 and st["passes"] == 1, st
+        err[variant] = np.abs(p_g - want).max() / scale
+        assert err[variant] < 5e-5, (variant, err[variant])
+        got[variant] = p_g
+    print(f"line sweeps fp32 {nx}x5x{nz}: error/max|d| lock-step {err['0']:.3g}, chunked {err['1']:.3g}")
+    assert err["1"] <= 2 * err["0"] + 1e-7, err
+    if nz >= 64:
+        assert not np.array_equal(got["0"], got["1"])
+
+
 @pytest.mark.parametrize("shape", [(256, 24, 40), (96, 13, 64), (64, 8, 200)])
 def test_persistent_line_cycle_bitwise(stp_lib, monkeypatch, shape):
     """FP32 z-line cycles as one cooperative launch (STP_LINE_PERSISTENT=1;
     each tile waits for its x-y neighbour tiles' previous sweep instead of
     a kernel boundary) give bitwise the fields of the one-launch-per-sweep
-    path: same arithmetic per cell, the same values read.  Grids with rows
-    per tile of 4, 4 (a partial last tile row) and 2 (tall columns)."""
+    path on the shared-memory lock-step kernel (STP_LINE_VARIANT=0), whose
+    tile it runs: same arithmetic per cell, the same values read.  Grids
+    with rows per tile of 4, 4 (a partial last tile row) and 2 (tall
+    columns)."""
     nx, ny, nz = shape
     cfg = case(nx=nx, ny=ny, nz=nz, stretch=2.0, les=1, nu=1 / 500.0, cn_sweeps=4, zline=1)
     om = line_schedule(cfg, 32)
+    monkeypatch.setenv("STP_LINE_VARIANT", "0")
     out = []
     for mode in ("0", "1"):
         monkeypatch.setenv("STP_LINE_PERSISTENT", mode)
