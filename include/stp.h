@@ -231,6 +231,13 @@ int stp_stats_read(stp_handle *h, double *moments, double *corr, long long *nsam
    timed, its time per sweep in microseconds (*us may be NULL). */
 int stp_sweep_tile(const stp_handle *h, float *us);
 
+/* The z-line sweep kernel of a handle with line relaxation (Sec. 3.4):
+   1 for the register-chunked FP32 kernel (rows of a multiple of 32 cells,
+   columns of 2 to 192 levels), 0 for the shared-memory lock-step kernel
+   (FP64, other grids, or STP_LINE_VARIANT=0 at stp_init); -1 for point
+   sweeps or a NULL handle.  No GPU work. */
+int stp_line_kernel(const stp_handle *h);
+
 /* Lock-step groups of the batch (built at the first stp_batch_step).
    Channels of at most 2^17 cells in FP32 with refinement that share the SRJ
    cycle length M (at least two of them, rows a multiple of 4 cells, no

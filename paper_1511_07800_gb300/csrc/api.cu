@@ -2177,6 +2177,11 @@ int stp_sweep_tile(const stp_handle* h, float* us) {
   return h->sweep_variant;
 }
 
+int stp_line_kernel(const stp_handle* h) {
+  if (!h || !h->cfg.zline) return -1;
+  return h->line_variant;
+}
+
 int stp_batch_groups(const stp_batch* b, int max_groups, stp_batch_group* out) {
   if (!b) return STP_EINVAL;
   const int n = (int)b->groups.size();

@@ -85,7 +85,8 @@ EXPORTS = ("stp_config_defaults", "stp_init", "stp_destroy", "stp_last_error", "
            "stp_set_learned_guess", "stp_set_harvest", "stp_unet_set_output_scale", "stp_state_size",
            "stp_get_state", "stp_set_state", "stp_batch_create", "stp_batch_destroy", "stp_batch_last_error",
            "stp_batch_step", "stp_batch_groups", "stp_sweep_tile", "stp_stats_reset",
-           "stp_stats_accumulate", "stp_stats_read", "stp_unet_layer", "stp_set_learned_mode")
+           "stp_stats_accumulate", "stp_stats_read", "stp_unet_layer", "stp_set_learned_mode",
+           "stp_line_kernel")
 
 _lib = None
 
@@ -140,6 +141,7 @@ def lib():
     L.stp_batch_step.argtypes = [vp, ctypes.c_int, ctypes.POINTER(BatchStats), ctypes.POINTER(StepStats)]
     L.stp_batch_groups.argtypes = [vp, ctypes.c_int, ctypes.POINTER(BatchGroup)]
     L.stp_sweep_tile.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
+    L.stp_line_kernel.argtypes = [vp]
     L.stp_stats_reset.argtypes = [vp, ctypes.c_int]
     L.stp_stats_accumulate.argtypes = [vp]
     L.stp_stats_read.argtypes = [vp, dp, dp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_int)]
@@ -348,6 +350,11 @@ class Channel:
         us = ctypes.c_float()
         v = lib().stp_sweep_tile(self._h, ctypes.byref(us))
         return v, us.value
+
+    def line_kernel(self):
+        """z-line sweep kernel: 1 register-chunked (FP32), 0 shared-memory
+        lock step, -1 point sweeps."""
+        return lib().stp_line_kernel(self._h)
 
     def close(self):
         if getattr(self, "_h", None) is not None and _lib is not None:
