@@ -425,9 +425,8 @@ int stp_set_harvest(stp_handle *h, float *r_out, float *dp_out);
    every GPU that loads the library until the process exits), limited to
    nz <= 4096 and ceil(nx/32) * ceil(ny/8) * nz <= 65536; larger grids are
    rejected with STP_EINVAL.  The first call on a device looks up the
-   array's device address, so make it before any stream capture on that
-   device; under CUDA's lazy module loading (the default) that first call
-   can also load the library's device code, array included, onto the
+   array's device address; under CUDA's lazy module loading (the default)
+   that first call can also load the library's device code, array included, onto the
    device, a one-time allocation made by the CUDA runtime (to have it
    happen earlier, set CUDA_MODULE_LOADING=EAGER or make one call during
    set-up).  All calls share the array: calls whose work overlaps on the GPU

@@ -11,17 +11,16 @@
 //
 // The array is a host-side stand-in in host code: its device address is
 // obtained once per device with cudaGetSymbolAddress (the first call on a
-// device does this set-up, so make that first call before any stream
-// capture on that device).  With CUDA's lazy module loading (the default
+// device does this set-up).  With CUDA's lazy module loading (the default
 // since CUDA 12.2) that first call can also be what loads this library's
 // device code on the device, and with it the array: that one-time load is
 // a device allocation made by the CUDA runtime, not by this call.  A caller
 // that must not see it at all can load the module eagerly
-// (CUDA_MODULE_LOADING=EAGER) or make one call during its set-up.  Every call shares the array, which keeps the
-// last call's contents; the arrival counter is cleared at the start of each
-// call.  Calls whose work overlaps on the GPU (different streams, or
-// several host threads) race on the array and must be serialised by the
-// caller.
+// (CUDA_MODULE_LOADING=EAGER) or make one call during its set-up.  Every
+// call shares the array, which keeps the last call's contents; the arrival
+// counter is cleared at the start of each call.  Calls whose work overlaps
+// on the GPU (different streams, or several host threads) race on the
+// array and must be serialised by the caller.
 #include <cmath>
 #include <cstring>
 #include <mutex>
