@@ -55,7 +55,7 @@ struct stp_handle {
   // the fields before the current step, restored when the step diverges
   void *bu = nullptr, *bv = nullptr, *bw = nullptr;
   double* bp = nullptr;
-  void* cn_scr = nullptr;  // z-line Crank-Nicolson: (c', d') pairs of the forward elimination
+  void* cn_scr = nullptr;  // z-line Crank-Nicolson: the columns' 1/pivots, or (c', d') pairs of tall columns
 
   Red red{};
   double* h_sc = nullptr;  // pinned copies of red.sc and red.flag
@@ -1001,12 +1001,20 @@ int step_pre(stp_handle* h, const Geom<T>& g, cudaStream_t s) {
   void* Tb[3] = {h->tu, h->tv, h->tw};
   void** cur = R;
   const int n = h->cn_sweeps;
+  // z-line sweeps: the columns' pivots once per step (nu_T is fixed within
+  // it), then every sweep in level chunks; columns too tall for the chunks
+  // eliminate column by column with the scratch array
+  const T* piv = nullptr;
+  if (c.cn_zline && n > 0 && cn_chunk_ok(h->nz)) {
+    CUDA_TRY(h, launch_cn_pivots<T>(g, c.les != 0, nu, nu0, (T)(0.5 * c.dt), (T*)h->cn_scr, s));
+    piv = (const T*)h->cn_scr;
+  }
   for (int k = 0; k < n; k++) {
     void** out = ((n - 1 - k) % 2 == 0) ? U : Tb;
     if (c.cn_zline)
       CUDA_TRY(h, launch_cn_line<T>(g, c.les != 0, nu, nu0, (T)(0.5 * c.dt), (const T*)h->ru, (const T*)h->rv,
                                     (const T*)h->rw, (const T*)cur[0], (const T*)cur[1], (const T*)cur[2],
-                                    (T*)out[0], (T*)out[1], (T*)out[2], h->cn_scr, s));
+                                    (T*)out[0], (T*)out[1], (T*)out[2], h->cn_scr, piv, s));
     else
       CUDA_TRY(h, launch_cn_sweep<T>(g, c.les != 0, nu, nu0, (T)(0.5 * c.dt), (const T*)h->ru, (const T*)h->rv,
                                      (const T*)h->rw, (const T*)cur[0], (const T*)cur[1], (const T*)cur[2],

@@ -481,6 +481,193 @@ __global__ void __launch_bounds__(128) k_cn_line(Geom<T> g, Visc<T, LES> N, T h,
   }
 }
 
+// The z-line Crank-Nicolson sweep in level chunks.  Within a step nu_T is
+// fixed, so the column matrices of every sweep are the same: the forward
+// pivots m_k of each column (one-sided Thomas from the bottom wall,
+// m_0 = di_0, m_k = di_k - lo_k up_{k-1} / m_{k-1}) are formed once per
+// step (k_cn_pivots, 1/m_k stored), and each sweep then runs two linear
+// recurrences per column,
+//   y_k = rhs'_k / m_k + f_k y_{k-1},   f_k = -lo_k / m_k,
+//   x_k = y_k + e_k x_{k+1},            e_k = -up_k / m_k,
+// with rhs'_k = rhs_k + h (x-y neighbour terms of the previous iterate).
+// The rows of a column are cut into NCH chunks; each thread holds one
+// column's rows of one chunk in registers, runs each recurrence inside the
+// chunk from zero and adds the carry entering the chunk times the running
+// product of its coefficients (the carries come from the chunk boundary
+// values in shared memory).  In exact arithmetic this is the Thomas solve
+// of k_cn_line; the rounding differs by a few units in the last place.
+//
+// Row m of component comp (u, v: level m; w: interior face m + 1) of column
+// (i, j): lo x_{m-1} + di x_m + up x_{m+1} = rhs_m + h xy, the coefficients
+// and wall ghosts of the point sweep (visc_u / visc_v / visc_w); xy only
+// when a is given.
+template <typename T>
+struct CnRow {
+  T lo, di, up, xy;
+};
+
+template <typename T, bool LES>
+__device__ __forceinline__ CnRow<T> cn_row(const Geom<T>& g, const Visc<T, LES>& N, T h, int comp, int i, int j,
+                                           int m, const T* __restrict__ a) {
+  const int nx = g.nx, ny = g.ny, nz = g.nz;
+  const int im = i == 0 ? nx - 1 : i - 1, ip = i == nx - 1 ? 0 : i + 1;
+  const int jm = j == 0 ? ny - 1 : j - 1, jp = j == ny - 1 ? 0 : j + 1;
+  const int plane = nx * ny;
+  const T idx2 = g.idx2, idy2 = g.idy2;
+  CnRow<T> r;
+  T nxp, nxm, nyp, nym, sd;
+  int lev;
+  if (comp < 2) {
+    const int k = m;
+    lev = k * plane;
+    const int aA = comp == 0 ? im : i, bA = comp == 0 ? j : jm;
+    const T A0 = N.c(aA, bA, k), B0 = N.c(i, j, k);
+    const T Am = N.c(aA, bA, k - 1), Bm = N.c(i, j, k - 1), Ap = N.c(aA, bA, k + 1), Bp = N.c(i, j, k + 1);
+    if (comp == 0) {
+      nxp = B0;
+      nxm = A0;
+      nyp = T(0.25) * (A0 + B0 + N.c(im, jp, k) + N.c(i, jp, k));
+      nym = T(0.25) * (N.c(im, jm, k) + N.c(i, jm, k) + A0 + B0);
+    } else {
+      nxp = T(0.25) * (A0 + N.c(ip, jm, k) + B0 + N.c(ip, j, k));
+      nxm = T(0.25) * (N.c(im, jm, k) + A0 + N.c(im, j, k) + B0);
+      nyp = B0;
+      nym = A0;
+    }
+    const T nzp = T(0.25) * (A0 + B0 + Ap + Bp), nzm = T(0.25) * (Am + Bm + A0 + B0);
+    const T idz = __ldg(g.idz + k), izp = __ldg(g.idzf + k + 1), izm = __ldg(g.idzf + k);
+    const T gu = (k == nz - 1) ? T(2) : T(1), gd = (k == 0) ? T(2) : T(1);
+    sd = (nxp + nxm) * idx2 + (nyp + nym) * idy2 + (gu * nzp * izp + gd * nzm * izm) * idz;
+    r.lo = k > 0 ? -h * nzm * izm * idz : T(0);
+    r.up = k < nz - 1 ? -h * nzp * izp * idz : T(0);
+  } else {
+    const int c = m + 1;
+    lev = c * plane;
+    const T p0 = N.c(i, j, c), p1 = N.c(ip, j, c), p2 = N.c(im, j, c), p3 = N.c(i, jp, c), p4 = N.c(i, jm, c);
+    const T q0 = N.c(i, j, c - 1), q1 = N.c(ip, j, c - 1), q2 = N.c(im, j, c - 1), q3 = N.c(i, jp, c - 1),
+            q4 = N.c(i, jm, c - 1);
+    nxp = T(0.25) * (q0 + q1 + p0 + p1);
+    nxm = T(0.25) * (q2 + q0 + p2 + p0);
+    nyp = T(0.25) * (q0 + q3 + p0 + p3);
+    nym = T(0.25) * (q4 + q0 + p4 + p0);
+    const T nzp = p0, nzm = q0;
+    const T ih = __ldg(g.ihz + c), izp = __ldg(g.idz + c), izm = __ldg(g.idz + c - 1);
+    sd = (nxp + nxm) * idx2 + (nyp + nym) * idy2 + (nzp * izp + nzm * izm) * ih;
+    r.lo = c > 1 ? -h * nzm * izm * ih : T(0);
+    r.up = c < nz - 1 ? -h * nzp * izp * ih : T(0);
+  }
+  r.di = T(1) + h * sd;
+  r.xy = a ? (nxp * __ldg(a + lev + j * nx + ip) + nxm * __ldg(a + lev + j * nx + im)) * idx2 +
+                 (nyp * __ldg(a + lev + jp * nx + i) + nym * __ldg(a + lev + jm * nx + i)) * idy2
+           : T(0);
+  return r;
+}
+
+// 1/m_k of every column and component (piv: three arrays of (nz + 1)
+// levels x ny x nx, row m at level m for u and v, at face m + 1 for w);
+// one thread a column and component.
+template <typename T, bool LES>
+__global__ void __launch_bounds__(128) k_cn_pivots(Geom<T> g, Visc<T, LES> N, T h, T* __restrict__ piv) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, comp = blockIdx.z;
+  if (i >= g.nx) return;
+  const int plane = g.nx * g.ny, n = comp < 2 ? g.nz : g.nz - 1, off = comp < 2 ? 0 : 1;
+  T* __restrict__ P = piv + (size_t)comp * (g.nz + 1) * plane + j * g.nx + i;
+  T cp = T(0);
+  for (int m = 0; m < n; m++) {
+    const CnRow<T> r = cn_row<T, LES>(g, N, h, comp, i, j, m, nullptr);
+    const T inv = T(1) / (r.di - r.lo * cp);
+    cp = r.up * inv;
+    P[(m + off) * plane] = inv;
+  }
+}
+
+// The sweep: a block is 32 consecutive x columns of one row and one
+// component x NCH chunks (a warp is one chunk, so row loads are coalesced).
+template <typename T, bool LES, int NCH, int LMAX>
+__global__ void __launch_bounds__(32 * NCH, sizeof(T) == 4 ? 2 : 1) k_cn_line_chunk(Geom<T> g, Visc<T, LES> N, T h,
+                                                                const T* __restrict__ ru, const T* __restrict__ rv,
+                                                                const T* __restrict__ rw, const T* __restrict__ au,
+                                                                const T* __restrict__ av, const T* __restrict__ aw,
+                                                                T* __restrict__ ou, T* __restrict__ ov,
+                                                                T* __restrict__ ow, const T* __restrict__ piv) {
+  __shared__ T ZB[NCH][32], FB[NCH][32];
+  const int nx = g.nx, nz = g.nz, comp = blockIdx.z, j = blockIdx.y;
+  const int col = threadIdx.x & 31, c = threadIdx.x >> 5;
+  const int i0 = blockIdx.x * 32 + col;
+  const bool act = i0 < nx;
+  const int i = act ? i0 : nx - 1;  // in-bounds stand-in for columns past the row end
+  const int plane = nx * g.ny, n = comp < 2 ? nz : nz - 1, off = comp < 2 ? 0 : 1;
+  const int k0 = c * n / NCH, k1 = (c + 1) * n / NCH, L = k1 - k0;
+  const T* __restrict__ a = comp == 0 ? au : comp == 1 ? av : aw;
+  const T* __restrict__ rr = comp == 0 ? ru : comp == 1 ? rv : rw;
+  T* __restrict__ o = comp == 0 ? ou : comp == 1 ? ov : ow;
+  const T* __restrict__ P = piv + (size_t)comp * (nz + 1) * plane;
+  const int c0 = j * nx + i;
+  T G[LMAX], F[LMAX], E[LMAX];
+#pragma unroll
+  for (int q = 0; q < LMAX; q++)
+    if (q < L) {
+      const int m = k0 + q, lev = (m + off) * plane;
+      const CnRow<T> r = cn_row<T, LES>(g, N, h, comp, i, j, m, a);
+      const T inv = __ldg(P + lev + c0);
+      G[q] = (__ldg(rr + lev + c0) + h * r.xy) * inv;
+      F[q] = -r.lo * inv;
+      E[q] = -r.up * inv;
+    }
+  // elimination inside the chunk from zero, then the carry from below
+  T z = T(0), Fp = T(1);
+#pragma unroll
+  for (int q = 0; q < LMAX; q++)
+    if (q < L) {
+      z = G[q] + F[q] * z;
+      Fp *= F[q];
+      G[q] = z;
+    }
+  ZB[c][col] = z;
+  FB[c][col] = Fp;
+  __syncthreads();
+  T carry = T(0);
+  for (int cc = 0; cc < c; cc++) carry = ZB[cc][col] + FB[cc][col] * carry;
+  Fp = T(1);
+#pragma unroll
+  for (int q = 0; q < LMAX; q++)
+    if (q < L) {
+      Fp *= F[q];
+      G[q] += Fp * carry;
+    }
+  __syncthreads();  // every carry read before the buffers take the substitution's values
+  // substitution inside the chunk from zero, then the carry from above
+  T w = T(0), Ep = T(1);
+#pragma unroll
+  for (int q = LMAX - 1; q >= 0; q--)
+    if (q < L) {
+      w = G[q] + E[q] * w;
+      Ep *= E[q];
+      G[q] = w;
+    }
+  ZB[c][col] = w;
+  FB[c][col] = Ep;
+  __syncthreads();
+  carry = T(0);
+  for (int cc = NCH - 1; cc > c; cc--) carry = ZB[cc][col] + FB[cc][col] * carry;
+  Ep = T(1);
+#pragma unroll
+  for (int q = LMAX - 1; q >= 0; q--)
+    if (q < L) {
+      Ep *= E[q];
+      G[q] += Ep * carry;
+    }
+  if (act) {
+#pragma unroll
+    for (int q = 0; q < LMAX; q++)
+      if (q < L) o[(k0 + q + off) * plane + c0] = G[q];
+    if (comp == 2 && c == 0) {
+      o[c0] = T(0);
+      o[nz * plane + c0] = T(0);
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Eq. presdiv right-hand side b = D u* / dt, with ||b||_2 reduced in FP64.
 // Also clears the convergence flags of the coming solve.  The differences
@@ -692,10 +879,42 @@ cudaError_t launch_cn_sweep(const Geom<T>& g, bool les, const T* nu, T nu0, T hd
   return cudaGetLastError();
 }
 
+// chunks of the z-line Crank-Nicolson sweep and rows a chunk holds at most:
+// columns of up to 16 x 12 = 192 rows
+constexpr int kCnChunks = 16, kCnChunkRows = 12;
+
+bool cn_chunk_ok(int nz) { return nz >= 2 && nz <= kCnChunks * kCnChunkRows; }
+
+template <typename T>
+cudaError_t launch_cn_pivots(const Geom<T>& g, bool les, const T* nu, T nu0, T hdt, T* piv, cudaStream_t s) {
+  const dim3 block(128), grid((g.nx + 127) / 128, g.ny, 3);
+  if (les) {
+    Visc<T, true> N{nu, nu0, g.nx, g.ny, g.nz};
+    k_cn_pivots<T, true><<<grid, block, 0, s>>>(g, N, hdt, piv);
+  } else {
+    Visc<T, false> N{nu, nu0, g.nx, g.ny, g.nz};
+    k_cn_pivots<T, false><<<grid, block, 0, s>>>(g, N, hdt, piv);
+  }
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_cn_line(const Geom<T>& g, bool les, const T* nu, T nu0, T hdt, const T* ru, const T* rv,
                            const T* rw, const T* au, const T* av, const T* aw, T* ou, T* ov, T* ow, void* scratch,
-                           cudaStream_t s) {
+                           const T* piv, cudaStream_t s) {
+  if (piv && cn_chunk_ok(g.nz)) {
+    const dim3 block(32 * kCnChunks), grid((g.nx + 31) / 32, g.ny, 3);
+    if (les) {
+      Visc<T, true> N{nu, nu0, g.nx, g.ny, g.nz};
+      k_cn_line_chunk<T, true, kCnChunks, kCnChunkRows><<<grid, block, 0, s>>>(g, N, hdt, ru, rv, rw, au, av, aw,
+                                                                                ou, ov, ow, piv);
+    } else {
+      Visc<T, false> N{nu, nu0, g.nx, g.ny, g.nz};
+      k_cn_line_chunk<T, false, kCnChunks, kCnChunkRows><<<grid, block, 0, s>>>(g, N, hdt, ru, rv, rw, au, av, aw,
+                                                                                 ou, ov, ow, piv);
+    }
+    return cudaGetLastError();
+  }
   const dim3 block(128), grid((g.nx + 127) / 128, g.ny, 3);
   using V2 = typename Pair<T>::V;
   if (les) {
@@ -780,7 +999,8 @@ cudaError_t launch_convert(Td* dst, const Ts* src, size_t n, cudaStream_t s) {
   template cudaError_t launch_cn_sweep<T>(const Geom<T>&, bool, const T*, T, T, const T*, const T*, const T*,      \
                                           const T*, const T*, const T*, T*, T*, T*, cudaStream_t);                  \
   template cudaError_t launch_cn_line<T>(const Geom<T>&, bool, const T*, T, T, const T*, const T*, const T*,       \
-                                         const T*, const T*, const T*, T*, T*, T*, void*, cudaStream_t);            \
+                                         const T*, const T*, const T*, T*, T*, T*, void*, const T*, cudaStream_t);  \
+  template cudaError_t launch_cn_pivots<T>(const Geom<T>&, bool, const T*, T, T, T*, cudaStream_t);               \
   template cudaError_t launch_explicit_only<T>(const Geom<T>&, bool, const T*, const T*, const T*, const T*, T, T, \
                                                T*, T*, T*, cudaStream_t);                                           \
   template cudaError_t launch_diffusion_only<T>(const Geom<T>&, bool, const T*, const T*, const T*, const T*, T,   \

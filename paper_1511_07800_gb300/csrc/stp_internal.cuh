@@ -156,7 +156,12 @@ cudaError_t launch_cn_sweep(const Geom<T>& g, bool les, const T* nu, T nu0, T hd
 template <typename T>
 cudaError_t launch_cn_line(const Geom<T>& g, bool les, const T* nu, T nu0, T hdt, const T* ru, const T* rv,
                            const T* rw, const T* au, const T* av, const T* aw, T* ou, T* ov, T* ow, void* scratch,
-                           cudaStream_t s);
+                           const T* piv, cudaStream_t s);
+// 1/pivot of every z column's Crank-Nicolson matrix (once per step, before
+// the sweeps that pass piv to launch_cn_line; columns of 2 to 192 levels)
+template <typename T>
+cudaError_t launch_cn_pivots(const Geom<T>& g, bool les, const T* nu, T nu0, T hdt, T* piv, cudaStream_t s);
+bool cn_chunk_ok(int nz);
 
 // b = D u / dt (FP64 arithmetic in both precisions), ||b||^2 reduced into
 // sc[SC_BNORM] (as the norm), flags reset; sc[SC_BMEAN] = 0 (b telescopes).
