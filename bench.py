@@ -225,10 +225,12 @@ def oracle_us_per_sweep(cfg, zline, seed=5):
 def learned_comparison(cfg, steps, oracle_sample=True):
     """Poisson time to 1e-8, learned against plain, on the workload grid:
     train the U-Net on (residual, correction) pairs harvested from channels
-    of the same workload (seeds 0-3, 10 steps each), then step one channel
-    (seed 7) plainly, with the network as the initial guess of every solve
-    and with it as a preconditioner at every refinement pass (FP32) or SRJ
-    cycle (FP64), and compare the solves."""
+    of the same workload (seeds 0-9, 60 steps each), then step two unseen
+    channels (seeds 7 and 50, each with its own random mode amplitude and
+    noise level) plainly, with the network as the initial guess of every
+    solve and with it as a preconditioner at every refinement pass (FP32)
+    or SRJ cycle (FP64), and compare the solves.  A mode's speed-up is the
+    geometric mean over the two channels."""
     import numpy as np
     import torch
     from paper_1511_07800_gb300 import learn, stp
@@ -237,7 +239,7 @@ def learned_comparison(cfg, steps, oracle_sample=True):
     R, DP = learn.harvest(cfg, seeds=range(10), steps_per_seed=60)
     K = learn.output_scale(R, DP, 4, shape)
     net = stp.UNet(4, *shape)
-    theta = learn.he_init(3)
+    theta = learn.he_init(0)
     net.set_params(theta)
     net.set_output_scale(K)
     losses = learn.train(net, R, DP, 1500, 4, 1e-3) + learn.train(net, R, DP, 500, 4, 3e-4)
@@ -250,8 +252,13 @@ def learned_comparison(cfg, steps, oracle_sample=True):
     one.set_output_scale(K)
     net.close()
     net = one
-    res = learn.compare_modes(cfg, net, seed=7, nsteps=max(3, min(steps, 8)), precision="fp32")
-    res64 = learn.compare_modes(cfg, net, seed=7, nsteps=8, precision="fp64")
+    eval_seeds = (7, 50)
+    res = {sd: learn.compare_modes(cfg, net, seed=sd, nsteps=max(3, min(steps, 8)), precision="fp32")
+           for sd in eval_seeds}
+    res64 = {sd: learn.compare_modes(cfg, net, seed=sd, nsteps=8, precision="fp64") for sd in eval_seeds}
+
+    def gmean(runs, mode):
+        return float(np.exp(np.mean([np.log(r[mode]["speedup"]) for r in runs.values()])))
     # one forward of the trained network on the workload grid (CUDA events)
     fwd_ms = None
     try:
@@ -286,18 +293,19 @@ def learned_comparison(cfg, steps, oracle_sample=True):
                                                             shape[0])}
         except Exception as ex:  # report, never fake
             out_cpu = {"value": None, "error": str(ex)[:200]}
-    return {"speedup_by_mode": {"fp64_guess": res64["guess"]["speedup"], "fp64_preconditioner": res64["precond"]["speedup"],
-                                "fp32_guess": res["guess"]["speedup"], "fp32_preconditioner": res["precond"]["speedup"]},
-            "speedup": max(res64["guess"]["speedup"], res64["precond"]["speedup"], res["guess"]["speedup"],
-                           res["precond"]["speedup"]),
-            "forward_ms": fwd_ms, "fp32": res, "fp64": res64,
+    by_mode = {"fp64_guess": gmean(res64, "guess"), "fp64_preconditioner": gmean(res64, "precond"),
+               "fp32_guess": gmean(res, "guess"), "fp32_preconditioner": gmean(res, "precond")}
+    return {"speedup_by_mode": by_mode, "speedup": max(by_mode.values()),
+            "forward_ms": fwd_ms, "fp32": {"seed_%d" % sd: r for sd, r in res.items()},
+            "fp64": {"seed_%d" % sd: r for sd, r in res64.items()},
             "train": {"pairs": npairs, "adam_steps": len(losses), "batch": 4,
                       "final_loss": float(np.mean(losses[-10:])), "output_scale": K, "seconds": t_train},
             "cpu_baseline": out_cpu,
-            "note": "time per pressure solve to 1e-8 (GPU events) on an unseen channel of the instability workload "
-                    "(128x64x128), previous-step pressure as the plain guess; guess: the network once per solve; "
-                    "precond: at every refinement pass (FP32) or SRJ cycle (FP64); speedup: the best mode. The "
-                    "20k-pair experiment is learn.config4"}
+            "note": "time per pressure solve to 1e-8 (GPU events) on two unseen channels of the instability "
+                    "workload (128x64x128), previous-step pressure as the plain guess; guess: the network once per "
+                    "solve; precond: at every refinement pass (FP32) or SRJ cycle (FP64); a mode's speed-up is the "
+                    "geometric mean over the channels, speedup the best mode. The 20k-pair experiment is "
+                    "learn.config4"}
 
 
 def batched_channels(steps, warmup, peak, oracle_sample=True):
