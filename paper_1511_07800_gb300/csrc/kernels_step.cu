@@ -670,13 +670,15 @@ __global__ void __launch_bounds__(32 * NCH, sizeof(T) == 4 ? 2 : 1) k_cn_line_ch
 
 // ---------------------------------------------------------------------------
 // Eq. presdiv right-hand side b = D u* / dt, with ||b||_2 reduced in FP64.
-// Also clears the convergence flags of the coming solve.  The differences
-// are taken in FP64 (exact for FP32 inputs) and scaled in FP64: the three
-// terms of b nearly cancel (u* is divergence-free up to O(dt)), so FP32
-// arithmetic here would put rounding of the size of the terms into b; and
-// the sum of b over the box telescopes to zero to FP64 rounding, so b has
-// no mean the Poisson iteration could not remove (sc[SC_BMEAN] = 0).  FP32
-// fields sum the squares in FP32 per warp and FP64 across warps.
+// Also clears the convergence flags of the coming solve.  The three terms
+// of b nearly cancel (u* is divergence-free up to O(dt)), so plain FP32
+// arithmetic here would put rounding of the size of the terms into b; the
+// differences and their products with the metric are kept to FP64 accuracy
+// (FP64 fields: FP64 arithmetic; FP32 fields: exact two-float differences
+// and products, see below), so the sum of b over the box telescopes to
+// zero to FP64 rounding and b has no mean the Poisson iteration could not
+// remove (sc[SC_BMEAN] = 0).  FP32 fields sum the squares in FP32 per warp
+// and FP64 across warps.
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(kBX* kBY) k_divergence(Geom<T> g, const T* __restrict__ u, const T* __restrict__ v,
@@ -688,9 +690,42 @@ __global__ void __launch_bounds__(kBX* kBY) k_divergence(Geom<T> g, const T* __r
   if (i < g.nx && j < g.ny) {
     const int ip = i == g.nx - 1 ? 0 : i + 1, jp = j == g.ny - 1 ? 0 : j + 1;
     const int q = at(g.nx, g.ny, i, j, k);
-    const double d = ((double)__ldg(u + at(g.nx, g.ny, ip, j, k)) - (double)__ldg(u + q)) * (double)g.idx +
-                     ((double)__ldg(v + at(g.nx, g.ny, i, jp, k)) - (double)__ldg(v + q)) * (double)g.idy +
-                     ((double)__ldg(w + q + g.nx * g.ny) - (double)__ldg(w + q)) * (double)__ldg(g.idz + k);
+    double d;
+    if constexpr (sizeof(T) == sizeof(float)) {
+      // FP32 fields: each face difference and its product with the metric
+      // carried exactly as an unevaluated sum of two floats (Knuth's
+      // two-sum, the fma product error), the three terms added with their
+      // errors; only the final value goes through the FP64 pipe (GB300 runs
+      // FP64 at 1/64 of FP32).  Accurate to about 2^-46 of the terms, as the
+      // FP64 arithmetic it replaces.
+      auto term = [](float a, float bb, float c, float& lo) {
+        const float s = __fsub_rn(a, bb);
+        const float bp = __fsub_rn(s, a), ap = __fsub_rn(s, bp);
+        const float e = __fadd_rn(__fsub_rn(a, ap), __fsub_rn(-bb, bp));  // a - bb = s + e exactly
+        const float hi = __fmul_rn(s, c);
+        lo = __fmaf_rn(e, c, __fmaf_rn(s, c, -hi));  // s c = hi + (fma error) exactly; plus e c
+        return hi;
+      };
+      float l1, l2, l3;
+      const float t1 = term(__ldg(u + at(g.nx, g.ny, ip, j, k)), __ldg(u + q), g.idx, l1);
+      const float t2 = term(__ldg(v + at(g.nx, g.ny, i, jp, k)), __ldg(v + q), g.idy, l2);
+      const float t3 = term(__ldg(w + q + g.nx * g.ny), __ldg(w + q), __ldg(g.idz + k), l3);
+      auto two_sum = [](float a, float bb, float& err) {
+        const float s = __fadd_rn(a, bb);
+        const float bp = __fsub_rn(s, a), ap = __fsub_rn(s, bp);
+        err = __fadd_rn(__fsub_rn(a, ap), __fsub_rn(bb, bp));
+        return s;
+      };
+      float e1, e2;
+      const float h1 = two_sum(t1, t2, e1);
+      const float h2 = two_sum(h1, t3, e2);
+      const float lo = __fadd_rn(__fadd_rn(__fadd_rn(l1, l2), __fadd_rn(l3, e1)), e2);
+      d = (double)h2 + (double)lo;
+    } else {
+      d = (__ldg(u + at(g.nx, g.ny, ip, j, k)) - __ldg(u + q)) * g.idx +
+          (__ldg(v + at(g.nx, g.ny, i, jp, k)) - __ldg(v + q)) * g.idy +
+          (__ldg(w + q + g.nx * g.ny) - __ldg(w + q)) * __ldg(g.idz + k);
+    }
     bt = d * idt;
     b[q] = bt;
   }

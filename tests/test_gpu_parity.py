@@ -65,6 +65,31 @@ def test_terms_parity(stp_lib, orc, stretch, les):
 
 
 @pytest.mark.parametrize("stretch", [0.0, 2.0])
+def test_divergence_fp32_fields(stp_lib, orc, stretch):
+    """Eq. presdiv with FP32 fields: the kernel keeps each face difference
+    and its product with the (FP32) metric as exact two-float sums, so b
+    equals the FP64 evaluation of the same FP32 numbers to FP64 rounding
+    (1e-13 against a numpy FP64 evaluation with the metric rounded to FP32
+    as the library rounds it); against the oracle's FP64 divergence of the
+    rounded fields, which uses the FP64 metric, the metric's FP32 rounding
+    remains (below 1e-6)."""
+    cfg = case(stretch=stretch, nx=40, ny=19, nz=14)
+    u, v, w = turbulent_like(cfg, 4)
+    u32, v32, w32 = (np.asarray(a, np.float32).astype(np.float64) for a in (u, v, w))
+    zf = inputs.zfaces(cfg)
+    idx = float(np.float32(1.0 / (cfg["Lx"] / cfg["nx"])))
+    idy = float(np.float32(1.0 / (cfg["Ly"] / cfg["ny"])))
+    idz = (1.0 / np.diff(zf)).astype(np.float32).astype(np.float64)[:, None, None]
+    want = ((np.roll(u32, -1, axis=2) - u32) * idx + (np.roll(v32, -1, axis=1) - v32) * idy +
+            (w32[1:] - w32[:-1]) * idz)
+    with stp_lib.Channel(cfg, precision="fp32") as ch:
+        ch.set_fields(u, v, w)
+        got = ch.eval("divergence")
+    assert rel_err(got, want) < 1e-13
+    assert rel_err(got, orc.Oracle(cfg).divergence(u32, v32, w32)) < 1e-6
+
+
+@pytest.mark.parametrize("stretch", [0.0, 2.0])
 def test_srj_fixed_sweeps_parity(stp_lib, orc, stretch):
     """Sec. 3.4: the same schedule applied for the same number of sweeps
     gives the same pressure."""
