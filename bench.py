@@ -454,7 +454,7 @@ def headline_config(args):
     if args.grid:
         nx, ny, nz = (int(x) for x in args.grid.lower().split("x"))
         cfg.update(nx=nx, ny=ny, nz=nz)
-    cfg["cn_sweeps"] = _auto_cn(cfg)
+    cfg["cn_sweeps"] = _auto_cn(cfg, args.precision)
     return cfg
 
 
@@ -518,12 +518,12 @@ def run_reference(args):
     return 0
 
 
-def _auto_cn(cfg):
+def _auto_cn(cfg, precision="fp32"):
     """Crank-Nicolson Jacobi sweeps for the workload, by the library's rule
-    (contraction hS/(1+hS) per sweep, down to 1e-12; S the largest diagonal
-    weight for point sweeps, the x-y coupling weights alone for z-line
-    sweeps); both arms get the count explicitly so they run the same
-    sweeps."""
+    (contraction hS/(1+hS) per sweep, down to the storage precision: 2^-24
+    for FP32 fields, 1e-12 for FP64; S the largest diagonal weight for point
+    sweeps, the x-y coupling weights alone for z-line sweeps); both arms
+    get the count explicitly so they run the same sweeps."""
     from paper_1511_07800_gb300 import inputs
     zf = inputs.zfaces(cfg)
     dz = [zf[k + 1] - zf[k] for k in range(cfg["nz"])]
@@ -540,7 +540,8 @@ def _auto_cn(cfg):
     if rho <= 0:
         return 1
     lo = 1 if cfg.get("cn_zline") else 2
-    return max(lo, min(int(math.ceil(math.log(1e-12) / math.log(rho))), 200))
+    target = 2.0 ** -24 if precision == "fp32" else 1e-12
+    return max(lo, min(int(math.ceil(math.log(target) / math.log(rho))), 200))
 
 
 def timed_steps(ch, steps, stream, flush):
@@ -756,14 +757,15 @@ def run_ours(args):
             line["les_channel_point_srj"] = {"error": str(ex)[:300]}
         try:
             c2 = inputs.preset("os_instability")
-            c2["cn_sweeps"] = _auto_cn(c2)
             f2 = inputs.initial_fields("os_instability", c2, seed=0)
             line["os_instability"] = {
                 "workload": "os_instability 128x64x128 Re 7500 dt 2e-3, Poiseuille + OS mode 1e-4 + noise 1e-6, "
                             "point SRJ to 1e-8",
-                "fp32_refine": side_steps(stp, c2, "fp32", f2, max(3, min(args.steps, 10)), 3, stream, flush, peak,
+                "fp32_refine": side_steps(stp, dict(c2, cn_sweeps=_auto_cn(c2, "fp32")), "fp32", f2,
+                                          max(3, min(args.steps, 10)), 3, stream, flush, peak,
                                           "point_sweep_fp32_os_instability"),
-                "fp64": side_steps(stp, c2, "fp64", f2, max(3, min(args.steps, 5)), 3, stream, flush, peak,
+                "fp64": side_steps(stp, dict(c2, cn_sweeps=_auto_cn(c2, "fp64")), "fp64", f2,
+                                   max(3, min(args.steps, 5)), 3, stream, flush, peak,
                                    "point_sweep_fp64_os_instability")}
         except Exception as ex:  # report, never fake
             line["os_instability"] = {"error": str(ex)[:300]}
@@ -773,8 +775,7 @@ def run_ours(args):
             line["srj_sweeps_above_l2"] = {"error": str(ex)[:300]}
     if side and not args.no_learned:
         try:
-            c2 = inputs.preset("os_instability")
-            c2["cn_sweeps"] = _auto_cn(c2)
+            c2 = inputs.preset("os_instability")  # cn_sweeps 0: the library's count for each precision
             line["poisson_learned_vs_plain"] = learned_comparison(c2, args.steps, not args.no_cpu_baseline)
         except Exception as ex:  # report, never fake
             line["poisson_learned_vs_plain"] = {"error": str(ex)[:200]}

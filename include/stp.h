@@ -93,7 +93,9 @@ typedef struct stp_config {
     int precision;           /* STP_FP64 or STP_FP32_REFINE                     */
     double ptol;             /* pressure: stop when ||b - Lp||_2 <= ptol ||b||_2 */
     int pmaxit;              /* cap on SRJ sweeps per solve                      */
-    int cn_sweeps;           /* Jacobi sweeps of the CN system; 0: automatic     */
+    int cn_sweeps;           /* Jacobi sweeps of the CN system; 0: automatic
+                                (the count whose contraction bound reaches the
+                                storage precision: 1e-12 in FP64, 2^-24 in FP32) */
     int srj_m;               /* SRJ cycle length; 0: automatic (power of two)    */
     const double *srj_omega; /* optional schedule omega_1..omega_M (M = srj_m);
                                 NULL: Chebyshev schedule built by the library     */

@@ -328,10 +328,9 @@ int auto_cycle(double mn, double mx) {
   return M;
 }
 
-// Jacobi sweeps for the CN system: the iteration contracts by at most
-// hS/(1+hS), S the largest diagonal weight (nu_T bounded by 4 nu with LES);
-// enough sweeps to reach 1e-12.
-// Crank-Nicolson sweeps to a 1e-12 contraction.  Point Jacobi contracts by
+// Crank-Nicolson Jacobi sweeps to the storage precision: the smallest count
+// whose contraction reaches 1e-12 with FP64 fields, 2^-24 with FP32 fields
+// (more sweeps cannot change what FP32 stores).  Point Jacobi contracts by
 // hS/(1+hS) a sweep with S the largest diagonal weight; z-line Jacobi by the
 // same bound with S the x-y coupling weights alone (the column matrix is an
 // M-matrix whose row sums are at least 1 + h S_xy).  nu_T is bounded by 4 nu
@@ -348,7 +347,8 @@ int auto_cn_sweeps(const stp_config& c, const ZGrid& z) {
   const double hs = 0.5 * c.dt * nu * smax;
   const double rho = hs / (1.0 + hs);
   if (rho <= 0) return 1;
-  int k = (int)std::ceil(std::log(1e-12) / std::log(rho));
+  const double target = c.precision == STP_FP32_REFINE ? std::ldexp(1.0, -24) : 1e-12;
+  int k = (int)std::ceil(std::log(target) / std::log(rho));
   return std::max(c.cn_zline ? 1 : 2, std::min(k, 200));
 }
 

@@ -253,15 +253,18 @@ __global__ void __launch_bounds__(kBX* kBY) k_momentum(Geom<T> g, const T* __res
     b1 = T(-16.0 / 12.0);
     b2 = T(5.0 / 12.0);
   }
-  T* __restrict__ Nu0 = H.u[s0];
-  T* __restrict__ Nv0 = H.v[s0];
-  T* __restrict__ Nw0 = H.w[s0];
-  const T* __restrict__ Nu1 = H.u[s1];
-  const T* __restrict__ Nv1 = H.v[s1];
-  const T* __restrict__ Nw1 = H.w[s1];
-  const T* __restrict__ Nu2 = H.u[s2];
-  const T* __restrict__ Nv2 = H.v[s2];
-  const T* __restrict__ Nw2 = H.w[s2];
+  // slot pointers by selection (a runtime index into the parameter arrays
+  // would copy them to local memory)
+  auto slot = [](T* const* a, int sl) { return sl == 0 ? a[0] : sl == 1 ? a[1] : a[2]; };
+  T* __restrict__ Nu0 = slot(H.u, s0);
+  T* __restrict__ Nv0 = slot(H.v, s0);
+  T* __restrict__ Nw0 = slot(H.w, s0);
+  const T* __restrict__ Nu1 = slot(H.u, s1);
+  const T* __restrict__ Nv1 = slot(H.v, s1);
+  const T* __restrict__ Nw1 = slot(H.w, s1);
+  const T* __restrict__ Nu2 = slot(H.u, s2);
+  const T* __restrict__ Nv2 = slot(H.v, s2);
+  const T* __restrict__ Nw2 = slot(H.w, s2);
   Pt<T> P(g, i, j, k);
   const int q = at(g.nx, g.ny, i, j, k);
   const T hdt = T(0.5) * dt;

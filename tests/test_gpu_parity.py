@@ -207,6 +207,31 @@ def test_step_cn_zline_fp32_and_converged(stp_lib, orc, shape):
         assert rel_err(out[1][k], out[0][k]) < 1e-10, k
 
 
+def test_cn_auto_count_fp32_reaches_storage_precision(stp_lib):
+    """With FP32 fields the automatic Crank-Nicolson count stops at a 2^-24
+    contraction bound instead of 1e-12: 3 z-line sweeps on the LES channel's
+    x-y spacing, where FP64 fields take 5.  Three steps of a channel with
+    that spacing give the same fields with the automatic count as with 12
+    sweeps, to FP32 rounding (2e-6 of the velocity scale, 1e-3 of the
+    pressure)."""
+    import math
+    import bench
+    cfg = inputs.preset("les_channel", nx=64, ny=32, nz=48, Lx=math.pi, Ly=math.pi / 2, zline=1, cn_zline=1)
+    assert bench._auto_cn(cfg, "fp32") == 3 and bench._auto_cn(cfg, "fp64") == 5
+    f0 = inputs.initial_fields("les_channel", cfg, seed=3)
+    out = {}
+    for n in (0, 12):
+        with stp_lib.Channel(dict(cfg, cn_sweeps=n), precision="fp32") as ch:
+            ch.set_fields(*f0)
+            st = ch.step(3)
+            assert st["converged"]
+            out[n] = ch.get_fields()
+    scale = max(np.abs(out[12][k]).max() for k in ("u", "v", "w"))
+    for k in ("u", "v", "w"):
+        assert np.abs(out[0][k] - out[12][k]).max() / scale < 2e-6, k
+    assert rel_err(out[0]["p"] - out[0]["p"].mean(), out[12]["p"] - out[12]["p"].mean()) < 1e-3
+
+
 def test_step_parity_converged_solves(stp_lib, orc):
     """Steps with tolerance-driven solves take the same sweep counts and
     agree to 1e-10 (instability workload shape on a 2-D slice)."""
