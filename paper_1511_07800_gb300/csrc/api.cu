@@ -403,6 +403,10 @@ Geom<T> geom_from(const stp_handle* h, T* pack) {
   g.tli = pack + 13 * L;
   g.tlf = pack + 14 * L;
   g.tlb = pack + 15 * L;
+  // the packed level coefficients follow the kMetricArrays arrays (offset
+  // 64 L bytes: 16-byte aligned)
+  if constexpr (sizeof(T) == sizeof(float)) g.lz4 = reinterpret_cast<const float4*>(pack + kMetricArrays * L);
+  else g.lz4 = nullptr;
   return g;
 }
 
@@ -1227,7 +1231,7 @@ int stp_init(const stp_config* cfg, stp_handle** out) {
   };
   const int L = h->nz + 1;
   A((void**)&h->m64, sizeof(double) * kMetricArrays * L);
-  A((void**)&h->m32, sizeof(float) * kMetricArrays * L);
+  A((void**)&h->m32, sizeof(float) * (kMetricArrays + 4) * L);
   A(&h->u, es * nc);
   A(&h->v, es * nc);
   A(&h->w, es * nw);
@@ -1307,6 +1311,18 @@ int stp_init(const stp_config* cfg, stp_handle** out) {
   // metrics
   const std::vector<double> m = metric_pack(*cfg);
   std::vector<float> mf(m.begin(), m.end());
+  {
+    // {cup, cdn, tli, tlf} per level, after the arrays (see geom_from)
+    const int L = h->nz + 1;
+    mf.resize((size_t)(kMetricArrays + 4) * L, 0.f);
+    float* pk = mf.data() + (size_t)kMetricArrays * L;
+    for (int k = 0; k < h->nz; k++) {
+      pk[4 * k + 0] = mf[5 * L + k];
+      pk[4 * k + 1] = mf[6 * L + k];
+      pk[4 * k + 2] = mf[13 * L + k];
+      pk[4 * k + 3] = mf[14 * L + k];
+    }
+  }
   h->g64 = geom_from<double>(h, h->m64);
   h->g32 = geom_from<float>(h, h->m32);
   e = cudaMemcpyAsync(h->m64, m.data(), sizeof(double) * m.size(), cudaMemcpyHostToDevice, h->st);

@@ -705,7 +705,8 @@ __global__ void __launch_bounds__(8 * NCH, 4) k_line_sweep_chunk(Geom<float> g, 
         const float4 zu = k < nz - 1 ? __ldg(reinterpret_cast<const float4*>(p + lev + plane + c0)) : cc;
         const float4 bq = __ldg(reinterpret_cast<const float4*>(b + lev + c0));
         const float left = __ldg(p + lev + xl), right = __ldg(p + lev + xr);
-        const float cup = __ldg(g.cup + k), cdn = __ldg(g.cdn + k), li = __ldg(g.tli + k);
+        const float4 cf = __ldg(g.lz4 + k);  // cup, cdn, tli, tlf
+        const float cup = cf.x, cdn = cf.y, li = cf.z;
         float4 o;
 #pragma unroll
         for (int e = 0; e < 4; e++) {
@@ -736,7 +737,7 @@ __global__ void __launch_bounds__(8 * NCH, 4) k_line_sweep_chunk(Geom<float> g, 
 #pragma unroll
       for (int q = 0; q < LMAX; q++)
         if (q < L) {
-          const float f = __ldg(g.tlf + k0 + q);
+          const float f = __ldg(g.lz4 + k0 + q).w;
           z = axpy(f, z, G[q]);
           F *= f;
           G[q] = z;
@@ -745,7 +746,7 @@ __global__ void __launch_bounds__(8 * NCH, 4) k_line_sweep_chunk(Geom<float> g, 
 #pragma unroll
       for (int q = LMAX - 1; q >= 0; q--)
         if (q < L && (q > 0 || !twist)) {
-          const float f = __ldg(g.tlf + k0 + q);
+          const float f = __ldg(g.lz4 + k0 + q).w;
           z = axpy(f, z, G[q]);
           F *= f;
           G[q] = z;
@@ -764,7 +765,7 @@ __global__ void __launch_bounds__(8 * NCH, 4) k_line_sweep_chunk(Geom<float> g, 
 #pragma unroll
       for (int q = 0; q < LMAX; q++)
         if (q < L) {
-          F *= __ldg(g.tlf + k0 + q);
+          F *= __ldg(g.lz4 + k0 + q).w;
           G[q] = axpy(F, carry, G[q]);
         }
     } else {
@@ -773,14 +774,14 @@ __global__ void __launch_bounds__(8 * NCH, 4) k_line_sweep_chunk(Geom<float> g, 
 #pragma unroll
       for (int q = LMAX - 1; q >= 0; q--)
         if (q < L && (q > 0 || !twist)) {
-          F *= __ldg(g.tlf + k0 + q);
+          F *= __ldg(g.lz4 + k0 + q).w;
           G[q] = axpy(F, carry, G[q]);
         }
       if (twist) {
         float4 ylow = zero;  // y_{t-1}
         for (int cc = 0; cc < H; cc++) ylow = axpy(FB[cc], ylow, ZB[cc][u]);
         const float4 yup = L >= 2 ? G[1] : carry;  // y_{t+1}
-        const float ft = t > 0 ? __ldg(g.tlf + t) : 0.f, et = t < nz - 1 ? __ldg(g.tlb + t) : 0.f;
+        const float ft = t > 0 ? __ldg(g.lz4 + t).w : 0.f, et = t < nz - 1 ? __ldg(g.tlb + t) : 0.f;
         G[0] = axpy(et, yup, axpy(ft, ylow, G[0]));
       }
     }

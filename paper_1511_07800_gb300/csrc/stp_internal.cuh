@@ -46,6 +46,9 @@ struct Geom {
   const T* tli;    // [nz]    1/m_k (k < t), 1/gamma_t (k = t), 1/m'_k (k > t)
   const T* tlf;    // [nz]    elimination: cdn_k/m_k (k < t), cdn_t/gamma_t, cup_k/m'_k (k > t)
   const T* tlb;    // [nz]    substitution: cup_k/m_k (k < t), cup_t/gamma_t, cdn_k/m'_k (k > t)
+  // FP32 only (null in FP64): {cup_k, cdn_k, tli_k, tlf_k} packed per level,
+  // one 16-byte load for the z-line sweep's level coefficients
+  const float4* lz4;
 };
 
 // Number of metric arrays packed into one device allocation per precision.
