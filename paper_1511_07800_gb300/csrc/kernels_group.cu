@@ -111,8 +111,7 @@ __global__ void __launch_bounds__(kBX* kBY) kg_outer(Group G, int after_pass, cu
   const double bmean = __ldcg(C.red.sc + SC_BMEAN);
   float r2 = 0.f;
   if (i < nx && j < ny) {
-    double pc;
-    const float r = (float)(point_residual(g, C.p, C.b, i, j, k, &pc) - bmean);
+    const float r = (float)(point_residual_sum(g, C.p, C.b, i, j, k) - bmean);
     C.r32[(k * ny + j) * nx + i] = r;
     r2 = r * r;
   }

@@ -960,10 +960,10 @@ __global__ void __launch_bounds__(kBX* kBY) k_check(Geom<T> g, const T* __restri
   }
 }
 
-// Refinement residual: r = b - mean(b) - L p in FP64 (difference form; the
-// volume mean of b that FP32 differences leave, zero otherwise), stored in
-// FP32 for the inner solve, its norm summed from the stored values; decides
-// whether another refinement pass runs.
+// Refinement residual: r = b - mean(b) - L p in FP64 (neighbour-sum form,
+// point_residual_sum; the reduced volume mean of b, zero when b telescopes),
+// stored in FP32 for the inner solve, its norm summed from the stored
+// values; decides whether another refinement pass runs.
 __global__ void __launch_bounds__(kBX* kBY) k_outer(Geom<double> g, const double* __restrict__ p,
                                                      const double* __restrict__ b, float* __restrict__ r32,
                                                      SolveCtl* ctl, Red red, unsigned nblocks, int after_pass,
@@ -973,8 +973,7 @@ __global__ void __launch_bounds__(kBX* kBY) k_outer(Geom<double> g, const double
   const double bmean = __ldcg(red.sc + SC_BMEAN);
   float r2 = 0.f;
   if (i < g.nx && j < g.ny) {
-    double pc;
-    const float r = (float)(point_residual(g, p, b, i, j, k, &pc) - bmean);
+    const float r = (float)(point_residual_sum(g, p, b, i, j, k) - bmean);
     r32[(k * g.ny + j) * g.nx + i] = r;
     r2 = r * r;
   }

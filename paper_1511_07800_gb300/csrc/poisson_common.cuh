@@ -34,6 +34,27 @@ __device__ __forceinline__ T point_residual(const Geom<T>& g, const T* __restric
   return __ldg(b + q) - lap;
 }
 
+// b - L p at one point in FP64, neighbour-sum form: b - (sum_nb c p_nb -
+// S p), eight FP64 operations against twelve for the difference form (GB300
+// issues FP64 at 1/64 of the FP32 rate).  It rounds with the size of S p
+// rather than of the differences, which for a pressure of order one is far
+// below the refinement's 1e-8; the FP32 refinement residual uses it, the FP64
+// solve keeps the difference form (its sweep counts are compared with the
+// oracle's).
+__device__ __forceinline__ double point_residual_sum(const Geom<double>& g, const double* __restrict__ p,
+                                                     const double* __restrict__ b, int i, int j, int k) {
+  const int nx = g.nx, plane = g.nx * g.ny;
+  const int ip = i == nx - 1 ? 0 : i + 1, im = i == 0 ? nx - 1 : i - 1;
+  const int jp = j == g.ny - 1 ? 0 : j + 1, jm = j == 0 ? g.ny - 1 : j - 1;
+  const int row = k * plane;
+  const int q = row + j * nx + i;
+  double nb = g.idx2 * (__ldg(p + row + j * nx + ip) + __ldg(p + row + j * nx + im));
+  nb = fma(g.idy2, __ldg(p + row + jp * nx + i) + __ldg(p + row + jm * nx + i), nb);
+  if (k < g.nz - 1) nb = fma(__ldg(g.cup + k), __ldg(p + q + plane), nb);
+  if (k > 0) nb = fma(__ldg(g.cdn + k), __ldg(p + q - plane), nb);
+  return fma(__ldg(g.S + k), __ldg(p + q), __ldg(b + q) - nb);
+}
+
 // One FP32 SRJ update in difference form with a fixed rounding sequence
 // (explicit round-to-nearest operations), shared by every FP32 sweep kernel
 // so that all of them produce bitwise the same values.
