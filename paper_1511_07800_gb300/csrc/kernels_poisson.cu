@@ -1105,16 +1105,17 @@ template <int TY, int TZ>
 static cudaError_t launch_pair(const Geom<float>& g, const float* p, const float* b, float om_a, float om_b,
                                float* out, cudaStream_t s) {
   const size_t smem = pair_smem_bytes(TY, TZ, g.nx);
-  static size_t attr_bytes = 0;  // the kernel's shared-memory limit, raised as needed
-  if (smem > attr_bytes) {
+  {
+    // the kernel's shared-memory limit, raised to the device's opt-in
+    // maximum once a device
+    static std::atomic<unsigned> done{0u};
     int dev = 0, optin = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
     if (smem > (size_t)optin) return cudaErrorInvalidConfiguration;
-    e = cudaFuncSetAttribute(k_sweep_f32_pair<TY, TZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    e = smem_limit_once(k_sweep_f32_pair<TY, TZ>, optin, done);
     if (e != cudaSuccess) return e;
-    attr_bytes = (size_t)optin;
   }
   const dim3 grid(g.ny / TY, g.nz / TZ), block(256);
   cudaLaunchConfig_t cfg = {};
@@ -1228,19 +1229,14 @@ static int line_rows(int nz, size_t es) {
 }
 
 // the shared-memory line sweeps at RB rows per block (the vector kernel when
-// rows hold whole vectors); raises their shared-memory limit once
+// rows hold whole vectors); raises their shared-memory limit once a device
 template <typename T, int RB>
 static cudaError_t launch_line_rows(const Geom<T>& g, const T* p, const T* b, T omega, T* out, cudaStream_t s,
                                     cudaLaunchAttribute* attr) {
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_line_sweep_smem<T, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         96 * 1024);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_line_sweep_vec<T, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  static std::atomic<unsigned> done_smem{0u}, done_vec{0u};
+  cudaError_t e0 = smem_limit_once(k_line_sweep_smem<T, RB>, 96 * 1024, done_smem);
+  if (e0 == cudaSuccess) e0 = smem_limit_once(k_line_sweep_vec<T, RB>, 96 * 1024, done_vec);
+  if (e0 != cudaSuccess) return e0;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(((g.nx + 31) / 32) * ((g.ny + RB - 1) / RB)));
   cfg.blockDim = dim3(512);

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include <string>
 #include <vector>
 
@@ -335,5 +337,20 @@ cudaError_t launch_norm(const double* a, size_t n, int slot, Red red, cudaStream
 // learned guess (unet.cu)
 bool unet_matches(const stp_unet* n, int nz, int ny, int nx);
 int unet_guess(stp_unet* n, const float* r, const double* norm, float* d, cudaStream_t st, int* kernels);
+
+// Raise a kernel's dynamic shared-memory limit on the current device the
+// first time it is launched there (the attribute is per device; `done`
+// holds one bit per device, devices 0-31; setting it twice is harmless).
+template <typename K>
+inline cudaError_t smem_limit_once(K kern, int bytes, std::atomic<unsigned>& done) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned bit = 1u << (dev & 31);
+  if (done.load(std::memory_order_acquire) & bit) return cudaSuccess;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) done.fetch_or(bit, std::memory_order_acq_rel);
+  return e;
+}
 
 }  // namespace stp

@@ -1029,11 +1029,8 @@ int conv3(stp_unet* n, const Dims& dm, const bf16* x, int ldx, int cin, const bf
           const float* bias, int cout, bf16* y, int ldy, int relu, const bf16* mask, int ldm) {
   const long long V = dm.vox();
   if (conv3_tc_ok(n, dm, ldx, cin, cout, ldy)) {
-    static bool attr_set = false;
-    if (!attr_set) {
-      UTRY(n, cudaFuncSetAttribute(k_conv3_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmemMax));
-      attr_set = true;
-    }
+    static std::atomic<unsigned> done{0u};
+    UTRY(n, smem_limit_once(k_conv3_tc, (int)kTcSmemMax, done));
     const bool resident = conv3_tc_smem(cin, cout, true, 1) <= kTcSmemMax;
     const int zt = conv3_tc_planes(n, dm, cin, cout, resident);
     const unsigned blocks = (unsigned)(V / (TC_TX * TC_TY * zt));
