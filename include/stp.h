@@ -269,9 +269,11 @@ int stp_batch_step(stp_batch *b, int nsteps, stp_batch_stats *stats, stp_step_st
 
 /* Checkpoint: the whole state of the time stepper (velocities, pressure,
    the two Adams-Bashforth history levels, the history depth and the step
-   counter) as one opaque FP64 host buffer of stp_state_size() doubles;
+   counter) as one opaque host buffer of stp_state_size() doubles, its
+   fields kept in the handle's precision (an FP32 handle packs its FP32
+   arrays two values to a double; the pressure is FP64 in both);
    stp_set_state resumes bitwise where stp_get_state was taken (same
-   configuration). */
+   configuration and precision; another grid or precision: STP_EINVAL). */
 long long stp_state_size(const stp_handle *h);
 int stp_get_state(stp_handle *h, double *buf);
 int stp_set_state(stp_handle *h, const double *buf);

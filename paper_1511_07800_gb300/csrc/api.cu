@@ -1112,6 +1112,30 @@ int check_where(stp_handle* h, int where) {
 
 }  // namespace
 
+// State buffer: a header of four doubles (format tag, history depth, step
+// counter, cells), then u, v, w, p and the two latest history levels of
+// u, v, w.  Fields are kept in the handle's precision: an FP64 handle
+// stores doubles (tag 1511.07800); an FP32 handle stores its FP32 fields
+// as raw floats, each array padded to a whole number of doubles, and p in
+// FP64 (tag 1511.07832): about half the bytes that widening them would take.
+namespace {
+constexpr double kStateTag64 = 1511.07800, kStateTag32 = 1511.07832;
+long long state_words(const stp_handle* h, long long n) {  // doubles holding n field values
+  return h->prec == STP_FP64 ? n : (n + 1) / 2;
+}
+// copy n field values between the device array f and the buffer section q
+int state_get(stp_handle* h, double* q, const void* f, long long n) {
+  if (h->prec == STP_FP64) return get_any(h, q, f, (size_t)n, STP_HOST);
+  CUDA_TRY(h, cudaMemcpyAsync(q, f, sizeof(float) * n, cudaMemcpyDeviceToHost, h->st));
+  return STP_OK;
+}
+int state_put(stp_handle* h, void* f, const double* q, long long n) {
+  if (h->prec == STP_FP64) return put_any(h, f, q, (size_t)n, STP_HOST);
+  CUDA_TRY(h, cudaMemcpyAsync(f, q, sizeof(float) * n, cudaMemcpyHostToDevice, h->st));
+  return STP_OK;
+}
+}  // namespace
+
 // ===========================================================================
 // C ABI
 // ===========================================================================
@@ -1521,36 +1545,38 @@ int stp_poisson_solve(stp_handle* h, const double* rhs, double* p_inout, double 
 // state layout: header [4] (magic, nhist, step, nc) | u | v | w | p | Nu,Nv,Nw of levels n, n-1 (history)
 long long stp_state_size(const stp_handle* h) {
   if (!h) return 0;
-  return 4 + 3 * (long long)h->nc + (long long)h->nw + 2 * (2 * (long long)h->nc + (long long)h->nw);
+  const long long nc = h->nc, nw = h->nw;
+  return 4 + 3 * state_words(h, nc) + state_words(h, nw) + nc + 2 * (2 * state_words(h, nc) + state_words(h, nw));
 }
 
 int stp_get_state(stp_handle* h, double* buf) {
   if (!h || !buf) return STP_EINVAL;
   CUDA_TRY(h, cudaSetDevice(h->dev));
-  buf[0] = 1511.07800;
+  buf[0] = h->prec == STP_FP64 ? kStateTag64 : kStateTag32;
   buf[1] = h->nhist;
   buf[2] = (double)h->step;
   buf[3] = (double)h->nc;
   double* q = buf + 4;
   int rc;
+  const long long nc = h->nc, nw = h->nw;
   // the latest history level is in slot (step - 1) % 3, the one before in (step - 2) % 3
   const int sl[2] = {(int)((h->step + 2) % 3), (int)((h->step + 1) % 3)};
-  if ((rc = get_any(h, q, h->u, h->nc, STP_HOST))) return rc;
-  q += h->nc;
-  if ((rc = get_any(h, q, h->v, h->nc, STP_HOST))) return rc;
-  q += h->nc;
-  if ((rc = get_any(h, q, h->w, h->nw, STP_HOST))) return rc;
-  q += h->nw;
-  CUDA_TRY(h, cudaMemcpyAsync(q, h->p, sizeof(double) * h->nc, cudaMemcpyDeviceToHost, h->st));
-  q += h->nc;
+  if ((rc = state_get(h, q, h->u, nc))) return rc;
+  q += state_words(h, nc);
+  if ((rc = state_get(h, q, h->v, nc))) return rc;
+  q += state_words(h, nc);
+  if ((rc = state_get(h, q, h->w, nw))) return rc;
+  q += state_words(h, nw);
+  CUDA_TRY(h, cudaMemcpyAsync(q, h->p, sizeof(double) * nc, cudaMemcpyDeviceToHost, h->st));
+  q += nc;
   for (int i = 0; i < 2; i++) {
     const int l = sl[i];
-    if ((rc = get_any(h, q, h->Nu[l], h->nc, STP_HOST))) return rc;
-    q += h->nc;
-    if ((rc = get_any(h, q, h->Nv[l], h->nc, STP_HOST))) return rc;
-    q += h->nc;
-    if ((rc = get_any(h, q, h->Nw[l], h->nw, STP_HOST))) return rc;
-    q += h->nw;
+    if ((rc = state_get(h, q, h->Nu[l], nc))) return rc;
+    q += state_words(h, nc);
+    if ((rc = state_get(h, q, h->Nv[l], nc))) return rc;
+    q += state_words(h, nc);
+    if ((rc = state_get(h, q, h->Nw[l], nw))) return rc;
+    q += state_words(h, nw);
   }
   CUDA_TRY(h, cudaStreamSynchronize(h->st));
   return STP_OK;
@@ -1558,28 +1584,30 @@ int stp_get_state(stp_handle* h, double* buf) {
 
 int stp_set_state(stp_handle* h, const double* buf) {
   if (!h || !buf) return STP_EINVAL;
-  if (buf[0] != 1511.07800 || buf[3] != (double)h->nc) return fail(h, STP_EINVAL, "state buffer does not match");
+  if (buf[0] != (h->prec == STP_FP64 ? kStateTag64 : kStateTag32) || buf[3] != (double)h->nc)
+    return fail(h, STP_EINVAL, "state buffer does not match (grid or precision)");
   CUDA_TRY(h, cudaSetDevice(h->dev));
   const double* q = buf + 4;
   int rc;
+  const long long nc = h->nc, nw = h->nw;
   const long long step = (long long)buf[2];
   const int sl[2] = {(int)((step + 2) % 3), (int)((step + 1) % 3)};
-  if ((rc = put_any(h, h->u, q, h->nc, STP_HOST))) return rc;
-  q += h->nc;
-  if ((rc = put_any(h, h->v, q, h->nc, STP_HOST))) return rc;
-  q += h->nc;
-  if ((rc = put_any(h, h->w, q, h->nw, STP_HOST))) return rc;
-  q += h->nw;
-  CUDA_TRY(h, cudaMemcpyAsync(h->p, q, sizeof(double) * h->nc, cudaMemcpyHostToDevice, h->st));
-  q += h->nc;
+  if ((rc = state_put(h, h->u, q, nc))) return rc;
+  q += state_words(h, nc);
+  if ((rc = state_put(h, h->v, q, nc))) return rc;
+  q += state_words(h, nc);
+  if ((rc = state_put(h, h->w, q, nw))) return rc;
+  q += state_words(h, nw);
+  CUDA_TRY(h, cudaMemcpyAsync(h->p, q, sizeof(double) * nc, cudaMemcpyHostToDevice, h->st));
+  q += nc;
   for (int i = 0; i < 2; i++) {
     const int l = sl[i];
-    if ((rc = put_any(h, h->Nu[l], q, h->nc, STP_HOST))) return rc;
-    q += h->nc;
-    if ((rc = put_any(h, h->Nv[l], q, h->nc, STP_HOST))) return rc;
-    q += h->nc;
-    if ((rc = put_any(h, h->Nw[l], q, h->nw, STP_HOST))) return rc;
-    q += h->nw;
+    if ((rc = state_put(h, h->Nu[l], q, nc))) return rc;
+    q += state_words(h, nc);
+    if ((rc = state_put(h, h->Nv[l], q, nc))) return rc;
+    q += state_words(h, nc);
+    if ((rc = state_put(h, h->Nw[l], q, nw))) return rc;
+    q += state_words(h, nw);
   }
   const int dstep = (int)step;
   CUDA_TRY(h, cudaMemcpyAsync(h->d_step, &dstep, sizeof(int), cudaMemcpyHostToDevice, h->st));

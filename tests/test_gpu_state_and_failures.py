@@ -33,6 +33,16 @@ def test_checkpoint_resume_bitwise(stp_lib, precision):
         got = c.get_fields()
     for k in ("u", "v", "w", "p", "nu"):
         assert np.array_equal(got[k], ref[k]), k
+    # the buffer keeps the handle's precision: FP32 fields packed two to a
+    # double (p stays FP64), refused by a handle of the other precision
+    other = "fp64" if precision == "fp32" else "fp32"
+    with stp_lib.Channel(cfg, precision=other, omega=om) as d:
+        if precision == "fp32":
+            nc = cfg["nx"] * cfg["ny"] * cfg["nz"]
+            assert len(state) < 0.6 * d.state_size() and len(state) >= 5.5 * nc
+        with pytest.raises(stp_lib.StpError) as e:
+            d.set_state(state)
+        assert e.value.code == stp_lib.STP_EINVAL
 
 
 def test_not_converged_is_reported(stp_lib):
