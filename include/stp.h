@@ -115,7 +115,8 @@ typedef struct stp_config {
                                 iterate (Sec. 3.1 names no solver; the wall-
                                 normal couplings of a stretched grid then cost
                                 no sweeps: automatic count from the x-y
-                                couplings alone)                                  */
+                                couplings alone); needs ny <= 65535 (else
+                                stp_init returns STP_EINVAL)                      */
 } stp_config;
 
 typedef struct stp_step_stats {

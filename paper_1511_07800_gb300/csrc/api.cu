@@ -367,6 +367,7 @@ int validate(const stp_config* c, std::string* why) {
   if (c->srj_m % 2) return *why = "the SRJ cycle length must be even", STP_EINVAL;
   if (c->zline != 0 && c->zline != 1) return *why = "zline must be 0 or 1", STP_EINVAL;
   if (c->cn_zline != 0 && c->cn_zline != 1) return *why = "cn_zline must be 0 or 1", STP_EINVAL;
+  if (c->cn_zline && c->ny > 65535) return *why = "z-line Crank-Nicolson needs ny <= 65535 (one grid row a block row)", STP_EINVAL;
   if (!c->srj_omega && c->srj_m > 0 && !pow2(c->srj_m)) return *why = "library schedules need srj_m a power of two", STP_EINVAL;
   if (c->les && !(c->cs >= 0 && c->vd_a > 0 && c->re_tau > 0)) return *why = "bad LES constants", STP_EINVAL;
   return STP_OK;

@@ -37,7 +37,7 @@ def test_config_struct_layout(stp_lib):
 
 
 @pytest.mark.parametrize("bad", [dict(nx=2), dict(nz=1), dict(dt=0.0), dict(precision=7), dict(Lz=-1.0),
-                                 dict(srj_m=6)])
+                                 dict(srj_m=6), dict(cn_zline=1, nx=4, ny=70000, nz=2)])
 def test_init_rejects_bad_config(stp_lib, bad):
     cfg = inputs.preset("laminar_startup")
     prec = bad.pop("precision", 0)
